@@ -1,0 +1,368 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a special case that reduces to the local constitutive law, a
+derivative taken numerically from the energy, an independent solve with
+Lagrange multipliers instead of the periodic null-space map, or an invariant
+(symmetry, bounds, Hill-Mandel, shift/rotation invariance).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse
+
+from oracle import fe2_oracle as O
+from paper_2312_12771_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def voigt2(C):
+    """4x4 tangent (iJ row-major) -> 3x3 Voigt [xx, yy, xy] (engineering shear)."""
+    idx = [(0, 0), (1, 1), (0, 1)]
+    V = np.zeros((3, 3))
+    for a, (i, j) in enumerate(idx):
+        for b, (k, l) in enumerate(idx):
+            V[a, b] = C[2 * i + j, 2 * k + l]
+    return V
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def plane_strain_C(E, nu):
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    return np.array([[lam + 2 * mu, lam, 0], [lam, lam + 2 * mu, 0], [0, 0, mu]])
+
+
+def laminate_closed_form(Cs, fr):
+    """Textbook layered-medium average, interface normal y: n = (yy, xy), t = (xx)."""
+    n, t = [1, 2], [0]
+    inv_nn = sum(f * np.linalg.inv(C[np.ix_(n, n)]) for C, f in zip(Cs, fr))
+    Cnn = np.linalg.inv(inv_nn)
+    a = sum(f * np.linalg.inv(C[np.ix_(n, n)]) @ C[np.ix_(n, t)] for C, f in zip(Cs, fr))
+    Cnt = Cnn @ a
+    Ctt = sum(f * (C[np.ix_(t, t)] - C[np.ix_(t, n)] @ np.linalg.inv(C[np.ix_(n, n)]) @ C[np.ix_(n, t)])
+              for C, f in zip(Cs, fr)) + a.T @ Cnn @ a
+    out = np.zeros((3, 3))
+    out[np.ix_(n, n)] = Cnn
+    out[np.ix_(n, t)] = Cnt
+    out[np.ix_(t, n)] = Cnt.T
+    out[np.ix_(t, t)] = Ctt
+    return out
+
+
+# --------------------------------------------------------------------------
+def test_laminate_closed_form_and_golden():
+    b = W.laminate_batch(1, 8)
+    s = O.rve_solve(8, 2, b.phase[0], b.mat[0], b.Fbar[0])
+    V = voigt2(s["Cbar"])
+    ref = laminate_closed_form([plane_strain_C(1, .3), plane_strain_C(10, .3)], [.5, .5])
+    assert np.abs(V - ref).max() < 1e-12
+    g = read_golden("laminate_8x8.txt")
+    assert abs(V[0, 0] - g["C11"]) < 1e-12 and abs(V[1, 1] - g["C22"]) < 1e-12
+    assert abs(V[0, 1] - g["C12"]) < 1e-12 and abs(V[2, 2] - g["C66"]) < 1e-12
+    assert abs(V[0, 2]) < 1e-12 and abs(V[1, 2]) < 1e-12
+    sig = s["sigma_eff"]
+    assert abs(sig[0] - g["S11"]) < 1e-14 and abs(sig[3] - g["S22"]) < 1e-14
+
+
+@pytest.mark.parametrize("rows", [1, 2, 4])
+def test_laminate_any_layer_width(rows):
+    N = 8
+    ph = W.laminate_phase(N, rows)
+    mat = W.linear_mat(2.0, 0.25, 7.0, 0.35)
+    s = O.rve_solve(N, 2, ph, mat, np.eye(2))
+    ref = laminate_closed_form([plane_strain_C(2, .25), plane_strain_C(7, .35)], [.5, .5])
+    assert np.abs(voigt2(s["Cbar"]) - ref).max() < 1e-11
+
+
+@pytest.mark.parametrize("d,N", [(2, 3), (2, 4), (3, 2)])
+@pytest.mark.parametrize("model", ["linear", "nh"])
+def test_homogeneous_rve_recovers_local_law(d, N, model):
+    rng = np.random.default_rng(3)
+    F = np.eye(d) + 0.15 * rng.standard_normal((d, d))
+    if model == "linear":
+        m = np.array([0, 3.0, 0.3, 0])
+    else:
+        m = np.array([1, 1.5, 12.0, 0])
+    mat = np.stack([m, m])
+    ph = (rng.random(N ** d) < 0.5).astype(np.uint8)
+    s = O.rve_solve(N, d, ph, mat, F)
+    P, A = O.material(F[None], m, d)
+    assert np.abs(s["K_mM"]).max() < 1e-12
+    assert np.abs(s["r_m"]).max() < 1e-12
+    assert np.allclose(s["Cbar"], A[0].reshape(d * d, d * d), rtol=0, atol=1e-12 * np.abs(A).max())
+    assert np.allclose(s["sigma_eff"], P[0].ravel(), rtol=0, atol=1e-12 * max(1, np.abs(P).max()))
+
+
+@pytest.mark.parametrize("d,N", [(2, 4), (3, 2)])
+def test_neohooke_at_identity_equals_linear(d, N):
+    rng = np.random.default_rng(5)
+    ph = (rng.random(N ** d) < 0.4).astype(np.uint8)
+    mu0, k0, mu1, k1 = 1.0, 10.0, 20.0, 200.0
+    nh = W.neohooke_mat(mu0, k0, mu1, k1)
+
+    def E_nu(mu, lam):
+        return mu * (3 * lam + 2 * mu) / (lam + mu), lam / (2 * (lam + mu))
+    E0, n0 = E_nu(mu0, k0)
+    E1, n1 = E_nu(mu1, k1)
+    lin = W.linear_mat(E0, n0, E1, n1)
+    a = O.rve_solve(N, d, ph, nh, np.eye(d))
+    b = O.rve_solve(N, d, ph, lin, np.eye(d))
+    assert O.rel_err(a["Cbar"], b["Cbar"]) < 1e-13
+    assert np.abs(a["sigma_eff"]).max() < 1e-13
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("model", [0, 1])
+def test_stress_and_tangent_are_energy_derivatives(d, model):
+    """Complex-step derivatives of the energy give P; of P give A."""
+    rng = np.random.default_rng(11 + d)
+    F = np.eye(d) + 0.2 * rng.standard_normal((d, d))
+    m = np.array([model, 2.0, 0.3 if model == 0 else 9.0, 0])
+    P, A = O.material(F[None], m, d)
+    hcs = 1e-30
+    Pc = np.zeros((d, d))
+    Ac = np.zeros((d, d, d, d))
+    for k in range(d):
+        for L in range(d):
+            Fz = F.astype(complex)
+            Fz[k, L] += 1j * hcs
+            Pc[k, L] = O.energy(Fz[None], m, d)[0].imag / hcs
+            Pz, _ = O.material(Fz[None], m, d)
+            Ac[:, :, k, L] = Pz[0].imag / hcs
+    assert np.allclose(P[0], Pc, rtol=1e-13, atol=1e-13)
+    assert np.allclose(A[0], Ac, rtol=1e-12, atol=1e-12)
+    # major symmetry of the tangent
+    assert np.allclose(A[0], A[0].transpose(2, 3, 0, 1), atol=1e-12)
+
+
+def total_energy(N, d, phase, mat, Fbar, w):
+    ints = O.rve_integrals(N, d, phase, mat, Fbar, w)
+    Ft, wq = ints["Ft"], ints["wq"]
+    e = 0.0
+    for ph in np.unique(phase):
+        e += O.energy(Ft[phase == ph], mat[ph], d).sum() * wq
+    return e
+
+
+@pytest.mark.parametrize("d,N", [(2, 3), (3, 2)])
+def test_residual_and_hessian_are_energy_derivatives(d, N):
+    """r_m = dPi/dw, K_mm = dr_m/dw, K_mM = dr_m/dFbar, Pint = dPi/dFbar,
+    K_MM = dPint/dFbar (central differences of the discrete energy)."""
+    rng = np.random.default_rng(7)
+    ph = (rng.random(N ** d) < 0.5).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 8.0, 5.0, 30.0)
+    F = np.eye(d) + 0.1 * rng.standard_normal((d, d))
+    nm = d * (N ** d - 1)
+    w = 0.02 * rng.standard_normal(nm)
+
+    def parts(Fb, wv):
+        ints = O.rve_integrals(N, d, ph, mat, Fb, wv)
+        K_mm, r_m, K_mM = O.reduce_periodic(ints)
+        return dict(K_mm=K_mm, r_m=r_m, K_mM=K_mM, K_MM=ints["K_MM"], Pint=ints["Pint"])
+    s = parts(F, w)
+    h = 1e-6
+    g = np.zeros(nm)
+    for i in range(nm):
+        e = np.zeros(nm)
+        e[i] = h
+        g[i] = (total_energy(N, d, ph, mat, F, w + e) - total_energy(N, d, ph, mat, F, w - e)) / (2 * h)
+    assert np.abs(g - s["r_m"]).max() < 1e-7 * max(1, np.abs(s["r_m"]).max())
+    for i in range(0, nm, max(1, nm // 5)):
+        e = np.zeros(nm)
+        e[i] = h
+        rp = parts(F, w + e)["r_m"]
+        rm = parts(F, w - e)["r_m"]
+        assert np.abs((rp - rm) / (2 * h) - s["K_mm"][:, i]).max() < 1e-6 * np.abs(s["K_mm"]).max()
+    for kL in range(d * d):
+        dF = np.zeros(d * d)
+        dF[kL] = h
+        sp = parts(F + dF.reshape(d, d), w)
+        sm = parts(F - dF.reshape(d, d), w)
+        assert np.abs((sp["r_m"] - sm["r_m"]) / (2 * h) - s["K_mM"][:, kL]).max() < 1e-6
+        assert np.abs((sp["Pint"] - sm["Pint"]) / (2 * h) - s["K_MM"][:, kL]).max() < 1e-6
+        ep = total_energy(N, d, ph, mat, F + dF.reshape(d, d), w)
+        em = total_energy(N, d, ph, mat, F - dF.reshape(d, d), w)
+        assert abs((ep - em) / (2 * h) - s["Pint"][kL]) < 1e-7
+
+
+def kkt_cbar(N, d, phase, mat, F, pin_node=0):
+    """Brute force: full-grid system, periodicity and the pin as explicit
+    Lagrange-multiplier constraints (no null-space map), dense solve."""
+    ints = O.rve_integrals(N, d, phase, mat, F)
+    K = ints["K"].toarray()
+    KM = ints["KM"]
+    n1 = N + 1
+    nfull = n1 ** d
+    rows = []
+    master = {}
+    for node in range(nfull):
+        ijk = tuple((node // n1 ** k) % n1 for k in range(d))
+        key = tuple(v % N for v in ijk)
+        if key not in master:
+            master[key] = node
+        else:
+            for c in range(d):
+                r = np.zeros(d * nfull)
+                r[d * node + c] = 1
+                r[d * master[key] + c] = -1
+                rows.append(r)
+    pin = master[tuple((pin_node // N ** k) % N for k in range(d))]
+    for c in range(d):
+        r = np.zeros(d * nfull)
+        r[d * pin + c] = 1
+        rows.append(r)
+    C = np.array(rows)
+    nc = len(rows)
+    KKT = np.block([[K, C.T], [C, np.zeros((nc, nc))]])
+    rhs = np.vstack([KM, np.zeros((nc, d * d))])
+    X = np.linalg.solve(KKT, rhs)[: d * nfull]
+    return (ints["K_MM"] - KM.T @ X) / ints["vol"]
+
+
+@pytest.mark.parametrize("d,N", [(2, 2), (2, 3), (2, 4), (3, 2)])
+def test_brute_force_lagrange_periodicity(d, N):
+    rng = np.random.default_rng(N + 10 * d)
+    ph = (rng.random(N ** d) < 0.5).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.eye(d) + 0.02 * rng.standard_normal((d, d))
+    s = O.rve_solve(N, d, ph, mat, F)
+    ref = kkt_cbar(N, d, ph, mat, F)
+    assert O.rel_err(s["Cbar"], ref) < 1e-11
+    # the pinned node is arbitrary: pinning another node gives the same Cbar
+    ref2 = kkt_cbar(N, d, ph, mat, F, pin_node=N ** d - 1)
+    assert O.rel_err(ref2, ref) < 1e-11
+
+
+def test_cbar_is_derivative_of_equilibrium_stress():
+    """Cbar = d Pbar / d Fbar along the equilibrium path (central FD)."""
+    N, d = 4, 2
+    rng = np.random.default_rng(2)
+    ph = (rng.random(N * N) < 0.4).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.1, 0.05], [-0.02, 0.97]])
+    w, _ = O.micro_equilibrate(N, d, ph, mat, F)
+    s = O.rve_solve(N, d, ph, mat, F, w)
+    assert O.rel_err(s["sigma_eff"], s["Pbar"]) < 1e-12   # at r_m = 0 they coincide
+    h = 1e-5
+    Cfd = np.zeros((4, 4))
+    for kL in range(4):
+        dF = np.zeros(4)
+        dF[kL] = h
+        wp, _ = O.micro_equilibrate(N, d, ph, mat, F + dF.reshape(2, 2), w)
+        wm, _ = O.micro_equilibrate(N, d, ph, mat, F - dF.reshape(2, 2), w)
+        Pp = O.rve_solve(N, d, ph, mat, F + dF.reshape(2, 2), wp)["Pbar"].ravel()
+        Pm = O.rve_solve(N, d, ph, mat, F - dF.reshape(2, 2), wm)["Pbar"].ravel()
+        Cfd[:, kL] = (Pp - Pm) / (2 * h)
+    assert O.rel_err(s["Cbar"], Cfd) < 1e-8
+
+
+def test_hill_mandel_at_equilibrium():
+    """<P~ : dF~> = Pbar : dFbar for any periodic virtual fluctuation."""
+    N, d = 4, 2
+    rng = np.random.default_rng(4)
+    ph = (rng.random(N * N) < 0.5).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.15, 0.1], [0.0, 0.95]])
+    w, _ = O.micro_equilibrate(N, d, ph, mat, F)
+    ints = O.rve_integrals(N, d, ph, mat, F, w)
+    dFbar = rng.standard_normal((2, 2))
+    dw = rng.standard_normal(2 * (N * N - 1))
+    conn, nnode = O.full_grid(N, d)
+    dwe = (ints["T"] @ dw).reshape(nnode, d)[conn]
+    dFt = dFbar[None, None] + np.einsum("eai,qaJ->eqiJ", dwe, ints["G"])
+    lhs = np.einsum("eqiJ,eqiJ->", ints["P"], dFt) * ints["wq"] / ints["vol"]
+    rhs = np.sum(ints["Pint"].reshape(2, 2) / ints["vol"] * dFbar)
+    assert abs(lhs - rhs) < 1e-11
+
+
+def test_voigt_reuss_bounds_and_symmetry():
+    N = 8
+    ph = W.fiber_phase(N)
+    mat = W.linear_mat(1.0, 0.3, 10.0, 0.3)
+    s = O.rve_solve(N, 2, ph, mat, np.eye(2))
+    C = voigt2(s["Cbar"])
+    assert np.abs(s["Cbar"] - s["Cbar"].T).max() < 1e-12
+    f1 = ph.mean()
+    C0, C1 = plane_strain_C(1, .3), plane_strain_C(10, .3)
+    voigt = (1 - f1) * C0 + f1 * C1
+    reuss = np.linalg.inv((1 - f1) * np.linalg.inv(C0) + f1 * np.linalg.inv(C1))
+    assert np.linalg.eigvalsh(voigt - C).min() > -1e-12
+    assert np.linalg.eigvalsh(C - reuss).min() > -1e-12
+    assert np.linalg.eigvalsh(C).min() > 0
+
+
+def test_shift_and_rotation_invariance():
+    N = 6
+    rng = np.random.default_rng(9)
+    ph = (rng.random(N * N) < 0.4).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.05, 0.03], [0.01, 0.98]])
+    a = O.rve_solve(N, 2, ph, mat, F)
+    w, _ = O.micro_equilibrate(N, 2, ph, mat, F)
+    a_eq = O.rve_solve(N, 2, ph, mat, F, w)
+    grid = ph.reshape(N, N)                      # [ey][ex]
+    shifted = np.roll(np.roll(grid, 2, axis=0), -1, axis=1).ravel()
+    ws, _ = O.micro_equilibrate(N, 2, shifted, mat, F)
+    b = O.rve_solve(N, 2, shifted, mat, F, ws)
+    assert O.rel_err(b["Cbar"], a_eq["Cbar"]) < 1e-10
+    assert O.rel_err(b["Pbar"], a_eq["Pbar"]) < 1e-12
+    # rotation by 90 degrees: X' = R X, F' = R F R^T, C' = R R C R^T R^T
+    R = np.array([[0.0, -1.0], [1.0, 0.0]])
+    rot = np.rot90(grid, 1).ravel()              # counter-clockwise in (x, y)
+    Fr = R @ F @ R.T
+    wr, _ = O.micro_equilibrate(N, 2, rot, mat, Fr)
+    c = O.rve_solve(N, 2, rot, mat, Fr, wr)
+    C4 = a_eq["Cbar"].reshape(2, 2, 2, 2)
+    Crot = np.einsum("ia,Jb,kc,Ld,abcd->iJkL", R, R, R, R, C4).reshape(4, 4)
+    assert O.rel_err(c["Cbar"], Crot) < 1e-10
+    assert O.rel_err(c["Pbar"], (R @ a_eq["Pbar"].reshape(2, 2) @ R.T).ravel()) < 1e-12
+    assert a["Cbar"].shape == (4, 4)
+
+
+def test_macro_patch_test():
+    """Homogeneous RVEs + affine Dirichlet data: the macro solution is affine,
+    every Gauss point sees Fbar = F_final and Pbar = P(F_final)."""
+    macro = O.macro_mesh(2, 2)
+    m = np.array([1, 1.0, 10.0, 0])
+    rves = [dict(N=3, phase=np.zeros(9, np.uint8), mat=np.stack([m, m])) for _ in range(16)]
+    Ff = np.array([[1.1, 0.05], [0.0, 0.95]])
+    out, iters, q = O.monolithic_fe2(macro, rves, Ff, n_steps=2)
+    P, _ = O.material(Ff[None], m, 2)
+    for o in out:
+        assert np.abs(o["Fbar"] - Ff).max() < 1e-12
+        assert np.abs(o["Pbar"] - P[0].ravel()).max() < 1e-10
+    X = macro[0]
+    assert np.abs(q - X @ Ff.T).max() < 1e-12
+
+
+def test_monolithic_newton_converges_quadratically():
+    """Heterogeneous RVEs: the monolithic scheme converges in a few iterations
+    with a quadratically falling residual (Section 4.2, Table 2 pattern), and
+    its converged state is micro-equilibrated."""
+    macro = O.macro_mesh(1, 1)
+    rves = []
+    for b in range(4):
+        c, r = W.random_inclusions(W.GLOBAL_SEED, b)
+        rves.append(dict(N=4, phase=W.inclusion_phase(4, 2, c, r),
+                         mat=W.neohooke_mat(1.0, 10.0, 20.0, 200.0)))
+    rec = []
+    out, iters, _ = O.monolithic_fe2(macro, rves, np.diag([1.2, 1.0]), n_steps=2,
+                                     tol_macro=1e-10, tol_micro=1e-10, record=rec)
+    assert max(iters) <= 6
+    for o, r in zip(out, rves):
+        s = O.rve_solve(4, 2, r["phase"], r["mat"], o["Fbar"], o["w"])
+        assert np.linalg.norm(s["r_m"]) < 1e-9
