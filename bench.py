@@ -1,0 +1,414 @@
+"""Benchmark of the RVE block: RVE solves/s (sigma_eff + Cbar per macro Gauss point).
+
+Default workload: 4096 periodic 32x32 Q4 RVEs (macro 32x32 Q4 mesh x 2x2 Gauss
+points), one centred fiber of volume fraction 0.3, E_f = 10, E_m = 1 +- 5 %
+per RVE, nu = 0.3, plane strain; macro strain H = diag(1e-3, 0) plus a seeded
+perturbation.  One step = the whole RVE block (fused assembly + periodic
+reduction, band Cholesky, solves, FP64 refinement, Schur complement) for all
+RVEs.  The headline value is the mixed path (FP32 factor + FP64 residual
+refinement); the plain FP64 GPU path is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own 4096 RVEs (independent macro Gauss
+points, no collective on the data path: weak scaling); rank 0 prints the JSON
+line.  ``--impl reference`` times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2312_12771_gb300 import workloads as W  # noqa: E402
+
+METRIC = "RVE solves/s (sigma_eff + Cbar per macro Gauss point)"
+UNIT = "RVE solves/s"
+N_RVE, N_MESH = 4096, 32
+SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
+
+
+def peaks():
+    p = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+    except OSError:
+        pass
+    mhz = float(p.get("sm_max_mhz", SM_MAX_MHZ))
+    return {
+        "hbm_gbs": float(p.get("hbm_gbs", 6800.0)),
+        "hbm_src": "measured" if "hbm_gbs" in p else "fallback",
+        # plain-ALU peaks derived from unit counts x clock (no measured figure exists)
+        "fp32_tflops": SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12,
+        "fp64_tflops": SM_COUNT * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12,
+    }
+
+
+def workload(n=N_RVE, N=N_MESH, seed=W.GLOBAL_SEED):
+    return W.fiber_batch(n, N, seed=seed, dF_scale=1e-3)
+
+
+# ------------------------------------------------------------------ algorithmic work
+def band_counts(nm, kd):
+    c = np.minimum(kd, nm - 1 - np.arange(nm)).astype(np.float64)
+    return c
+
+
+def work_per_rve(N, d=2):
+    """Algorithmic flops / bytes per RVE for every kernel of the step (2D Q4)."""
+    nn = N * N
+    nm = d * (nn - 1)
+    kd = 4 * N + 5
+    nr = d * d + 1
+    c = band_counts(nm, kd)
+    chol = float(np.sum(c * c + 2 * c + 1))          # sqrt, scale, rank-1 update
+    tri = float(np.sum(2 * c + 1))                   # one triangular solve, one RHS
+    nnz = 18 * nm                                    # 9 node blocks of 2x2 per reduced row
+    stencil_bytes = 9 * d * d * nn * 8 + nr * nm * 8  # FP64 node-row stencil + [K_mM | r_m]
+    L_bytes = 4 * nm * (kd + 1)
+    return {
+        "assemble_reduce_linear": {"bytes": stencil_bytes + nn, "flops64": nn * 2 * (128 + 64 + 44 + 8)},
+        "band_factor_fp32": {"flops": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
+        "band_backward_fp32": {"flops": nr * tri, "bytes": L_bytes + 4 * nr * nm + 8 * nr * nm},
+        "band_refine_fp32": {"flops": 2 * nr * tri, "bytes": 2 * L_bytes + 8 * 3 * nr * nm},
+        "residual_fp64": {"flops64": 2 * nr * nnz, "bytes": 9 * d * d * nn * 8 + 3 * nr * nm * 8},
+        "schur": {"flops64": 2 * 2 * d * d * nr * nm, "bytes": 3 * nr * nm * 8},
+        "band_factor_fp64": {"flops64": chol + nr * tri, "bytes": stencil_bytes + 2 * L_bytes + 8 * nr * nm},
+        "band_backward_fp64": {"flops64": nr * tri, "bytes": 2 * L_bytes + 8 * 2 * nr * nm},
+    }
+
+
+def roofline_for(name, avg_ms, nrve, pk, N=N_MESH):
+    w = work_per_rve(N).get(name)
+    if w is None or avg_ms <= 0:
+        return None
+    s = avg_ms * 1e-3
+    if "flops" in w:
+        ach = w["flops"] * nrve / s / 1e12
+        return {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 2),
+                "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 4),
+                "peak_src": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    if "flops64" in w:
+        ach = w["flops64"] * nrve / s / 1e12
+        hbm = w["bytes"] * nrve / s / 1e9
+        return {"bound": "alu", "achieved": round(ach, 4), "peak": round(pk["fp64_tflops"], 3),
+                "unit": "TFLOP/s", "frac": round(ach / pk["fp64_tflops"], 4),
+                "peak_src": "derived: 152 SMs x 2 FP64 FMA/clk x 2 x max SM clock",
+                "hbm_gbs": round(hbm, 1), "hbm_frac": round(hbm / pk["hbm_gbs"], 4)}
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu=0):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+# ------------------------------------------------------------------ oracle (CPU) leg
+def _oracle_one(args):
+    from oracle import fe2_oracle as O
+    N, phase, mat, F = args
+    t = time.perf_counter()
+    s = O.rve_solve(N, 2, phase, mat, F)
+    return time.perf_counter() - t, s["Cbar"], s["sigma_eff"]
+
+
+def oracle_pool(nproc):
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    pool = mp.get_context("spawn").Pool(nproc)
+    for k, v in env.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return pool
+
+
+def oracle_sample(pool, batch, idx):
+    args = [(int(batch.N[k]), batch.phase[k], batch.mat[k], batch.Fbar[k]) for k in idx]
+    t = time.perf_counter()
+    res = pool.map(_oracle_one, args, chunksize=1)
+    return time.perf_counter() - t, res
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    batch = workload(args.rves, args.N, seed=W.GLOBAL_SEED + rank)
+    nrve = batch.nrve
+    pk = peaks()
+
+    def timed(ctx, ids, F, steps, warmup, outs, profile=True):
+        for _ in range(warmup):
+            ctx.rve_solve(ids, F, out=outs)
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        stream = ctx.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if profile:
+            ctx.profile(True)
+        l0 = ctx.launch_count()
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.rve_solve(ids, F, out=outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        prof = ctx.profile_read() if profile else {}
+        ctx.profile(False)
+        return ms, prof, ctx.launch_count() - l0
+
+    results = {}
+    F = torch.tensor(batch.Fbar, device=dev)
+    for prec in ("mixed", "fp64"):
+        ctx = Fe2Context(dim=2, precision=prec, max_refine=args.refine)
+        ids = ctx.register_batch(batch)
+        outs = ctx._outs(nrve)
+        steps = args.steps if prec == "mixed" else max(2, min(args.steps, 3))
+        warm = args.warmup if prec == "mixed" else 3
+        if prec == "mixed":
+            with ClockSampler(dev.index) as cs:
+                ms, prof, launches = timed(ctx, ids, F, steps, warm, outs)
+            clocks = cs.summary()
+        else:
+            ms, prof, launches = timed(ctx, ids, F, steps, warm, outs)
+        res = {"ms": ms, "steps": steps, "prof": prof, "launches": launches,
+               "sigma": outs[0].double().cpu().numpy().copy(), "Cbar": outs[1].cpu().numpy().copy(),
+               "status": outs[2].cpu().numpy().copy(), "err": outs[3].cpu().numpy().copy()}
+        if prec == "mixed":
+            res["clocks"] = clocks
+            # end to end through the public API with host buffers: H2D of Fbar,
+            # solve, D2H of sigma, Cbar, status, err -- inside the timed region
+            Fh = torch.tensor(batch.Fbar).pin_memory()
+            Fd = torch.empty_like(F)
+            hs = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
+            for _ in range(2):
+                Fd.copy_(Fh, non_blocking=True)
+                ctx.rve_solve(ids, Fd, out=outs)
+                for h, t in zip(hs, outs):
+                    h.copy_(t, non_blocking=True)
+            torch.cuda.synchronize()
+            if dist:
+                torch.distributed.barrier()
+            t0 = time.perf_counter()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                Fd.copy_(Fh, non_blocking=True)
+                ctx.rve_solve(ids, Fd, out=outs)
+                for h, t in zip(hs, outs):
+                    h.copy_(t, non_blocking=True)
+                torch.cuda.current_stream().synchronize()   # the caller reads its results each step
+            e1.record()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            res["e2e_ms"] = max(e0.elapsed_time(e1), wall * 1e3)
+            res["h2d"] = Fh.numel() * 8
+            res["d2h"] = sum(h.numel() * h.element_size() for h in hs)
+        results[prec] = res
+        ctx.close()
+        del ctx
+    return batch, results, pk
+
+
+def max_over_ranks(v, dist):
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rel_errs(C, Cref, s, sref, F):
+    eC = np.linalg.norm((C - Cref).reshape(len(C), -1), axis=1) / np.linalg.norm(Cref.reshape(len(C), -1), axis=1)
+    floor = np.linalg.norm(Cref.reshape(len(C), -1), axis=1) * np.linalg.norm((F - np.eye(2)).reshape(len(C), -1), axis=1)
+    eS = np.linalg.norm(s - sref, axis=1) / np.maximum(np.linalg.norm(sref, axis=1), floor)
+    return float(max(eC.max(), eS.max()))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rves", type=int, default=N_RVE)
+    ap.add_argument("--N", type=int, default=N_MESH)
+    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = world > 1
+    workload_name = (f"fiber vf=0.3 periodic {args.N}x{args.N} Q4 RVE (n_m={2 * (args.N ** 2 - 1)}), "
+                     f"{args.rves} RVEs per GPU = macro 32x32 Q4 x 2x2 Gauss; linear plane strain, "
+                     f"E_f=10, E_m=1+-5%, nu=0.3")
+    cfg = {"workload": workload_name, "rves_per_gpu": args.rves, "N": args.N,
+           "n_m": 2 * (args.N ** 2 - 1), "kd": 4 * args.N + 5,
+           "l2": "inputs larger than L2 (per-step working set > 5 GB)",
+           "parallelism": f"rve-sharded x{args.gpus} (no data-path collective)"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nproc = os.cpu_count() or 1
+        batch = workload(args.rves, args.N)
+        per = max(nproc, min(args.cpu_sample, 64))
+        pool = oracle_pool(nproc)
+        rng = np.random.default_rng(0)
+        times = []
+        for s in range(args.warmup + args.steps):
+            idx = rng.choice(batch.nrve, size=per, replace=False)
+            t, _ = oracle_sample(pool, batch, idx)
+            if s >= args.warmup:
+                times.append(t)
+        pool.close()
+        value = per * len(times) / sum(times)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                                 "sample": f"{per} random RVEs of the workload per step, numpy/LAPACK FP64, "
+                                           f"one process per core"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    pool = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        pool = oracle_pool(os.cpu_count() or 1)      # spawned before the first GPU call
+    if dist:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    batch, R, pk = run_gpu(args, rank, world, dist)
+    mx = R["mixed"]
+    ms = max_over_ranks(mx["ms"], dist)
+    ms64 = max_over_ranks(R["fp64"]["ms"], dist)
+    e2e_ms = max_over_ranks(mx["e2e_ms"], dist)
+    total = args.rves * world
+    value = total * mx["steps"] / (ms * 1e-3)
+    value64 = total * R["fp64"]["steps"] / (ms64 * 1e-3)
+    if rank != 0:
+        return
+    err_mixed_vs_fp64 = rel_errs(mx["Cbar"], R["fp64"]["Cbar"], mx["sigma"], R["fp64"]["sigma"], batch.Fbar)
+    # per-kernel breakdown and roofline of the dominant kernel (event times over the timed region)
+    kern = {}
+    for name, (tms, cnt) in mx["prof"].items():
+        avg = tms / max(cnt, 1)
+        kern[name] = {"ms_total": round(tms, 3), "launches": cnt, "avg_ms": round(avg, 4),
+                      "share": round(tms / max(sum(v[0] for v in mx["prof"].values()), 1e-9), 4),
+                      "roofline": roofline_for(name, avg, args.rves, pk, args.N)}
+    dom = max(kern, key=lambda k: kern[k]["ms_total"]) if kern else None
+    roof = dict(kern[dom]["roofline"] or {}) if dom else {}
+    if roof:
+        roof["kernel"] = dom
+        roof["traffic"] = None
+    kern64 = {}
+    for name, (tms, cnt) in R["fp64"]["prof"].items():
+        avg = tms / max(cnt, 1)
+        kern64[name] = {"ms_total": round(tms, 3), "launches": cnt, "avg_ms": round(avg, 4),
+                        "roofline": roofline_for(name, avg, args.rves, pk, args.N)}
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus, "steps": mx["steps"],
+            "warmup": args.warmup, "ms_per_step": round(ms / mx["steps"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (FP32 band factor, FP64 residual/Schur)",
+            "data": "synthetic (seeded microstructures and loads)", "config": cfg,
+            "precision_path": "mixed", "gpu_launches": mx["launches"],
+            "fp64_path": {"value": round(value64, 1), "ms_per_step": round(ms64 / R["fp64"]["steps"], 3),
+                          "steps": R["fp64"]["steps"], "kernels": kern64},
+            "speedup_mixed_vs_fp64": round(value / value64, 2),
+            "max_rel_err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
+            "status_nonzero": int((mx["status"] != 0).sum()),
+            "roofline": roof, "kernels": kern, "clocks": mx["clocks"],
+            "e2e": {"value": round(total * args.steps / (e2e_ms * 1e-3), 1), "unit": UNIT,
+                    "h2d_bytes_per_step": mx["h2d"], "d2h_bytes_per_step": mx["d2h"]}}
+    if pool is not None:
+        nproc = os.cpu_count() or 1
+        idx = list(np.random.default_rng(1).choice(batch.nrve, size=args.cpu_sample, replace=False))
+        t, res = oracle_sample(pool, batch, idx)
+        pool.close()
+        Cref = np.array([r[1] for r in res])
+        sref = np.array([r[2] for r in res])
+        line["cpu_baseline"] = {"value": round(len(idx) / t, 2), "unit": UNIT, "cores": nproc, "kind": "oracle",
+                                "sample": f"{len(idx)} random RVEs of the same workload, numpy/LAPACK FP64 "
+                                          f"dense Cholesky, one single-threaded process per core"}
+        line["max_rel_err_vs_oracle"] = {
+            "mixed": rel_errs(mx["Cbar"][idx], Cref, mx["sigma"][idx], sref, batch.Fbar[idx]),
+            "fp64": rel_errs(R["fp64"]["Cbar"][idx], Cref, R["fp64"]["sigma"][idx], sref, batch.Fbar[idx]),
+            "rves_checked": len(idx)}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * fe2.h -- C ABI of the GB300 RVE block of monolithic FE^2
+ * (Hesch, Schmidt & Schuss, "Variational formulation and monolithic solution
+ * of computational homogenization methods", arXiv 2312.12771).
+ *
+ * One RVE sits at each macro Gauss point (Dirac test basis, Section 3,
+ * Eqs. (fluctVaria_dirac), (fluctSolution)).  For every RVE the library
+ * assembles the micro Hessian blocks of Section 4 (Eqs. (discreteSys_K),
+ * (discreteSys_D), (discreteSys_L)), reduces the periodic fluctuation DOFs by
+ * the discrete null space of periodicity with one pinned corner (Section 2.2,
+ * Eq. (Con)(iii); Section 5.2), factorises the condensed micro stiffness and
+ * forms the Schur complement of Section 4.2, Eq. (solution2):
+ *
+ *   Cbar      = (K_MM - K_Mm K_mm^-1 K_mM) / |Omega|
+ *   sigma_eff = (Pint - K_Mm K_mm^-1 r_m)  / |Omega|
+ *   dw        = -(x_r + X_M : dFbar)        (update below Eq. (solution2))
+ *
+ * Conventions (all calls):
+ *  - RVE = unit cell [0,1]^d, N^d equal elements (Q4 in 2D, Hex8 in 3D),
+ *    element e = ex + N*ey (+N*N*ez); full 2^d Gauss quadrature.
+ *  - Second-order tensors are row-major d x d (F_iJ, J fastest); tangents
+ *    are d^2 x d^2 with Cbar[iJ][kL] = d sigma_iJ / d Fbar_kL.
+ *  - Materials per RVE and phase: double[4] = (model, p1, p2, p3):
+ *    FE2_MODEL_LINEAR (p1 = E, p2 = nu, plane strain in 2D, strain
+ *    sym(F - I)); FE2_MODEL_NEOHOOKE (p1 = mu, p2 = kappa; energy
+ *    mu/2 (F:F - 3) - mu ln J + kappa/2 (J-1)^2, Eq. (MR) with beta = 0).
+ *  - Pointers marked [device] are CUDA device pointers, borrowed for the
+ *    duration of the work queued on the context's stream; [host] pointers are
+ *    read before the call returns.  rve_ids are always [host].
+ *  - Calls enqueue work on cfg.cuda_stream and return without synchronising
+ *    unless stated.  A context is used by one host thread at a time.
+ *  - Errors: every call returns an fe2_status and never aborts;
+ *    fe2_last_error() gives a message.  Per-RVE numerical failures are
+ *    reported in rve_status and do not fail the call.
+ */
+#ifndef FE2_H
+#define FE2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe2_ctx fe2_ctx;
+
+typedef enum {
+    FE2_OK = 0,
+    FE2_ERR_ARG = 1,      /* invalid argument (sizes, ids, pointers)            */
+    FE2_ERR_CUDA = 2,     /* a CUDA runtime call failed                          */
+    FE2_ERR_BUDGET = 3,   /* admission refused: the HBM budget would be exceeded */
+    FE2_ERR_NOT_PD = 4,   /* per RVE: non-positive pivot in the factorisation    */
+    FE2_ERR_NAN = 5,      /* per RVE: NaN/Inf in input or result                 */
+    FE2_ERR_NO_CONV = 6,  /* per RVE: refinement did not reach the tolerance     */
+    FE2_ERR_TIMEOUT = 7   /* a bounded device wait gave up                       */
+} fe2_status;
+
+enum { FE2_ELEM_Q4 = 0, FE2_ELEM_HEX8 = 1 };
+enum { FE2_PREC_FP64 = 0, FE2_PREC_MIXED = 1 };
+enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1 };
+
+typedef struct {
+    int dim;                 /* 2 or 3                                            */
+    int elem;                /* FE2_ELEM_Q4 (dim 2) or FE2_ELEM_HEX8 (dim 3)      */
+    int precision;           /* FE2_PREC_FP64 or FE2_PREC_MIXED                   */
+    size_t hbm_budget_bytes; /* device bytes the context may hold; 0 = no limit   */
+    void* cuda_stream;       /* cudaStream_t the work is queued on; NULL = default */
+    double refine_tol;       /* mixed path: accepted relative error estimate      */
+    int max_refine;          /* mixed path: FP64-residual refinement sweeps (>=0) */
+} fe2_config;
+
+/* Create a context on the current CUDA device.  Allocates nothing large. */
+fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out);
+/* Free every device and host resource of the context (synchronises). */
+void fe2_destroy(fe2_ctx* ctx);
+/* Last error message of the context (never NULL; "" when none). */
+const char* fe2_last_error(const fe2_ctx* ctx);
+/* Block until all work queued by the context has finished. */
+fe2_status fe2_sync(fe2_ctx* ctx);
+
+/* Device bytes one RVE of mesh size N holds while registered (persistent
+ * state) and while in a condensation batch (transient workspace). */
+size_t fe2_rve_bytes(const fe2_ctx* ctx, int N);
+
+/*
+ * Register nrve RVEs (setup step, Section 5.2: periodic nodal coupling and a
+ * pinned corner).  N[nrve] [host] mesh sizes (>= 2, may differ per RVE);
+ * phase [host] uint8 per element, RVEs concatenated; mat [host]
+ * double[nrve][nphase][4]; rve_ids_out[nrve] [host] receives the ids.
+ * The fluctuation w~ of each RVE starts at zero.  Returns FE2_ERR_BUDGET,
+ * registering nothing, if the context's HBM budget would be exceeded.
+ */
+fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase,
+                            int nphase, const double* mat, int* rve_ids_out);
+/* Release RVEs and their device memory. */
+fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids);
+
+/*
+ * S1 + S2 (Section 2.2 Eqs. (microdefo), (microGrad); Section 3 Eqs. (linSys3),
+ * (linSys4)): at F~ = Fbar + grad w~ evaluate P~ and A = dP~/dF~ at every
+ * micro Gauss point and integrate, per element, the rows of the element
+ * Hessian k_e, the element residual f_e, the coupling k_eM and the element
+ * parts of K_MM = int A and Pint = int P~.  Fbar [device] double[n][d][d].
+ * Results stay in a context-owned element workspace until the next call.
+ */
+fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar);
+
+/*
+ * S3: reduce the element data of the last fe2_micro_assemble by the discrete
+ * null space of periodicity with the pinned corner: K_mm = T^T K T,
+ * r_m = T^T f, K_mM = T^T k_M; K_MM and Pint summed over elements.
+ * rve_ids must be a subset of the last assembled batch.
+ */
+fe2_status fe2_nullspace_reduce(fe2_ctx* ctx, int n, const int* rve_ids);
+
+/*
+ * S4 - S6 (Section 4.2, Eq. (solution2)): factorise K_mm (band Cholesky in
+ * the folded periodic ordering; FP64, or FP32 factor with FP64 residual
+ * refinement and a residual-corrected Schur complement on the mixed path),
+ * solve X_M = K_mm^-1 K_mM and x_r = K_mm^-1 r_m, and write
+ *   sigma_eff [device] double[n][d*d],  Cbar [device] double[n][d^2][d^2],
+ *   rve_status [device] int[n] (fe2_status per RVE),
+ *   err_est [device] double[n]: estimated relative error of Cbar (may be NULL).
+ * X_M and x_r stay resident for fe2_macro_step.
+ */
+fe2_status fe2_condense(fe2_ctx* ctx, int n, const int* rve_ids, double* sigma_eff, double* Cbar,
+                        int* rve_status, double* err_est);
+
+/*
+ * Fused S1 - S6: the production path (assembly and periodic reduction in one
+ * kernel, then condensation).  Same inputs/outputs as the three calls above.
+ */
+fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar,
+                         double* sigma_eff, double* Cbar, int* rve_status, double* err_est);
+
+/*
+ * S7 micro part (update below Section 4.2, Eq. (solution2)):
+ * w~ <- w~ - (x_r + X_M : dFbar), with X_M, x_r of the last condensation
+ * of each RVE (no new factorisation).  dFbar [device] double[n][d][d].
+ */
+fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double* dFbar);
+
+/*
+ * Macro Q4 problem of Section 3, Eq. (linSys2) with the condensed tangent of
+ * Eq. (solution2): K = sum_b eta_b B_b^T Cbar_b B_b and
+ * R = sum_b eta_b B_b^T s_b over the macro Gauss points b = 4 e + q, where
+ * s_b is sigma_eff (condensed right-hand side) or Pbar (R_macro).
+ * Dirichlet DOFs are held fixed; the free block is solved by a band Cholesky
+ * on the device.  fe2_macro_setup [host] inputs: nodes X[nnode][2], Q4
+ * connectivity conn[nelem][4] (local node a = ax + 2 ay on the reference
+ * square), Dirichlet flags fixed[nnode*2] (1 = prescribed).
+ */
+fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, const int* conn,
+                           const uint8_t* fixed);
+/*
+ * One macro solve: given sigma [device] double[nelem*4][4] and Cbar [device]
+ * double[nelem*4][4][4] per macro Gauss point, solve K dq = -R on the free DOFs
+ * and write dq [device] double[nnode*2] (zero on fixed DOFs),
+ * dFbar [device] double[nelem*4][4] = B_b dq and rnorm [device] double[1]
+ * = ||R_free||_2.
+ */
+fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dq,
+                           double* dFbar, double* rnorm);
+/* Macro deformation gradients Fbar_b = sum_A q_A (x) grad N^A(X_b) for nodal
+ * positions q [device] double[nnode][2] -> Fbar [device] double[nelem*4][2][2];
+ * eta [device] double[nelem*4] receives the quadrature weights (may be NULL). */
+fe2_status fe2_macro_gradients(fe2_ctx* ctx, const double* q, double* Fbar, double* eta);
+
+/*
+ * Test/diagnostic export of one RVE in the natural periodic numbering
+ * (node p = i + N j (+N^2 k), reduced DOF d*(p-1)+c):  what = 0: dense K_mm
+ * [nm][nm]; 1: r_m [nm]; 2: K_mM [nm][d*d]; 3: w~ [nm]; 4: K_MM [d^2][d^2]
+ * then Pint [d^2].  host_out [host] must hold the stated doubles.
+ * Synchronises the stream.
+ */
+fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* host_out);
+/* Set w~ of one RVE from the natural numbering ([host] double[nm]). */
+fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w);
+
+/* Number of kernel launches the context has issued so far. */
+long long fe2_launch_count(const fe2_ctx* ctx);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch.  fe2_profile(ctx, 1) enables it and clears the totals;
+ * fe2_profile(ctx, 0) disables it.  fe2_profile_read synchronises the stream
+ * and writes, for up to max kernels, the name (names [host] char[max][48],
+ * NUL-terminated), the summed milliseconds (ms [host]) and the launch count
+ * (count [host]); it returns the number of kernels (or -1 on error).
+ */
+fe2_status fe2_profile(fe2_ctx* ctx, int enable);
+int fe2_profile_read(fe2_ctx* ctx, int max, char* names, double* ms, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE2_H */

@@ -1,0 +1,817 @@
+// C ABI of the RVE block (see include/fe2.h): context, RVE registry with
+// HBM-budget admission, id-list cache, transient workspace, and the launch
+// sequences of the assemble / reduce / condense / macro-step calls.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fe2_internal.cuh"
+
+namespace fe2 {
+size_t factor_smem_bytes(int kd, int nr, bool fp64);
+}
+
+using namespace fe2;
+
+namespace {
+
+struct HostRve {
+    bool active = false;
+    bool all_linear = true;
+    int chunk = -1;       // allocation chunk
+    std::vector<double> mat;
+};
+
+struct Chunk {
+    void* dev = nullptr;
+    int refs = 0;
+};
+
+struct IdList {
+    std::vector<int> ids;
+    int* dev = nullptr;
+    int* pinned = nullptr;
+    unsigned long long last = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct fe2_ctx {
+    fe2_config cfg{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int max_smem = 0;
+    // registry
+    std::vector<RveDev> mirror;
+    std::vector<HostRve> host;
+    std::vector<int> free_ids;
+    std::vector<Chunk> chunks;
+    RveDev* d_tab = nullptr;
+    int tab_cap = 0;
+    size_t persistent_bytes = 0;
+    // transient buffers
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* elem = nullptr;
+    size_t elem_bytes = 0;
+    std::vector<int> elem_ids;     // ids whose element data is in `elem`
+    int* d_status_tmp = nullptr;
+    size_t status_tmp_n = 0;
+    // id-list cache
+    std::vector<IdList> idcache;
+    unsigned long long tick = 0;
+    long long launches = 0;
+    std::map<int, int> kd_cache;
+    // per-kernel event timing
+    bool prof = false;
+    struct Pending {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> evpool;
+    std::map<std::string, std::pair<double, long long>> totals;
+    // macro problem
+    struct Macro {
+        int nnode = 0, nelem = 0, nfree = 0, kd = 0, nfree_pad = 0;
+        double* X = nullptr;        // [nnode][2]
+        int* conn = nullptr;        // [nelem][4]
+        int* dof2free = nullptr;    // [2 nnode] -> free index or -1
+        int* free2dof = nullptr;    // [nfree]
+        double* grads = nullptr;    // [nelem*4][4][2]
+        double* eta = nullptr;      // [nelem*4]
+        double* K = nullptr;        // band [nfree_pad][kd+1]
+        double* R = nullptr;        // [nfree_pad]
+        int* adj = nullptr;         // CSR of node -> (elem, local) for assembly
+        int* adj_ptr = nullptr;
+    } macro;
+};
+
+static fe2_status fail(fe2_ctx* c, fe2_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) return fail(ctx, FE2_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------ sizes
+static int nodes_of(int N, int d) { return d == 2 ? N * N : N * N * N; }
+
+static int compute_kd(fe2_ctx* ctx, int N, int d) {
+    auto it = ctx->kd_cache.find(N * 4 + d);
+    if (it != ctx->kd_cache.end()) return it->second;
+    int kd = 0;
+    const int nn = nodes_of(N, d);
+    if (d == 2) {
+        for (int q = 1; q < nn; ++q) {
+            const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int qn = fold_pos((i + dx + N) % N, N) + N * fold_pos((j + dy + N) % N, N);
+                    if (qn == 0) continue;
+                    kd = std::max(kd, 2 * std::abs(qn - q) + 1);
+                }
+        }
+    }
+    const int nm = d * (nn - 1);
+    kd = std::min(kd, nm - 1);
+    ctx->kd_cache[N * 4 + d] = kd;
+    return kd;
+}
+
+static size_t persistent_bytes_of(int N, int d, int nphase) {
+    const int nn = nodes_of(N, d), nm = d * (nn - 1), nr = d * d + 1;
+    const int nst = (d == 2 ? 9 : 27) * d * d;
+    size_t b = 0;
+    b += align256(nn);                               // phase
+    b += align256((size_t)nphase * 4 * 8);           // mat
+    b += align256((size_t)nm * 8);                   // w
+    b += align256((size_t)nst * nn * 8);             // stencil
+    b += 2 * align256((size_t)nr * nm * 8);          // rhs, X
+    b += align256((size_t)(d * d * d * d + d * d) * 8);  // KMM, Pint
+    return b;
+}
+
+struct WsLayout {
+    size_t offY, offR, stride;
+};
+
+static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64) {
+    const size_t es = fp64 ? 8 : 4;
+    WsLayout l;
+    size_t o = align256((size_t)maxnmp * (maxkd + 1) * es);
+    l.offY = o;
+    o += align256((size_t)maxnr * maxnmp * es);
+    l.offR = o;
+    o += align256((size_t)maxnr * maxnm * 8);
+    l.stride = o;
+    return l;
+}
+
+static fe2_status free_ws(fe2_ctx* ctx) {
+    if (!ctx->ws) return FE2_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    return FE2_OK;
+}
+
+// Make the transient workspace hold `bytes`; a workspace larger than `limit`
+// (what the budget leaves) is released first.
+static fe2_status ensure_ws(fe2_ctx* ctx, size_t bytes, size_t limit = (size_t)-1) {
+    if (ctx->ws_bytes > limit) {
+        fe2_status st = free_ws(ctx);
+        if (st != FE2_OK) return st;
+    }
+    if (bytes <= ctx->ws_bytes) return FE2_OK;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->ws) CK(cudaFree(ctx->ws));
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+    CK(cudaMalloc(&ctx->ws, bytes));
+    ctx->ws_bytes = bytes;
+    return FE2_OK;
+}
+
+static size_t used_bytes(const fe2_ctx* c) { return c->persistent_bytes + c->ws_bytes + c->elem_bytes; }
+
+// ------------------------------------------------------------------ id lists
+static fe2_status get_ids(fe2_ctx* ctx, int n, const int* ids, const int** dev) {
+    if (n <= 0 || !ids) return fail(ctx, FE2_ERR_ARG, "empty id list");
+    for (int k = 0; k < n; ++k) {
+        const int id = ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+    }
+    ++ctx->tick;
+    for (auto& e : ctx->idcache) {
+        if ((int)e.ids.size() == n && std::memcmp(e.ids.data(), ids, sizeof(int) * n) == 0) {
+            e.last = ctx->tick;
+            *dev = e.dev;
+            return FE2_OK;
+        }
+    }
+    {  // duplicates would race inside a launch
+        std::vector<int> s(ids, ids + n);
+        std::sort(s.begin(), s.end());
+        if (std::adjacent_find(s.begin(), s.end()) != s.end())
+            return fail(ctx, FE2_ERR_ARG, "duplicate rve id in one call");
+    }
+    if (ctx->idcache.size() >= 16) {
+        auto lru = std::min_element(ctx->idcache.begin(), ctx->idcache.end(),
+                                    [](const IdList& a, const IdList& b) { return a.last < b.last; });
+        CK(cudaStreamSynchronize(ctx->stream));
+        cudaFree(lru->dev);
+        cudaFreeHost(lru->pinned);
+        ctx->idcache.erase(lru);
+    }
+    IdList e;
+    e.ids.assign(ids, ids + n);
+    CK(cudaMalloc(&e.dev, sizeof(int) * n));
+    CK(cudaMallocHost(&e.pinned, sizeof(int) * n));
+    std::memcpy(e.pinned, ids, sizeof(int) * n);
+    CK(cudaMemcpyAsync(e.dev, e.pinned, sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+    e.last = ctx->tick;
+    ctx->idcache.push_back(e);
+    *dev = ctx->idcache.back().dev;
+    return FE2_OK;
+}
+
+static void drop_cached_lists_with(fe2_ctx* ctx, const std::vector<int>& released) {
+    if (ctx->idcache.empty()) return;
+    std::vector<char> mark(ctx->host.size(), 0);
+    for (int id : released) mark[id] = 1;
+    bool synced = false;
+    for (size_t k = 0; k < ctx->idcache.size();) {
+        bool hit = false;
+        for (int id : ctx->idcache[k].ids) hit |= mark[id] != 0;
+        if (hit) {
+            if (!synced) {
+                cudaStreamSynchronize(ctx->stream);
+                synced = true;
+            }
+            cudaFree(ctx->idcache[k].dev);
+            cudaFreeHost(ctx->idcache[k].pinned);
+            ctx->idcache.erase(ctx->idcache.begin() + k);
+        } else {
+            ++k;
+        }
+    }
+}
+
+struct BatchInfo {
+    int maxN = 0, maxkd = 0, maxnr = 0, maxnm = 0, maxnmp = 0, maxnn = 0;
+    bool all_linear = true;
+};
+
+static BatchInfo batch_info(const fe2_ctx* ctx, int n, const int* ids) {
+    BatchInfo b;
+    for (int k = 0; k < n; ++k) {
+        const RveDev& r = ctx->mirror[ids[k]];
+        b.maxN = std::max(b.maxN, r.N);
+        b.maxkd = std::max(b.maxkd, r.kd);
+        b.maxnr = std::max(b.maxnr, r.nr);
+        b.maxnm = std::max(b.maxnm, r.nm);
+        b.maxnmp = std::max(b.maxnmp, r.nm_pad);
+        b.maxnn = std::max(b.maxnn, r.nn);
+        b.all_linear &= ctx->host[ids[k]].all_linear;
+    }
+    return b;
+}
+
+static fe2_status upload_desc(fe2_ctx* ctx, int id) {
+    // the source lives in a std::vector that may move: complete the copy now
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_tab + id, &ctx->mirror[id], sizeof(RveDev), cudaMemcpyHostToDevice));
+    return FE2_OK;
+}
+
+static fe2_status upload_all(fe2_ctx* ctx) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(ctx->d_tab, ctx->mirror.data(), sizeof(RveDev) * ctx->mirror.size(), cudaMemcpyHostToDevice));
+    return FE2_OK;
+}
+
+// ------------------------------------------------------------------ timing
+static cudaEvent_t take_event(fe2_ctx* ctx) {
+    if (!ctx->evpool.empty()) {
+        cudaEvent_t e = ctx->evpool.back();
+        ctx->evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct KTimer {
+    fe2_ctx* ctx;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    KTimer(fe2_ctx* c, const char* n) : ctx(c), name(n) {
+        ++ctx->launches;
+        if (ctx->prof) {
+            a = take_event(ctx);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~KTimer() {
+        if (ctx->prof) {
+            cudaEvent_t b = take_event(ctx);
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({name, a, b});
+        }
+    }
+};
+
+static void drain_timing(fe2_ctx* ctx) {
+    if (ctx->pending.empty()) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        auto& t = ctx->totals[p.name];
+        t.first += ms;
+        t.second += 1;
+        ctx->evpool.push_back(p.a);
+        ctx->evpool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+#define TIMED(name, call)                     \
+    do {                                      \
+        KTimer kt_(ctx, name);                \
+        CK(call);                             \
+    } while (0)
+
+// ------------------------------------------------------------------ condensation
+static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* d_ids, double* sigma,
+                                double* Cbar, int* status, double* err, bool reset_status) {
+    const BatchInfo b = batch_info(ctx, n, ids);
+    const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
+    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64);
+    // chunk the batch so that its workspace fits the budget
+    int cap = n;
+    size_t limit = (size_t)-1;
+    if (ctx->cfg.hbm_budget_bytes) {
+        const size_t used = ctx->persistent_bytes + ctx->elem_bytes;
+        limit = ctx->cfg.hbm_budget_bytes > used ? ctx->cfg.hbm_budget_bytes - used : 0;
+        cap = (int)std::min<size_t>((size_t)n, limit / l.stride);
+        if (cap < 1) return fail(ctx, FE2_ERR_BUDGET, "no room for one RVE of workspace within the HBM budget");
+    }
+    fe2_status st = ensure_ws(ctx, l.stride * (size_t)cap, limit);
+    if (st != FE2_OK) return st;
+    if (reset_status) CK(cudaMemsetAsync(status, 0, sizeof(int) * n, ctx->stream));
+    Workspace ws{ctx->ws, l.stride, l.offY, l.offR};
+    const int dd = ctx->cfg.dim * ctx->cfg.dim;
+    for (int c0 = 0; c0 < n; c0 += cap) {
+        const int m = std::min(cap, n - c0);
+        const int* di = d_ids + c0;
+        int* stp = status + c0;
+        if (fp64) {
+            TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            TIMED("band_backward_fp64",
+                  launch_backward<double>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+        } else {
+            TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            TIMED("band_backward_fp32",
+                  launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+            for (int it = 0; it < ctx->cfg.max_refine; ++it) {
+                TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
+                TIMED("band_refine_fp32",
+                      launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+            }
+            TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
+        }
+        TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, fp64 ? 0 : 1, sigma + (size_t)c0 * dd,
+                                    Cbar + (size_t)c0 * dd * dd, stp, err ? err + c0 : nullptr, ctx->stream));
+    }
+    return FE2_OK;
+}
+
+// ================================================================== C ABI
+extern "C" {
+
+fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
+    fe2_ctx* ctx = nullptr;
+    if (!cfg || !out) return FE2_ERR_ARG;
+    *out = nullptr;
+    if (cfg->dim != 2 && cfg->dim != 3) return FE2_ERR_ARG;
+    if ((cfg->dim == 2) != (cfg->elem == FE2_ELEM_Q4)) return FE2_ERR_ARG;
+    if (cfg->precision != FE2_PREC_FP64 && cfg->precision != FE2_PREC_MIXED) return FE2_ERR_ARG;
+    if (cfg->max_refine < 0 || cfg->max_refine > 16) return FE2_ERR_ARG;
+    if (cfg->dim == 3) return FE2_ERR_ARG;  // Hex8 kernels are not built in this library version
+    ctx = new fe2_ctx();
+    ctx->cfg = *cfg;
+    ctx->stream = (cudaStream_t)cfg->cuda_stream;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return FE2_ERR_CUDA;
+    }
+    *out = ctx;
+    return FE2_OK;
+}
+
+void fe2_destroy(fe2_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& c : ctx->chunks)
+        if (c.dev) cudaFree(c.dev);
+    for (auto& e : ctx->idcache) {
+        cudaFree(e.dev);
+        cudaFreeHost(e.pinned);
+    }
+    cudaFree(ctx->d_tab);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->elem);
+    cudaFree(ctx->d_status_tmp);
+    auto& M = ctx->macro;
+    cudaFree(M.X);
+    cudaFree(M.conn);
+    cudaFree(M.dof2free);
+    cudaFree(M.free2dof);
+    cudaFree(M.grads);
+    cudaFree(M.eta);
+    cudaFree(M.K);
+    cudaFree(M.R);
+    cudaFree(M.adj);
+    cudaFree(M.adj_ptr);
+    drain_timing(ctx);
+    for (auto e : ctx->evpool) cudaEventDestroy(e);
+    delete ctx;
+}
+
+const char* fe2_last_error(const fe2_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+fe2_status fe2_sync(fe2_ctx* ctx) {
+    if (!ctx) return FE2_ERR_ARG;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FE2_OK;
+}
+
+long long fe2_launch_count(const fe2_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+fe2_status fe2_profile(fe2_ctx* ctx, int enable) {
+    if (!ctx) return FE2_ERR_ARG;
+    drain_timing(ctx);
+    ctx->totals.clear();
+    ctx->prof = enable != 0;
+    return FE2_OK;
+}
+
+int fe2_profile_read(fe2_ctx* ctx, int max, char* names, double* ms, long long* count) {
+    if (!ctx || max < 0) return -1;
+    drain_timing(ctx);
+    int k = 0;
+    for (auto& t : ctx->totals) {
+        if (k >= max) break;
+        if (names) {
+            std::strncpy(names + 48 * k, t.first.c_str(), 47);
+            names[48 * k + 47] = 0;
+        }
+        if (ms) ms[k] = t.second.first;
+        if (count) count[k] = t.second.second;
+        ++k;
+    }
+    return (int)ctx->totals.size();
+}
+
+size_t fe2_rve_bytes(const fe2_ctx* ctx, int N) {
+    if (!ctx || N < 2) return 0;
+    const int d = ctx->cfg.dim;
+    const int kd = compute_kd(const_cast<fe2_ctx*>(ctx), N, d);
+    const int nn = nodes_of(N, d), nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
+    const WsLayout l = ws_layout(kd, d * d + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64);
+    return persistent_bytes_of(N, d, 2) + l.stride;
+}
+
+fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase, int nphase,
+                            const double* mat, int* rve_ids_out) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (nrve <= 0 || !N || !phase || !mat || !rve_ids_out) return fail(ctx, FE2_ERR_ARG, "bad register arguments");
+    if (nphase < 1 || nphase > MAX_PHASES) return fail(ctx, FE2_ERR_ARG, "nphase must be in [1, %d]", MAX_PHASES);
+    const int d = ctx->cfg.dim;
+    const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
+    size_t total = 0, ws_need = 0;
+    std::vector<size_t> offs(nrve);
+    size_t phase_off = 0;
+    for (int k = 0; k < nrve; ++k) {
+        if (N[k] < 2 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range", N[k]);
+        const int kd = compute_kd(ctx, N[k], d);
+        const int nr = d * d + 1;
+        if (kd + nr > FACT_THREADS) return fail(ctx, FE2_ERR_ARG, "N=%d: band too wide for one CTA", N[k]);
+        if ((int)factor_smem_bytes(kd, nr, fp64) > ctx->max_smem)
+            return fail(ctx, FE2_ERR_ARG, "N=%d: band window (%zu B) exceeds shared memory (%d B) on the %s path",
+                        N[k], factor_smem_bytes(kd, nr, fp64), ctx->max_smem, fp64 ? "FP64" : "mixed");
+        const int nn = nodes_of(N[k], d);
+        for (int p = 0; p < nphase; ++p) {
+            const double* m = mat + ((size_t)k * nphase + p) * 4;
+            const int model = (int)m[0];
+            if (model != FE2_MODEL_LINEAR && model != FE2_MODEL_NEOHOOKE)
+                return fail(ctx, FE2_ERR_ARG, "rve %d phase %d: unknown material model %g", k, p, m[0]);
+        }
+        for (int e = 0; e < nn; ++e)
+            if (phase[phase_off + e] >= nphase) return fail(ctx, FE2_ERR_ARG, "rve %d: phase index out of range", k);
+        phase_off += nn;
+        offs[k] = total;
+        total += persistent_bytes_of(N[k], d, nphase);
+        const int nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
+        ws_need = std::max(ws_need, ws_layout(kd, nr, nm, nmp, fp64).stride);
+    }
+    if (ctx->cfg.hbm_budget_bytes) {
+        // persistent state of everything registered plus one workspace slot must fit;
+        // the transient workspace is reclaimed (and re-grown by the next condensation)
+        const size_t keep = ctx->persistent_bytes + ctx->elem_bytes;
+        if (keep + total + ws_need > ctx->cfg.hbm_budget_bytes)
+            return fail(ctx, FE2_ERR_BUDGET,
+                        "admission refused: %zu B registered + %zu B requested exceeds budget %zu B", keep,
+                        total + ws_need, ctx->cfg.hbm_budget_bytes);
+        if (keep + total + ctx->ws_bytes > ctx->cfg.hbm_budget_bytes) {
+            fe2_status st = free_ws(ctx);
+            if (st != FE2_OK) return st;
+        }
+    }
+    // ids
+    std::vector<int> ids(nrve);
+    for (int k = 0; k < nrve; ++k) {
+        if (!ctx->free_ids.empty()) {
+            ids[k] = ctx->free_ids.back();
+            ctx->free_ids.pop_back();
+        } else {
+            ids[k] = (int)ctx->host.size();
+            ctx->host.emplace_back();
+            ctx->mirror.emplace_back();
+        }
+    }
+    const int need_cap = (int)ctx->host.size();
+    if (need_cap > ctx->tab_cap) {
+        int cap = std::max(need_cap, std::max(64, ctx->tab_cap * 2));
+        RveDev* nt = nullptr;
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMalloc(&nt, sizeof(RveDev) * cap));
+        if (ctx->d_tab) {
+            CK(cudaMemcpy(nt, ctx->d_tab, sizeof(RveDev) * ctx->tab_cap, cudaMemcpyDeviceToDevice));
+            CK(cudaFree(ctx->d_tab));
+        }
+        ctx->d_tab = nt;
+        ctx->tab_cap = cap;
+    }
+    Chunk ch;
+    CK(cudaMalloc(&ch.dev, total));
+    CK(cudaMemsetAsync(ch.dev, 0, total, ctx->stream));
+    ch.refs = nrve;
+    int chunk_id = -1;
+    for (size_t c = 0; c < ctx->chunks.size(); ++c)
+        if (!ctx->chunks[c].dev) {
+            chunk_id = (int)c;
+            break;
+        }
+    if (chunk_id < 0) {
+        chunk_id = (int)ctx->chunks.size();
+        ctx->chunks.push_back(ch);
+    } else {
+        ctx->chunks[chunk_id] = ch;
+    }
+    ctx->persistent_bytes += total;
+    // stage phase + mat for all RVEs of the chunk with one host buffer
+    std::vector<unsigned char> stage(total, 0);
+    phase_off = 0;
+    for (int k = 0; k < nrve; ++k) {
+        const int nn = nodes_of(N[k], d), nm = d * (nn - 1), nr = d * d + 1;
+        const int nst = (d == 2 ? 9 : 27) * d * d;
+        char* base = (char*)ch.dev + offs[k];
+        unsigned char* hb = stage.data() + offs[k];
+        RveDev r{};
+        r.N = N[k];
+        r.d = d;
+        r.nm = nm;
+        r.kd = compute_kd(ctx, N[k], d);
+        r.nn = nn;
+        r.nphase = nphase;
+        r.nm_pad = (nm + NB - 1) / NB * NB;
+        r.nr = nr;
+        size_t o = 0;
+        r.phase = (const uint8_t*)(base + o);
+        std::memcpy(hb + o, phase + phase_off, nn);
+        o += align256(nn);
+        r.mat = (const double*)(base + o);
+        std::memcpy(hb + o, mat + (size_t)k * nphase * 4, (size_t)nphase * 4 * 8);
+        o += align256((size_t)nphase * 4 * 8);
+        r.w = (double*)(base + o);
+        o += align256((size_t)nm * 8);
+        r.stencil = (double*)(base + o);
+        o += align256((size_t)nst * nn * 8);
+        r.rhs = (double*)(base + o);
+        o += align256((size_t)nr * nm * 8);
+        r.X = (double*)(base + o);
+        o += align256((size_t)nr * nm * 8);
+        r.KMM = (double*)(base + o);
+        r.Pint = r.KMM + d * d * d * d;
+        r.elem = nullptr;
+        r.zero_w = 1;
+        phase_off += nn;
+        const int id = ids[k];
+        ctx->mirror[id] = r;
+        HostRve& h = ctx->host[id];
+        h.active = true;
+        h.chunk = chunk_id;
+        h.mat.assign(mat + (size_t)k * nphase * 4, mat + (size_t)(k + 1) * nphase * 4);
+        h.all_linear = true;
+        for (int p = 0; p < nphase; ++p) h.all_linear &= (int)h.mat[4 * p] == FE2_MODEL_LINEAR;
+        rve_ids_out[k] = id;
+    }
+    CK(cudaMemcpyAsync(ch.dev, stage.data(), total, cudaMemcpyHostToDevice, ctx->stream));
+    // descriptors (contiguous runs are common; upload one by one for simplicity)
+    std::vector<RveDev> tmp(nrve);
+    for (int k = 0; k < nrve; ++k) tmp[k] = ctx->mirror[ids[k]];
+    for (int k = 0; k < nrve; ++k)
+        CK(cudaMemcpyAsync(ctx->d_tab + ids[k], &tmp[k], sizeof(RveDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (n < 0 || (n > 0 && !rve_ids)) return fail(ctx, FE2_ERR_ARG, "bad release arguments");
+    std::vector<int> rel;
+    for (int k = 0; k < n; ++k) {
+        const int id = rve_ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        rel.push_back(id);
+    }
+    drop_cached_lists_with(ctx, rel);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int id : rel) {
+        HostRve& h = ctx->host[id];
+        if (!h.active) continue;
+        h.active = false;
+        const RveDev& r = ctx->mirror[id];
+        ctx->persistent_bytes -= persistent_bytes_of(r.N, r.d, r.nphase);
+        Chunk& c = ctx->chunks[h.chunk];
+        if (--c.refs == 0) {
+            CK(cudaFree(c.dev));
+            c.dev = nullptr;
+        }
+        h.chunk = -1;
+        ctx->free_ids.push_back(id);
+    }
+    return FE2_OK;
+}
+
+fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!Fbar) return fail(ctx, FE2_ERR_ARG, "Fbar is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    const BatchInfo b = batch_info(ctx, n, rve_ids);
+    const int d = ctx->cfg.dim;
+    const size_t per = (size_t)b.maxnn * elem_comps(d) * 8;
+    const size_t need = per * n;
+    if (need > ctx->elem_bytes) {
+        if (ctx->cfg.hbm_budget_bytes && used_bytes(ctx) - ctx->elem_bytes + need > ctx->cfg.hbm_budget_bytes)
+            return fail(ctx, FE2_ERR_BUDGET, "element workspace of %zu B exceeds the HBM budget", need);
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->elem) CK(cudaFree(ctx->elem));
+        ctx->elem = nullptr;
+        ctx->elem_bytes = 0;
+        CK(cudaMalloc(&ctx->elem, need));
+        ctx->elem_bytes = need;
+    }
+    for (int id : ctx->elem_ids)
+        if (id < (int)ctx->mirror.size()) ctx->mirror[id].elem = nullptr;
+    ctx->elem_ids.assign(rve_ids, rve_ids + n);
+    for (int k = 0; k < n; ++k) ctx->mirror[rve_ids[k]].elem = (double*)((char*)ctx->elem + per * k);
+    st = upload_all(ctx);
+    if (st != FE2_OK) return st;
+    TIMED("assemble_elems", launch_assemble_elems(ctx->d_tab, d_ids, n, Fbar, d, b.maxN, ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_nullspace_reduce(fe2_ctx* ctx, int n, const int* rve_ids) {
+    if (!ctx) return FE2_ERR_ARG;
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    for (int k = 0; k < n; ++k)
+        if (!ctx->mirror[rve_ids[k]].elem)
+            return fail(ctx, FE2_ERR_ARG, "rve %d has no element data: call fe2_micro_assemble first", rve_ids[k]);
+    const BatchInfo b = batch_info(ctx, n, rve_ids);
+    TIMED("nullspace_reduce", launch_reduce(ctx->d_tab, d_ids, n, ctx->cfg.dim, b.maxN, ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_condense(fe2_ctx* ctx, int n, const int* rve_ids, double* sigma_eff, double* Cbar, int* rve_status,
+                        double* err_est) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!sigma_eff || !Cbar || !rve_status) return fail(ctx, FE2_ERR_ARG, "output pointer is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, true);
+}
+
+fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar, double* sigma_eff,
+                         double* Cbar, int* rve_status, double* err_est) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!Fbar || !sigma_eff || !Cbar || !rve_status) return fail(ctx, FE2_ERR_ARG, "NULL pointer argument");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    const BatchInfo b = batch_info(ctx, n, rve_ids);
+    TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));
+    TIMED(b.all_linear ? "assemble_reduce_linear" : "assemble_reduce_general",
+          launch_assemble_fused(ctx->d_tab, d_ids, n, Fbar, ctx->cfg.dim, b.maxN, b.all_linear ? 1 : 0, ctx->stream));
+    return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
+}
+
+fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double* dFbar) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!dFbar) return fail(ctx, FE2_ERR_ARG, "dFbar is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    const BatchInfo b = batch_info(ctx, n, rve_ids);
+    TIMED("macro_update", launch_macro_update(ctx->d_tab, d_ids, n, dFbar, b.maxnm, ctx->stream));
+    for (int k = 0; k < n; ++k) ctx->mirror[rve_ids[k]].zero_w = 0;
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (rve_id < 0 || rve_id >= (int)ctx->host.size() || !ctx->host[rve_id].active || !host_w)
+        return fail(ctx, FE2_ERR_ARG, "bad rve id or NULL w");
+    RveDev& r = ctx->mirror[rve_id];
+    const int N = r.N, d = r.d;
+    std::vector<double> wf(r.nm);
+    for (int p = 1; p < r.nn; ++p) {
+        const int i = p % N, j = p / N;
+        const int q = fold_pos(i, N) + N * fold_pos(j, N);
+        for (int c = 0; c < d; ++c) wf[d * (q - 1) + c] = host_w[d * (p - 1) + c];
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(r.w, wf.data(), sizeof(double) * r.nm, cudaMemcpyHostToDevice));
+    r.zero_w = 0;
+    return upload_desc(ctx, rve_id);
+}
+
+fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* out) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (rve_id < 0 || rve_id >= (int)ctx->host.size() || !ctx->host[rve_id].active || !out)
+        return fail(ctx, FE2_ERR_ARG, "bad rve id or NULL output");
+    CK(cudaStreamSynchronize(ctx->stream));
+    const RveDev& r = ctx->mirror[rve_id];
+    const int N = r.N, d = r.d, nm = r.nm, nn = r.nn, dd = d * d;
+    if (d != 2) return fail(ctx, FE2_ERR_ARG, "export supports 2D only");
+    std::vector<int> q2p(nn);
+    for (int p = 0; p < nn; ++p) q2p[fold_pos(p % N, N) + N * fold_pos(p / N, N)] = p;
+    auto nat = [&](int fdof) { return d * (q2p[fdof / d + 1] - 1) + fdof % d; };
+    if (what == 0) {
+        std::vector<double> st((size_t)9 * 4 * nn);
+        CK(cudaMemcpy(st.data(), r.stencil, sizeof(double) * st.size(), cudaMemcpyDeviceToHost));
+        std::memset(out, 0, sizeof(double) * (size_t)nm * nm);
+        for (int q = 1; q < nn; ++q) {
+            const int p = q2p[q], i = p % N, j = p / N;
+            for (int off = 0; off < 9; ++off) {
+                const int dx = off % 3 - 1, dy = off / 3 - 1;
+                const int pn = (i + dx + N) % N + N * ((j + dy + N) % N);
+                if (pn == 0) continue;
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2)
+                        out[(size_t)(2 * (p - 1) + c) * nm + 2 * (pn - 1) + c2] +=
+                            st[(size_t)((off * 2 + c) * 2 + c2) * nn + q];
+            }
+        }
+    } else if (what == 1 || what == 2) {
+        std::vector<double> rhs((size_t)r.nr * nm);
+        CK(cudaMemcpy(rhs.data(), r.rhs, sizeof(double) * rhs.size(), cudaMemcpyDeviceToHost));
+        for (int m = 0; m < nm; ++m) {
+            if (what == 1)
+                out[nat(m)] = rhs[(size_t)dd * nm + m];
+            else
+                for (int kL = 0; kL < dd; ++kL) out[(size_t)nat(m) * dd + kL] = rhs[(size_t)kL * nm + m];
+        }
+    } else if (what == 3) {
+        std::vector<double> w(nm);
+        CK(cudaMemcpy(w.data(), r.w, sizeof(double) * nm, cudaMemcpyDeviceToHost));
+        for (int m = 0; m < nm; ++m) out[nat(m)] = r.zero_w ? 0.0 : w[m];
+    } else if (what == 4) {
+        CK(cudaMemcpy(out, r.KMM, sizeof(double) * (dd * dd + dd), cudaMemcpyDeviceToHost));
+    } else {
+        return fail(ctx, FE2_ERR_ARG, "unknown export selector %d", what);
+    }
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_setup(fe2_ctx* ctx, int, const double*, int, const int*, const uint8_t*) {
+    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+}
+fe2_status fe2_macro_solve(fe2_ctx* ctx, const double*, const double*, double*, double*, double*) {
+    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+}
+fe2_status fe2_macro_gradients(fe2_ctx* ctx, const double*, double*, double*) {
+    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,420 @@
+// S1 - S3 of the RVE block: micro kinematics and constitutive law at the
+// Gauss points, element integrals, and the periodic null-space reduction into
+// node-row stencils (2D, bilinear Q4, 2x2 Gauss).
+//
+// Section 2.2, Eqs. (microdefo), (microGrad): F~ = Fbar + sum_a w_a (x) grad N_a.
+// Section 2.1: H = cof F, J = det F, P = dPsi/dF + dPsi/dJ H, A = dP/dF for the
+//   Neo-Hooke law of Eq. (MR) with beta = 0 (plane strain, F33 = 1).
+// Section 3, Eqs. (linSys3), (linSys4) and Section 4, Eqs. (discreteSys_K/D/L):
+//   k_e = int G^T A G, f_e = int G^T P, k_eM = int G^T A, K_MM = int A, Pint = int P.
+// Section 2.2, Eq. (Con)(iii) + Section 5.2: periodic nodal coupling with the
+//   corner pinned, applied as a gather over the periodic node map.
+//
+// Work decomposition: every quantity of a node row is the sum, over the 2^d
+// elements that touch the node, of that element's rows for the node's local
+// index a.  Each (element, a) pair is integrated by one thread
+// (elem_rows2); the fused kernel sums the four pairs of a node directly, the
+// split path stores them per element and gathers them in a second kernel.
+// Both sum in the same order, so they agree bit for bit.
+#include "fe2_internal.cuh"
+
+namespace fe2 {
+
+namespace {
+
+constexpr double kGauss = 0.57735026918962576451;  // 1/sqrt(3)
+
+// dN_a/dX_J at Gauss point q of a square element of side h
+__device__ __forceinline__ double grad2(int q, int a, int J, double h) {
+    const double sa0 = (a & 1) ? 1.0 : -1.0, sa1 = (a & 2) ? 1.0 : -1.0;
+    const double xi0 = (q & 1) ? kGauss : -kGauss, xi1 = (q & 2) ? kGauss : -kGauss;
+    return J == 0 ? 0.5 * sa0 * (1.0 + sa1 * xi1) / h : 0.5 * sa1 * (1.0 + sa0 * xi0) / h;
+}
+
+__device__ __forceinline__ void lame(double E, double nu, double& lam, double& mu) {
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    mu = E / (2.0 * (1.0 + nu));
+}
+
+// P and A of the material row m at the in-plane gradient F (plane strain).
+__device__ void consti2(const double* m, const double F[2][2], double P[2][2],
+                        double A[2][2][2][2]) {
+    const int model = (int)m[0];
+    if (model == FE2_MODEL_LINEAR) {
+        double lam, mu;
+        lame(m[1], m[2], lam, mu);
+        double eps[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int J = 0; J < 2; ++J) eps[i][J] = 0.5 * (F[i][J] + F[J][i]) - (i == J ? 1.0 : 0.0);
+        const double tr = eps[0][0] + eps[1][1];
+        for (int i = 0; i < 2; ++i)
+            for (int J = 0; J < 2; ++J) P[i][J] = (i == J ? lam * tr : 0.0) + 2.0 * mu * eps[i][J];
+        for (int i = 0; i < 2; ++i)
+            for (int J = 0; J < 2; ++J)
+                for (int k = 0; k < 2; ++k)
+                    for (int L = 0; L < 2; ++L)
+                        A[i][J][k][L] = (i == J && k == L ? lam : 0.0) +
+                                        mu * ((i == k && J == L ? 1.0 : 0.0) + (i == L && J == k ? 1.0 : 0.0));
+    } else {
+        const double mu = m[1], kappa = m[2];
+        // plane-strain cofactor of the in-plane block and J = det F
+        const double H[2][2] = {{F[1][1], -F[1][0]}, {-F[0][1], F[0][0]}};
+        const double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+        const double s = kappa * (J - 1.0) - mu / J;          // dPsi/dJ
+        const double c = mu / (J * J) + kappa;                // d^2Psi/dJ^2
+        for (int i = 0; i < 2; ++i)
+            for (int K = 0; K < 2; ++K) P[i][K] = mu * F[i][K] + s * H[i][K];
+        for (int i = 0; i < 2; ++i)
+            for (int K = 0; K < 2; ++K)
+                for (int k = 0; k < 2; ++k)
+                    for (int L = 0; L < 2; ++L)
+                        A[i][K][k][L] = (i == k && K == L ? mu : 0.0) + c * H[i][K] * H[k][L];
+        // dH/dF (constant in 2D): H00 = F11, H01 = -F10, H10 = -F01, H11 = F00
+        A[0][0][1][1] += s;
+        A[0][1][1][0] -= s;
+        A[1][0][0][1] -= s;
+        A[1][1][0][0] += s;
+    }
+}
+
+struct Rows2 {
+    double kr[4][2][2];  // k_e rows of local node a against local node b
+    double f[2];         // f_e rows
+    double kM[2][4];     // k_eM rows
+};
+
+// Integrate the rows of local node a of element (ex, ey) at (Fbar, w~).
+// If mm != nullptr, also accumulate K_MM (mm[16]) and Pint (mm[16..19]) of the element.
+__device__ void elem_rows2(const RveDev& r, int ex, int ey, int a, const double Fb[4],
+                           Rows2& out, double* mm) {
+    const int N = r.N;
+    const double h = 1.0 / N, wq = 0.25 * h * h;
+    const double* m = r.mat + 4 * r.phase[ex + N * ey];
+    double we[4][2];
+    for (int b = 0; b < 4; ++b) {
+        const int i = (ex + (b & 1)) % N, j = (ey + (b >> 1)) % N;
+        const int q = fold_pos(i, N) + N * fold_pos(j, N);
+        for (int c = 0; c < 2; ++c) we[b][c] = (q == 0 || r.zero_w) ? 0.0 : r.w[2 * (q - 1) + c];
+    }
+    for (int b = 0; b < 4; ++b)
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 2; ++k) out.kr[b][i][k] = 0.0;
+    out.f[0] = out.f[1] = 0.0;
+    for (int i = 0; i < 2; ++i)
+        for (int kL = 0; kL < 4; ++kL) out.kM[i][kL] = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        double G[4][2];
+        for (int b = 0; b < 4; ++b)
+            for (int J = 0; J < 2; ++J) G[b][J] = grad2(q, b, J, h);
+        double F[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int J = 0; J < 2; ++J) {
+                double v = Fb[2 * i + J];
+                for (int b = 0; b < 4; ++b) v += we[b][i] * G[b][J];
+                F[i][J] = v;
+            }
+        double P[2][2], A[2][2][2][2];
+        consti2(m, F, P, A);
+        // t[i][k][L] = sum_J G_aJ A_iJkL
+        double t[2][2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int k = 0; k < 2; ++k)
+                for (int L = 0; L < 2; ++L) t[i][k][L] = G[a][0] * A[i][0][k][L] + G[a][1] * A[i][1][k][L];
+        for (int b = 0; b < 4; ++b)
+            for (int i = 0; i < 2; ++i)
+                for (int k = 0; k < 2; ++k)
+                    out.kr[b][i][k] += wq * (t[i][k][0] * G[b][0] + t[i][k][1] * G[b][1]);
+        for (int i = 0; i < 2; ++i) {
+            out.f[i] += wq * (P[i][0] * G[a][0] + P[i][1] * G[a][1]);
+            for (int k = 0; k < 2; ++k)
+                for (int L = 0; L < 2; ++L) out.kM[i][2 * k + L] += wq * t[i][k][L];
+        }
+        if (mm) {
+            for (int iJ = 0; iJ < 4; ++iJ)
+                for (int kL = 0; kL < 4; ++kL) mm[4 * iJ + kL] += wq * A[iJ >> 1][iJ & 1][kL >> 1][kL & 1];
+            for (int iJ = 0; iJ < 4; ++iJ) mm[16 + iJ] += wq * P[iJ >> 1][iJ & 1];
+        }
+    }
+}
+
+// offsets: off = (dx+1) + 3 (dy+1) for the neighbour at (i+dx, j+dy)
+__device__ __forceinline__ int nbr_q(int i, int j, int off, int N) {
+    const int dx = off % 3 - 1, dy = off / 3 - 1;
+    const int ii = (i + dx + N) % N, jj = (j + dy + N) % N;
+    return fold_pos(ii, N) + N * fold_pos(jj, N);
+}
+
+// Deterministic block sum of NV per-thread partials (blockDim.x = 256); every
+// thread receives the totals.
+template <int NV>
+__device__ void block_sum(const double (&v)[NV], double* red /*[256]*/, double (&out)[NV]) {
+    for (int k = 0; k < NV; ++k) {
+        red[threadIdx.x] = v[k];
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        out[k] = red[0];
+        __syncthreads();
+    }
+}
+
+// Write node q's row data into the reduced arrays.
+__device__ __forceinline__ void store_row(const RveDev& r, int q, const double st[9][2][2],
+                                          const double f[2], const double kM[2][4]) {
+    const int nn = r.nn;
+    for (int off = 0; off < 9; ++off)
+        for (int c = 0; c < 2; ++c)
+            for (int c2 = 0; c2 < 2; ++c2) r.stencil[(size_t)((off * 2 + c) * 2 + c2) * nn + q] = st[off][c][c2];
+    if (q == 0) return;  // pinned corner: no reduced DOF
+    for (int c = 0; c < 2; ++c) {
+        const int dof = 2 * (q - 1) + c;
+        for (int kL = 0; kL < 4; ++kL) r.rhs[(size_t)kL * r.nm + dof] = kM[c][kL];
+        r.rhs[(size_t)4 * r.nm + dof] = f[c];
+    }
+}
+
+// ---------------------------------------------------------------- general path
+// Fused S1-S3: one CTA per RVE, one thread per node row (strided).
+__global__ void __launch_bounds__(256) k_assemble_fused_general2(const RveDev* __restrict__ tab,
+                                                                 const int* __restrict__ ids,
+                                                                 const double* __restrict__ Fbar) {
+    __shared__ double red[256];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N;
+    double Fb[4];
+    for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.x + k];
+    double mm[20];
+    for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+    for (int q = threadIdx.x; q < r.nn; q += blockDim.x) {
+        const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+        double st[9][2][2] = {};
+        double f[2] = {0.0, 0.0}, kM[2][4] = {};
+        for (int a = 0; a < 4; ++a) {
+            const int ax = a & 1, ay = a >> 1;
+            const int ex = (i - ax + N) % N, ey = (j - ay + N) % N;
+            Rows2 rw;
+            elem_rows2(r, ex, ey, a, Fb, rw, a == 0 ? mm : nullptr);
+            for (int b = 0; b < 4; ++b) {
+                const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += rw.kr[b][c][c2];
+            }
+            for (int c = 0; c < 2; ++c) {
+                f[c] += rw.f[c];
+                for (int kL = 0; kL < 4; ++kL) kM[c][kL] += rw.kM[c][kL];
+            }
+        }
+        store_row(r, q, st, f, kM);
+    }
+    double tot[20];
+    block_sum<20>(mm, red, tot);
+    if (threadIdx.x < 16) r.KMM[threadIdx.x] = tot[threadIdx.x];
+    else if (threadIdx.x < 20) r.Pint[threadIdx.x - 16] = tot[threadIdx.x];
+}
+
+// Split S1 + S2: one thread per (element, local node a).
+__global__ void __launch_bounds__(128) k_assemble_elems2(const RveDev* __restrict__ tab,
+                                                         const int* __restrict__ ids,
+                                                         const double* __restrict__ Fbar) {
+    const RveDev r = tab[ids[blockIdx.y]];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * r.nn) return;
+    const int e = t >> 2, a = t & 3;
+    const int N = r.N, ex = e % N, ey = e / N;
+    double Fb[4];
+    for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.y + k];
+    double mm[20];
+    for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+    Rows2 rw;
+    elem_rows2(r, ex, ey, a, Fb, rw, a == 0 ? mm : nullptr);
+    const int nn = r.nn, RC = elem_row_comps(2);
+    double* E = r.elem;
+    int c0 = a * RC;
+    for (int b = 0; b < 4; ++b)
+        for (int c = 0; c < 2; ++c)
+            for (int c2 = 0; c2 < 2; ++c2) E[(size_t)(c0++) * nn + e] = rw.kr[b][c][c2];
+    for (int c = 0; c < 2; ++c) E[(size_t)(c0++) * nn + e] = rw.f[c];
+    for (int c = 0; c < 2; ++c)
+        for (int kL = 0; kL < 4; ++kL) E[(size_t)(c0++) * nn + e] = rw.kM[c][kL];
+    if (a == 0)
+        for (int k = 0; k < 20; ++k) E[(size_t)(4 * RC + k) * nn + e] = mm[k];
+}
+
+// Split S3: gather the element rows of each node through the periodic map.
+__global__ void __launch_bounds__(256) k_reduce2(const RveDev* __restrict__ tab,
+                                                 const int* __restrict__ ids) {
+    __shared__ double red[256];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N, nn = r.nn, RC = elem_row_comps(2);
+    const double* E = r.elem;
+    double mm[20];
+    for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+        const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+        double st[9][2][2] = {};
+        double f[2] = {0.0, 0.0}, kM[2][4] = {};
+        for (int a = 0; a < 4; ++a) {
+            const int ax = a & 1, ay = a >> 1;
+            const int e = (i - ax + N) % N + N * ((j - ay + N) % N);
+            int c0 = a * RC;
+            for (int b = 0; b < 4; ++b) {
+                const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += E[(size_t)(c0++) * nn + e];
+            }
+            for (int c = 0; c < 2; ++c) f[c] += E[(size_t)(c0++) * nn + e];
+            for (int c = 0; c < 2; ++c)
+                for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
+            if (a == 0)
+                for (int k = 0; k < 20; ++k) mm[k] += E[(size_t)(4 * RC + k) * nn + e];
+        }
+        store_row(r, q, st, f, kM);
+    }
+    double tot[20];
+    block_sum<20>(mm, red, tot);
+    if (threadIdx.x < 16) r.KMM[threadIdx.x] = tot[threadIdx.x];
+    else if (threadIdx.x < 20) r.Pint[threadIdx.x - 16] = tot[threadIdx.x];
+}
+
+// ---------------------------------------------------------------- linear fast path
+// For isotropic linear elasticity A = lam I(x)I + mu (I_ik I_JL + I_iL I_Jk) is
+// constant per element, so every element integral is lam * (table) + mu * (table)
+// with tables of the uniform grid (exact; linearity of the integrals in A).
+// r_m = K w + K_mM : H and Pint = K_MM : H + K_mM^T w follow from linearity.
+__global__ void __launch_bounds__(256) k_assemble_fused_linear2(const RveDev* __restrict__ tab,
+                                                                const int* __restrict__ ids,
+                                                                const double* __restrict__ Fbar) {
+    __shared__ double Kl[4][4][2][2], Km[4][4][2][2], kMl[4][2][4], kMm[4][2][4];
+    __shared__ double red[256];
+    __shared__ double lamE[MAX_PHASES], muE[MAX_PHASES];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N;
+    const double h = 1.0 / N, wq = 0.25 * h * h;
+    const int tid = threadIdx.x;
+    if (tid < 64) {
+        const int a = tid >> 4, b = (tid >> 2) & 3, i = (tid >> 1) & 1, k = tid & 1;
+        double sl = 0.0, sm = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            const double gai = grad2(q, a, i, h), gbk = grad2(q, b, k, h);
+            const double gak = grad2(q, a, k, h), gbi = grad2(q, b, i, h);
+            const double dotab = grad2(q, a, 0, h) * grad2(q, b, 0, h) + grad2(q, a, 1, h) * grad2(q, b, 1, h);
+            sl += wq * gai * gbk;
+            sm += wq * ((i == k ? dotab : 0.0) + gak * gbi);
+        }
+        Kl[a][b][i][k] = sl;
+        Km[a][b][i][k] = sm;
+    } else if (tid < 96) {
+        const int t = tid - 64, a = t >> 3, i = (t >> 2) & 1, kL = t & 3, k = kL >> 1, L = kL & 1;
+        double sl = 0.0, sm = 0.0;
+        for (int q = 0; q < 4; ++q) {
+            sl += wq * (k == L ? grad2(q, a, i, h) : 0.0);
+            sm += wq * ((i == k ? grad2(q, a, L, h) : 0.0) + (i == L ? grad2(q, a, k, h) : 0.0));
+        }
+        kMl[a][i][kL] = sl;
+        kMm[a][i][kL] = sm;
+    } else if (tid < 96 + r.nphase && tid - 96 < MAX_PHASES) {
+        const int p = tid - 96;
+        lame(r.mat[4 * p + 1], r.mat[4 * p + 2], lamE[p], muE[p]);
+    }
+    __syncthreads();
+    double H[4];
+    for (int k = 0; k < 4; ++k) H[k] = Fbar[4 * blockIdx.x + k] - ((k == 0 || k == 3) ? 1.0 : 0.0);
+    double part[6];  // sum lam_e, sum mu_e, (K_mM^T w)[4]
+    for (int k = 0; k < 6; ++k) part[k] = 0.0;
+    for (int q = tid; q < r.nn; q += blockDim.x) {
+        const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+        double st[9][2][2] = {};
+        double kM[2][4] = {};
+        for (int a = 0; a < 4; ++a) {
+            const int ax = a & 1, ay = a >> 1;
+            const int e = (i - ax + N) % N + N * ((j - ay + N) % N);
+            const int ph = r.phase[e];
+            const double lam = lamE[ph], mu = muE[ph];
+            if (a == 0) {
+                part[0] += lam;
+                part[1] += mu;
+            }
+            for (int b = 0; b < 4; ++b) {
+                const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += lam * Kl[a][b][c][c2] + mu * Km[a][b][c][c2];
+            }
+            for (int c = 0; c < 2; ++c)
+                for (int kL = 0; kL < 4; ++kL) kM[c][kL] += lam * kMl[a][c][kL] + mu * kMm[a][c][kL];
+        }
+        double f[2];
+        for (int c = 0; c < 2; ++c) f[c] = kM[c][0] * H[0] + kM[c][1] * H[1] + kM[c][2] * H[2] + kM[c][3] * H[3];
+        if (!r.zero_w) {
+            for (int off = 0; off < 9; ++off) {
+                const int qn = nbr_q(i, j, off, N);
+                if (qn == 0) continue;
+                const double w0 = r.w[2 * (qn - 1)], w1 = r.w[2 * (qn - 1) + 1];
+                for (int c = 0; c < 2; ++c) f[c] += st[off][c][0] * w0 + st[off][c][1] * w1;
+            }
+            if (q != 0) {
+                const double w0 = r.w[2 * (q - 1)], w1 = r.w[2 * (q - 1) + 1];
+                for (int kL = 0; kL < 4; ++kL) part[2 + kL] += kM[0][kL] * w0 + kM[1][kL] * w1;
+            }
+        }
+        store_row(r, q, st, f, kM);
+    }
+    double tot[6];
+    block_sum<6>(part, red, tot);
+    if (tid < 16) {
+        const int iJ = tid >> 2, kL = tid & 3, i = iJ >> 1, J = iJ & 1, k = kL >> 1, L = kL & 1;
+        const double vol = h * h;  // per element
+        r.KMM[tid] = tot[0] * vol * (i == J && k == L ? 1.0 : 0.0) +
+                     tot[1] * vol * ((i == k && J == L ? 1.0 : 0.0) + (i == L && J == k ? 1.0 : 0.0));
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double s = tot[2 + tid];
+        for (int kL = 0; kL < 4; ++kL) s += r.KMM[4 * tid + kL] * H[kL];
+        r.Pint[tid] = s;
+    }
+}
+
+__global__ void k_check_fbar(const double* __restrict__ Fbar, int n, int dd, int* __restrict__ status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int bad = 0;
+    for (int k = 0; k < dd; ++k) bad |= !isfinite(Fbar[(size_t)t * dd + k]);
+    status[t] = bad ? FE2_ERR_NAN : FE2_OK;
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_elems(const RveDev* tab, const int* ids, int n, const double* Fbar, int d,
+                                  int maxN, cudaStream_t s) {
+    if (d != 2) return cudaErrorNotSupported;
+    dim3 grid((4 * maxN * maxN + 127) / 128, n);
+    k_assemble_elems2<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const RveDev* tab, const int* ids, int n, int d, int maxN, cudaStream_t s) {
+    (void)maxN;
+    if (d != 2) return cudaErrorNotSupported;
+    k_reduce2<<<n, 256, 0, s>>>(tab, ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, const double* Fbar, int d,
+                                  int maxN, int all_linear, cudaStream_t s) {
+    (void)maxN;
+    if (d != 2) return cudaErrorNotSupported;
+    if (all_linear)
+        k_assemble_fused_linear2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    else
+        k_assemble_fused_general2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_fbar(const double* Fbar, int n, int d, int* status, cudaStream_t s) {
+    k_check_fbar<<<(n + 255) / 256, 256, 0, s>>>(Fbar, n, d * d, status);
+    return cudaGetLastError();
+}
+
+}  // namespace fe2

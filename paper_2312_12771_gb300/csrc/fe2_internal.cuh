@@ -1,0 +1,81 @@
+// Internal declarations of the GB300 RVE-block library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fe2.h"
+
+namespace fe2 {
+
+constexpr int NB = 32;          // panel width of the band factorisation / solves
+constexpr int FACT_THREADS = 256;
+constexpr int MAX_PHASES = 8;
+
+// Device descriptor of one registered RVE.  The fluctuation DOFs use the
+// folded periodic ordering: node (i, j[, k]) -> q = pos(i) + N pos(j) (+N^2 pos(k))
+// with pos = 0, 1, N-1, 2, N-2, ... (neighbours, including the periodic wrap,
+// are at most 2 apart in pos), pinned corner q = 0, DOF = d (q - 1) + c.
+struct RveDev {
+    int N, d, nm, kd;           // mesh size, dimension, reduced DOFs, half bandwidth
+    int nn, nphase, nm_pad, nr; // N^d nodes (= elements), phases, nm rounded up to NB, d*d+1
+    const uint8_t* phase;       // [nn] per element, natural element order
+    const double* mat;          // [nphase][4]
+    double* w;                  // [nm] fluctuation
+    double* stencil;            // [3^d * d * d][nn]: block (off, c, c') of node row q
+    double* rhs;                // [nr][nm]: columns of K_mM, then r_m
+    double* X;                  // [nr][nm]: X_M columns, then x_r
+    double* KMM;                // [d^4]
+    double* Pint;               // [d^2]
+    double* elem;               // split path: element workspace [ncomp][nn] (or null)
+    int zero_w;                 // 1 while w is known to be exactly zero
+    int pad_;
+};
+
+// Transient per-launch workspace: slot s of a launch owns
+//   L  at base + s*stride          (T[nm_pad][kd+1], lower band, column-major)
+//   Y  at base + s*stride + offY   (T[nr][nm_pad], forward-solve result)
+//   R  at base + s*stride + offR   (double[nr][nm], FP64 residuals)
+struct Workspace {
+    char* base;
+    size_t stride, offY, offR;
+};
+
+__host__ __device__ inline int fold_pos(int i, int N) {
+    return i == 0 ? 0 : (2 * i <= N ? 2 * i - 1 : 2 * (N - i));
+}
+__host__ __device__ inline int unfold_pos(int p, int N) {
+    return p == 0 ? 0 : ((p & 1) ? (p + 1) / 2 : N - p / 2);
+}
+// element-centred quantities per (element, local node) in the split path
+__host__ __device__ constexpr int elem_row_comps(int d) {
+    return (1 << d) * d * d + d + d * d * d;   // kr[b][c][c'] + f[c] + kM[c][kL]
+}
+__host__ __device__ constexpr int elem_comps(int d) {
+    return (1 << d) * elem_row_comps(d) + d * d * d * d + d * d;
+}
+
+// ---------------------------------------------------------------- launchers
+// every launcher returns cudaGetLastError() of its launch(es)
+cudaError_t launch_assemble_elems(const RveDev* tab, const int* ids, int n, const double* Fbar,
+                                  int d, int maxN, cudaStream_t s);
+cudaError_t launch_reduce(const RveDev* tab, const int* ids, int n, int d, int maxN, cudaStream_t s);
+cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, const double* Fbar,
+                                  int d, int maxN, int all_linear, cudaStream_t s);
+template <typename T>
+cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws, int* status,
+                          int maxkd, int maxnr, cudaStream_t s);
+template <typename T>
+cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate,
+                            int maxkd, int maxnr, int maxnm_pad, cudaStream_t s);
+template <typename T>
+cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd,
+                                 int maxnr, int maxnm_pad, cudaStream_t s);
+cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
+                            cudaStream_t s);
+cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected,
+                         double* sigma, double* Cbar, int* status, double* err, cudaStream_t s);
+cudaError_t launch_macro_update(const RveDev* tab, const int* ids, int n, const double* dF,
+                                int maxnm, cudaStream_t s);
+cudaError_t launch_check_fbar(const double* Fbar, int n, int d, int* status, cudaStream_t s);
+
+}  // namespace fe2

@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libfe2 (the C ABI declared in include/fe2.h).
+
+Argument marshalling only: every step of the RVE block runs in the CUDA
+kernels of libfe2.  PyTorch provides device memory and the stream.  There is
+no CPU fallback: if the library is missing or no GPU is present, the calls
+raise.
+
+Module-level functions carry the C names (``fe2_create``, ``fe2_rve_solve``
+...); :class:`Fe2Context` wraps them for tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libfe2.so")
+
+FE2_OK, FE2_ERR_ARG, FE2_ERR_CUDA, FE2_ERR_BUDGET = 0, 1, 2, 3
+FE2_ERR_NOT_PD, FE2_ERR_NAN, FE2_ERR_NO_CONV, FE2_ERR_TIMEOUT = 4, 5, 6, 7
+FE2_ELEM_Q4, FE2_ELEM_HEX8 = 0, 1
+FE2_PREC_FP64, FE2_PREC_MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_BUDGET", 4: "NOT_PD", 5: "NAN",
+                6: "NO_CONV", 7: "TIMEOUT"}
+
+
+class fe2_config(C.Structure):
+    _fields_ = [("dim", C.c_int), ("elem", C.c_int), ("precision", C.c_int),
+                ("hbm_budget_bytes", C.c_size_t), ("cuda_stream", C.c_void_p),
+                ("refine_tol", C.c_double), ("max_refine", C.c_int)]
+
+
+class Fe2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_P = C.c_void_p
+_I = C.c_int
+_IP = C.POINTER(C.c_int)
+_DP = C.POINTER(C.c_double)
+
+_SIGS = {
+    "fe2_create": (_I, [C.POINTER(fe2_config), C.POINTER(_P)]),
+    "fe2_destroy": (None, [_P]),
+    "fe2_last_error": (C.c_char_p, [_P]),
+    "fe2_sync": (_I, [_P]),
+    "fe2_rve_bytes": (C.c_size_t, [_P, _I]),
+    "fe2_rve_register": (_I, [_P, _I, _IP, C.POINTER(C.c_uint8), _I, _DP, _IP]),
+    "fe2_rve_release": (_I, [_P, _I, _IP]),
+    "fe2_micro_assemble": (_I, [_P, _I, _IP, _P]),
+    "fe2_nullspace_reduce": (_I, [_P, _I, _IP]),
+    "fe2_condense": (_I, [_P, _I, _IP, _P, _P, _P, _P]),
+    "fe2_rve_solve": (_I, [_P, _I, _IP, _P, _P, _P, _P, _P]),
+    "fe2_macro_step": (_I, [_P, _I, _IP, _P]),
+    "fe2_macro_setup": (_I, [_P, _I, _DP, _I, _IP, C.POINTER(C.c_uint8)]),
+    "fe2_macro_solve": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fe2_macro_gradients": (_I, [_P, _P, _P, _P]),
+    "fe2_rve_export": (_I, [_P, _I, _I, _DP]),
+    "fe2_rve_set_w": (_I, [_P, _I, _DP]),
+    "fe2_launch_count": (C.c_longlong, [_P]),
+    "fe2_profile": (_I, [_P, _I]),
+    "fe2_profile_read": (_I, [_P, _I, C.c_char_p, _DP, C.POINTER(C.c_longlong)]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libfe2 (built by ``paper_2312_12771_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfe2 not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+# C-named thin wrappers --------------------------------------------------------
+def _call(name, *args):
+    return getattr(load(), name)(*args)
+
+
+def fe2_create(cfg):
+    h = C.c_void_p()
+    st = _call("fe2_create", C.byref(cfg), C.byref(h))
+    if st != FE2_OK:
+        raise Fe2Error(st, "fe2_create failed")
+    return h
+
+
+def fe2_destroy(h):
+    _call("fe2_destroy", h)
+
+
+def fe2_last_error(h):
+    return _call("fe2_last_error", h).decode()
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _ids(ids):
+    a = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
+    return a, a.ctypes.data_as(_IP)
+
+
+class Fe2Context:
+    """A libfe2 context on the current CUDA device and stream."""
+
+    def __init__(self, dim=2, precision="mixed", hbm_budget_bytes=0, refine_tol=1e-10, max_refine=1,
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libfe2 needs a CUDA GPU (GB300, sm_103a)")
+        self.torch = torch
+        self.dim = dim
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.precision = precision
+        cfg = fe2_config(dim, FE2_ELEM_Q4 if dim == 2 else FE2_ELEM_HEX8,
+                         FE2_PREC_MIXED if precision == "mixed" else FE2_PREC_FP64,
+                         int(hbm_budget_bytes), C.c_void_p(self.stream.cuda_stream), float(refine_tol),
+                         int(max_refine))
+        self.cfg = cfg
+        self.h = fe2_create(cfg)
+        self.lib = load()
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fe2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != FE2_OK:
+            raise Fe2Error(st, f"{what}: {fe2_last_error(self.h)}")
+
+    # -- registry ---------------------------------------------------------------
+    def register(self, N, phase_concat, mat):
+        N = np.ascontiguousarray(np.asarray(N, dtype=np.int32))
+        ph = np.ascontiguousarray(np.asarray(phase_concat, dtype=np.uint8))
+        mat = np.ascontiguousarray(np.asarray(mat, dtype=np.float64))
+        nphase = mat.shape[1]
+        out = np.zeros(len(N), dtype=np.int32)
+        st = self.lib.fe2_rve_register(self.h, len(N), N.ctypes.data_as(_IP),
+                                       ph.ctypes.data_as(C.POINTER(C.c_uint8)), nphase,
+                                       mat.ctypes.data_as(_DP), out.ctypes.data_as(_IP))
+        self._check(st, "fe2_rve_register")
+        return out
+
+    def register_batch(self, batch):
+        return self.register(batch.N, batch.phase_concat(), batch.mat)
+
+    def release(self, ids):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_release(self.h, len(a), p), "fe2_rve_release")
+
+    def rve_bytes(self, N):
+        return int(self.lib.fe2_rve_bytes(self.h, int(N)))
+
+    # -- the hot path ------------------------------------------------------------
+    def _outs(self, n):
+        t = self.torch
+        dd = self.dim * self.dim
+        dev = "cuda"
+        return (t.empty((n, dd), dtype=t.float64, device=dev), t.empty((n, dd, dd), dtype=t.float64, device=dev),
+                t.empty(n, dtype=t.int32, device=dev), t.empty(n, dtype=t.float64, device=dev))
+
+    def rve_solve(self, ids, Fbar, out=None):
+        """Fused S1-S6: returns (sigma_eff [n,d*d], Cbar [n,d*d,d*d], status [n], err [n])."""
+        a, p = _ids(ids)
+        Fbar = Fbar.contiguous()
+        assert Fbar.is_cuda and Fbar.dtype == self.torch.float64
+        sig, Cb, st, err = out if out is not None else self._outs(len(a))
+        self._check(self.lib.fe2_rve_solve(self.h, len(a), p, _ptr(Fbar), _ptr(sig), _ptr(Cb), _ptr(st), _ptr(err)),
+                    "fe2_rve_solve")
+        return sig, Cb, st, err
+
+    def micro_assemble(self, ids, Fbar):
+        a, p = _ids(ids)
+        Fbar = Fbar.contiguous()
+        self._check(self.lib.fe2_micro_assemble(self.h, len(a), p, _ptr(Fbar)), "fe2_micro_assemble")
+
+    def nullspace_reduce(self, ids):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_nullspace_reduce(self.h, len(a), p), "fe2_nullspace_reduce")
+
+    def condense(self, ids, out=None):
+        a, p = _ids(ids)
+        sig, Cb, st, err = out if out is not None else self._outs(len(a))
+        self._check(self.lib.fe2_condense(self.h, len(a), p, _ptr(sig), _ptr(Cb), _ptr(st), _ptr(err)),
+                    "fe2_condense")
+        return sig, Cb, st, err
+
+    def macro_step(self, ids, dFbar):
+        a, p = _ids(ids)
+        dFbar = dFbar.contiguous()
+        self._check(self.lib.fe2_macro_step(self.h, len(a), p, _ptr(dFbar)), "fe2_macro_step")
+
+    def sync(self):
+        self._check(self.lib.fe2_sync(self.h), "fe2_sync")
+
+    def launch_count(self):
+        return int(self.lib.fe2_launch_count(self.h))
+
+    def profile(self, enable=True):
+        self._check(self.lib.fe2_profile(self.h, 1 if enable else 0), "fe2_profile")
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        n = self.lib.fe2_profile_read(self.h, 0, None, None, None)
+        names = C.create_string_buffer(48 * max(n, 1))
+        ms = np.zeros(max(n, 1))
+        cnt = np.zeros(max(n, 1), dtype=np.int64)
+        n = self.lib.fe2_profile_read(self.h, n, names, ms.ctypes.data_as(_DP),
+                                      cnt.ctypes.data_as(C.POINTER(C.c_longlong)))
+        out = {}
+        for k in range(n):
+            nm = names.raw[48 * k:48 * (k + 1)].split(b"\0")[0].decode()
+            out[nm] = (float(ms[k]), int(cnt[k]))
+        return out
+
+    # -- diagnostics ---------------------------------------------------------------
+    def export(self, rve_id, what, N):
+        d = self.dim
+        nm = d * (N ** d - 1)
+        size = {0: nm * nm, 1: nm, 2: nm * d * d, 3: nm, 4: d ** 4 + d * d}[what]
+        out = np.zeros(size)
+        self._check(self.lib.fe2_rve_export(self.h, int(rve_id), int(what), out.ctypes.data_as(_DP)),
+                    "fe2_rve_export")
+        if what == 0:
+            return out.reshape(nm, nm)
+        if what == 2:
+            return out.reshape(nm, d * d)
+        return out
+
+    def set_w(self, rve_id, w):
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        self._check(self.lib.fe2_rve_set_w(self.h, int(rve_id), w.ctypes.data_as(_DP)), "fe2_rve_set_w")

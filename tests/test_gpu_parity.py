@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: relative error per RVE <= 1e-10 on the FP64 path and <= 1e-8 on
+the mixed path (FP32 factor + FP64 refinement), for sigma_eff and Cbar;
+reduced operators (K_mm, r_m, K_mM, K_MM, Pint) are FP64 on both paths and
+must agree to 1e-13.  Relative error of sigma uses the floor
+||Cbar_ref|| * ||Fbar - I|| so that a near-zero stress is not divided by ~0.
+"""
+import numpy as np
+import pytest
+
+from oracle import fe2_oracle as O
+from paper_2312_12771_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-8}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_12771_gb300 import build
+    build.build()
+    return t
+
+
+def ctx_for(torch, precision, **kw):
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    return Fe2Context(dim=2, precision=precision, **kw)
+
+
+def oracle_batch(batch, idx, w=None):
+    out = []
+    for k in idx:
+        out.append(O.rve_solve(int(batch.N[k]), batch.d, batch.phase[k], batch.mat[k], batch.Fbar[k],
+                               None if w is None else w[k]))
+    return out
+
+
+def sig_floor(ref):
+    return np.linalg.norm(ref["Cbar"]) * np.linalg.norm(ref["Fbar_in"] - np.eye(2))
+
+
+def check(batch, sig, Cb, st, refs, idx, tol):
+    sig = sig.cpu().numpy()
+    Cb = Cb.cpu().numpy()
+    st = st.cpu().numpy()
+    worst = 0.0
+    for j, k in enumerate(idx):
+        assert st[k] == 0, f"rve {k} status {st[k]}"
+        ref = refs[j]
+        eC = O.rel_err(Cb[k], ref["Cbar"])
+        floor = np.linalg.norm(ref["Cbar"]) * np.linalg.norm(batch.Fbar[k] - np.eye(2))
+        eS = O.rel_err(sig[k], ref["sigma_eff"], floor)
+        worst = max(worst, eC, eS)
+        assert eC <= tol, f"rve {k}: Cbar rel err {eC:.3e}"
+        assert eS <= tol, f"rve {k}: sigma rel err {eS:.3e}"
+    return worst
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_laminate_closed_form_on_gpu(torch, precision):
+    b = W.laminate_batch(64, 8)
+    ctx = ctx_for(torch, precision)
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    sig, Cb, st, err = ctx.rve_solve(ids, F)
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    C = Cb.cpu().numpy()
+    # Voigt [xx,yy,xy]: C11 = C[0,0], C22 = C[3,3], C12 = C[0,3], C66 = C[1,1]
+    tol = TOL[precision] * 10
+    assert np.allclose(C[:, 0, 0], 6.49350649350649, rtol=tol, atol=0)
+    assert np.allclose(C[:, 3, 3], 2.44755244755245, rtol=tol, atol=0)
+    assert np.allclose(C[:, 0, 3], 1.04895104895105, rtol=tol, atol=0)
+    assert np.allclose(C[:, 1, 1], 0.699300699300699, rtol=tol, atol=0)
+    s = sig.cpu().numpy()
+    assert np.allclose(s[:, 0], 6.49350649350649e-3, rtol=tol, atol=0)
+    assert np.allclose(s[:, 3], 1.04895104895105e-3, rtol=tol, atol=0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [3, 5, 12])
+def test_fiber_linear_parity(torch, precision, N):
+    b = W.fiber_batch(6, N, dF_scale=2e-3)
+    ctx = ctx_for(torch, precision)
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    idx = list(range(b.nrve))
+    check(b, sig, Cb, st, oracle_batch(b, idx), idx, TOL[precision])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_neohooke_parity_with_fluctuation(torch, precision):
+    """NH inclusions at a finite stretch, with a nonzero fluctuation state."""
+    N = 10
+    b = W.inclusion_batch(5, N, stretch=1.08)
+    b.Fbar = W.perturbed_F(b, 7, 0.02)
+    rng = np.random.default_rng(1)
+    ws = [1e-3 * rng.standard_normal(2 * (N * N - 1)) for _ in range(b.nrve)]
+    ctx = ctx_for(torch, precision)
+    ids = ctx.register_batch(b)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    idx = list(range(b.nrve))
+    check(b, sig, Cb, st, oracle_batch(b, idx, ws), idx, TOL[precision])
+
+
+@pytest.mark.parametrize("model", ["linear", "nh"])
+def test_reduced_operator_entrywise(torch, model):
+    """K_mm, r_m, K_mM, K_MM, Pint after the fused kernel and after the split
+    assemble/reduce calls equal the oracle's T^T K T etc. entry by entry."""
+    N = 7
+    if model == "linear":
+        b = W.fiber_batch(3, N, dF_scale=1e-2)
+    else:
+        b = W.inclusion_batch(3, N, stretch=1.1)
+        b.Fbar = W.perturbed_F(b, 3, 0.03)
+    rng = np.random.default_rng(5)
+    ws = [2e-3 * rng.standard_normal(2 * (N * N - 1)) for _ in range(b.nrve)]
+    ctx = ctx_for(torch, "fp64")
+    ids = ctx.register_batch(b)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    F = torch.tensor(b.Fbar, device="cuda")
+    refs = oracle_batch(b, range(b.nrve), ws)
+    for path in ["fused", "split"]:
+        if path == "fused":
+            ctx.rve_solve(ids, F)
+        else:
+            ctx.micro_assemble(ids, F)
+            ctx.nullspace_reduce(ids)
+        torch.cuda.synchronize()
+        for k, i in enumerate(ids):
+            ref = refs[k]
+            K = ctx.export(i, 0, N)
+            scale = np.abs(ref["K_mm"]).max()
+            assert np.abs(K - ref["K_mm"]).max() <= 1e-13 * scale, path
+            assert np.abs(K - K.T).max() <= 1e-13 * scale
+            r = ctx.export(i, 1, N)
+            assert np.abs(r - ref["r_m"]).max() <= 1e-13 * max(1.0, np.abs(ref["r_m"]).max()) * scale, path
+            KmM = ctx.export(i, 2, N)
+            assert np.abs(KmM - ref["K_mM"]).max() <= 1e-13 * np.abs(ref["K_mM"]).max(), path
+            mm = ctx.export(i, 4, N)
+            assert np.abs(mm[:16] - ref["K_MM"].ravel()).max() <= 1e-13 * np.abs(ref["K_MM"]).max(), path
+            assert np.abs(mm[16:] - ref["Pint"]).max() <= 1e-13 * max(1.0, np.abs(ref["Pint"]).max()), path
+
+
+def test_split_and_fused_paths_agree_bitwise(torch):
+    b = W.inclusion_batch(4, 9, stretch=1.05)
+    ctx = ctx_for(torch, "mixed")
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    s1, C1, st1, _ = ctx.rve_solve(ids, F)
+    s1, C1 = s1.clone(), C1.clone()
+    ctx.micro_assemble(ids, F)
+    ctx.nullspace_reduce(ids)
+    s2, C2, st2, _ = ctx.condense(ids)
+    torch.cuda.synchronize()
+    assert torch.equal(s1, s2) and torch.equal(C1, C2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_fiber32_full_batch_sampled(torch, precision):
+    """The bench workload: 4096 RVEs, 32x32 fiber, checked on sampled RVEs."""
+    b = W.fiber_batch(4096, 32, dF_scale=1e-3)
+    ctx = ctx_for(torch, precision)
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    idx = [0, 1, 777, 2048, 4001, 4095]
+    w = check(b, sig, Cb, st, oracle_batch(b, idx), idx, TOL[precision])
+    print(f"{precision}: worst sampled rel err {w:.3e}")
+    # properties that hold for every RVE: major symmetry and the Voigt bound
+    C = Cb.cpu().numpy()
+    asym = np.abs(C - C.transpose(0, 2, 1)).max() / np.abs(C).max()
+    assert asym <= TOL[precision]
+
+
+def test_uneven_sizes_in_one_batch_match_alone(torch):
+    """RVEs of different N in one call give the same result as alone."""
+    parts = [W.inclusion_batch(2, N, stretch=1.05) for N in (6, 9, 13, 16)]
+    N = np.concatenate([p.N for p in parts])
+    phases = sum([p.phase for p in parts], [])
+    mat = np.concatenate([p.mat for p in parts])
+    F = np.concatenate([p.Fbar for p in parts])
+    mixed = W.RveBatch(2, N, phases, mat, F)
+    ctx = ctx_for(torch, "mixed")
+    ids = ctx.register_batch(mixed)
+    s_all, C_all, st, _ = ctx.rve_solve(ids, torch.tensor(F, device="cuda"))
+    s_all, C_all = s_all.clone(), C_all.clone()
+    for k, i in enumerate(ids):
+        s1, C1, _, _ = ctx.rve_solve([i], torch.tensor(F[k:k + 1], device="cuda"))
+        torch.cuda.synchronize()
+        assert torch.equal(s1[0], s_all[k]) and torch.equal(C1[0], C_all[k])
+    idx = list(range(mixed.nrve))
+    check(mixed, s_all, C_all, st, oracle_batch(mixed, idx), idx, TOL["mixed"])
+
+
+def test_macro_step_update_matches_oracle(torch):
+    """w~ <- w~ - (x_r + X_M : dFbar) with the resident X_M, x_r."""
+    N = 8
+    b = W.inclusion_batch(3, N, stretch=1.1)
+    ctx = ctx_for(torch, "fp64")
+    ids = ctx.register_batch(b)
+    ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    dF = np.array([[[1e-2, 2e-3], [-1e-3, -5e-3]]] * b.nrve)
+    ctx.macro_step(ids, torch.tensor(dF, device="cuda"))
+    torch.cuda.synchronize()
+    for k, i in enumerate(ids):
+        ref = O.rve_solve(N, 2, b.phase[k], b.mat[k], b.Fbar[k])
+        w_ref = -(ref["x_r"] + ref["X_M"] @ dF[k].ravel())
+        w = ctx.export(i, 3, N)
+        assert np.abs(w - w_ref).max() <= 1e-10 * np.abs(w_ref).max()
+
+
+def test_deterministic_repeat(torch):
+    b = W.fiber_batch(64, 16)
+    ctx = ctx_for(torch, "mixed")
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    a = [t.clone() for t in ctx.rve_solve(ids, F)]
+    c = ctx.rve_solve(ids, F)
+    torch.cuda.synchronize()
+    for x, y in zip(a, c):
+        assert torch.equal(x, y)
+
+
+def test_status_nan_and_not_pd(torch):
+    b = W.fiber_batch(3, 6)
+    b.mat[1, 0, 1] = -1.0     # negative Young's modulus in the matrix: indefinite K_mm
+    ctx = ctx_for(torch, "fp64")
+    ids = ctx.register_batch(b)
+    F = b.Fbar.copy()
+    F[2, 0, 0] = np.nan
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(F, device="cuda"))
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    assert st[0] == 0 and st[1] == 4 and st[2] == 5
+
+
+def test_argument_errors(torch):
+    from paper_2312_12771_gb300.fe2 import Fe2Error
+    b = W.fiber_batch(2, 6)
+    ctx = ctx_for(torch, "mixed")
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    with pytest.raises(Fe2Error):
+        ctx.rve_solve([ids[0], ids[0]], F)           # duplicate id
+    with pytest.raises(Fe2Error):
+        ctx.rve_solve([12345], F[:1])                # unknown id
+    with pytest.raises(Fe2Error):
+        ctx.nullspace_reduce(ids)                    # no element data yet
+
+
+def test_budget_admission(torch):
+    """Registration is refused (nothing admitted) once the HBM budget would be
+    exceeded, and admitted again after a release frees room."""
+    from paper_2312_12771_gb300.fe2 import Fe2Error, FE2_ERR_BUDGET
+    ctx = ctx_for(torch, "mixed", hbm_budget_bytes=0)
+    per = ctx.rve_bytes(16)          # persistent state + one workspace slot
+    ctx.close()
+    ctx = ctx_for(torch, "mixed", hbm_budget_bytes=int(per * 3))
+    ids = ctx.register_batch(W.fiber_batch(3, 16))
+    with pytest.raises(Fe2Error) as ei:
+        ctx.register_batch(W.fiber_batch(10, 16))
+    assert ei.value.status == FE2_ERR_BUDGET
+    # the refused call admitted nothing: the three RVEs still solve
+    b = W.fiber_batch(3, 16)
+    sig, Cb, st, _ = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    ctx.release(ids)
+    ctx.register_batch(W.fiber_batch(2, 16))      # fits again after release
