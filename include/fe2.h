@@ -16,7 +16,7 @@
  *   dw        = -(x_r + X_M : dFbar)        (update below Eq. (solution2))
  *
  * Conventions (all calls):
- *  - RVE = unit cell [0,1]^d, N^d equal elements (Q4 in 2D, Hex8 in 3D),
+ *  - RVE = unit cell [0,1]^d, N^d equal elements (Q4 in 2D, Hex8 in 3D), N >= 3,
  *    element e = ex + N*ey (+N*N*ez); full 2^d Gauss quadrature.
  *  - Second-order tensors are row-major d x d (F_iJ, J fastest); tangents
  *    are d^2 x d^2 with Cbar[iJ][kL] = d sigma_iJ / d Fbar_kL.
@@ -85,7 +85,7 @@ size_t fe2_rve_bytes(const fe2_ctx* ctx, int N);
 
 /*
  * Register nrve RVEs (setup step, Section 5.2: periodic nodal coupling and a
- * pinned corner).  N[nrve] [host] mesh sizes (>= 2, may differ per RVE);
+ * pinned corner).  N[nrve] [host] mesh sizes (>= 3, may differ per RVE);
  * phase [host] uint8 per element, RVEs concatenated; mat [host]
  * double[nrve][nphase][4]; rve_ids_out[nrve] [host] receives the ids.
  * The fluctuation w~ of each RVE starts at zero.  Returns FE2_ERR_BUDGET,

@@ -68,6 +68,7 @@ struct fe2_ctx {
     unsigned long long tick = 0;
     long long launches = 0;
     std::map<int, int> kd_cache;
+    std::map<int, int*> nbr_tabs;   // N -> device table [N^d][3^d]
     // per-kernel event timing
     bool prof = false;
     struct Pending {
@@ -128,10 +129,42 @@ static int compute_kd(fe2_ctx* ctx, int N, int d) {
                 }
         }
     }
-    const int nm = d * (nn - 1);
-    kd = std::min(kd, nm - 1);
+    // the factorisation window needs kd >= NB (a panel must lie inside the band
+    // storage); for small meshes the extra band rows are structural zeros
+    kd = std::max(kd, NB);
     ctx->kd_cache[N * 4 + d] = kd;
     return kd;
+}
+
+static const int* nbr_table(fe2_ctx* ctx, int N, int d) {
+    auto it = ctx->nbr_tabs.find(N * 4 + d);
+    if (it != ctx->nbr_tabs.end()) return it->second;
+    const int nn = nodes_of(N, d), ns = d == 2 ? 9 : 27;
+    std::vector<int> t((size_t)nn * ns);
+    for (int q = 0; q < nn; ++q) {
+        int c[3] = {0, 0, 0};
+        int qq = q;
+        for (int k = 0; k < d; ++k) {
+            c[k] = unfold_pos(qq % N, N);
+            qq /= N;
+        }
+        for (int off = 0; off < ns; ++off) {
+            int o = off, qn = 0, mul = 1;
+            for (int k = 0; k < d; ++k) {
+                const int dk = o % 3 - 1;
+                o /= 3;
+                const int v = (c[k] + dk + N) % N;
+                qn += fold_pos(v, N) * mul;
+                mul *= N;
+            }
+            t[(size_t)q * ns + off] = qn;
+        }
+    }
+    int* dptr = nullptr;
+    if (cudaMalloc(&dptr, sizeof(int) * t.size()) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(dptr, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    ctx->nbr_tabs[N * 4 + d] = dptr;
+    return dptr;
 }
 
 static size_t persistent_bytes_of(int N, int d, int nphase) {
@@ -148,7 +181,7 @@ static size_t persistent_bytes_of(int N, int d, int nphase) {
 }
 
 struct WsLayout {
-    size_t offY, offR, stride;
+    size_t offY, offR, offD, stride;
 };
 
 static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64) {
@@ -159,6 +192,8 @@ static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64
     o += align256((size_t)maxnr * maxnmp * es);
     l.offR = o;
     o += align256((size_t)maxnr * maxnm * 8);
+    l.offD = o;
+    o += align256((size_t)maxnmp * es);
     l.stride = o;
     return l;
 }
@@ -359,7 +394,7 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
     fe2_status st = ensure_ws(ctx, l.stride * (size_t)cap, limit);
     if (st != FE2_OK) return st;
     if (reset_status) CK(cudaMemsetAsync(status, 0, sizeof(int) * n, ctx->stream));
-    Workspace ws{ctx->ws, l.stride, l.offY, l.offR};
+    Workspace ws{ctx->ws, l.stride, l.offY, l.offR, l.offD};
     const int dd = ctx->cfg.dim * ctx->cfg.dim;
     for (int c0 = 0; c0 < n; c0 += cap) {
         const int m = std::min(cap, n - c0);
@@ -368,15 +403,15 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
         if (fp64) {
             TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp64",
-                  launch_backward<double>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+                  launch_backward<double>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
         } else {
             TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp32",
-                  launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+                  launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
             for (int it = 0; it < ctx->cfg.max_refine; ++it) {
                 TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
                 TIMED("band_refine_fp32",
-                      launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp, ctx->stream));
+                      launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
             }
             TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
         }
@@ -436,6 +471,7 @@ void fe2_destroy(fe2_ctx* ctx) {
     cudaFree(M.R);
     cudaFree(M.adj);
     cudaFree(M.adj_ptr);
+    for (auto& t : ctx->nbr_tabs) cudaFree(t.second);
     drain_timing(ctx);
     for (auto e : ctx->evpool) cudaEventDestroy(e);
     delete ctx;
@@ -496,10 +532,10 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
     std::vector<size_t> offs(nrve);
     size_t phase_off = 0;
     for (int k = 0; k < nrve; ++k) {
-        if (N[k] < 2 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range", N[k]);
+        if (N[k] < 3 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range (N >= 3)", N[k]);
         const int kd = compute_kd(ctx, N[k], d);
         const int nr = d * d + 1;
-        if (kd + nr > FACT_THREADS) return fail(ctx, FE2_ERR_ARG, "N=%d: band too wide for one CTA", N[k]);
+        if (kd + nr + 32 > FACT_THREADS) return fail(ctx, FE2_ERR_ARG, "N=%d: band too wide for one CTA", N[k]);
         if ((int)factor_smem_bytes(kd, nr, fp64) > ctx->max_smem)
             return fail(ctx, FE2_ERR_ARG, "N=%d: band window (%zu B) exceeds shared memory (%d B) on the %s path",
                         N[k], factor_smem_bytes(kd, nr, fp64), ctx->max_smem, fp64 ? "FP64" : "mixed");
@@ -608,6 +644,8 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         r.KMM = (double*)(base + o);
         r.Pint = r.KMM + d * d * d * d;
         r.elem = nullptr;
+        r.nbr = nbr_table(ctx, N[k], d);
+        if (!r.nbr) return fail(ctx, FE2_ERR_CUDA, "neighbour table allocation failed");
         r.zero_w = 1;
         phase_off += nn;
         const int id = ids[k];

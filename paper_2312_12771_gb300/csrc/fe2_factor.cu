@@ -5,408 +5,555 @@
 // mixed-precision refinement.
 //
 // One CTA factors one RVE.  K_mm is banded in the folded periodic ordering
-// (half bandwidth kd).  The active part of the band -- kd + NB columns, each
-// stored as rows c..c+kd -- lives in a ring buffer in shared memory and
-// slides down the matrix NB columns at a time; columns enter the ring
-// straight from the FP64 node-row stencil and leave it once as finished
-// columns of L.  Per panel of NB columns:
-//   A  one warp factors the NB x NB diagonal block,
-//   B  one thread per row solves L21 = A21 L11^-T; the d^2+1 right-hand-side
-//      rows are extra rows of the same solve (forward elimination y = L^-1 b),
-//   C  rank-NB update of the trailing (kd x kd) window and of the RHS rows
-//      below the panel, register-tiled 4x4; finished columns are streamed out,
-//   D  the freed ring slots receive the next NB columns.
+// (half bandwidth kd).  The active part of the band -- S = kd + NB columns,
+// each stored as rows c..c+kd -- lives in a ring buffer in shared memory and
+// slides down the matrix NB columns at a time; columns enter the ring from
+// the FP64 node-row stencil and leave it once, as finished columns of L.
+// Per panel of NB columns:
+//   A  warp 0 factors the NB x NB diagonal block;
+//   B  one thread per row solves L21 = A21 L11^-T (right-looking, in
+//      registers); the d^2+1 right-hand-side rows are extra rows of the same
+//      solve (forward elimination y = L^-1 b).  Idle threads prefetch the
+//      stencil rows of the next NB columns into shared memory (coalesced);
+//   C  rank-NB update of the trailing kd x kd window and of the RHS rows,
+//      8x8 register tiles; the finished panel is streamed to HBM;
+//   D  the freed ring slots are cleared and receive the next NB columns.
+// Ring slots are addressed with a running base and a compare-subtract wrap.
 #include "fe2_internal.cuh"
+#include "fe2_ptx.cuh"
 
 namespace fe2 {
 
 namespace {
 
+constexpr int STG_NODES = NB / 2 + 1;   // nodes spanned by NB consecutive 2D DOFs
+constexpr int STG_COMPS = 36;           // 9 neighbour blocks x 2 x 2 per node row
+
+__device__ __forceinline__ int wrapS(int x, int S) { return x >= S ? x - S : x; }
+
 template <typename T>
 struct FactLayout {
-    int kd, S, LDW, KR, KDP, nr;
-    size_t offPn, offBw, offDinv, offTiles, total;
-    int ntiles;
+    int kd, S, LDW, KR, KP, nr, nblk;
+    size_t offPn, offBw, offDinv, offBlk, offStg, offBstg, total;
     __host__ __device__ void init(int kd_, int nr_) {
         kd = kd_;
         nr = nr_;
         S = kd + NB;
         LDW = kd + 1;
         KR = kd + nr;
-        KDP = (KR + 3) & ~3;
-        const int TR = KDP / 4, TC = (kd + 3) / 4;
-        ntiles = 0;
-        for (int tk = 0; tk < TC; ++tk) ntiles += TR - tk;
+        KP = (KR + 31) & ~31;
+        const int RB = KP / 32, CB = (kd + 31) / 32;
+        nblk = 0;
+        for (int K = 0; K < CB; ++K) nblk += RB - K;
         size_t o = (size_t)S * LDW * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offPn = o;
-        o += (size_t)NB * KDP * sizeof(T);
+        o += (size_t)NB * KP * sizeof(T);
         offBw = o;
         o += (size_t)nr * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offDinv = o;
         o += NB * sizeof(T);
         o = (o + 15) & ~(size_t)15;
-        offTiles = o;
-        o += (size_t)ntiles * 4;
+        offBlk = o;
+        o += (size_t)nblk * 4;
+        o = (o + 15) & ~(size_t)15;
+        offStg = o;
+        o += (size_t)STG_COMPS * STG_NODES * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offBstg = o;
+        o += (size_t)nr * NB * sizeof(T);
         total = (o + 15) & ~(size_t)15;
     }
 };
 
-// Column c (< nm) of K_mm, rows >= c, scattered from node row (q, c % 2) of the stencil.
 template <typename T>
-__device__ void load_column2(T* __restrict__ Wc, int c, const RveDev& r) {
-    const int N = r.N, nn = r.nn;
-    const int q = c / 2 + 1, cc = c & 1;
-    const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
-    for (int off = 0; off < 9; ++off) {
-        const int dx = off % 3 - 1, dy = off / 3 - 1;
-        const int qn = fold_pos((i + dx + N) % N, N) + N * fold_pos((j + dy + N) % N, N);
-        if (qn == 0) continue;
-        for (int c2 = 0; c2 < 2; ++c2) {
-            const int row = 2 * (qn - 1) + c2;
-            if (row >= c) Wc[row - c] += (T)r.stencil[(size_t)((off * 2 + cc) * 2 + c2) * nn + q];
-        }
+struct Vec4;
+template <>
+struct Vec4<float> {
+    __device__ __forceinline__ static void load(const float* p, float* o) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+    }
+};
+template <>
+struct Vec4<double> {
+    __device__ __forceinline__ static void load(const double* p, double* o) {
+        const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = v0.x, o[1] = v0.y, o[2] = v1.x, o[3] = v1.y;
+    }
+};
+
+__device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Stage the stencil rows (36 per node) and RHS rows behind columns [c0, c0+NB)
+// into shared memory with coalesced loads by threads t0, t0+nt, ...
+template <typename T>
+__device__ __forceinline__ void prefetch_columns(T* __restrict__ Stg, T* __restrict__ Bstg,
+                                                 const double* __restrict__ sten, const double* __restrict__ rhs,
+                                                 int c0, int nm, int nn, int nr, int t0, int nt) {
+    if (c0 >= nm) return;
+    const int qa = c0 / 2 + 1;
+    const int nq = min(STG_NODES, nn - qa);
+    for (int k = t0; k < STG_COMPS * STG_NODES; k += nt) {
+        const int comp = k / STG_NODES, t = k - comp * STG_NODES;
+        Stg[k] = (t < nq) ? (T)sten[(size_t)comp * nn + qa + t] : T(0);
+    }
+    for (int k = t0; k < nr * NB; k += nt) {
+        const int rr = k / NB, c = k - rr * NB;
+        Bstg[k] = (c0 + c < nm) ? (T)rhs[(size_t)rr * nm + c0 + c] : T(0);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void fill_slot(T* __restrict__ W, T* __restrict__ Bw, const FactLayout<T>& lay,
-                                          int c, const RveDev& r) {
-    const int slot = c % lay.S;
-    T* Wc = W + (size_t)slot * lay.LDW;
-    for (int k = 0; k <= lay.kd; ++k) Wc[k] = T(0);
-    if (c < r.nm)
-        load_column2<T>(Wc, c, r);
-    else if (c < r.nm_pad)
-        Wc[0] = T(1);  // padding columns: identity
-    for (int rr = 0; rr < lay.nr; ++rr)
-        Bw[rr * lay.S + slot] = (c < r.nm) ? (T)r.rhs[(size_t)rr * r.nm + c] : T(0);
-}
-
-template <typename T>
-__device__ __forceinline__ T rsqrt_t(T x);
-template <>
-__device__ __forceinline__ float rsqrt_t<float>(float x) { return 1.0f / sqrtf(x); }
-template <>
-__device__ __forceinline__ double rsqrt_t<double>(double x) { return 1.0 / sqrt(x); }
-
-template <typename T>
-__global__ void __launch_bounds__(FACT_THREADS) k_band_factor(const RveDev* __restrict__ tab,
-                                                              const int* __restrict__ ids, Workspace ws,
-                                                              int* __restrict__ status) {
+__global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_factor(const RveDev* __restrict__ tab,
+                                                                                      const int* __restrict__ ids,
+                                                                                      Workspace ws,
+                                                                                      int* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const RveDev r = tab[ids[blockIdx.x]];
     FactLayout<T> lay;
     lay.init(r.kd, r.nr);
-    const int kd = lay.kd, S = lay.S, LDW = lay.LDW, KR = lay.KR, KDP = lay.KDP, nr = lay.nr;
-    const int nmp = r.nm_pad;
+    const int kd = lay.kd, S = lay.S, LDW = lay.LDW, KR = lay.KR, KP = lay.KP, nr = lay.nr;
+    const int nmp = r.nm_pad, nm = r.nm, nn = r.nn;
     T* W = (T*)smem;
     T* Pn = (T*)(smem + lay.offPn);
     T* Bw = (T*)(smem + lay.offBw);
     T* dinv = (T*)(smem + lay.offDinv);
-    unsigned* tiles = (unsigned*)(smem + lay.offTiles);
+    unsigned* blk = (unsigned*)(smem + lay.offBlk);
+    T* Stg = (T*)(smem + lay.offStg);
+    T* Bstg = (T*)(smem + lay.offBstg);
     __shared__ int s_bad;
     T* Lg = (T*)(ws.base + blockIdx.x * ws.stride);
     T* Yg = (T*)(ws.base + blockIdx.x * ws.stride + ws.offY);
+    T* Dg = (T*)(ws.base + blockIdx.x * ws.stride + ws.offD);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const double* __restrict__ sten = r.stencil;
+    const int* __restrict__ nbr = r.nbr;
 
-    // ---- init: tile list, zero staging, first window
+    // ---- init: block list, zero buffers, first kd columns straight from HBM
     if (tid == 0) {
         s_bad = 0;
-        const int TR = KDP / 4, TC = (kd + 3) / 4;
+        const int RB = KP / 32, CB = (kd + 31) / 32;
         int x = 0;
-        for (int tk = 0; tk < TC; ++tk)
-            for (int ti = tk; ti < TR; ++ti) tiles[x++] = (unsigned)ti | ((unsigned)tk << 16);
+        for (int K = 0; K < CB; ++K)
+            for (int I = K; I < RB; ++I) blk[x++] = (unsigned)I | ((unsigned)K << 16);
     }
-    for (int k = tid; k < NB * KDP; k += blockDim.x) Pn[k] = T(0);
-    const int ncol0 = min(S, nmp);
-    for (int c = tid; c < S; c += blockDim.x) {
-        if (c < ncol0) {
-            fill_slot<T>(W, Bw, lay, c, r);
+    for (int k = tid; k < NB * KP; k += blockDim.x) Pn[k] = T(0);
+    for (int k = tid; k < S * LDW; k += blockDim.x) W[k] = T(0);
+    for (int k = tid; k < nr * S; k += blockDim.x) {
+        const int rr = k / S, c = k - rr * S;
+        Bw[k] = (c < nm && c < kd) ? (T)r.rhs[(size_t)rr * nm + c] : T(0);
+    }
+    prefetch_columns<T>(Stg, Bstg, sten, r.rhs, kd, nm, nn, nr, tid, blockDim.x);
+    __syncthreads();
+    for (int c = tid; c < min(kd, nmp); c += blockDim.x) {
+        T* Wc = W + (size_t)c * LDW;
+        if (c < nm) {
+            const int q = c / 2 + 1, cc = c & 1;
+            for (int off = 0; off < 9; ++off) {
+                const int qn = nbr[q * 9 + off];
+                if (qn == 0) continue;
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int row = 2 * (qn - 1) + c2;
+                    if (row >= c) Wc[row - c] = (T)sten[(size_t)((off * 2 + cc) * 2 + c2) * nn + q];
+                }
+            }
         } else {
-            T* Wc = W + (size_t)c * LDW;
-            for (int k = 0; k <= kd; ++k) Wc[k] = T(0);
-            for (int rr = 0; rr < nr; ++rr) Bw[rr * S + c] = T(0);
+            Wc[0] = T(1);  // padding columns: identity
         }
     }
     __syncthreads();
 
+    int base = 0;  // ring slot of column j0
     for (int j0 = 0; j0 < nmp; j0 += NB) {
-        // ---- A: diagonal block, one warp
+        // ---- 1: warp 0 factors the diagonal block in registers (lane = row);
+        //         the other warps bring columns [j0+kd, j0+kd+NB) into the ring
         if (warp == 0) {
+            T a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] : T(0);
+#pragma unroll
             for (int k = 0; k < NB; ++k) {
-                T* Wk = W + (size_t)((j0 + k) % S) * LDW;
+                T piv = __shfl_sync(0xffffffffu, a[k], k);
+                const bool badk = !(piv > T(0));
+                if (badk) piv = T(1);
+                const T dk = T(1) / sqrt(piv);
+                if (lane == k) a[k] = piv * dk;
+                else if (lane > k) a[k] *= dk;
                 if (lane == 0) {
-                    T piv = Wk[0];
-                    if (!(piv > T(0))) {  // non-positive or NaN pivot
-                        s_bad = 1;
-                        piv = T(1);
+                    dinv[k] = dk;
+                    if (badk) s_bad = 1;
+                }
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    if (c > k) {
+                        const T lck = __shfl_sync(0xffffffffu, a[k], c);
+                        if (lane >= c) a[c] -= a[k] * lck;
                     }
-                    const T di = rsqrt_t<T>(piv);
-                    Wk[0] = piv * di;
-                    dinv[k] = di;
                 }
-                __syncwarp();
-                const T di = dinv[k];
-                if (lane > k && lane - k <= kd) Wk[lane - k] *= di;
-                __syncwarp();
-                if (lane > k && lane - k <= kd) {
-                    const T lck = Wk[lane - k];
-                    T* Wl = W + (size_t)((j0 + lane) % S) * LDW;
-                    for (int rr = lane; rr < NB && rr - k <= kd; ++rr) Wl[rr - lane] -= Wk[rr - k] * lck;
+            }
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c <= lane && lane - c <= kd) W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] = a[c];
+            Dg[j0 + lane] = dinv[lane];
+        } else {
+            const int t0 = tid - 32, nt = blockDim.x - 32;
+            const int c0 = j0 + kd;  // first entering column; its slot is base + kd (mod S)
+            for (int c = warp - 1; c < NB; c += nwarps - 1) {
+                T* Wc = W + (size_t)wrapS(base + kd + c, S) * LDW;
+                for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
+            }
+            bar_sync_named(1, nt);
+            const int qa = c0 / 2 + 1;
+            for (int p = t0; p < NB * 9; p += nt) {
+                const int x = p / 9, off = p - 9 * x, cn = c0 + x;
+                T* Wc = W + (size_t)wrapS(base + kd + x, S) * LDW;
+                if (cn < nm) {
+                    const int q = cn / 2 + 1, cc = cn & 1;
+                    const int qn = nbr[q * 9 + off];
+                    if (qn != 0) {
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int row = 2 * (qn - 1) + c2;
+                            if (row >= cn) Wc[row - cn] = Stg[((off * 2 + cc) * 2 + c2) * STG_NODES + (q - qa)];
+                        }
+                    }
+                } else if (cn < nmp && off == 0) {
+                    Wc[0] = T(1);
                 }
-                __syncwarp();
+            }
+            for (int p = t0; p < nr * NB; p += nt) {
+                const int rr = p / NB, x = p - rr * NB;
+                Bw[rr * S + wrapS(base + kd + x, S)] = (c0 + x < nm) ? Bstg[p] : T(0);
             }
         }
         __syncthreads();
-        // ---- B: L21 = A21 L11^-T (rows below the panel) and y = L11^-1 b (RHS rows)
+        // ---- 2: panel rows (L21 and y) / prefetch of the next entering columns
         if (tid < KR) {
-            T row[NB];
+            T v[NB];
+            if (tid < kd) {
 #pragma unroll
-            for (int c = 0; c < NB; ++c) {
-                T v;
-                if (tid < kd) {
+                for (int c = 0; c < NB; ++c) {
                     const int off = NB + tid - c;
-                    v = (off <= kd) ? W[(size_t)((j0 + c) % S) * LDW + off] : T(0);
-                } else {
-                    v = Bw[(tid - kd) * S + (j0 + c) % S];
+                    v[c] = (off <= kd) ? W[(size_t)wrapS(base + c, S) * LDW + off] : T(0);
                 }
+            } else {
+                const T* Bp = Bw + (tid - kd) * S;
 #pragma unroll
-                for (int c2 = 0; c2 < c; ++c2) {
-                    if (c - c2 <= kd) v -= row[c2] * W[(size_t)((j0 + c2) % S) * LDW + (c - c2)];
-                }
-                row[c] = v * dinv[c];
+                for (int c = 0; c < NB; ++c) v[c] = Bp[wrapS(base + c, S)];
             }
 #pragma unroll
             for (int c = 0; c < NB; ++c) {
-                Pn[c * KDP + tid] = row[c];
-                if (tid < kd) {
-                    const int off = NB + tid - c;
-                    if (off <= kd) W[(size_t)((j0 + c) % S) * LDW + off] = row[c];
-                } else {
-                    Bw[(tid - kd) * S + (j0 + c) % S] = row[c];
-                }
+                const T* Lc = W + (size_t)wrapS(base + c, S) * LDW;
+                v[c] *= dinv[c];
+#pragma unroll
+                for (int c2 = 0; c2 < NB; ++c2)
+                    if (c2 > c && c2 - c <= kd) v[c2] -= v[c] * Lc[c2 - c];
             }
+#pragma unroll
+            for (int c = 0; c < NB; ++c) Pn[c * KP + tid] = v[c];
+            if (tid < kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = NB + tid - c;
+                    if (off <= kd) W[(size_t)wrapS(base + c, S) * LDW + off] = v[c];
+                }
+            } else {
+                T* Bp = Bw + (tid - kd) * S;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) Bp[wrapS(base + c, S)] = v[c];
+            }
+        } else {
+            prefetch_columns<T>(Stg, Bstg, sten, r.rhs, j0 + S, nm, nn, nr, tid - KR, blockDim.x - KR);
         }
         __syncthreads();
-        // ---- C: trailing update (window + RHS rows) and stream out the panel
-        for (int x = tid; x < lay.ntiles; x += blockDim.x) {
-            const unsigned tv = tiles[x];
-            const int ti = tv & 0xffff, tk = tv >> 16;
-            T acc[4][4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-#pragma unroll 4
-            for (int c = 0; c < NB; ++c) {
-                const T* pc = Pn + c * KDP;
-                T a[4], b[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    a[u] = pc[4 * ti + u];
-                    b[u] = pc[4 * tk + u];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int t1 = 4 * ti + u;
-                if (t1 >= KR) continue;
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    const int t2 = 4 * tk + v;
-                    if (t2 >= kd || t1 < t2) continue;
-                    const int col = j0 + NB + t2;
-                    if (t1 < kd)
-                        W[(size_t)(col % S) * LDW + (t1 - t2)] -= acc[u][v];
-                    else
-                        Bw[(t1 - kd) * S + col % S] -= acc[u][v];
-                }
-            }
-        }
+        // ---- 3: rank-NB update of the window and RHS rows, 32x32 blocks per warp
         {
+            const int rg = lane >> 3, cg = lane & 7;
+            for (int b = warp; b < lay.nblk; b += nwarps) {
+                const unsigned bv = blk[b];
+                const int I = bv & 0xffff, K = bv >> 16;
+                const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
+                T acc[8][4];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+                for (int c = 0; c < NB; ++c) {
+                    const T* pc = Pn + c * KP;
+                    T a[8], bb[4];
+                    Vec4<T>::load(pc + r0, a);
+                    Vec4<T>::load(pc + r0 + 4, a + 4);
+                    Vec4<T>::load(pc + q0, bb);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
+                }
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int t2 = q0 + w;
+                    if (t2 >= kd) continue;
+                    const int slot = wrapS(base + NB + t2, S);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int t1 = r0 + u;
+                        if (t1 < t2 || t1 >= KR) continue;
+                        if (t1 < kd)
+                            W[(size_t)slot * LDW + (t1 - t2)] -= acc[u][w];
+                        else
+                            Bw[(t1 - kd) * S + slot] -= acc[u][w];
+                    }
+                }
+            }
             const int LDL = kd + 1;
-            for (int k = tid; k < NB * LDL; k += blockDim.x) {
-                const int c = k / LDL, off = k - c * LDL;
-                Lg[(size_t)(j0 + c) * LDL + off] = W[(size_t)((j0 + c) % S) * LDW + off];
+            for (int c = warp; c < NB; c += nwarps) {
+                const T* Wc = W + (size_t)wrapS(base + c, S) * LDW;
+                T* dst = Lg + (size_t)(j0 + c) * LDL;
+                for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
             }
             for (int k = tid; k < nr * NB; k += blockDim.x) {
                 const int rr = k / NB, c = k - rr * NB;
-                Yg[(size_t)rr * nmp + j0 + c] = Bw[rr * S + (j0 + c) % S];
+                Yg[(size_t)rr * nmp + j0 + c] = Bw[rr * S + wrapS(base + c, S)];
             }
         }
         __syncthreads();
-        // ---- D: next NB columns into the freed slots
-        if (tid < NB) {
-            const int cn = j0 + S + tid;
-            const int slot = (j0 + tid) % S;
-            T* Wc = W + (size_t)slot * LDW;
-            if (cn < nmp) {
-                fill_slot<T>(W, Bw, lay, cn, r);
-            } else {
-                for (int k = 0; k <= kd; ++k) Wc[k] = T(0);
-                for (int rr = 0; rr < nr; ++rr) Bw[rr * S + slot] = T(0);
-            }
-        }
-        __syncthreads();
+        base = wrapS(base + NB, S);
     }
     if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
 }
 
 // ------------------------------------------------------------------ solves
+// L is read block by block (NB columns = NB*(kd+1) contiguous elements) with
+// double-buffered 1D TMA bulk copies.
 template <typename T>
 struct SolveLayout {
     int kd, S, LDL, nr, nmp;
-    size_t offX, offY, total;
+    size_t blk, offL1, offX, offY, offBar, total;
     __host__ __device__ void init(int kd_, int nr_, int nmp_, bool ysm) {
         kd = kd_;
         nr = nr_;
         nmp = nmp_;
         S = kd + NB;
         LDL = kd + 1;
-        size_t o = (size_t)NB * LDL * sizeof(T);  // L block
+        blk = ((size_t)NB * LDL * sizeof(T) + NB * sizeof(T) + 127) & ~(size_t)127;
+        offL1 = blk;
+        size_t o = 2 * blk;
+        offX = o;                                   // x ring [nr][2S] (mirrored) or rhs ring [nr][S]
+        o += (size_t)nr * 2 * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
-        offX = o;                                 // ring [nr][S] (x or rhs)
-        o += (size_t)nr * S * sizeof(T);
-        o = (o + 15) & ~(size_t)15;
-        offY = o;                                 // full y [nr][nmp] (refinement solve only)
+        offY = o;                                   // full y [nr][nmp] (refinement solve only)
         if (ysm) o += (size_t)nr * nmp * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offBar = o;
+        o += 16;
         total = (o + 15) & ~(size_t)15;
     }
 };
 
+// Double-buffered stream of L blocks.  issue(k, j0) loads block j0 into buffer
+// k & 1; wait(k) waits for it (all threads; bounded) and returns false on timeout.
 template <typename T>
-__device__ __forceinline__ void load_block(T* __restrict__ Lb, const T* __restrict__ Lg, int j0, int LDL) {
-    // NB columns are contiguous: NB*LDL elements starting at j0*LDL
-    const T* src = Lg + (size_t)j0 * LDL;
-    const int n = NB * LDL;
-    if ((sizeof(T) * n) % 16 == 0 && ((uintptr_t)src & 15) == 0) {
-        const float4* s4 = (const float4*)src;
-        float4* d4 = (float4*)Lb;
-        const int n4 = (int)(sizeof(T) * n / 16);
-        for (int k = threadIdx.x; k < n4; k += blockDim.x) d4[k] = s4[k];
-    } else {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) Lb[k] = src[k];
+struct LStream {
+    T* buf0;
+    uint64_t* bar;
+    const T* Lg;
+    const T* Dg;
+    uint32_t bytes;
+    int LDL, stride;   // stride: elements between the two buffers
+    // buffer k & 1 holds NB columns of L followed by their NB reciprocal diagonals
+    __device__ __forceinline__ const T* buf(int k) const { return buf0 + (k & 1) * stride; }
+    __device__ __forceinline__ const T* dinv(int k) const { return buf(k) + NB * LDL; }
+    __device__ __forceinline__ void init(unsigned char* smem, const SolveLayout<T>& lay, const T* L, const T* D) {
+        buf0 = (T*)smem;
+        stride = (int)(lay.offL1 / sizeof(T));
+        bar = (uint64_t*)(smem + lay.offBar);
+        Lg = L;
+        Dg = D;
+        LDL = lay.LDL;
+        bytes = (uint32_t)(NB * LDL * sizeof(T));
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init(bar + 1, 1);
+            mbar_fence_init();
+        }
+        __syncthreads();
     }
-}
+    __device__ __forceinline__ void issue(int k, int j0) {
+        if (threadIdx.x == 0) {
+            const uint32_t db = (uint32_t)(NB * sizeof(T));
+            T* dst = buf0 + (k & 1) * stride;
+            uint64_t* b = bar + (k & 1);
+            mbar_arrive_expect_tx(b, bytes + db);
+            bulk_g2s(dst, Lg + (size_t)j0 * LDL, bytes, b);
+            bulk_g2s(dst + NB * LDL, Dg + j0, db, b);
+        }
+    }
+    __device__ __forceinline__ bool wait(int k) { return mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1)); }
+};
 
-// Backward substitution x = L^-T y over the whole band, block by block from
-// the bottom.  y from global (Yg) or shared memory (ysm).  Result written to X
-// (accumulate = 0) or added to X (accumulate = 1) in FP64.
+// Backward substitution x = L^-T y over the band, blocks from the bottom.
+// `k0` is the running block counter of the stream (continues across passes).
+// Result written to X (accumulate = 0) or added to X (accumulate = 1) in FP64.
 template <typename T>
-__device__ void backward_pass(const RveDev& r, const SolveLayout<T>& lay, T* __restrict__ Lb,
-                              T* __restrict__ xw, const T* __restrict__ ysrc, const T* __restrict__ Lg,
-                              int accumulate) {
+__device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout<T>& lay, LStream<T>& ls, int& k0,
+                              T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to) {
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k = tid; k < nr * S; k += blockDim.x) xw[k] = T(0);
-    __syncthreads();
     __shared__ T tv[16][NB];
-    for (int j0 = nmp - NB; j0 >= 0; j0 -= NB) {
-        load_block<T>(Lb, Lg, j0, LDL);
+    for (int k = tid; k < nr * 2 * S; k += blockDim.x) xr[k] = T(0);
+    const int nblk = nmp / NB;
+    ls.issue(k0, nmp - NB);
+    __syncthreads();
+    int jb = (nmp - NB) % S;  // ring index of row j0
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int k = k0 + (nblk - 1 - b);
+        const int j0 = b * NB;
+        if (b > 0) ls.issue(k + 1, j0 - NB);
+        if (!ls.wait(k)) *s_to = 1;
         __syncthreads();
+        if (*s_to) return false;
+        const T* Lb = ls.buf(k);
+        const T* db = ls.dinv(k);
+        const int s0 = wrapS(jb + NB, S);
         // t = y_b - sum_{i >= j0+NB} L(i, c) x(i)
-        for (int k = tid; k < NB * nr; k += blockDim.x) {
-            const int c = k % NB, rr = k / NB;
-            T s = ysrc[(size_t)rr * nmp + j0 + c];
+        for (int t = tid; t < NB * nr; t += blockDim.x) {
+            const int c = t % NB, rr = t / NB;
             const T* Lc = Lb + c * LDL;
-            for (int off = NB - c; off <= kd; ++off) s -= Lc[off] * xw[rr * S + (j0 + c + off) % S];
-            tv[rr][c] = s;
+            const T* xp = xr + rr * 2 * S + s0 + c - NB;   // x(j0 + c + off) = xp[off]
+            T s0a = T(0), s1a = T(0), s2a = T(0), s3a = T(0);
+            int off = NB - c;
+            for (; off + 3 <= kd; off += 4) {
+                s0a += Lc[off] * xp[off];
+                s1a += Lc[off + 1] * xp[off + 1];
+                s2a += Lc[off + 2] * xp[off + 2];
+                s3a += Lc[off + 3] * xp[off + 3];
+            }
+            for (; off <= kd; ++off) s0a += Lc[off] * xp[off];
+            tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - ((s0a + s1a) + (s2a + s3a));
         }
         __syncthreads();
         // NB x NB triangle L11^T x = t: warp rr handles RHS rr, lane c owns x_c
         for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
             T acc = tv[rr][lane], xc = T(0);
             for (int c2 = NB - 1; c2 >= 0; --c2) {
-                T xv = (lane == c2) ? acc / Lb[c2 * LDL] : T(0);
+                T xv = (lane == c2) ? acc * db[c2] : T(0);
                 xv = __shfl_sync(0xffffffffu, xv, c2);
                 if (lane == c2) xc = xv;
                 if (lane < c2 && c2 - lane <= kd) acc -= Lb[lane * LDL + (c2 - lane)] * xv;
             }
+            const int idx = wrapS(jb + lane, S);
+            xr[rr * 2 * S + idx] = xc;
+            xr[rr * 2 * S + idx + S] = xc;
             const int row = j0 + lane;
-            xw[rr * S + row % S] = xc;
             if (row < nm) {
                 double* Xp = r.X + (size_t)rr * nm + row;
                 *Xp = accumulate ? (*Xp + (double)xc) : (double)xc;
             }
         }
         __syncthreads();
+        jb = jb - NB < 0 ? jb - NB + S : jb - NB;
     }
+    k0 += nblk;
+    return true;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __restrict__ tab,
                                                                 const int* __restrict__ ids, Workspace ws,
-                                                                int accumulate) {
-    extern __shared__ __align__(16) unsigned char smem[];
+                                                                int accumulate, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_to;
     const RveDev r = tab[ids[blockIdx.x]];
     SolveLayout<T> lay;
     lay.init(r.kd, r.nr, r.nm_pad, false);
-    T* Lb = (T*)smem;
-    T* xw = (T*)(smem + lay.offX);
-    const T* Lg = (const T*)(ws.base + blockIdx.x * ws.stride);
+    if (threadIdx.x == 0) s_to = 0;
+    LStream<T> ls;
+    ls.init(smem, lay, (const T*)(ws.base + blockIdx.x * ws.stride),
+            (const T*)(ws.base + blockIdx.x * ws.stride + ws.offD));
+    T* xr = (T*)(smem + lay.offX);
     const T* Yg = (const T*)(ws.base + blockIdx.x * ws.stride + ws.offY);
-    backward_pass<T>(r, lay, Lb, xw, Yg, Lg, accumulate);
+    int k0 = 0;
+    if (!backward_pass<T>(r, lay, ls, k0, xr, Yg, accumulate, &s_to) && threadIdx.x == 0)
+        status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
 // Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx.
 template <typename T>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDev* __restrict__ tab,
-                                                                     const int* __restrict__ ids,
-                                                                     Workspace ws) {
-    extern __shared__ __align__(16) unsigned char smem[];
+                                                                     const int* __restrict__ ids, Workspace ws,
+                                                                     int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_to;
     const RveDev r = tab[ids[blockIdx.x]];
     SolveLayout<T> lay;
     lay.init(r.kd, r.nr, r.nm_pad, true);
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
-    T* Lb = (T*)smem;
-    T* bw = (T*)(smem + lay.offX);
+    if (threadIdx.x == 0) s_to = 0;
+    LStream<T> ls;
+    ls.init(smem, lay, (const T*)(ws.base + blockIdx.x * ws.stride),
+            (const T*)(ws.base + blockIdx.x * ws.stride + ws.offD));
+    T* bw = (T*)(smem + lay.offX);   // ring [nr][S] of pending right-hand-side rows
     T* ys = (T*)(smem + lay.offY);
-    const T* Lg = (const T*)(ws.base + blockIdx.x * ws.stride);
     const double* Rg = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // forward: y = L^-1 R, ring of pending right-hand-side rows [j0, j0+S)
     for (int k = tid; k < nr * S; k += blockDim.x) {
         const int rr = k / S, row = k - rr * S;
         bw[k] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
     }
+    const int nblk = nmp / NB;
+    ls.issue(0, 0);
     __syncthreads();
-    for (int j0 = 0; j0 < nmp; j0 += NB) {
-        load_block<T>(Lb, Lg, j0, LDL);
+    int jb = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const int j0 = b * NB;
+        if (b + 1 < nblk) ls.issue(b + 1, j0 + NB);
+        if (!ls.wait(b)) s_to = 1;
         __syncthreads();
+        if (s_to) {
+            if (tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
+            return;
+        }
+        const T* Lb = ls.buf(b);
+        const T* db = ls.dinv(b);
         // triangle: warp rr, lane c owns b_c; column sweep
         for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
-            T b = bw[rr * S + (j0 + lane) % S], yc = T(0);
+            T bv = bw[rr * S + wrapS(jb + lane, S)], yc = T(0);
             for (int c = 0; c < NB; ++c) {
-                T yv = (lane == c) ? b / Lb[c * LDL] : T(0);
+                T yv = (lane == c) ? bv * db[c] : T(0);
                 yv = __shfl_sync(0xffffffffu, yv, c);
                 if (lane == c) yc = yv;
-                if (lane > c && lane - c <= kd) b -= Lb[c * LDL + (lane - c)] * yv;
+                if (lane > c && lane - c <= kd) bv -= Lb[c * LDL + (lane - c)] * yv;
             }
             ys[(size_t)rr * nmp + j0 + lane] = yc;
         }
         __syncthreads();
-        // rows below the block: b_i -= sum_c L(i, c) y_c ; then refill freed ring rows
+        // rows below the block: b_i -= sum_c L(i, c) y_c ; refill the freed ring rows
         for (int k = tid; k < nr * kd; k += blockDim.x) {
             const int rr = k / kd, t = k - rr * kd;
-            const int row = j0 + NB + t;
+            const T* yb = ys + (size_t)rr * nmp + j0;
             T s = T(0);
-            for (int c = max(0, NB + t - kd); c < NB; ++c) s += Lb[c * LDL + (NB + t - c)] * ys[(size_t)rr * nmp + j0 + c];
-            bw[rr * S + row % S] -= s;
+            for (int c = max(0, NB + t - kd); c < NB; ++c) s += Lb[c * LDL + (NB + t - c)] * yb[c];
+            int idx = jb + NB + t;
+            idx = idx >= 2 * S ? idx - 2 * S : (idx >= S ? idx - S : idx);
+            bw[rr * S + idx] -= s;
         }
         for (int k = tid; k < nr * NB; k += blockDim.x) {
             const int rr = k / NB, c = k - rr * NB;
             const int row = j0 + S + c;
-            bw[rr * S + (j0 + c) % S] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
+            bw[rr * S + wrapS(jb + c, S)] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
         }
         __syncthreads();
+        jb = wrapS(jb + NB, S);
     }
-    backward_pass<T>(r, lay, Lb, bw, ys, Lg, 1);
+    int k0 = nblk;
+    if (!backward_pass<T>(r, lay, ls, k0, bw, ys, 1, &s_to) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
 // FP64 residual R = [K_mM | r_m] - K_mm X from the node-row stencil.
@@ -415,27 +562,31 @@ __global__ void __launch_bounds__(256) k_residual2(const RveDev* __restrict__ ta
     const RveDev r = tab[ids[blockIdx.y]];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= r.nn || q == 0) return;
-    const int N = r.N, nn = r.nn, nm = r.nm, nr = r.nr;
+    const int nn = r.nn, nm = r.nm;
     double* R = (double*)(ws.base + blockIdx.y * ws.stride + ws.offR);
-    const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
     double acc[2][5];
+#pragma unroll
     for (int c = 0; c < 2; ++c)
+#pragma unroll
         for (int rr = 0; rr < 5; ++rr) acc[c][rr] = 0.0;
+#pragma unroll
     for (int off = 0; off < 9; ++off) {
-        const int dx = off % 3 - 1, dy = off / 3 - 1;
-        const int qn = fold_pos((i + dx + N) % N, N) + N * fold_pos((j + dy + N) % N, N);
+        const int qn = r.nbr[q * 9 + off];
         if (qn == 0) continue;
         const double k00 = r.stencil[(size_t)(off * 4 + 0) * nn + q], k01 = r.stencil[(size_t)(off * 4 + 1) * nn + q];
         const double k10 = r.stencil[(size_t)(off * 4 + 2) * nn + q], k11 = r.stencil[(size_t)(off * 4 + 3) * nn + q];
-        for (int rr = 0; rr < nr; ++rr) {
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr) {
             const double x0 = r.X[(size_t)rr * nm + 2 * (qn - 1)], x1 = r.X[(size_t)rr * nm + 2 * (qn - 1) + 1];
             acc[0][rr] += k00 * x0 + k01 * x1;
             acc[1][rr] += k10 * x0 + k11 * x1;
         }
     }
+#pragma unroll
     for (int c = 0; c < 2; ++c) {
         const int dof = 2 * (q - 1) + c;
-        for (int rr = 0; rr < nr; ++rr) R[(size_t)rr * nm + dof] = r.rhs[(size_t)rr * nm + dof] - acc[c][rr];
+#pragma unroll
+        for (int rr = 0; rr < 5; ++rr) R[(size_t)rr * nm + dof] = r.rhs[(size_t)rr * nm + dof] - acc[c][rr];
     }
 }
 
@@ -459,23 +610,23 @@ cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws
 
 template <typename T>
 cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate, int maxkd,
-                            int maxnr, int maxnm_pad, cudaStream_t s) {
+                            int maxnr, int maxnm_pad, int* status, cudaStream_t s) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, false);
     cudaError_t e = set_smem(k_band_backward<T>, lay.total);
     if (e != cudaSuccess) return e;
-    k_band_backward<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, accumulate);
+    k_band_backward<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, accumulate, status);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd, int maxnr,
-                                 int maxnm_pad, cudaStream_t s) {
+                                 int maxnm_pad, int* status, cudaStream_t s) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, true);
     cudaError_t e = set_smem(k_band_solve_correct<T>, lay.total);
     if (e != cudaSuccess) return e;
-    k_band_solve_correct<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws);
+    k_band_solve_correct<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status);
     return cudaGetLastError();
 }
 
@@ -498,13 +649,13 @@ size_t factor_smem_bytes(int kd, int nr, bool fp64) {
 
 template cudaError_t launch_factor<float>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
 template cudaError_t launch_factor<double>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
-template cudaError_t launch_backward<float>(const RveDev*, const int*, int, Workspace, int, int, int, int,
+template cudaError_t launch_backward<float>(const RveDev*, const int*, int, Workspace, int, int, int, int, int*,
                                             cudaStream_t);
-template cudaError_t launch_backward<double>(const RveDev*, const int*, int, Workspace, int, int, int, int,
+template cudaError_t launch_backward<double>(const RveDev*, const int*, int, Workspace, int, int, int, int, int*,
                                              cudaStream_t);
-template cudaError_t launch_solve_correct<float>(const RveDev*, const int*, int, Workspace, int, int, int,
+template cudaError_t launch_solve_correct<float>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
                                                  cudaStream_t);
-template cudaError_t launch_solve_correct<double>(const RveDev*, const int*, int, Workspace, int, int, int,
+template cudaError_t launch_solve_correct<double>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
                                                   cudaStream_t);
 
 }  // namespace fe2

@@ -27,6 +27,7 @@ struct RveDev {
     double* KMM;                // [d^4]
     double* Pint;               // [d^2]
     double* elem;               // split path: element workspace [ncomp][nn] (or null)
+    const int* nbr;             // [nn][3^d] folded index of each node's neighbours (shared per N)
     int zero_w;                 // 1 while w is known to be exactly zero
     int pad_;
 };
@@ -35,9 +36,10 @@ struct RveDev {
 //   L  at base + s*stride          (T[nm_pad][kd+1], lower band, column-major)
 //   Y  at base + s*stride + offY   (T[nr][nm_pad], forward-solve result)
 //   R  at base + s*stride + offR   (double[nr][nm], FP64 residuals)
+//   D  at base + s*stride + offD   (T[nm_pad], reciprocal diagonal of L)
 struct Workspace {
     char* base;
-    size_t stride, offY, offR;
+    size_t stride, offY, offR, offD;
 };
 
 __host__ __device__ inline int fold_pos(int i, int N) {
@@ -66,10 +68,10 @@ cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws
                           int maxkd, int maxnr, cudaStream_t s);
 template <typename T>
 cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate,
-                            int maxkd, int maxnr, int maxnm_pad, cudaStream_t s);
+                            int maxkd, int maxnr, int maxnm_pad, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd,
-                                 int maxnr, int maxnm_pad, cudaStream_t s);
+                                 int maxnr, int maxnm_pad, int* status, cudaStream_t s);
 cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
                             cudaStream_t s);
 cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected,
