@@ -142,30 +142,48 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
 fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double* dFbar);
 
 /*
- * Macro Q4 problem of Section 3, Eq. (linSys2) with the condensed tangent of
- * Eq. (solution2): K = sum_b eta_b B_b^T Cbar_b B_b and
- * R = sum_b eta_b B_b^T s_b over the macro Gauss points b = 4 e + q, where
- * s_b is sigma_eff (condensed right-hand side) or Pbar (R_macro).
- * Dirichlet DOFs are held fixed; the free block is solved by a band Cholesky
- * on the device.  fe2_macro_setup [host] inputs: nodes X[nnode][2], Q4
- * connectivity conn[nelem][4] (local node a = ax + 2 ay on the reference
- * square), Dirichlet flags fixed[nnode*2] (1 = prescribed).
+ * Macro Q4 problem of Section 3, Eq. (linSys2), solved with the condensed
+ * tangent of Section 4.2, Eq. (solution2):
+ *   K = sum_b eta_b B_b^T Cbar_b B_b,   R = sum_b eta_b B_b^T s_b,
+ * over the macro Gauss points b = 4 e + q (q = qx + 2 qy, 2x2 Gauss), with
+ * B_b dq = sum_A dq_A (x) grad N^A(X_b).  Dirichlet DOFs are held at their
+ * prescribed positions; the free block is factorised by a band Cholesky on the
+ * device.  The macro state (nodal positions q, starting at X) is owned by the
+ * context.
+ *
+ * fe2_macro_setup [host]: nodes X[nnode][2], connectivity conn[nelem][4]
+ * (local node a = ax + 2 ay on the reference square, counter-clockwise
+ * elements), fixed[2*nnode] (1 = prescribed DOF).  Returns FE2_ERR_ARG for an
+ * inverted element.
  */
 fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, const int* conn,
                            const uint8_t* fixed);
-/*
- * One macro solve: given sigma [device] double[nelem*4][4] and Cbar [device]
- * double[nelem*4][4][4] per macro Gauss point, solve K dq = -R on the free DOFs
- * and write dq [device] double[nnode*2] (zero on fixed DOFs),
- * dFbar [device] double[nelem*4][4] = B_b dq and rnorm [device] double[1]
- * = ||R_free||_2.
- */
-fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dq,
-                           double* dFbar, double* rnorm);
-/* Macro deformation gradients Fbar_b = sum_A q_A (x) grad N^A(X_b) for nodal
- * positions q [device] double[nnode][2] -> Fbar [device] double[nelem*4][2][2];
- * eta [device] double[nelem*4] receives the quadrature weights (may be NULL). */
-fe2_status fe2_macro_gradients(fe2_ctx* ctx, const double* q, double* Fbar, double* eta);
+/* Overwrite nodal positions from q_host [host] double[nnode][2]: every DOF, or
+ * only those with which[t] != 0 when `which` [host] is not NULL (e.g. the
+ * Dirichlet DOFs at the start of a load step).  Synchronises. */
+fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which);
+/* Copy the current nodal positions to q_host [host] double[nnode][2].  Synchronises. */
+fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host);
+/* Fbar_b = sum_A q_A (x) grad N^A(X_b) into Fbar [device] double[4 nelem][2][2];
+ * eta [device] double[4 nelem] receives the quadrature weights (may be NULL). */
+fe2_status fe2_macro_gradients(fe2_ctx* ctx, double* Fbar, double* eta);
+/* R_macro on the free DOFs for the stress s_b = stress [device]
+ * double[4 nelem][2][2] (Pbar for the equilibrium residual); rnorm [device]
+ * double[1] = ||R_free||_2. */
+fe2_status fe2_macro_residual(fe2_ctx* ctx, const double* stress, double* rnorm);
+/* One monolithic macro update: assemble K from Cbar [device] double[4 nelem][4][4]
+ * and R from sigma [device] (sigma_eff: condensed right-hand side), solve
+ * K dq = -R, update q += dq and write dFbar [device] double[4 nelem][2][2] = B_b dq,
+ * rnorm [device] double[1] = ||R_free||, status [device] int[1] (may be NULL):
+ * FE2_ERR_NOT_PD if the macro tangent had a non-positive pivot. */
+fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dFbar, double* rnorm,
+                           int* status);
+/* Volume-averaged stress Pbar = Pint / |Omega| (Section 2.2, Eq. (averageStress))
+ * of each RVE at its last assembly: Pbar [device] double[n][d*d]. */
+fe2_status fe2_rve_average_stress(fe2_ctx* ctx, int n, const int* rve_ids, double* Pbar);
+/* ||r_m||_2 of each RVE's reduced micro residual at its last assembly (the
+ * micro part of the Newton stop test, Section 4): rnorm [device] double[n]. */
+fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double* rnorm);
 
 /*
  * Test/diagnostic export of one RVE in the natural periodic numbering

@@ -63,6 +63,9 @@ struct fe2_ctx {
     std::vector<int> elem_ids;     // ids whose element data is in `elem`
     int* d_status_tmp = nullptr;
     size_t status_tmp_n = 0;
+    int* d_redo = nullptr;          // per-slot "refine again" flags of the mixed path
+    size_t redo_n = 0;
+    double* d_tol = nullptr;        // device copy of cfg.refine_tol
     // id-list cache
     std::vector<IdList> idcache;
     unsigned long long tick = 0;
@@ -79,19 +82,10 @@ struct fe2_ctx {
     std::vector<cudaEvent_t> evpool;
     std::map<std::string, std::pair<double, long long>> totals;
     // macro problem
-    struct Macro {
-        int nnode = 0, nelem = 0, nfree = 0, kd = 0, nfree_pad = 0;
-        double* X = nullptr;        // [nnode][2]
-        int* conn = nullptr;        // [nelem][4]
-        int* dof2free = nullptr;    // [2 nnode] -> free index or -1
-        int* free2dof = nullptr;    // [nfree]
-        double* grads = nullptr;    // [nelem*4][4][2]
-        double* eta = nullptr;      // [nelem*4]
-        double* K = nullptr;        // band [nfree_pad][kd+1]
-        double* R = nullptr;        // [nfree_pad]
-        int* adj = nullptr;         // CSR of node -> (elem, local) for assembly
-        int* adj_ptr = nullptr;
-    } macro;
+    bool macro_ready = false;
+    MacroDev macro{};
+    std::vector<void*> macro_bufs;  // device buffers owned by the macro problem
+    int* d_macro_status = nullptr;
 };
 
 static fe2_status fail(fe2_ctx* c, fe2_status s, const char* fmt, ...) {
@@ -400,24 +394,52 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
         const int m = std::min(cap, n - c0);
         const int* di = d_ids + c0;
         int* stp = status + c0;
+        double* sg = sigma + (size_t)c0 * dd;
+        double* cb = Cbar + (size_t)c0 * dd * dd;
+        double* er = err ? err + c0 : nullptr;
         if (fp64) {
             TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp64",
                   launch_backward<double>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
+            TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 0, sg, cb, stp, er, nullptr, nullptr, ctx->stream));
         } else {
+            // FP32 factor, one FP64 residual and the residual-corrected Schur complement;
+            // RVEs whose error estimate exceeds refine_tol get up to max_refine sweeps
+            // of FP64-residual refinement (the others skip the launches' work)
+            if ((size_t)cap > ctx->redo_n) {
+                CK(cudaStreamSynchronize(ctx->stream));
+                cudaFree(ctx->d_redo);
+                ctx->d_redo = nullptr;
+                CK(cudaMalloc(&ctx->d_redo, sizeof(int) * cap));
+                ctx->redo_n = cap;
+            }
+            int* redo = ctx->cfg.max_refine > 0 ? ctx->d_redo : nullptr;
             TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp32",
                   launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
+            TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, nullptr, ctx->stream));
+            TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->stream,
+                                        ctx->cfg.max_refine > 0 ? 0 : 3));
             for (int it = 0; it < ctx->cfg.max_refine; ++it) {
-                TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
-                TIMED("band_refine_fp32",
-                      launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
+                const bool last = it + 1 == ctx->cfg.max_refine;
+                TIMED("band_refine_fp32", launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp,
+                                                                      stp, ctx->d_redo, ctx->stream));
+                TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->d_redo, ctx->stream));
+                TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 1, sg, cb, stp, er, ctx->d_tol, ctx->d_redo,
+                                            ctx->stream, last ? 2 : 1));
             }
-            TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->stream));
         }
-        TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, fp64 ? 0 : 1, sigma + (size_t)c0 * dd,
-                                    Cbar + (size_t)c0 * dd * dd, stp, err ? err + c0 : nullptr, ctx->stream));
     }
+    return FE2_OK;
+}
+
+template <typename V>
+static fe2_status upload_vec(fe2_ctx* ctx, const std::vector<V>& h, V** out) {
+    V* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(V) * std::max<size_t>(h.size(), 1)));
+    ctx->macro_bufs.push_back(d);
+    if (!h.empty()) CK(cudaMemcpy(d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+    *out = d;
     return FE2_OK;
 }
 
@@ -435,10 +457,13 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     if (cfg->dim == 3) return FE2_ERR_ARG;  // Hex8 kernels are not built in this library version
     ctx = new fe2_ctx();
     ctx->cfg = *cfg;
+    if (!(ctx->cfg.refine_tol > 0.0)) ctx->cfg.refine_tol = 1e-10;
     ctx->stream = (cudaStream_t)cfg->cuda_stream;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tol, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tol, &ctx->cfg.refine_tol, sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         delete ctx;
         return FE2_ERR_CUDA;
@@ -460,17 +485,10 @@ void fe2_destroy(fe2_ctx* ctx) {
     cudaFree(ctx->ws);
     cudaFree(ctx->elem);
     cudaFree(ctx->d_status_tmp);
-    auto& M = ctx->macro;
-    cudaFree(M.X);
-    cudaFree(M.conn);
-    cudaFree(M.dof2free);
-    cudaFree(M.free2dof);
-    cudaFree(M.grads);
-    cudaFree(M.eta);
-    cudaFree(M.K);
-    cudaFree(M.R);
-    cudaFree(M.adj);
-    cudaFree(M.adj_ptr);
+    cudaFree(ctx->d_redo);
+    cudaFree(ctx->d_tol);
+    for (void* p : ctx->macro_bufs) cudaFree(p);
+    cudaFree(ctx->d_macro_status);
     for (auto& t : ctx->nbr_tabs) cudaFree(t.second);
     drain_timing(ctx);
     for (auto e : ctx->evpool) cudaEventDestroy(e);
@@ -842,14 +860,163 @@ fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* out) {
     return FE2_OK;
 }
 
-fe2_status fe2_macro_setup(fe2_ctx* ctx, int, const double*, int, const int*, const uint8_t*) {
-    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, const int* conn,
+                           const uint8_t* fixed) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (ctx->cfg.dim != 2) return fail(ctx, FE2_ERR_ARG, "the macro problem is 2D (Q4)");
+    if (nnode <= 0 || nelem <= 0 || !X || !conn || !fixed) return fail(ctx, FE2_ERR_ARG, "bad macro mesh");
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (void* p : ctx->macro_bufs) cudaFree(p);
+    ctx->macro_bufs.clear();
+    ctx->macro_ready = false;
+    const int ngp = 4 * nelem;
+    std::vector<int> cn(conn, conn + 4 * nelem);
+    for (int v : cn)
+        if (v < 0 || v >= nnode) return fail(ctx, FE2_ERR_ARG, "connectivity references node %d", v);
+    // free DOFs in natural order; band width from the element couplings
+    std::vector<int> d2f(2 * nnode, -1);
+    int nfree = 0;
+    for (int t = 0; t < 2 * nnode; ++t)
+        if (!fixed[t]) d2f[t] = nfree++;
+    if (nfree == 0) return fail(ctx, FE2_ERR_ARG, "no free macro DOFs");
+    int kd = 0;
+    for (int e = 0; e < nelem; ++e)
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 4; ++b)
+                for (int c = 0; c < 2; ++c)
+                    for (int k = 0; k < 2; ++k) {
+                        const int i = d2f[2 * cn[4 * e + a] + c], j = d2f[2 * cn[4 * e + b] + k];
+                        if (i >= 0 && j >= 0) kd = std::max(kd, std::abs(i - j));
+                    }
+    // Gauss-point gradients and weights (2x2 Gauss on the isoparametric Q4)
+    std::vector<double> grads((size_t)ngp * 8), eta(ngp);
+    const double g = 0.57735026918962576451;
+    for (int e = 0; e < nelem; ++e)
+        for (int q = 0; q < 4; ++q) {
+            const double xi[2] = {(q & 1) ? g : -g, (q & 2) ? g : -g};
+            double dN[4][2], Jm[2][2] = {{0, 0}, {0, 0}};
+            for (int a = 0; a < 4; ++a) {
+                const double s0 = (a & 1) ? 1.0 : -1.0, s1 = (a & 2) ? 1.0 : -1.0;
+                dN[a][0] = 0.25 * s0 * (1.0 + s1 * xi[1]);
+                dN[a][1] = 0.25 * s1 * (1.0 + s0 * xi[0]);
+                for (int i = 0; i < 2; ++i)
+                    for (int k = 0; k < 2; ++k) Jm[i][k] += X[2 * cn[4 * e + a] + i] * dN[a][k];
+            }
+            const double det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+            if (!(det > 0.0)) return fail(ctx, FE2_ERR_ARG, "macro element %d is inverted", e);
+            const double inv[2][2] = {{Jm[1][1] / det, -Jm[0][1] / det}, {-Jm[1][0] / det, Jm[0][0] / det}};
+            const int b = 4 * e + q;
+            for (int a = 0; a < 4; ++a)
+                for (int J = 0; J < 2; ++J) grads[(size_t)(b * 4 + a) * 2 + J] = dN[a][0] * inv[0][J] + dN[a][1] * inv[1][J];
+            eta[b] = det;
+        }
+    std::vector<int> adj_ptr(nnode + 1, 0), adj;
+    for (int e = 0; e < nelem; ++e)
+        for (int a = 0; a < 4; ++a) ++adj_ptr[cn[4 * e + a] + 1];
+    for (int n = 0; n < nnode; ++n) adj_ptr[n + 1] += adj_ptr[n];
+    adj.assign(adj_ptr[nnode], 0);
+    std::vector<int> fill(adj_ptr.begin(), adj_ptr.end() - 1);
+    for (int e = 0; e < nelem; ++e)
+        for (int a = 0; a < 4; ++a) adj[fill[cn[4 * e + a]]++] = 4 * e + a;
+    MacroDev M{};
+    M.nnode = nnode;
+    M.nelem = nelem;
+    M.nfree = nfree;
+    M.kd = kd;
+    M.ngp = ngp;
+    fe2_status st;
+    int *dconn, *dd2f, *dadjp, *dadj;
+    double *dgr, *deta, *dq, *dK, *dR, *ddq;
+    if ((st = upload_vec(ctx, cn, &dconn)) || (st = upload_vec(ctx, d2f, &dd2f)) ||
+        (st = upload_vec(ctx, grads, &dgr)) || (st = upload_vec(ctx, eta, &deta)) ||
+        (st = upload_vec(ctx, adj_ptr, &dadjp)) || (st = upload_vec(ctx, adj, &dadj)))
+        return st;
+    std::vector<double> q0(X, X + 2 * nnode);
+    if ((st = upload_vec(ctx, q0, &dq))) return st;
+    if ((st = upload_vec(ctx, std::vector<double>((size_t)nfree * (kd + 1)), &dK))) return st;
+    if ((st = upload_vec(ctx, std::vector<double>(nfree), &dR))) return st;
+    if ((st = upload_vec(ctx, std::vector<double>(2 * nnode), &ddq))) return st;
+    M.conn = dconn;
+    M.dof2free = dd2f;
+    M.grads = dgr;
+    M.eta = deta;
+    M.adj_ptr = dadjp;
+    M.adj = dadj;
+    M.q = dq;
+    M.K = dK;
+    M.R = dR;
+    M.dq = ddq;
+    if (!ctx->d_macro_status) CK(cudaMalloc(&ctx->d_macro_status, sizeof(int)));
+    ctx->macro = M;
+    ctx->macro_ready = true;
+    return FE2_OK;
 }
-fe2_status fe2_macro_solve(fe2_ctx* ctx, const double*, const double*, double*, double*, double*) {
-    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+
+fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !q_host) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL positions");
+    const int nd = 2 * ctx->macro.nnode;
+    std::vector<double> q(nd);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(q.data(), ctx->macro.q, sizeof(double) * nd, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < nd; ++t)
+        if (!which || which[t]) q[t] = q_host[t];
+    CK(cudaMemcpy(ctx->macro.q, q.data(), sizeof(double) * nd, cudaMemcpyHostToDevice));
+    return FE2_OK;
 }
-fe2_status fe2_macro_gradients(fe2_ctx* ctx, const double*, double*, double*) {
-    return ctx ? fail(ctx, FE2_ERR_ARG, "macro problem not available in this build") : FE2_ERR_ARG;
+
+fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !q_host) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL output");
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(q_host, ctx->macro.q, sizeof(double) * 2 * ctx->macro.nnode, cudaMemcpyDeviceToHost));
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_gradients(fe2_ctx* ctx, double* Fbar, double* eta) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !Fbar) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL output");
+    TIMED("macro_gradients", launch_macro_gradients(ctx->macro, Fbar, eta, ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_residual(fe2_ctx* ctx, const double* stress, double* rnorm) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !stress || !rnorm) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    TIMED("macro_residual", launch_macro_residual(ctx->macro, stress, rnorm, ctx->stream));
+    ctx->launches += 1;
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dFbar, double* rnorm,
+                           int* status) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !sigma || !Cbar || !dFbar || !rnorm)
+        return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    TIMED("macro_solve", launch_macro_solve(ctx->macro, sigma, Cbar, dFbar, rnorm,
+                                            status ? status : ctx->d_macro_status, ctx->stream));
+    ctx->launches += 6;
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_average_stress(fe2_ctx* ctx, int n, const int* rve_ids, double* Pbar) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!Pbar) return fail(ctx, FE2_ERR_ARG, "Pbar is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    TIMED("rve_average_stress", launch_rve_avg_stress(ctx->d_tab, d_ids, n, Pbar, ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double* rnorm) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!rnorm) return fail(ctx, FE2_ERR_ARG, "rnorm is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    TIMED("rve_residual_norm", launch_rve_rnorm(ctx->d_tab, d_ids, n, rnorm, ctx->stream));
+    return FE2_OK;
 }
 
 }  // extern "C"

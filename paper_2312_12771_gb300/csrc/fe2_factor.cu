@@ -488,9 +488,11 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
 template <typename T>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDev* __restrict__ tab,
                                                                      const int* __restrict__ ids, Workspace ws,
-                                                                     int* __restrict__ status) {
+                                                                     int* __restrict__ status,
+                                                                     const int* __restrict__ active) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_to;
+    if (active && !active[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
     SolveLayout<T> lay;
     lay.init(r.kd, r.nr, r.nm_pad, true);
@@ -558,7 +560,8 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
 
 // FP64 residual R = [K_mM | r_m] - K_mm X from the node-row stencil.
 __global__ void __launch_bounds__(256) k_residual2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
-                                                   Workspace ws) {
+                                                   Workspace ws, const int* __restrict__ active) {
+    if (active && !active[blockIdx.y]) return;
     const RveDev r = tab[ids[blockIdx.y]];
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= r.nn || q == 0) return;
@@ -621,18 +624,19 @@ cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace 
 
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd, int maxnr,
-                                 int maxnm_pad, int* status, cudaStream_t s) {
+                                 int maxnm_pad, int* status, const int* active, cudaStream_t s) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, true);
     cudaError_t e = set_smem(k_band_solve_correct<T>, lay.total);
     if (e != cudaSuccess) return e;
-    k_band_solve_correct<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status);
+    k_band_solve_correct<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status, active);
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn, cudaStream_t s) {
+cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn, const int* active,
+                            cudaStream_t s) {
     dim3 grid((maxnn + 255) / 256, n);
-    k_residual2<<<grid, 256, 0, s>>>(tab, ids, ws);
+    k_residual2<<<grid, 256, 0, s>>>(tab, ids, ws, active);
     return cudaGetLastError();
 }
 
@@ -654,8 +658,8 @@ template cudaError_t launch_backward<float>(const RveDev*, const int*, int, Work
 template cudaError_t launch_backward<double>(const RveDev*, const int*, int, Workspace, int, int, int, int, int*,
                                              cudaStream_t);
 template cudaError_t launch_solve_correct<float>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
-                                                 cudaStream_t);
+                                                 const int*, cudaStream_t);
 template cudaError_t launch_solve_correct<double>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
-                                                  cudaStream_t);
+                                                  const int*, cudaStream_t);
 
 }  // namespace fe2

@@ -71,13 +71,38 @@ cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace 
                             int maxkd, int maxnr, int maxnm_pad, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd,
-                                 int maxnr, int maxnm_pad, int* status, cudaStream_t s);
+                                 int maxnr, int maxnm_pad, int* status, const int* active, cudaStream_t s);
+// `active` (may be null): only slots with active[slot] != 0 do work
 cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
-                            cudaStream_t s);
+                            const int* active, cudaStream_t s);
+// Schur complement; with `redo` != null, redo[i] = 1 marks RVEs whose error
+// estimate exceeds *tol (device scalar) for another refinement sweep.
 cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected,
-                         double* sigma, double* Cbar, int* status, double* err, cudaStream_t s);
+                         double* sigma, double* Cbar, int* status, double* err, const double* tol,
+                         int* redo, cudaStream_t s, int refine_sweep = 0);
 cudaError_t launch_macro_update(const RveDev* tab, const int* ids, int n, const double* dF,
                                 int maxnm, cudaStream_t s);
 cudaError_t launch_check_fbar(const double* Fbar, int n, int d, int* status, cudaStream_t s);
+
+// macro problem (fe2_macro.cu)
+struct MacroDev {
+    int nnode, nelem, nfree, kd, ngp;
+    const int* conn;      // [nelem][4]
+    const int* dof2free;  // [2 nnode] -> free index or -1
+    const double* grads;  // [ngp][4][2]
+    const double* eta;    // [ngp]
+    const int* adj_ptr;   // [nnode+1] CSR: node -> (elem * 4 + local) entries
+    const int* adj;       //
+    double* q;            // [nnode][2] current nodal positions
+    double* K;            // [nfree][kd+1] lower band, column-major
+    double* R;            // [nfree]
+    double* dq;           // [2 nnode]
+};
+cudaError_t launch_macro_gradients(const MacroDev& M, double* Fbar, double* eta, cudaStream_t s);
+cudaError_t launch_macro_residual(const MacroDev& M, const double* stress, double* rnorm, cudaStream_t s);
+cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
+                               double* rnorm, int* status, cudaStream_t s);
+cudaError_t launch_rve_avg_stress(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
+cudaError_t launch_rve_rnorm(const RveDev* tab, const int* ids, int n, double* out, cudaStream_t s);
 
 }  // namespace fe2

@@ -16,69 +16,92 @@ namespace fe2 {
 
 namespace {
 
-__global__ void __launch_bounds__(256) k_schur(const RveDev* __restrict__ tab, const int* __restrict__ ids,
-                                               Workspace ws, int corrected, double* __restrict__ sigma,
-                                               double* __restrict__ Cbar, int* __restrict__ status,
-                                               double* __restrict__ err) {
-    constexpr int MAXV = 2 * 9 * 10;  // 3D: 9 x 10 per product
-    __shared__ double red[256];
-    __shared__ double tot[MAXV];
-    const RveDev r = tab[ids[blockIdx.x]];
-    const int nm = r.nm, dd = r.d * r.d, nr = r.nr;
-    const double* R = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
-    const int nv = dd * nr;
-    // G1[a][b] = sum_m rhs[a][m] X[b][m];  G2[a][b] = sum_m X[a][m] R[b][m]
-    for (int base = 0; base < (corrected ? 2 : 1) * nv; base += 20) {
-        double acc[20];
-        for (int k = 0; k < 20; ++k) acc[k] = 0.0;
-        for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-            for (int k = 0; k < 20; ++k) {
-                const int v = base + k;
-                if (v >= (corrected ? 2 : 1) * nv) break;
-                const int which = v / nv, a = (v % nv) / nr, b = v % nr;
-                if (which == 0)
-                    acc[k] += r.rhs[(size_t)a * nm + m] * r.X[(size_t)b * nm + m];
-                else
-                    acc[k] += r.X[(size_t)a * nm + m] * R[(size_t)b * nm + m];
-            }
-        }
-        for (int k = 0; k < 20; ++k) {
-            red[threadIdx.x] = acc[k];
-            __syncthreads();
-            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-                if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0 && base + k < MAXV) tot[base + k] = red[0];
-            __syncthreads();
+// Deterministic CTA sum of NV partials per thread; thread 0 receives the totals.
+template <int NV>
+__device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[k * 33 + warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = 0.0;
+            for (int w = 0; w < nw; ++w) x += red[k * 33 + w];
+            v[k] = x;
         }
     }
+}
+
+// One CTA per RVE (2D: d^2 = 4, nr = 5).  G1 = rhs^T X (4 x 5), G2 = X_M^T R (4 x 5).
+__global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
+                                                Workspace ws, int corrected, double* __restrict__ sigma,
+                                                double* __restrict__ Cbar, int* __restrict__ status,
+                                                double* __restrict__ err, const double* __restrict__ tol,
+                                                int* __restrict__ redo, int only_flagged, int final_sweep) {
+    __shared__ double red[40 * 33];
+    if (only_flagged && !redo[blockIdx.x]) return;
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int nm = r.nm;
+    const double* __restrict__ R = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
+    const double* __restrict__ B = r.rhs;
+    const double* __restrict__ X = r.X;
+    double acc[40];
+#pragma unroll
+    for (int k = 0; k < 40; ++k) acc[k] = 0.0;
+    for (int m = threadIdx.x; m < nm; m += blockDim.x) {
+        double b[4], x[5], rr[5];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) b[a] = B[(size_t)a * nm + m];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) x[c] = X[(size_t)c * nm + m];
+        if (corrected) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) rr[c] = R[(size_t)c * nm + m];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) rr[c] = 0.0;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                acc[a * 5 + c] += b[a] * x[c];
+                acc[20 + a * 5 + c] += x[a] * rr[c];
+            }
+    }
+    cta_sum<40>(acc, red);
     if (threadIdx.x == 0) {
-        const double vol = 1.0;  // unit cell
         double cn = 0.0, corr = 0.0;
         int bad = 0;
-        for (int a = 0; a < dd; ++a) {
-            for (int b = 0; b < dd; ++b) {
-                double v = r.KMM[a * dd + b] - tot[a * nr + b];
+        for (int a = 0; a < 4; ++a) {
+            for (int b2 = 0; b2 < 4; ++b2) {
+                double v = r.KMM[a * 4 + b2] - acc[a * 5 + b2];
                 if (corrected) {
-                    const double g2 = tot[nv + a * nr + b];
-                    v -= g2;
-                    corr += g2 * g2;
+                    v -= acc[20 + a * 5 + b2];
+                    corr += acc[20 + a * 5 + b2] * acc[20 + a * 5 + b2];
                 }
-                v /= vol;
                 cn += v * v;
                 bad |= !isfinite(v);
-                Cbar[(size_t)blockIdx.x * dd * dd + a * dd + b] = v;
+                Cbar[(size_t)blockIdx.x * 16 + a * 4 + b2] = v;  // |Omega| = 1
             }
-            double s = r.Pint[a] - tot[a * nr + dd];
-            if (corrected) s -= tot[nv + a * nr + dd];
-            s /= vol;
-            bad |= !isfinite(s);
-            sigma[(size_t)blockIdx.x * dd + a] = s;
+            double sg = r.Pint[a] - acc[a * 5 + 4];
+            if (corrected) sg -= acc[20 + a * 5 + 4];
+            bad |= !isfinite(sg);
+            sigma[(size_t)blockIdx.x * 4 + a] = sg;
         }
-        const double e = corrected ? corr / fmax(cn, 1e-300) : 0.0;  // (first-order term)^2 / |Cbar|^2
+        // (first-order term)^2 / |Cbar|^2 estimates the error left after the correction
+        const double e = corrected ? corr / fmax(cn, 1e-300) : 0.0;
         if (err) err[blockIdx.x] = e;
         if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
+        const bool over = corrected && !(e <= *tol);
+        if (redo) redo[blockIdx.x] = (over && status[blockIdx.x] == FE2_OK) ? 1 : 0;
+        if (final_sweep && over && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NO_CONV;
     }
 }
 
@@ -99,8 +122,13 @@ __global__ void k_macro_update(RveDev* __restrict__ tab, const int* __restrict__
 }  // namespace
 
 cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
-                         double* Cbar, int* status, double* err, cudaStream_t s) {
-    k_schur<<<n, 256, 0, s>>>(tab, ids, ws, corrected, sigma, Cbar, status, err);
+                         double* Cbar, int* status, double* err, const double* tol, int* redo, cudaStream_t s,
+                         int refine_sweep) {
+    // refine_sweep: 0 = first pass over all RVEs; 1 = flagged RVEs only (after a
+    // refinement sweep); 2 = flagged only, last allowed sweep; 3 = all RVEs, no
+    // sweep allowed.  On the last pass an estimate above *tol sets FE2_ERR_NO_CONV.
+    k_schur2<<<n, 256, 0, s>>>(tab, ids, ws, corrected, sigma, Cbar, status, err, tol, redo,
+                               refine_sweep == 1 || refine_sweep == 2, refine_sweep >= 2);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,111 @@
+"""Monolithic FE^2 Newton driver (Section 4.2, Eq. (solution2)) over the C ABI.
+
+The loop control lives here; every arithmetic step is a libfe2 kernel:
+macro gradients, the fused RVE solve (S1-S6), the volume-averaged stress and
+micro residual norms, the macro assembly + band solve (S7) and the
+fluctuation update w~ <- w~ - (x_r + X_M : dFbar).  Load stepping follows
+Section 5.2: the Dirichlet data are applied in n_l increments and each load
+step starts from the previous converged state.  A step fails when the macro
+residual exceeds 1e10 (the failure criterion of Section 5.2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def macro_mesh(nx, ny, Lx=1.0, Ly=1.0):
+    """Structured Q4 mesh of [0,Lx]x[0,Ly]; boundary nodes flagged as Dirichlet."""
+    xs = np.linspace(0.0, Lx, nx + 1)
+    ys = np.linspace(0.0, Ly, ny + 1)
+    X = np.array([[x, y] for y in ys for x in xs])
+    conn = []
+    for ey in range(ny):
+        for ex in range(nx):
+            n0 = ex + (nx + 1) * ey
+            conn.append([n0, n0 + 1, n0 + nx + 1, n0 + nx + 2])
+    conn = np.array(conn, dtype=np.int32)
+    on_bnd = (np.abs(X[:, 0]) < 1e-12) | (np.abs(X[:, 1]) < 1e-12) | \
+        (np.abs(X[:, 0] - Lx) < 1e-12) | (np.abs(X[:, 1] - Ly) < 1e-12)
+    fixed = np.repeat(on_bnd, 2).astype(np.uint8)
+    return X, conn, fixed
+
+
+@dataclass
+class NewtonLog:
+    iters: list = field(default_factory=list)      # Newton iterations per load step
+    history: list = field(default_factory=list)    # (step, it, ||R_macro||, max ||r_m||)
+    failed: bool = False
+
+
+class MonolithicFE2:
+    """Macro Q4 problem with one RVE per macro Gauss point (b = 4 e + q)."""
+
+    def __init__(self, ctx, X, conn, fixed, batch):
+        import torch
+        self.t = torch
+        self.ctx = ctx
+        self.X = np.asarray(X, float)
+        self.fixed = np.asarray(fixed, np.uint8)
+        ngp = 4 * len(conn)
+        if batch.nrve != ngp:
+            raise ValueError(f"need one RVE per macro Gauss point ({ngp}), got {batch.nrve}")
+        ctx.macro_setup(self.X, conn, self.fixed)
+        self.ids = ctx.register_batch(batch)
+        dev = "cuda"
+        f64 = torch.float64
+        self.Fbar = torch.zeros((ngp, 2, 2), dtype=f64, device=dev)
+        self.dFbar = torch.zeros_like(self.Fbar)
+        self.Pbar = torch.zeros((ngp, 4), dtype=f64, device=dev)
+        self.outs = ctx._outs(ngp)
+        self.rn = torch.zeros(2, dtype=f64, device=dev)
+        self.rnm = torch.zeros(ngp, dtype=f64, device=dev)
+        self.mstatus = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ngp = ngp
+
+    def state(self):
+        """Current per-Gauss-point Fbar, Pbar, sigma_eff, Cbar (host arrays)."""
+        sig, Cb, st, err = self.outs
+        return dict(Fbar=self.Fbar.cpu().numpy().copy(), Pbar=self.Pbar.cpu().numpy().copy(),
+                    sigma_eff=sig.cpu().numpy().copy(), Cbar=Cb.cpu().numpy().copy(),
+                    status=st.cpu().numpy().copy(), err=err.cpu().numpy().copy())
+
+    def load_step(self, Fk, step, tol_macro=1e-9, tol_micro=1e-9, maxit=25, log=None):
+        ctx = self.ctx
+        q_fixed = self.X @ np.asarray(Fk).T
+        ctx.macro_set_positions(q_fixed, which=self.fixed)
+        sig, Cb, st, err = self.outs
+        for it in range(maxit):
+            ctx.macro_gradients(self.Fbar)
+            ctx.rve_solve(self.ids, self.Fbar, out=self.outs)
+            ctx.rve_average_stress(self.ids, self.Pbar)
+            ctx.macro_residual(self.Pbar, self.rn[0:1])
+            ctx.rve_residual_norm(self.ids, self.rnm)
+            self.t.cuda.current_stream().synchronize()
+            rmac = float(self.rn[0].item())
+            rmic = float(self.rnm.max().item())
+            bad = int((st != 0).sum().item())
+            if log is not None:
+                log.history.append((step, it, rmac, rmic))
+            if bad:
+                raise RuntimeError(f"{bad} RVEs failed (status {np.unique(st.cpu().numpy())})")
+            if rmac < tol_macro and rmic < tol_micro:
+                if log is not None:
+                    log.iters.append(it)
+                return it
+            if rmac > 1e10 or not np.isfinite(rmac):
+                if log is not None:
+                    log.failed = True
+                raise RuntimeError(f"macro residual {rmac:.3e}: Newton diverged")
+            ctx.macro_solve(sig, Cb, self.dFbar, self.rn[1:2], self.mstatus)
+            ctx.macro_step(self.ids, self.dFbar)
+        raise RuntimeError("macro Newton did not converge")
+
+    def run(self, F_final, n_steps, **kw):
+        log = NewtonLog()
+        F_final = np.asarray(F_final, float)
+        for k in range(1, n_steps + 1):
+            Fk = np.eye(2) + (k / n_steps) * (F_final - np.eye(2))
+            self.load_step(Fk, k, log=log, **kw)
+        return log

@@ -58,8 +58,13 @@ _SIGS = {
     "fe2_rve_solve": (_I, [_P, _I, _IP, _P, _P, _P, _P, _P]),
     "fe2_macro_step": (_I, [_P, _I, _IP, _P]),
     "fe2_macro_setup": (_I, [_P, _I, _DP, _I, _IP, C.POINTER(C.c_uint8)]),
+    "fe2_macro_set_positions": (_I, [_P, _DP, C.POINTER(C.c_uint8)]),
+    "fe2_macro_get_positions": (_I, [_P, _DP]),
+    "fe2_macro_gradients": (_I, [_P, _P, _P]),
+    "fe2_macro_residual": (_I, [_P, _P, _P]),
     "fe2_macro_solve": (_I, [_P, _P, _P, _P, _P, _P]),
-    "fe2_macro_gradients": (_I, [_P, _P, _P, _P]),
+    "fe2_rve_average_stress": (_I, [_P, _I, _IP, _P]),
+    "fe2_rve_residual_norm": (_I, [_P, _I, _IP, _P]),
     "fe2_rve_export": (_I, [_P, _I, _I, _DP]),
     "fe2_rve_set_w": (_I, [_P, _I, _DP]),
     "fe2_launch_count": (C.c_longlong, [_P]),
@@ -215,6 +220,46 @@ class Fe2Context:
         a, p = _ids(ids)
         dFbar = dFbar.contiguous()
         self._check(self.lib.fe2_macro_step(self.h, len(a), p, _ptr(dFbar)), "fe2_macro_step")
+
+    # -- macro problem (S7) --------------------------------------------------------
+    def macro_setup(self, X, conn, fixed):
+        X = np.ascontiguousarray(np.asarray(X, dtype=np.float64))
+        conn = np.ascontiguousarray(np.asarray(conn, dtype=np.int32))
+        fixed = np.ascontiguousarray(np.asarray(fixed, dtype=np.uint8))
+        self._check(self.lib.fe2_macro_setup(self.h, len(X), X.ctypes.data_as(_DP), len(conn),
+                                             conn.ctypes.data_as(_IP), fixed.ctypes.data_as(C.POINTER(C.c_uint8))),
+                    "fe2_macro_setup")
+        self.macro_nnode, self.macro_ngp = len(X), 4 * len(conn)
+
+    def macro_set_positions(self, q, which=None):
+        q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
+        w = None if which is None else np.ascontiguousarray(np.asarray(which, dtype=np.uint8))
+        self._check(self.lib.fe2_macro_set_positions(self.h, q.ctypes.data_as(_DP),
+                                                     None if w is None else w.ctypes.data_as(C.POINTER(C.c_uint8))),
+                    "fe2_macro_set_positions")
+
+    def macro_get_positions(self):
+        q = np.zeros((self.macro_nnode, 2))
+        self._check(self.lib.fe2_macro_get_positions(self.h, q.ctypes.data_as(_DP)), "fe2_macro_get_positions")
+        return q
+
+    def macro_gradients(self, Fbar):
+        self._check(self.lib.fe2_macro_gradients(self.h, _ptr(Fbar), None), "fe2_macro_gradients")
+
+    def macro_residual(self, stress, rnorm):
+        self._check(self.lib.fe2_macro_residual(self.h, _ptr(stress), _ptr(rnorm)), "fe2_macro_residual")
+
+    def macro_solve(self, sigma, Cbar, dFbar, rnorm, status=None):
+        self._check(self.lib.fe2_macro_solve(self.h, _ptr(sigma), _ptr(Cbar), _ptr(dFbar), _ptr(rnorm),
+                                             _ptr(status)), "fe2_macro_solve")
+
+    def rve_average_stress(self, ids, Pbar):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_average_stress(self.h, len(a), p, _ptr(Pbar)), "fe2_rve_average_stress")
+
+    def rve_residual_norm(self, ids, out):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_residual_norm(self.h, len(a), p, _ptr(out)), "fe2_rve_residual_norm")
 
     def sync(self):
         self._check(self.lib.fe2_sync(self.h), "fe2_sync")

@@ -280,3 +280,45 @@ def test_budget_admission(torch):
     assert (st.cpu().numpy() == 0).all()
     ctx.release(ids)
     ctx.register_batch(W.fiber_batch(2, 16))      # fits again after release
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_monolithic_newton_matches_oracle(torch, precision):
+    """Load-stepped monolithic Newton (macro 2x2 Q4, 16 NH RVEs with random
+    inclusions, uniaxial stretch 1.1 in 2 steps): converged per-Gauss-point
+    Pbar and Cbar, nodal positions and Newton iteration counts match the
+    oracle's monolithic scheme."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh
+    N = 6
+    X, conn, fixed = macro_mesh(2, 2)
+    b = W.inclusion_batch(16, N, stretch=1.0)
+    ctx = ctx_for(torch, precision, refine_tol=1e-14, max_refine=2)
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    Ff = np.diag([1.1, 1.0])
+    log = fe.run(Ff, 2, tol_macro=1e-10, tol_micro=1e-10)
+    st = fe.state()
+    rves = [dict(N=N, phase=b.phase[k], mat=b.mat[k]) for k in range(16)]
+    out, iters, q = O.monolithic_fe2(O.macro_mesh(2, 2), rves, Ff, n_steps=2, tol_macro=1e-10, tol_micro=1e-10)
+    assert log.iters == iters
+    tol = TOL[precision]
+    for k in range(16):
+        assert O.rel_err(st["Pbar"][k], out[k]["Pbar"]) <= tol
+        assert O.rel_err(st["Cbar"][k], out[k]["Cbar"]) <= tol
+    assert np.abs(fe.ctx.macro_get_positions() - q).max() <= 1e-12
+
+
+def test_macro_patch_test_on_gpu(torch):
+    """Homogeneous RVEs and affine Dirichlet data: every Gauss point converges
+    to Fbar = F_final and the nodal positions are affine."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh
+    X, conn, fixed = macro_mesh(3, 2)
+    m = np.array([[1, 1.0, 10.0, 0], [1, 1.0, 10.0, 0]])
+    b = W.RveBatch(2, np.full(24, 4, np.int32), [np.zeros(16, np.uint8)] * 24, np.repeat(m[None], 24, 0),
+                   np.repeat(np.eye(2)[None], 24, 0))
+    ctx = ctx_for(torch, "mixed")
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    Ff = np.array([[1.08, 0.03], [0.0, 0.96]])
+    fe.run(Ff, 2, tol_macro=1e-11, tol_micro=1e-11)
+    st = fe.state()
+    assert np.abs(st["Fbar"] - Ff[None]).max() < 1e-12
+    assert np.abs(fe.ctx.macro_get_positions() - X @ Ff.T).max() < 1e-12
