@@ -196,6 +196,37 @@ fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* host_out);
 /* Set w~ of one RVE from the natural numbering ([host] double[nm]). */
 fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w);
 
+/*
+ * Fused RVE solve that allocates nothing (the paper has no counterpart: this is
+ * an integration entry point).  For callers that cannot call cudaMalloc /
+ * cudaFree: code running inside another framework's memory pool or a plugin
+ * host that owns the device allocator, or real-time loops that must not touch
+ * the allocator.  Same computation as fe2_rve_solve on the mixed path (FP32
+ * band factor, FP64 residual, residual-corrected Schur complement, no
+ * refinement sweeps, rve_status FE2_ERR_NO_CONV when the error estimate
+ * exceeds 1e-10), for n RVEs of one mesh size N (2D Q4, zero fluctuation w~).
+ *
+ * Inputs [device]: phase uint8[n][N*N], mat double[n][nphase][4],
+ * Fbar double[n][2][2].  Outputs [device]: sigma_eff double[n][4],
+ * Cbar double[n][4][4], rve_status int[n], err_est double[n] (may be NULL).
+ * Work is queued on cuda_stream (NULL = default stream); no context is used.
+ *
+ * All intermediate data live in one library-owned __device__ array of
+ * FE2_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  Limits: N >= 3, and the n RVEs must fit the array
+ * (about 1.7 MB per RVE at N = 32, i.e. 37 RVEs; 0.45 MB at N = 16); larger
+ * requests return FE2_ERR_BUDGET without running anything.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make the first call on each device before any
+ * stream capture.  Every call reuses the same array and leaves the previous
+ * call's data in it: calls that overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other -- serialise them.
+ */
+#define FE2_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint8_t* phase, const double* mat,
+                                 const double* Fbar, double* sigma_eff, double* Cbar, int* rve_status,
+                                 double* err_est, void* cuda_stream);
+
 /* Number of kernel launches the context has issued so far. */
 long long fe2_launch_count(const fe2_ctx* ctx);
 

@@ -68,6 +68,7 @@ _SIGS = {
     "fe2_rve_export": (_I, [_P, _I, _I, _DP]),
     "fe2_rve_set_w": (_I, [_P, _I, _DP]),
     "fe2_launch_count": (C.c_longlong, [_P]),
+    "fe2_rve_solve_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fe2_profile": (_I, [_P, _I]),
     "fe2_profile_read": (_I, [_P, _I, C.c_char_p, _DP, C.POINTER(C.c_longlong)]),
 }
@@ -122,6 +123,24 @@ def _ptr(t):
 def _ids(ids):
     a = np.ascontiguousarray(np.asarray(ids, dtype=np.int32))
     return a, a.ctypes.data_as(_IP)
+
+
+def rve_solve_noalloc(N, phase, mat, Fbar, out, stream=None):
+    """Call fe2_rve_solve_noalloc: the fused mixed-precision RVE solve with all
+    intermediate data in the library's fixed device scratch array (no device
+    allocation by the library).  phase [n, N*N] uint8, mat [n, nphase, 4] f64,
+    Fbar [n, 2, 2] f64 and the outputs out = (sigma [n,4], Cbar [n,4,4],
+    status [n] int32, err [n] f64) are caller-owned CUDA tensors."""
+    import torch
+    n = Fbar.shape[0]
+    nphase = mat.shape[1]
+    s = stream if stream is not None else torch.cuda.current_stream()
+    sig, Cb, st, err = out
+    code = load().fe2_rve_solve_noalloc(int(N), int(n), int(nphase), _ptr(phase), _ptr(mat), _ptr(Fbar),
+                                        _ptr(sig), _ptr(Cb), _ptr(st), _ptr(err), C.c_void_p(s.cuda_stream))
+    if code != FE2_OK:
+        raise Fe2Error(code, f"fe2_rve_solve_noalloc(N={N}, n={n}) failed")
+    return out
 
 
 class Fe2Context:
