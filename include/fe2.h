@@ -227,6 +227,35 @@ fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint8_t* phase,
                                  const double* Fbar, double* sigma_eff, double* Cbar, int* rve_status,
                                  double* err_est, void* cuda_stream);
 
+/*
+ * Serving: continuous batching of RVE solve requests (S1 - S6 per request) as
+ * macro Newton iterations emit them.  RVE state stays resident in the context
+ * between requests; admission of new RVEs is by the context's HBM budget
+ * (fe2_rve_register).  The server runs `nlanes` execution lanes, each with its
+ * own CUDA stream, factorisation workspace, pinned staging and completion
+ * event: a batch formed while another runs is launched at once and overlaps it
+ * on the device.  A batch takes up to max_batch queued requests of one mesh
+ * size (that of the oldest request) whose RVE is not already in flight, in
+ * submission order.  Results are bit-identical to solving the RVE alone.
+ *
+ * fe2_server_submit: queue n requests (rve_ids [host], Fbar [host]
+ *   double[n][d][d]); tickets [host] long long[n] receives their ids.
+ * fe2_server_pump: harvest finished lanes and launch batches on idle lanes;
+ *   returns immediately (busy_lanes [host], may be NULL).  Call it repeatedly.
+ * fe2_server_take: move up to max finished results to the caller ([host]
+ *   arrays: tickets, sigma [max][d*d], Cbar [max][d^4], status, latency_ms
+ *   = completion - submission time); returns the number taken (-1 on error).
+ * fe2_server_pending: requests queued or in flight.
+ */
+typedef struct fe2_server fe2_server;
+fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server** out);
+void fe2_server_destroy(fe2_server* srv);
+fe2_status fe2_server_submit(fe2_server* srv, int n, const int* rve_ids, const double* Fbar, long long* tickets);
+fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes);
+int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma, double* Cbar, int* status,
+                    double* latency_ms);
+int fe2_server_pending(const fe2_server* srv);
+
 /* Number of kernel launches the context has issued so far. */
 long long fe2_launch_count(const fe2_ctx* ctx);
 

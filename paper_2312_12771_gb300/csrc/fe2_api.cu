@@ -2,7 +2,10 @@
 // HBM-budget admission, id-list cache, transient workspace, and the launch
 // sequences of the assemble / reduce / condense / macro-step calls.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
+#include <deque>
+#include <unordered_set>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -1017,6 +1020,272 @@ fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double
     if (st != FE2_OK) return st;
     TIMED("rve_residual_norm", launch_rve_rnorm(ctx->d_tab, d_ids, n, rnorm, ctx->stream));
     return FE2_OK;
+}
+
+}  // extern "C"
+
+// ================================================================== serving
+// Continuous batching over execution lanes.  Each lane owns a CUDA stream, a
+// factorisation workspace, device/pinned staging and a completion event, so a
+// batch formed while another is running is launched at once and overlaps it on
+// the device.  A batch takes queued requests of one mesh size (the oldest
+// request's) whose RVE is not already in flight; RVE state stays resident.
+namespace {
+
+struct ServeReq {
+    long long ticket;
+    int rve;
+    double F[9];
+    std::chrono::steady_clock::time_point t0;
+};
+
+struct ServeDone {
+    long long ticket;
+    double sigma[9];
+    double C[81];
+    int status;
+    double lat_ms;
+};
+
+struct Lane {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_ids = nullptr, *h_ids = nullptr, *d_st = nullptr, *h_st = nullptr, *d_redo = nullptr;
+    double *d_F = nullptr, *h_F = nullptr, *d_sig = nullptr, *h_sig = nullptr, *d_C = nullptr, *h_C = nullptr;
+    double *d_err = nullptr;
+    std::vector<ServeReq> batch;
+};
+
+}  // namespace
+
+struct fe2_server {
+    fe2_ctx* ctx = nullptr;
+    int max_batch = 0;
+    std::vector<Lane> lanes;
+    std::deque<ServeReq> queue;
+    std::deque<ServeDone> done;
+    std::unordered_set<int> inflight;
+    long long next_ticket = 1;
+};
+
+static fe2_status lane_launch(fe2_server* srv, Lane& L) {
+    fe2_ctx* ctx = srv->ctx;
+    const int n = (int)L.batch.size();
+    const int d = ctx->cfg.dim, dd = d * d;
+    std::vector<int> ids(n);
+    for (int k = 0; k < n; ++k) {
+        ids[k] = L.batch[k].rve;
+        L.h_ids[k] = ids[k];
+        std::memcpy(L.h_F + (size_t)k * dd, L.batch[k].F, sizeof(double) * dd);
+    }
+    const BatchInfo b = batch_info(ctx, n, ids.data());
+    const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
+    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64);
+    if (l.stride * (size_t)n > L.ws_bytes) {
+        CK(cudaStreamSynchronize(L.s));
+        if (L.ws) CK(cudaFree(L.ws));
+        L.ws = nullptr;
+        L.ws_bytes = 0;
+        CK(cudaMalloc(&L.ws, l.stride * (size_t)n));
+        L.ws_bytes = l.stride * (size_t)n;
+    }
+    cudaStream_t s = L.s;
+    CK(cudaMemcpyAsync(L.d_ids, L.h_ids, sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(L.d_F, L.h_F, sizeof(double) * dd * n, cudaMemcpyHostToDevice, s));
+    Workspace ws{L.ws, l.stride, l.offY, l.offR, l.offD};
+    CK(launch_check_fbar(L.d_F, n, d, L.d_st, s));
+    CK(launch_assemble_fused(ctx->d_tab, L.d_ids, n, L.d_F, d, b.maxN, b.all_linear ? 1 : 0, s));
+    if (fp64) {
+        CK(launch_factor<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        CK(launch_backward<double>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
+        CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 0, L.d_sig, L.d_C, L.d_st, L.d_err, nullptr, nullptr, s));
+        ctx->launches += 5;
+    } else {
+        CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        CK(launch_backward<float>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
+        CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, nullptr, s));
+        int* redo = ctx->cfg.max_refine > 0 ? L.d_redo : nullptr;
+        CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s,
+                        ctx->cfg.max_refine > 0 ? 0 : 3));
+        for (int it = 0; it < ctx->cfg.max_refine; ++it) {
+            CK(launch_solve_correct<float>(ctx->d_tab, L.d_ids, n, ws, b.maxkd, b.maxnr, b.maxnmp, L.d_st, L.d_redo, s));
+            CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, L.d_redo, s));
+            CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, L.d_redo, s,
+                            it + 1 == ctx->cfg.max_refine ? 2 : 1));
+        }
+        ctx->launches += 6 + 3 * ctx->cfg.max_refine;
+    }
+    CK(cudaMemcpyAsync(L.h_sig, L.d_sig, sizeof(double) * dd * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(L.h_C, L.d_C, sizeof(double) * dd * dd * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(L.h_st, L.d_st, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(L.ev, s));
+    L.busy = true;
+    return FE2_OK;
+}
+
+extern "C" {
+
+fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server** out) {
+    if (!ctx || !out) return FE2_ERR_ARG;
+    *out = nullptr;
+    if (max_batch < 1 || nlanes < 1 || nlanes > 8) return fail(ctx, FE2_ERR_ARG, "bad server sizes");
+    fe2_server* srv = new fe2_server();
+    srv->ctx = ctx;
+    srv->max_batch = max_batch;
+    srv->lanes.resize(nlanes);
+    const int dd = ctx->cfg.dim * ctx->cfg.dim;
+    for (auto& L : srv->lanes) {
+        cudaError_t e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_ids, sizeof(int) * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_st, sizeof(int) * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_redo, sizeof(int) * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_F, sizeof(double) * dd * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_sig, sizeof(double) * dd * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_C, sizeof(double) * dd * dd * max_batch);
+        if (e == cudaSuccess) e = cudaMalloc(&L.d_err, sizeof(double) * max_batch);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_ids, sizeof(int) * max_batch);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_st, sizeof(int) * max_batch);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_F, sizeof(double) * dd * max_batch);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_sig, sizeof(double) * dd * max_batch);
+        if (e == cudaSuccess) e = cudaMallocHost(&L.h_C, sizeof(double) * dd * dd * max_batch);
+        if (e != cudaSuccess) {
+            fe2_server_destroy(srv);
+            return fail(ctx, FE2_ERR_CUDA, "server lane allocation: %s", cudaGetErrorString(e));
+        }
+    }
+    *out = srv;
+    return FE2_OK;
+}
+
+void fe2_server_destroy(fe2_server* srv) {
+    if (!srv) return;
+    for (auto& L : srv->lanes) {
+        if (L.s) cudaStreamSynchronize(L.s);
+        cudaFree(L.ws);
+        cudaFree(L.d_ids);
+        cudaFree(L.d_st);
+        cudaFree(L.d_redo);
+        cudaFree(L.d_F);
+        cudaFree(L.d_sig);
+        cudaFree(L.d_C);
+        cudaFree(L.d_err);
+        cudaFreeHost(L.h_ids);
+        cudaFreeHost(L.h_st);
+        cudaFreeHost(L.h_F);
+        cudaFreeHost(L.h_sig);
+        cudaFreeHost(L.h_C);
+        if (L.ev) cudaEventDestroy(L.ev);
+        if (L.s) cudaStreamDestroy(L.s);
+    }
+    delete srv;
+}
+
+fe2_status fe2_server_submit(fe2_server* srv, int n, const int* rve_ids, const double* Fbar, long long* tickets) {
+    if (!srv) return FE2_ERR_ARG;
+    fe2_ctx* ctx = srv->ctx;
+    if (n < 0 || (n > 0 && (!rve_ids || !Fbar))) return fail(ctx, FE2_ERR_ARG, "bad submit arguments");
+    const int dd = ctx->cfg.dim * ctx->cfg.dim;
+    const auto now = std::chrono::steady_clock::now();
+    for (int k = 0; k < n; ++k) {
+        const int id = rve_ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        ServeReq r;
+        r.ticket = srv->next_ticket++;
+        r.rve = id;
+        std::memcpy(r.F, Fbar + (size_t)k * dd, sizeof(double) * dd);
+        r.t0 = now;
+        srv->queue.push_back(r);
+        if (tickets) tickets[k] = r.ticket;
+    }
+    return FE2_OK;
+}
+
+fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes) {
+    if (!srv) return FE2_ERR_ARG;
+    fe2_ctx* ctx = srv->ctx;
+    const int dd = ctx->cfg.dim * ctx->cfg.dim;
+    // harvest finished lanes
+    for (auto& L : srv->lanes) {
+        if (!L.busy) continue;
+        const cudaError_t q = cudaEventQuery(L.ev);
+        if (q == cudaErrorNotReady) continue;
+        CK(q);
+        const auto now = std::chrono::steady_clock::now();
+        for (size_t k = 0; k < L.batch.size(); ++k) {
+            ServeDone dn;
+            dn.ticket = L.batch[k].ticket;
+            std::memcpy(dn.sigma, L.h_sig + k * dd, sizeof(double) * dd);
+            std::memcpy(dn.C, L.h_C + k * dd * dd, sizeof(double) * dd * dd);
+            dn.status = L.h_st[k];
+            dn.lat_ms = std::chrono::duration<double, std::milli>(now - L.batch[k].t0).count();
+            srv->done.push_back(dn);
+            srv->inflight.erase(L.batch[k].rve);
+        }
+        L.batch.clear();
+        L.busy = false;
+    }
+    // launch new batches on idle lanes
+    for (auto& L : srv->lanes) {
+        if (L.busy || srv->queue.empty()) continue;
+        int Nsel = -1;
+        std::unordered_set<int> taken;
+        for (auto it = srv->queue.begin(); it != srv->queue.end() && (int)L.batch.size() < srv->max_batch;) {
+            const int id = it->rve;
+            if (srv->inflight.count(id) || taken.count(id)) {
+                ++it;
+                continue;
+            }
+            const int N = ctx->mirror[id].N;
+            if (Nsel < 0) Nsel = N;
+            if (N != Nsel) {
+                ++it;
+                continue;
+            }
+            taken.insert(id);
+            L.batch.push_back(*it);
+            it = srv->queue.erase(it);
+        }
+        if (L.batch.empty()) continue;
+        for (int id : taken) srv->inflight.insert(id);
+        fe2_status st = lane_launch(srv, L);
+        if (st != FE2_OK) return st;
+    }
+    if (busy_lanes) {
+        int b = 0;
+        for (auto& L : srv->lanes) b += L.busy;
+        *busy_lanes = b;
+    }
+    return FE2_OK;
+}
+
+int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma, double* Cbar, int* status,
+                    double* latency_ms) {
+    if (!srv || max < 0) return -1;
+    const int dd = srv->ctx->cfg.dim * srv->ctx->cfg.dim;
+    int k = 0;
+    while (k < max && !srv->done.empty()) {
+        const ServeDone& dn = srv->done.front();
+        if (tickets) tickets[k] = dn.ticket;
+        if (sigma) std::memcpy(sigma + (size_t)k * dd, dn.sigma, sizeof(double) * dd);
+        if (Cbar) std::memcpy(Cbar + (size_t)k * dd * dd, dn.C, sizeof(double) * dd * dd);
+        if (status) status[k] = dn.status;
+        if (latency_ms) latency_ms[k] = dn.lat_ms;
+        srv->done.pop_front();
+        ++k;
+    }
+    return k;
+}
+
+int fe2_server_pending(const fe2_server* srv) {
+    if (!srv) return -1;
+    int b = 0;
+    for (auto& L : srv->lanes) b += (int)L.batch.size();
+    return (int)srv->queue.size() + b;
 }
 
 }  // extern "C"

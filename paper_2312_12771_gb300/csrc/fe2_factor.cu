@@ -84,6 +84,46 @@ struct Vec4<double> {
     }
 };
 
+// Column K of the register-resident Cholesky of the NB x NB diagonal block
+// (lane r holds row r in a[]); template recursion keeps every index static so
+// the block never leaves registers.
+template <typename T, int K>
+__device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __restrict__ dinv, int& bad) {
+    if constexpr (K < NB) {
+        T piv = __shfl_sync(0xffffffffu, a[K], K);
+        const bool badk = !(piv > T(0));
+        if (badk) piv = T(1);
+        const T dk = rsqrt(piv);
+        if (lane == K)
+            a[K] = piv * dk;
+        else if (lane > K)
+            a[K] *= dk;
+        if (lane == 0) dinv[K] = dk;
+        bad |= badk;
+#pragma unroll
+        for (int c = K + 1; c < NB; ++c) {
+            const T lck = __shfl_sync(0xffffffffu, a[K], c);
+            if (lane >= c) a[c] -= a[K] * lck;
+        }
+        chol_block_steps<T, K + 1>(a, lane, dinv, bad);
+    }
+}
+
+// Step C of the right-looking solve of one panel row v against L11 (rows of
+// L11 read as broadcasts from the ring window).
+template <typename T, int C>
+__device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict__ W, int base, int S, int LDW,
+                                                int kd, const T* __restrict__ dinv) {
+    if constexpr (C < NB) {
+        const T* Lc = W + (size_t)(base + C >= S ? base + C - S : base + C) * LDW;
+        v[C] *= dinv[C];
+#pragma unroll
+        for (int c2 = C + 1; c2 < NB; ++c2)
+            if (c2 - C <= kd) v[c2] -= v[C] * Lc[c2 - C];
+        panel_row_steps<T, C + 1>(v, W, base, S, LDW, kd, dinv);
+    }
+}
+
 __device__ __forceinline__ void bar_sync_named(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -177,26 +217,9 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
             for (int c = 0; c < NB; ++c)
                 a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] : T(0);
-#pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                T piv = __shfl_sync(0xffffffffu, a[k], k);
-                const bool badk = !(piv > T(0));
-                if (badk) piv = T(1);
-                const T dk = T(1) / sqrt(piv);
-                if (lane == k) a[k] = piv * dk;
-                else if (lane > k) a[k] *= dk;
-                if (lane == 0) {
-                    dinv[k] = dk;
-                    if (badk) s_bad = 1;
-                }
-#pragma unroll
-                for (int c = 0; c < NB; ++c) {
-                    if (c > k) {
-                        const T lck = __shfl_sync(0xffffffffu, a[k], c);
-                        if (lane >= c) a[c] -= a[k] * lck;
-                    }
-                }
-            }
+            int badb = 0;
+            chol_block_steps<T, 0>(a, lane, dinv, badb);
+            if (lane == 0 && badb) s_bad = 1;
 #pragma unroll
             for (int c = 0; c < NB; ++c)
                 if (c <= lane && lane - c <= kd) W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] = a[c];
@@ -247,14 +270,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) v[c] = Bp[wrapS(base + c, S)];
             }
-#pragma unroll
-            for (int c = 0; c < NB; ++c) {
-                const T* Lc = W + (size_t)wrapS(base + c, S) * LDW;
-                v[c] *= dinv[c];
-#pragma unroll
-                for (int c2 = 0; c2 < NB; ++c2)
-                    if (c2 > c && c2 - c <= kd) v[c2] -= v[c] * Lc[c2 - c];
-            }
+            panel_row_steps<T, 0>(v, W, base, S, LDW, kd, dinv);
 #pragma unroll
             for (int c = 0; c < NB; ++c) Pn[c * KP + tid] = v[c];
             if (tid < kd) {

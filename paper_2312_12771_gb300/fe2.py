@@ -69,6 +69,12 @@ _SIGS = {
     "fe2_rve_set_w": (_I, [_P, _I, _DP]),
     "fe2_launch_count": (C.c_longlong, [_P]),
     "fe2_rve_solve_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fe2_server_create": (_I, [_P, _I, _I, C.POINTER(_P)]),
+    "fe2_server_destroy": (None, [_P]),
+    "fe2_server_submit": (_I, [_P, _I, _IP, _DP, C.POINTER(C.c_longlong)]),
+    "fe2_server_pump": (_I, [_P, _IP]),
+    "fe2_server_take": (_I, [_P, _I, C.POINTER(C.c_longlong), _DP, _DP, _IP, _DP]),
+    "fe2_server_pending": (_I, [_P]),
     "fe2_profile": (_I, [_P, _I]),
     "fe2_profile_read": (_I, [_P, _I, C.c_char_p, _DP, C.POINTER(C.c_longlong)]),
 }

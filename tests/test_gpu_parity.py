@@ -322,3 +322,26 @@ def test_macro_patch_test_on_gpu(torch):
     st = fe.state()
     assert np.abs(st["Fbar"] - Ff[None]).max() < 1e-12
     assert np.abs(fe.ctx.macro_get_positions() - X @ Ff.T).max() < 1e-12
+
+
+def test_serving_results_equal_alone_and_in_the_mix(torch):
+    """Continuous batching: requests of uneven sizes (16, 24, 32 and 48 squared)
+    served in overlapping batches give bit-identical sigma/Cbar to solving each
+    RVE alone, and every request completes with a latency."""
+    from paper_2312_12771_gb300.serve import Server, simulate
+    sizes = W.serving_sizes(11, 48)
+    b = W.inclusion_batch(48, sizes, stretch=1.02)
+    ctx = ctx_for(torch, "mixed")
+    ids = ctx.register_batch(b)
+    srv = Server(ctx, max_batch=8, lanes=2)
+    arrivals = W.poisson_arrivals(3, 48, rate=2000.0)
+    res, p50, p99, thr = simulate(srv, np.asarray(ids), b.Fbar, arrivals)
+    assert len(res["tickets"]) == 48 and (res["status"] == 0).all()
+    assert p99 >= p50 > 0
+    order = np.argsort(res["tickets"])
+    for j, k in enumerate(order):
+        s1, C1, st1, _ = ctx.rve_solve([ids[j]], torch.tensor(b.Fbar[j:j + 1], device="cuda"))
+        torch.cuda.synchronize()
+        assert np.array_equal(res["sigma"][k], s1.cpu().numpy()[0])
+        assert np.array_equal(res["Cbar"][k], C1.cpu().numpy()[0])
+    srv.close()
