@@ -278,6 +278,35 @@ def run_gpu(args, rank, world, dist):
     return batch, results, pk
 
 
+def run_serving(args, dev):
+    """Config-4 style serving: Neo-Hooke RVEs with random inclusions and mesh
+    sizes drawn from {16, 24, 32, 48}^2, one request per RVE per macro Newton
+    iteration, Poisson arrivals at ~80 % of the measured burst capacity."""
+    import torch
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    from paper_2312_12771_gb300.serve import Server, simulate
+    n = args.serve_rves
+    sizes = W.serving_sizes(W.GLOBAL_SEED, n)
+    batch = W.inclusion_batch(n, sizes, stretch=1.05)
+    Fb = W.perturbed_F(batch, 5, 0.01)
+    ctx = Fe2Context(dim=2, precision="mixed", max_refine=1, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30))
+    ids = np.asarray(ctx.register_batch(batch))
+    srv = Server(ctx, max_batch=args.serve_batch, lanes=2)
+    # burst: every request at t = 0 gives the capacity
+    _, _, _, cap = simulate(srv, ids, Fb, np.zeros(n))
+    rate = 0.8 * cap
+    arr = W.poisson_arrivals(W.GLOBAL_SEED, n, rate)
+    res, p50, p99, thr = simulate(srv, ids, Fb, arr)
+    out = {"workload": f"{n} NH RVEs, N in {{16,24,32,48}} (uniform), random inclusions; Poisson arrivals",
+           "capacity_solves_per_s": round(cap, 1), "offered_rate": round(rate, 1),
+           "throughput_solves_per_s": round(thr, 1), "p50_ms": round(p50, 3), "p99_ms": round(p99, 3),
+           "max_batch": args.serve_batch, "lanes": 2, "status_nonzero": int((res["status"] != 0).sum()),
+           "hbm_budget_gb": args.serve_budget_gb}
+    srv.close()
+    ctx.close()
+    return out
+
+
 def max_over_ranks(v, dist):
     if not dist:
         return v
@@ -305,6 +334,10 @@ def main():
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-rves", type=int, default=4096)
+    ap.add_argument("--serve-batch", type=int, default=512)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -353,6 +386,10 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     batch, R, pk = run_gpu(args, rank, world, dist)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        import torch
+        serving = run_serving(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
     mx = R["mixed"]
     ms = max_over_ranks(mx["ms"], dist)
     ms64 = max_over_ranks(R["fp64"]["ms"], dist)
@@ -393,6 +430,8 @@ def main():
             "roofline": roof, "kernels": kern, "clocks": mx["clocks"],
             "e2e": {"value": round(total * args.steps / (e2e_ms * 1e-3), 1), "unit": UNIT,
                     "h2d_bytes_per_step": mx["h2d"], "d2h_bytes_per_step": mx["d2h"]}}
+    if serving is not None:
+        line["serving"] = serving
     if pool is not None:
         nproc = os.cpu_count() or 1
         idx = list(np.random.default_rng(1).choice(batch.nrve, size=args.cpu_sample, replace=False))

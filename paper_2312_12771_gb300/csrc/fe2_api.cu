@@ -14,10 +14,6 @@
 
 #include "fe2_internal.cuh"
 
-namespace fe2 {
-size_t factor_smem_bytes(int kd, int nr, bool fp64);
-}
-
 using namespace fe2;
 
 namespace {
@@ -125,6 +121,18 @@ static int compute_kd(fe2_ctx* ctx, int N, int d) {
                     kd = std::max(kd, 2 * std::abs(qn - q) + 1);
                 }
         }
+    } else {
+        for (int q = 1; q < nn; ++q) {
+            const int i = unfold_pos(q % N, N), j = unfold_pos((q / N) % N, N), k = unfold_pos(q / (N * N), N);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const int qn = fold_pos((i + dx + N) % N, N) + N * fold_pos((j + dy + N) % N, N) +
+                                       N * N * fold_pos((k + dz + N) % N, N);
+                        if (qn == 0) continue;
+                        kd = std::max(kd, 3 * std::abs(qn - q) + 2);
+                    }
+        }
     }
     // the factorisation window needs kd >= NB (a panel must lie inside the band
     // storage); for small meshes the extra band rows are structural zeros
@@ -178,12 +186,20 @@ static size_t persistent_bytes_of(int N, int d, int nphase) {
 }
 
 struct WsLayout {
-    size_t offY, offR, offD, stride;
+    size_t offY, offR, offD, offWin, stride;
+    bool gw;  // wide band: the factor window lives in global memory
 };
 
-static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64) {
+// The shared-memory band factor serves bands whose window fits one CTA; wider
+// bands (3D) use the global-window kernel.
+static bool use_smem_factor(int kd, int nr, bool fp64, int max_smem, int d) {
+    return d == 2 && kd + nr + 32 <= FACT_THREADS && (int)factor_smem_bytes(kd, nr, fp64) <= max_smem;
+}
+
+static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64, int max_smem, int d) {
     const size_t es = fp64 ? 8 : 4;
     WsLayout l;
+    l.gw = !use_smem_factor(maxkd, maxnr, fp64, max_smem, d);
     size_t o = align256((size_t)maxnmp * (maxkd + 1) * es);
     l.offY = o;
     o += align256((size_t)maxnr * maxnmp * es);
@@ -191,6 +207,8 @@ static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64
     o += align256((size_t)maxnr * maxnm * 8);
     l.offD = o;
     o += align256((size_t)maxnmp * es);
+    l.offWin = o;
+    if (l.gw) o += align256((size_t)(maxkd + NB) * (maxkd + 1) * es);
     l.stride = o;
     return l;
 }
@@ -378,7 +396,7 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
                                 double* Cbar, int* status, double* err, bool reset_status) {
     const BatchInfo b = batch_info(ctx, n, ids);
     const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
-    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64);
+    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64, ctx->max_smem, ctx->cfg.dim);
     // chunk the batch so that its workspace fits the budget
     int cap = n;
     size_t limit = (size_t)-1;
@@ -391,8 +409,18 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
     fe2_status st = ensure_ws(ctx, l.stride * (size_t)cap, limit);
     if (st != FE2_OK) return st;
     if (reset_status) CK(cudaMemsetAsync(status, 0, sizeof(int) * n, ctx->stream));
-    Workspace ws{ctx->ws, l.stride, l.offY, l.offR, l.offD};
+    Workspace ws{ctx->ws, l.stride, l.offY, l.offR, l.offD, l.offWin};
     const int dd = ctx->cfg.dim * ctx->cfg.dim;
+    const bool d3 = ctx->cfg.dim == 3;
+    auto residual = [&](const int* di, int m, const int* active) {
+        return d3 ? launch_residual3(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream)
+                  : launch_residual(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream);
+    };
+    auto schur = [&](const int* di, int m, int corrected, double* sg, double* cb, int* stp, double* er,
+                     const double* tol, int* redo, int sweep) {
+        return d3 ? launch_schur3(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep)
+                  : launch_schur(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep);
+    };
     for (int c0 = 0; c0 < n; c0 += cap) {
         const int m = std::min(cap, n - c0);
         const int* di = d_ids + c0;
@@ -401,10 +429,13 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
         double* cb = Cbar + (size_t)c0 * dd * dd;
         double* er = err ? err + c0 : nullptr;
         if (fp64) {
-            TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            if (l.gw)
+                TIMED("band_factor_fp64_gw", launch_factor_gw<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            else
+                TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp64",
                   launch_backward<double>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
-            TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 0, sg, cb, stp, er, nullptr, nullptr, ctx->stream));
+            TIMED("schur", schur(di, m, 0, sg, cb, stp, er, nullptr, nullptr, 0));
         } else {
             // FP32 factor, one FP64 residual and the residual-corrected Schur complement;
             // RVEs whose error estimate exceeds refine_tol get up to max_refine sweeps
@@ -417,19 +448,20 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
                 ctx->redo_n = cap;
             }
             int* redo = ctx->cfg.max_refine > 0 ? ctx->d_redo : nullptr;
-            TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            if (l.gw)
+                TIMED("band_factor_fp32_gw", launch_factor_gw<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            else
+                TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp32",
                   launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
-            TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, nullptr, ctx->stream));
-            TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->stream,
-                                        ctx->cfg.max_refine > 0 ? 0 : 3));
+            TIMED("residual_fp64", residual(di, m, nullptr));
+            TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->cfg.max_refine > 0 ? 0 : 3));
             for (int it = 0; it < ctx->cfg.max_refine; ++it) {
                 const bool last = it + 1 == ctx->cfg.max_refine;
                 TIMED("band_refine_fp32", launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp,
                                                                       stp, ctx->d_redo, ctx->stream));
-                TIMED("residual_fp64", launch_residual(ctx->d_tab, di, m, ws, b.maxnn, ctx->d_redo, ctx->stream));
-                TIMED("schur", launch_schur(ctx->d_tab, di, m, ws, 1, sg, cb, stp, er, ctx->d_tol, ctx->d_redo,
-                                            ctx->stream, last ? 2 : 1));
+                TIMED("residual_fp64_refine", residual(di, m, ctx->d_redo));
+                TIMED("schur_refine", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol, ctx->d_redo, last ? 2 : 1));
             }
         }
     }
@@ -457,7 +489,6 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     if ((cfg->dim == 2) != (cfg->elem == FE2_ELEM_Q4)) return FE2_ERR_ARG;
     if (cfg->precision != FE2_PREC_FP64 && cfg->precision != FE2_PREC_MIXED) return FE2_ERR_ARG;
     if (cfg->max_refine < 0 || cfg->max_refine > 16) return FE2_ERR_ARG;
-    if (cfg->dim == 3) return FE2_ERR_ARG;  // Hex8 kernels are not built in this library version
     ctx = new fe2_ctx();
     ctx->cfg = *cfg;
     if (!(ctx->cfg.refine_tol > 0.0)) ctx->cfg.refine_tol = 1e-10;
@@ -538,7 +569,7 @@ size_t fe2_rve_bytes(const fe2_ctx* ctx, int N) {
     const int d = ctx->cfg.dim;
     const int kd = compute_kd(const_cast<fe2_ctx*>(ctx), N, d);
     const int nn = nodes_of(N, d), nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
-    const WsLayout l = ws_layout(kd, d * d + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64);
+    const WsLayout l = ws_layout(kd, d * d + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64, ctx->max_smem, d);
     return persistent_bytes_of(N, d, 2) + l.stride;
 }
 
@@ -556,10 +587,14 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         if (N[k] < 3 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range (N >= 3)", N[k]);
         const int kd = compute_kd(ctx, N[k], d);
         const int nr = d * d + 1;
-        if (kd + nr + 32 > FACT_THREADS) return fail(ctx, FE2_ERR_ARG, "N=%d: band too wide for one CTA", N[k]);
-        if ((int)factor_smem_bytes(kd, nr, fp64) > ctx->max_smem)
-            return fail(ctx, FE2_ERR_ARG, "N=%d: band window (%zu B) exceeds shared memory (%d B) on the %s path",
-                        N[k], factor_smem_bytes(kd, nr, fp64), ctx->max_smem, fp64 ? "FP64" : "mixed");
+        {
+            const int nmk = d * (nodes_of(N[k], d) - 1), nmpk = (nmk + NB - 1) / NB * NB;
+            if ((!use_smem_factor(kd, nr, fp64, ctx->max_smem, d) &&
+                 (int)factor_gw_smem_bytes(kd, nr, fp64) > ctx->max_smem) ||
+                (int)solve_smem_bytes(kd, nr, nmpk, fp64) > ctx->max_smem)
+                return fail(ctx, FE2_ERR_ARG, "N=%d: band of half width %d is too wide for the %s path", N[k], kd,
+                            fp64 ? "FP64" : "mixed");
+        }
         const int nn = nodes_of(N[k], d);
         for (int p = 0; p < nphase; ++p) {
             const double* m = mat + ((size_t)k * nphase + p) * 4;
@@ -573,7 +608,7 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         offs[k] = total;
         total += persistent_bytes_of(N[k], d, nphase);
         const int nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
-        ws_need = std::max(ws_need, ws_layout(kd, nr, nm, nmp, fp64).stride);
+        ws_need = std::max(ws_need, ws_layout(kd, nr, nm, nmp, fp64, ctx->max_smem, d).stride);
     }
     if (ctx->cfg.hbm_budget_bytes) {
         // persistent state of everything registered plus one workspace slot must fit;
@@ -744,7 +779,10 @@ fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const dou
     for (int k = 0; k < n; ++k) ctx->mirror[rve_ids[k]].elem = (double*)((char*)ctx->elem + per * k);
     st = upload_all(ctx);
     if (st != FE2_OK) return st;
-    TIMED("assemble_elems", launch_assemble_elems(ctx->d_tab, d_ids, n, Fbar, d, b.maxN, ctx->stream));
+    if (d == 3)
+        TIMED("assemble_elems_hex8", launch_assemble_elems3(ctx->d_tab, d_ids, n, Fbar, b.maxN, ctx->stream));
+    else
+        TIMED("assemble_elems", launch_assemble_elems(ctx->d_tab, d_ids, n, Fbar, d, b.maxN, ctx->stream));
     return FE2_OK;
 }
 
@@ -757,7 +795,10 @@ fe2_status fe2_nullspace_reduce(fe2_ctx* ctx, int n, const int* rve_ids) {
         if (!ctx->mirror[rve_ids[k]].elem)
             return fail(ctx, FE2_ERR_ARG, "rve %d has no element data: call fe2_micro_assemble first", rve_ids[k]);
     const BatchInfo b = batch_info(ctx, n, rve_ids);
-    TIMED("nullspace_reduce", launch_reduce(ctx->d_tab, d_ids, n, ctx->cfg.dim, b.maxN, ctx->stream));
+    if (ctx->cfg.dim == 3)
+        TIMED("nullspace_reduce_hex8", launch_reduce3(ctx->d_tab, d_ids, n, ctx->stream));
+    else
+        TIMED("nullspace_reduce", launch_reduce(ctx->d_tab, d_ids, n, ctx->cfg.dim, b.maxN, ctx->stream));
     return FE2_OK;
 }
 
@@ -779,6 +820,15 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
     fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
     if (st != FE2_OK) return st;
     const BatchInfo b = batch_info(ctx, n, rve_ids);
+    if (ctx->cfg.dim == 3) {
+        // Hex8: element rows to the element workspace, then the node-row gather
+        TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));
+        st = fe2_micro_assemble(ctx, n, rve_ids, Fbar);
+        if (st != FE2_OK) return st;
+        st = fe2_nullspace_reduce(ctx, n, rve_ids);
+        if (st != FE2_OK) return st;
+        return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
+    }
     TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));
     TIMED(b.all_linear ? "assemble_reduce_linear" : "assemble_reduce_general",
           launch_assemble_fused(ctx->d_tab, d_ids, n, Fbar, ctx->cfg.dim, b.maxN, b.all_linear ? 1 : 0, ctx->stream));
@@ -1083,7 +1133,7 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
     }
     const BatchInfo b = batch_info(ctx, n, ids.data());
     const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
-    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64);
+    const WsLayout l = ws_layout(b.maxkd, b.maxnr, b.maxnm, b.maxnmp, fp64, ctx->max_smem, d);
     if (l.stride * (size_t)n > L.ws_bytes) {
         CK(cudaStreamSynchronize(L.s));
         if (L.ws) CK(cudaFree(L.ws));
@@ -1095,16 +1145,22 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
     cudaStream_t s = L.s;
     CK(cudaMemcpyAsync(L.d_ids, L.h_ids, sizeof(int) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(L.d_F, L.h_F, sizeof(double) * dd * n, cudaMemcpyHostToDevice, s));
-    Workspace ws{L.ws, l.stride, l.offY, l.offR, l.offD};
+    Workspace ws{L.ws, l.stride, l.offY, l.offR, l.offD, l.offWin};
     CK(launch_check_fbar(L.d_F, n, d, L.d_st, s));
     CK(launch_assemble_fused(ctx->d_tab, L.d_ids, n, L.d_F, d, b.maxN, b.all_linear ? 1 : 0, s));
     if (fp64) {
-        CK(launch_factor<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        if (l.gw)
+            CK(launch_factor_gw<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        else
+            CK(launch_factor<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<double>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
         CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 0, L.d_sig, L.d_C, L.d_st, L.d_err, nullptr, nullptr, s));
         ctx->launches += 5;
     } else {
-        CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        if (l.gw)
+            CK(launch_factor_gw<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        else
+            CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<float>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
         CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, nullptr, s));
         int* redo = ctx->cfg.max_refine > 0 ? L.d_redo : nullptr;
@@ -1132,6 +1188,7 @@ fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server
     if (!ctx || !out) return FE2_ERR_ARG;
     *out = nullptr;
     if (max_batch < 1 || nlanes < 1 || nlanes > 8) return fail(ctx, FE2_ERR_ARG, "bad server sizes");
+    if (ctx->cfg.dim != 2) return fail(ctx, FE2_ERR_ARG, "the server batches 2D (Q4) RVEs");
     fe2_server* srv = new fe2_server();
     srv->ctx = ctx;
     srv->max_batch = max_batch;

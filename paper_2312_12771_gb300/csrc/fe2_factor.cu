@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             int badb = 0;
             chol_block_steps<T, 0>(a, lane, dinv, badb);
             if (lane == 0 && badb) s_bad = 1;
+            __syncwarp();
 #pragma unroll
             for (int c = 0; c < NB; ++c)
                 if (c <= lane && lane - c <= kd) W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] = a[c];
@@ -654,6 +655,17 @@ cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace 
     dim3 grid((maxnn + 255) / 256, n);
     k_residual2<<<grid, 256, 0, s>>>(tab, ids, ws, active);
     return cudaGetLastError();
+}
+
+size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64) {
+    if (fp64) {
+        SolveLayout<double> l;
+        l.init(kd, nr, nmp, true);
+        return l.total + 16 * NB * sizeof(double);
+    }
+    SolveLayout<float> l;
+    l.init(kd, nr, nmp, true);
+    return l.total + 16 * NB * sizeof(float);
 }
 
 size_t factor_smem_bytes(int kd, int nr, bool fp64) {

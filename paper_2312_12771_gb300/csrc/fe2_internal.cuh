@@ -37,9 +37,10 @@ struct RveDev {
 //   Y  at base + s*stride + offY   (T[nr][nm_pad], forward-solve result)
 //   R  at base + s*stride + offR   (double[nr][nm], FP64 residuals)
 //   D  at base + s*stride + offD   (T[nm_pad], reciprocal diagonal of L)
+//   Win at base + s*stride + offWin (T[kd+NB][kd+1], band window of the wide-band factor)
 struct Workspace {
     char* base;
-    size_t stride, offY, offR, offD;
+    size_t stride, offY, offR, offD, offWin;
 };
 
 __host__ __device__ inline int fold_pos(int i, int N) {
@@ -83,6 +84,22 @@ cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws,
 cudaError_t launch_macro_update(const RveDev* tab, const int* ids, int n, const double* dF,
                                 int maxnm, cudaStream_t s);
 cudaError_t launch_check_fbar(const double* Fbar, int n, int d, int* status, cudaStream_t s);
+
+// 3D (Hex8) and wide-band kernels (fe2_rve3d.cu)
+cudaError_t launch_assemble_elems3(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
+                                   cudaStream_t s);
+cudaError_t launch_reduce3(const RveDev* tab, const int* ids, int n, cudaStream_t s);
+cudaError_t launch_residual3(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn, const int* active,
+                             cudaStream_t s);
+cudaError_t launch_schur3(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
+                          double* Cbar, int* status, double* err, const double* tol, int* redo, cudaStream_t s,
+                          int refine_sweep = 0);
+template <typename T>
+cudaError_t launch_factor_gw(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                             int maxnr, cudaStream_t s);
+size_t factor_gw_smem_bytes(int kd, int nr, bool fp64);
+size_t factor_smem_bytes(int kd, int nr, bool fp64);
+size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64);  // refinement solve (the larger one)
 
 // macro problem (fe2_macro.cu)
 struct MacroDev {

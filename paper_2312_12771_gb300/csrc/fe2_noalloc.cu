@@ -18,10 +18,6 @@
 
 #include "fe2_internal.cuh"
 
-namespace fe2 {
-size_t factor_smem_bytes(int kd, int nr, bool fp64);
-}
-
 using namespace fe2;
 
 namespace {
@@ -160,7 +156,7 @@ extern "C" fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint
     const RveDev* tab = (const RveDev*)(base + L.off_desc);
     const int* ids = (const int*)(base + L.off_ids);
     const double* tol = (const double*)(base + L.off_tol);
-    Workspace ws{(char*)base + L.off_ws, L.ws_stride, L.offY, L.offR, L.offD};
+    Workspace ws{(char*)base + L.off_ws, L.ws_stride, L.offY, L.offR, L.offD, 0};
     if (launch_check_fbar(Fbar, n, 2, rve_status, s) != cudaSuccess) return FE2_ERR_CUDA;
     if (launch_assemble_fused(tab, ids, n, Fbar, 2, N, 0, s) != cudaSuccess) return FE2_ERR_CUDA;
     if (launch_factor<float>(tab, ids, n, ws, rve_status, L.kd, L.nr, s) != cudaSuccess) return FE2_ERR_CUDA;

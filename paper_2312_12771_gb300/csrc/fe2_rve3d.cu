@@ -1,0 +1,578 @@
+// 3D (Hex8) RVE block and the wide-band factorisation.
+//
+// S1 - S3 for trilinear Hex8 elements with 2x2x2 Gauss points (Section 2.2,
+// Eqs. (microdefo), (microGrad); Section 3, Eqs. (linSys3), (linSys4);
+// Section 4, Eqs. (discreteSys_K/D/L)); periodic reduction with the corner
+// pinned (Section 2.2, Eq. (Con)(iii); Section 5.2).  Constitutive laws in 3D:
+// H = cof F (Section 2.1), P = mu F + (kappa (J-1) - mu/J) H and
+// A = mu I + (mu/J^2 + kappa) H (x) H + (kappa (J-1) - mu/J) dH/dF for the
+// Neo-Hooke law of Eq. (MR) with beta = 0; isotropic linear elasticity.
+//
+// k_band_factor_gw: the band Cholesky of S4 for bands too wide for a
+// shared-memory window (3D: kd = 3 (2N^2 + 2N + 2) + 2, i.e. 440 at N = 8):
+// the sliding window lives in the launch slot's global workspace (L2), the
+// panel and the right-hand-side rows stay in shared memory.  Same panel
+// algorithm as the shared-memory kernel, any dimension.
+#include "fe2_internal.cuh"
+
+namespace fe2 {
+
+namespace {
+
+constexpr double kG = 0.57735026918962576451;  // 1/sqrt(3)
+
+// dN_a/dX_J at Gauss point q of a cube element of side h (a, q = bx + 2 by + 4 bz)
+__device__ __forceinline__ double grad3(int q, int a, int J, double h) {
+    double v = 1.0 / (4.0 * h);
+    for (int K = 0; K < 3; ++K) {
+        const double s = ((a >> K) & 1) ? 1.0 : -1.0;
+        const double xi = ((q >> K) & 1) ? kG : -kG;
+        v *= (K == J) ? s : (1.0 + s * xi);
+    }
+    return v;
+}
+
+__device__ void consti3(const double* m, const double F[3][3], double P[3][3], double A[3][3][3][3]) {
+    const int model = (int)m[0];
+    if (model == FE2_MODEL_LINEAR) {
+        const double E = m[1], nu = m[2];
+        const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)), mu = E / (2.0 * (1.0 + nu));
+        double eps[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int J = 0; J < 3; ++J) eps[i][J] = 0.5 * (F[i][J] + F[J][i]) - (i == J ? 1.0 : 0.0);
+        const double tr = eps[0][0] + eps[1][1] + eps[2][2];
+        for (int i = 0; i < 3; ++i)
+            for (int J = 0; J < 3; ++J) P[i][J] = (i == J ? lam * tr : 0.0) + 2.0 * mu * eps[i][J];
+        for (int i = 0; i < 3; ++i)
+            for (int J = 0; J < 3; ++J)
+                for (int k = 0; k < 3; ++k)
+                    for (int L = 0; L < 3; ++L)
+                        A[i][J][k][L] = (i == J && k == L ? lam : 0.0) +
+                                        mu * ((i == k && J == L ? 1.0 : 0.0) + (i == L && J == k ? 1.0 : 0.0));
+        return;
+    }
+    const double mu = m[1], kappa = m[2];
+    double H[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, J1 = (J + 1) % 3, J2 = (J + 2) % 3;
+            H[i][J] = F[i1][J1] * F[i2][J2] - F[i1][J2] * F[i2][J1];
+        }
+    const double Jd = F[0][0] * H[0][0] + F[0][1] * H[0][1] + F[0][2] * H[0][2];
+    const double s = kappa * (Jd - 1.0) - mu / Jd, c = mu / (Jd * Jd) + kappa;
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J) P[i][J] = mu * F[i][J] + s * H[i][J];
+    for (int i = 0; i < 3; ++i)
+        for (int J = 0; J < 3; ++J) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, J1 = (J + 1) % 3, J2 = (J + 2) % 3;
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) {
+                    // dH_iJ / dF_kL with H_iJ = F_i1J1 F_i2J2 - F_i1J2 F_i2J1
+                    double dH = 0.0;
+                    if (k == i1 && L == J1) dH += F[i2][J2];
+                    if (k == i2 && L == J2) dH += F[i1][J1];
+                    if (k == i1 && L == J2) dH -= F[i2][J1];
+                    if (k == i2 && L == J1) dH -= F[i1][J2];
+                    A[i][J][k][L] = (i == k && J == L ? mu : 0.0) + c * H[i][J] * H[k][L] + s * dH;
+                }
+        }
+}
+
+// S1 + S2: one thread per (element, local node a); rows of a written to the
+// element workspace [comp][nn]: per a: kr[b][i][k] (72), f[i] (3), kM[i][kL] (27);
+// after the 8 row groups: K_MM (81) and Pint (9) of the element (a == 0 only).
+__global__ void __launch_bounds__(128) k_assemble_elems3(const RveDev* __restrict__ tab, const int* __restrict__ ids,
+                                                         const double* __restrict__ Fbar) {
+    const RveDev r = tab[ids[blockIdx.y]];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 8 * r.nn) return;
+    const int e = t >> 3, a = t & 7, N = r.N, nn = r.nn;
+    const int ex = e % N, ey = (e / N) % N, ez = e / (N * N);
+    const double h = 1.0 / N, wq = 0.125 * h * h * h;
+    const double* m = r.mat + 4 * r.phase[e];
+    double Fb[9];
+    for (int k = 0; k < 9; ++k) Fb[k] = Fbar[9 * blockIdx.y + k];
+    double we[8][3];
+    for (int b = 0; b < 8; ++b) {
+        const int i = (ex + (b & 1)) % N, j = (ey + ((b >> 1) & 1)) % N, k = (ez + (b >> 2)) % N;
+        const int q = fold_pos(i, N) + N * fold_pos(j, N) + N * N * fold_pos(k, N);
+        for (int c = 0; c < 3; ++c) we[b][c] = (q == 0 || r.zero_w) ? 0.0 : r.w[3 * (q - 1) + c];
+    }
+    double kr[8][3][3], f[3], kM[3][9], mm[90];
+    for (int b = 0; b < 8; ++b)
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) kr[b][i][k] = 0.0;
+    for (int i = 0; i < 3; ++i) {
+        f[i] = 0.0;
+        for (int kL = 0; kL < 9; ++kL) kM[i][kL] = 0.0;
+    }
+    if (a == 0)
+        for (int k = 0; k < 90; ++k) mm[k] = 0.0;
+    for (int q = 0; q < 8; ++q) {
+        double G[8][3];
+        for (int b = 0; b < 8; ++b)
+            for (int J = 0; J < 3; ++J) G[b][J] = grad3(q, b, J, h);
+        double F[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int J = 0; J < 3; ++J) {
+                double v = Fb[3 * i + J];
+                for (int b = 0; b < 8; ++b) v += we[b][i] * G[b][J];
+                F[i][J] = v;
+            }
+        double P[3][3], A[3][3][3][3];
+        consti3(m, F, P, A);
+        for (int i = 0; i < 3; ++i) {
+            f[i] += wq * (P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2]);
+            for (int k = 0; k < 3; ++k)
+                for (int L = 0; L < 3; ++L) {
+                    const double tv = G[a][0] * A[i][0][k][L] + G[a][1] * A[i][1][k][L] + G[a][2] * A[i][2][k][L];
+                    kM[i][3 * k + L] += wq * tv;
+                    for (int b = 0; b < 8; ++b) kr[b][i][k] += wq * tv * G[b][L];
+                }
+        }
+        if (a == 0) {
+            for (int iJ = 0; iJ < 9; ++iJ)
+                for (int kL = 0; kL < 9; ++kL) mm[9 * iJ + kL] += wq * A[iJ / 3][iJ % 3][kL / 3][kL % 3];
+            for (int iJ = 0; iJ < 9; ++iJ) mm[81 + iJ] += wq * P[iJ / 3][iJ % 3];
+        }
+    }
+    const int RC = elem_row_comps(3);
+    double* E = r.elem;
+    int c0 = a * RC;
+    for (int b = 0; b < 8; ++b)
+        for (int i = 0; i < 3; ++i)
+            for (int k = 0; k < 3; ++k) E[(size_t)(c0++) * nn + e] = kr[b][i][k];
+    for (int i = 0; i < 3; ++i) E[(size_t)(c0++) * nn + e] = f[i];
+    for (int i = 0; i < 3; ++i)
+        for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0++) * nn + e] = kM[i][kL];
+    if (a == 0)
+        for (int k = 0; k < 90; ++k) E[(size_t)(8 * RC + k) * nn + e] = mm[k];
+}
+
+// S3: node-row gather through the periodic map (one CTA per RVE).  Each node row
+// is owned by one thread (deterministic order); K_MM and Pint are summed over
+// elements by one thread per component.
+__global__ void __launch_bounds__(256) k_reduce3(const RveDev* __restrict__ tab, const int* __restrict__ ids) {
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N, nn = r.nn, RC = elem_row_comps(3);
+    const double* E = r.elem;
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+        const int i = unfold_pos(q % N, N), j = unfold_pos((q / N) % N, N), k = unfold_pos(q / (N * N), N);
+        double* st = r.stencil;
+        for (int comp = 0; comp < 243; ++comp) st[(size_t)comp * nn + q] = 0.0;
+        double f[3] = {0.0, 0.0, 0.0}, kM[3][9];
+        for (int c = 0; c < 3; ++c)
+            for (int kL = 0; kL < 9; ++kL) kM[c][kL] = 0.0;
+        for (int a = 0; a < 8; ++a) {
+            const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
+            const int e = (i - ax + N) % N + N * ((j - ay + N) % N) + N * N * ((k - az + N) % N);
+            int c0 = a * RC;
+            for (int b = 0; b < 8; ++b) {
+                const int off = ((b & 1) - ax + 1) + 3 * (((b >> 1) & 1) - ay + 1) + 9 * ((b >> 2) - az + 1);
+                for (int c = 0; c < 3; ++c)
+                    for (int c2 = 0; c2 < 3; ++c2) st[(size_t)((off * 3 + c) * 3 + c2) * nn + q] += E[(size_t)(c0++) * nn + e];
+            }
+            for (int c = 0; c < 3; ++c) f[c] += E[(size_t)(c0++) * nn + e];
+            for (int c = 0; c < 3; ++c)
+                for (int kL = 0; kL < 9; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
+        }
+        if (q != 0) {
+            for (int c = 0; c < 3; ++c) {
+                const int dof = 3 * (q - 1) + c;
+                for (int kL = 0; kL < 9; ++kL) r.rhs[(size_t)kL * r.nm + dof] = kM[c][kL];
+                r.rhs[(size_t)9 * r.nm + dof] = f[c];
+            }
+        }
+    }
+    if (threadIdx.x < 90) {
+        double s = 0.0;
+        for (int e = 0; e < nn; ++e) s += E[(size_t)(8 * RC + threadIdx.x) * nn + e];
+        if (threadIdx.x < 81)
+            r.KMM[threadIdx.x] = s;
+        else
+            r.Pint[threadIdx.x - 81] = s;
+    }
+}
+
+// FP64 residual R = [K_mM | r_m] - K_mm X (3D stencil, 27 neighbour blocks)
+__global__ void __launch_bounds__(128) k_residual3(const RveDev* __restrict__ tab, const int* __restrict__ ids,
+                                                   Workspace ws, const int* __restrict__ active) {
+    if (active && !active[blockIdx.y]) return;
+    const RveDev r = tab[ids[blockIdx.y]];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= r.nn || q == 0) return;
+    const int nn = r.nn, nm = r.nm;
+    double* R = (double*)(ws.base + blockIdx.y * ws.stride + ws.offR);
+    double acc[3][10];
+    for (int c = 0; c < 3; ++c)
+        for (int rr = 0; rr < 10; ++rr) acc[c][rr] = 0.0;
+    for (int off = 0; off < 27; ++off) {
+        const int qn = r.nbr[q * 27 + off];
+        if (qn == 0) continue;
+        for (int c = 0; c < 3; ++c)
+            for (int c2 = 0; c2 < 3; ++c2) {
+                const double kv = r.stencil[(size_t)((off * 3 + c) * 3 + c2) * nn + q];
+                for (int rr = 0; rr < 10; ++rr) acc[c][rr] += kv * r.X[(size_t)rr * nm + 3 * (qn - 1) + c2];
+            }
+    }
+    for (int c = 0; c < 3; ++c) {
+        const int dof = 3 * (q - 1) + c;
+        for (int rr = 0; rr < 10; ++rr) R[(size_t)rr * nm + dof] = r.rhs[(size_t)rr * nm + dof] - acc[c][rr];
+    }
+}
+
+// S6 in 3D: G1 = rhs^T X (9 x 10), G2 = X_M^T R (9 x 10); corrected Schur.
+__global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, const int* __restrict__ ids,
+                                                Workspace ws, int corrected, double* __restrict__ sigma,
+                                                double* __restrict__ Cbar, int* __restrict__ status,
+                                                double* __restrict__ err, const double* __restrict__ tol,
+                                                int* __restrict__ redo, int only_flagged, int final_sweep) {
+    __shared__ double red[256];
+    __shared__ double tot[180];
+    if (only_flagged && !redo[blockIdx.x]) return;
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int nm = r.nm;
+    const double* R = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
+    for (int v = 0; v < (corrected ? 180 : 90); ++v) {
+        const int which = v / 90, a = (v % 90) / 10, b = v % 10;
+        double acc = 0.0;
+        for (int m = threadIdx.x; m < nm; m += blockDim.x)
+            acc += which == 0 ? r.rhs[(size_t)a * nm + m] * r.X[(size_t)b * nm + m]
+                              : r.X[(size_t)a * nm + m] * R[(size_t)b * nm + m];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) tot[v] = red[0];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double cn = 0.0, corr = 0.0;
+        int bad = 0;
+        for (int a = 0; a < 9; ++a) {
+            for (int b = 0; b < 9; ++b) {
+                double v = r.KMM[a * 9 + b] - tot[a * 10 + b];
+                if (corrected) {
+                    v -= tot[90 + a * 10 + b];
+                    corr += tot[90 + a * 10 + b] * tot[90 + a * 10 + b];
+                }
+                cn += v * v;
+                bad |= !isfinite(v);
+                Cbar[(size_t)blockIdx.x * 81 + a * 9 + b] = v;
+            }
+            double sg = r.Pint[a] - tot[a * 10 + 9];
+            if (corrected) sg -= tot[90 + a * 10 + 9];
+            bad |= !isfinite(sg);
+            sigma[(size_t)blockIdx.x * 9 + a] = sg;
+        }
+        const double e = corrected ? corr / fmax(cn, 1e-300) : 0.0;
+        if (err) err[blockIdx.x] = e;
+        if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
+        const bool over = corrected && !(e <= *tol);
+        if (redo) redo[blockIdx.x] = (over && status[blockIdx.x] == FE2_OK) ? 1 : 0;
+        if (final_sweep && over && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NO_CONV;
+    }
+}
+
+__device__ __forceinline__ int wrapS3(int x, int S) { return x >= S ? x - S : x; }
+
+template <typename T>
+struct GwLayout {
+    int kd, S, LDW, KR, KP, nr, nblk;
+    size_t offBw, offDinv, offBlk, total;
+    __host__ __device__ void init(int kd_, int nr_) {
+        kd = kd_;
+        nr = nr_;
+        S = kd + NB;
+        LDW = kd + 1;
+        KR = kd + nr;
+        KP = (KR + 31) & ~31;
+        const int RB = KP / 32, CB = (kd + 31) / 32;
+        nblk = 0;
+        for (int K = 0; K < CB; ++K) nblk += RB - K;
+        size_t o = (size_t)NB * KP * sizeof(T);  // Pn
+        offBw = o;
+        o += (size_t)nr * S * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offDinv = o;
+        o += NB * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offBlk = o;
+        o += (size_t)nblk * 4;
+        total = (o + 15) & ~(size_t)15;
+    }
+};
+
+template <typename T, int C>
+__device__ __forceinline__ void gw_row_steps(T (&v)[NB], const T* __restrict__ W, int base, int S, int LDW, int kd,
+                                             const T* __restrict__ dinv) {
+    if constexpr (C < NB) {
+        const T* Lc = W + (size_t)(base + C >= S ? base + C - S : base + C) * LDW;
+        v[C] *= dinv[C];
+#pragma unroll
+        for (int c2 = C + 1; c2 < NB; ++c2)
+            if (c2 - C <= kd) v[c2] -= v[C] * Lc[c2 - C];
+        gw_row_steps<T, C + 1>(v, W, base, S, LDW, kd, dinv);
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void gw_chol_steps(T (&a)[NB], int lane, T* __restrict__ dinv, int& bad) {
+    if constexpr (K < NB) {
+        T piv = __shfl_sync(0xffffffffu, a[K], K);
+        const bool badk = !(piv > T(0));
+        if (badk) piv = T(1);
+        const T dk = rsqrt(piv);
+        if (lane == K)
+            a[K] = piv * dk;
+        else if (lane > K)
+            a[K] *= dk;
+        if (lane == 0) dinv[K] = dk;
+        bad |= badk;
+#pragma unroll
+        for (int c = K + 1; c < NB; ++c) {
+            const T lck = __shfl_sync(0xffffffffu, a[K], c);
+            if (lane >= c) a[c] -= a[K] * lck;
+        }
+        gw_chol_steps<T, K + 1>(a, lane, dinv, bad);
+    }
+}
+
+// Column c (< nm) of K_mm (rows >= c) from the node-row stencil (any dimension).
+template <typename T>
+__device__ __forceinline__ void gw_load_column(T* __restrict__ Wc, int LDW, int c, const RveDev& r) {
+    const int d = r.d, ns = d == 2 ? 9 : 27, nn = r.nn;
+    const int q = c / d + 1, cc = c - d * (q - 1);
+    for (int off = 0; off < ns; ++off) {
+        const int qn = r.nbr[q * ns + off];
+        if (qn == 0) continue;
+        for (int c2 = 0; c2 < d; ++c2) {
+            const int row = d * (qn - 1) + c2;
+            if (row >= c) Wc[row - c] += (T)r.stencil[(size_t)((off * d + cc) * d + c2) * nn + q];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* __restrict__ tab,
+                                                                 const int* __restrict__ ids, Workspace ws,
+                                                                 int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RveDev r = tab[ids[blockIdx.x]];
+    GwLayout<T> lay;
+    lay.init(r.kd, r.nr);
+    const int kd = lay.kd, S = lay.S, LDW = lay.LDW, KR = lay.KR, KP = lay.KP, nr = lay.nr;
+    const int nmp = r.nm_pad, nm = r.nm;
+    T* Pn = (T*)smem;
+    T* Bw = (T*)(smem + lay.offBw);
+    T* dinv = (T*)(smem + lay.offDinv);
+    unsigned* blk = (unsigned*)(smem + lay.offBlk);
+    __shared__ int s_bad;
+    char* slot = ws.base + blockIdx.x * ws.stride;
+    T* Lg = (T*)slot;
+    T* Yg = (T*)(slot + ws.offY);
+    T* Dg = (T*)(slot + ws.offD);
+    T* W = (T*)(slot + ws.offWin);  // the sliding window, [S][LDW], in global memory
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    if (tid == 0) {
+        s_bad = 0;
+        const int RB = KP / 32, CB = (kd + 31) / 32;
+        int x = 0;
+        for (int K = 0; K < CB; ++K)
+            for (int I = K; I < RB; ++I) blk[x++] = (unsigned)I | ((unsigned)K << 16);
+    }
+    for (int k = tid; k < NB * KP; k += blockDim.x) Pn[k] = T(0);
+    for (size_t k = tid; k < (size_t)S * LDW; k += blockDim.x) W[k] = T(0);
+    for (int k = tid; k < nr * S; k += blockDim.x) {
+        const int rr = k / S, c = k - rr * S;
+        Bw[k] = (c < nm && c < kd) ? (T)r.rhs[(size_t)rr * nm + c] : T(0);
+    }
+    __syncthreads();
+    for (int c = tid; c < min(kd, nmp); c += blockDim.x) {
+        T* Wc = W + (size_t)c * LDW;
+        if (c < nm)
+            gw_load_column<T>(Wc, LDW, c, r);
+        else
+            Wc[0] = T(1);
+    }
+    __syncthreads();
+    int base = 0;
+    for (int j0 = 0; j0 < nmp; j0 += NB) {
+        // 1: diagonal block (warp 0) / entering columns [j0+kd, j0+kd+NB) (other warps)
+        if (warp == 0) {
+            T a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS3(base + c, S) * LDW + (lane - c)] : T(0);
+            int badb = 0;
+            gw_chol_steps<T, 0>(a, lane, dinv, badb);
+            if (lane == 0 && badb) s_bad = 1;
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c <= lane && lane - c <= kd) W[(size_t)wrapS3(base + c, S) * LDW + (lane - c)] = a[c];
+            Dg[j0 + lane] = dinv[lane];
+        } else {
+            const int nt = blockDim.x - 32, t0 = tid - 32;
+            for (int x = warp - 1; x < NB; x += nwarps - 1) {
+                T* Wc = W + (size_t)wrapS3(base + kd + x, S) * LDW;
+                for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+            for (int x = t0; x < NB; x += nt) {
+                const int cn = j0 + kd + x;
+                T* Wc = W + (size_t)wrapS3(base + kd + x, S) * LDW;
+                if (cn < nm)
+                    gw_load_column<T>(Wc, LDW, cn, r);
+                else if (cn < nmp)
+                    Wc[0] = T(1);
+            }
+            for (int p = t0; p < nr * NB; p += nt) {
+                const int rr = p / NB, x = p - rr * NB, cn = j0 + kd + x;
+                Bw[rr * S + wrapS3(base + kd + x, S)] = (cn < nm) ? (T)r.rhs[(size_t)rr * nm + cn] : T(0);
+            }
+        }
+        __syncthreads();
+        // 2: panel rows (L21, y)
+        for (int t = tid; t < KR; t += blockDim.x) {
+            T v[NB];
+            if (t < kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = NB + t - c;
+                    v[c] = (off <= kd) ? W[(size_t)wrapS3(base + c, S) * LDW + off] : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) v[c] = Bw[(t - kd) * S + wrapS3(base + c, S)];
+            }
+            gw_row_steps<T, 0>(v, W, base, S, LDW, kd, dinv);
+#pragma unroll
+            for (int c = 0; c < NB; ++c) Pn[c * KP + t] = v[c];
+            if (t < kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = NB + t - c;
+                    if (off <= kd) W[(size_t)wrapS3(base + c, S) * LDW + off] = v[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) Bw[(t - kd) * S + wrapS3(base + c, S)] = v[c];
+            }
+        }
+        __syncthreads();
+        // 3: rank-NB update (32x32 warp blocks) and stream out the finished panel
+        {
+            const int rg = lane >> 3, cg = lane & 7;
+            for (int b = warp; b < lay.nblk; b += nwarps) {
+                const unsigned bv = blk[b];
+                const int I = bv & 0xffff, K = bv >> 16;
+                const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
+                T acc[8][4];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+                for (int c = 0; c < NB; ++c) {
+                    const T* pc = Pn + c * KP;
+                    T av[8], bb[4];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) av[u] = pc[r0 + u];
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + w];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bb[w];
+                }
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const int t2 = q0 + w;
+                    if (t2 >= kd) continue;
+                    const int sl = wrapS3(base + NB + t2, S);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int t1 = r0 + u;
+                        if (t1 < t2 || t1 >= KR) continue;
+                        if (t1 < kd)
+                            W[(size_t)sl * LDW + (t1 - t2)] -= acc[u][w];
+                        else
+                            Bw[(t1 - kd) * S + sl] -= acc[u][w];
+                    }
+                }
+            }
+            const int LDL = kd + 1;
+            for (int c = warp; c < NB; c += nwarps) {
+                const T* Wc = W + (size_t)wrapS3(base + c, S) * LDW;
+                T* dst = Lg + (size_t)(j0 + c) * LDL;
+                for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
+            }
+            for (int k = tid; k < nr * NB; k += blockDim.x) {
+                const int rr = k / NB, c = k - rr * NB;
+                Yg[(size_t)rr * nmp + j0 + c] = Bw[rr * S + wrapS3(base + c, S)];
+            }
+        }
+        __syncthreads();
+        base = wrapS3(base + NB, S);
+    }
+    if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
+}
+
+}  // namespace
+
+cudaError_t launch_assemble_elems3(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
+                                   cudaStream_t s) {
+    dim3 grid((8 * maxN * maxN * maxN + 127) / 128, n);
+    k_assemble_elems3<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce3(const RveDev* tab, const int* ids, int n, cudaStream_t s) {
+    k_reduce3<<<n, 256, 0, s>>>(tab, ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual3(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn, const int* active,
+                             cudaStream_t s) {
+    dim3 grid((maxnn + 127) / 128, n);
+    k_residual3<<<grid, 128, 0, s>>>(tab, ids, ws, active);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_schur3(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
+                          double* Cbar, int* status, double* err, const double* tol, int* redo, cudaStream_t s,
+                          int refine_sweep) {
+    k_schur3<<<n, 256, 0, s>>>(tab, ids, ws, corrected, sigma, Cbar, status, err, tol, redo,
+                               refine_sweep == 1 || refine_sweep == 2, refine_sweep >= 2);
+    return cudaGetLastError();
+}
+
+size_t factor_gw_smem_bytes(int kd, int nr, bool fp64) {
+    if (fp64) {
+        GwLayout<double> l;
+        l.init(kd, nr);
+        return l.total;
+    }
+    GwLayout<float> l;
+    l.init(kd, nr);
+    return l.total;
+}
+
+template <typename T>
+cudaError_t launch_factor_gw(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                             int maxnr, cudaStream_t s) {
+    GwLayout<T> lay;
+    lay.init(maxkd, maxnr);
+    cudaError_t e = cudaFuncSetAttribute(k_band_factor_gw<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+    if (e != cudaSuccess) return e;
+    k_band_factor_gw<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_factor_gw<float>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
+template cudaError_t launch_factor_gw<double>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
+
+}  // namespace fe2

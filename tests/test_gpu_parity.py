@@ -345,3 +345,68 @@ def test_serving_results_equal_alone_and_in_the_mix(torch):
         assert np.array_equal(res["sigma"][k], s1.cpu().numpy()[0])
         assert np.array_equal(res["Cbar"][k], C1.cpu().numpy()[0])
     srv.close()
+
+
+def ctx3(torch, precision, **kw):
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    return Fe2Context(dim=3, precision=precision, **kw)
+
+
+def check3(batch, sig, Cb, st, idx, tol, w=None):
+    sig, Cb, st = sig.cpu().numpy(), Cb.cpu().numpy(), st.cpu().numpy()
+    worst = 0.0
+    for k in idx:
+        assert st[k] == 0, f"rve {k} status {st[k]}"
+        ref = O.rve_solve(int(batch.N[k]), 3, batch.phase[k], batch.mat[k], batch.Fbar[k])
+        eC = O.rel_err(Cb[k], ref["Cbar"])
+        floor = np.linalg.norm(ref["Cbar"]) * np.linalg.norm(batch.Fbar[k] - np.eye(3))
+        eS = O.rel_err(sig[k], ref["sigma_eff"], floor)
+        worst = max(worst, eC, eS)
+        assert eC <= tol and eS <= tol, (k, eC, eS)
+    return worst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [3, 4])
+def test_hex8_parity_small(torch, precision, N):
+    """Hex8 RVEs (3D, periodic, corner pinned): NH sphere inclusion under shear
+    and linear random phases, against the oracle."""
+    b = W.sphere_batch(3, N, gamma=0.05)
+    rng = np.random.default_rng(N)
+    lin = W.RveBatch(3, np.full(3, N, np.int32), [(rng.random(N ** 3) < 0.4).astype(np.uint8) for _ in range(3)],
+                     np.repeat(W.linear_mat(1.0, 0.3, 8.0, 0.25)[None], 3, 0),
+                     np.repeat((np.eye(3) + 1e-3 * rng.standard_normal((3, 3)))[None], 3, 0))
+    for batch in (b, lin):
+        ctx = ctx3(torch, precision)
+        ids = ctx.register_batch(batch)
+        sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(batch.Fbar, device="cuda"))
+        torch.cuda.synchronize()
+        check3(batch, sig, Cb, st, range(batch.nrve), TOL[precision])
+        ctx.close()
+
+
+def test_hex8_homogeneous_recovers_local_law(torch):
+    N = 4
+    m = np.array([[1, 1.3, 11.0, 0], [1, 1.3, 11.0, 0]])
+    F = np.eye(3) + np.array([[0.05, 0.02, -0.01], [0.0, -0.03, 0.04], [0.01, 0.0, 0.02]])
+    b = W.RveBatch(3, np.array([N], np.int32), [np.zeros(N ** 3, np.uint8)], m[None], F[None])
+    ctx = ctx3(torch, "mixed")
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    P, A = O.material(F[None], m[0], 3)
+    assert np.abs(Cb.cpu().numpy()[0] - A[0].reshape(9, 9)).max() <= 1e-10 * np.abs(A).max()
+    assert np.abs(sig.cpu().numpy()[0] - P[0].ravel()).max() <= 1e-10 * np.abs(P).max()
+
+
+def test_hex8_config5_rve_sampled(torch):
+    """The 3D workload RVE: 8^3 Hex8, centred sphere (vf 0.2), mu_i/mu_m = 10,
+    simple shear gamma = 0.02; mixed path against the oracle on sampled RVEs."""
+    b = W.sphere_batch(32, 8, gamma=0.02)
+    b.Fbar = W.perturbed_F(b, 9, 2e-3)
+    ctx = ctx3(torch, "mixed")
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    w = check3(b, sig, Cb, st, [0, 17, 31], TOL["mixed"])
+    print(f"hex8 8^3 worst sampled rel err {w:.3e}")
