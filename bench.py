@@ -39,6 +39,22 @@ METRIC = "RVE solves/s (sigma_eff + Cbar per macro Gauss point)"
 UNIT = "RVE solves/s"
 N_RVE, N_MESH = 4096, 32
 SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
+# DRAM bytes per RVE of the FP32 band factor from one ncu capture (304 RVEs,
+# profiles/band_factor_fp32_fiber32_304rves.md); valid only for the kernel
+# source it was taken on (sha1 prefix), else the bench reports traffic = null.
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "4b0037a9bfe8", "bytes": 406.0e6 / 304}
+
+
+def factor_traffic(nrve):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2312_12771_gb300", "csrc", "fe2_factor.cu")
+    try:
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    except OSError:
+        return None
+    if h != FACTOR_TRAFFIC_PER_RVE["sha1"]:
+        return None
+    return round(FACTOR_TRAFFIC_PER_RVE["bytes"] * nrve)
 
 
 def peaks():
@@ -307,6 +323,65 @@ def run_serving(args, dev):
     return out
 
 
+def run_hex8(args):
+    """Config-5 style: 8^3 Hex8 RVEs, centred sphere vf 0.2, mu_i/mu_m = 10,
+    kappa = 10 mu, simple shear gamma = 0.02 (first load step of 5); mixed path."""
+    import torch
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    b = W.sphere_batch(args.hex8_rves, 8, gamma=0.02)
+    b.Fbar = W.perturbed_F(b, 9, 1e-3)
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=1)
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    outs = ctx._outs(b.nrve)
+    for _ in range(2):
+        ctx.rve_solve(ids, F, out=outs)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    steps = 3
+    for _ in range(steps):
+        ctx.rve_solve(ids, F, out=outs)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = ctx.profile_read()
+    out = {"workload": f"{b.nrve} Hex8 8^3 RVEs (n_m = 1533, kd = 440), sphere vf 0.2, NH, shear 0.02",
+           "solves_per_s": round(b.nrve / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+           "status_nonzero": int((outs[2] != 0).sum().item()),
+           "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof.items()}}
+    ctx.close()
+    return out
+
+
+def run_nh_newton(args):
+    """Config-3 style: macro 32x32 Q4 x 2x2 Gauss = 4096 NH RVEs (32x32, 1-6 random
+    inclusions, mu_i/mu_m = 20, kappa = 10 mu), stretch diag(1.2, 1) in 10 load
+    steps, full monolithic Newton (micro and macro)."""
+    import torch
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    nx = args.nh_macro
+    X, conn, fixed = macro_mesh(nx, nx)
+    b = W.inclusion_batch(4 * nx * nx, 32, stretch=1.0)
+    ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    log = fe.run(np.diag([1.2, 1.0]), args.nh_steps, predictor=True, tol_macro=1e-8, tol_micro=1e-8)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    solves = sum(it + 1 for it in log.iters) * fe.ngp
+    out = {"workload": f"macro {nx}x{nx} Q4 x 4 Gauss = {fe.ngp} NH RVEs 32x32, stretch 1.2 in {args.nh_steps} steps "
+                       "(affine predictor per load step)",
+           "newton_iterations_per_step": log.iters, "rve_solves": solves, "wall_s": round(wall, 3),
+           "solves_per_s": round(solves / wall, 1),
+           "final_macro_residual": log.history[-1][2], "final_max_micro_residual": log.history[-1][3]}
+    ctx.close()
+    return out
+
+
 def max_over_ranks(v, dist):
     if not dist:
         return v
@@ -335,6 +410,10 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Hex8 and NH-Newton legs")
+    ap.add_argument("--hex8-rves", type=int, default=4096)
+    ap.add_argument("--nh-macro", type=int, default=32)
+    ap.add_argument("--nh-steps", type=int, default=10)
     ap.add_argument("--serve-rves", type=int, default=4096)
     ap.add_argument("--serve-batch", type=int, default=512)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
@@ -386,6 +465,13 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     batch, R, pk = run_gpu(args, rank, world, dist)
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton)):
+            try:
+                extra[key] = fn(args)
+            except Exception as exc:  # reported, not fatal: the headline leg is already measured
+                extra[key] = {"error": f"{type(exc).__name__}: {exc}"}
     serving = None
     if rank == 0 and not args.no_serve:
         import torch
@@ -411,7 +497,8 @@ def main():
     roof = dict(kern[dom]["roofline"] or {}) if dom else {}
     if roof:
         roof["kernel"] = dom
-        roof["traffic"] = None
+        roof["traffic"] = factor_traffic(args.rves) if dom == "band_factor_fp32" else None
+        roof["traffic_unit"] = "bytes per launch (ncu capture of 304 RVEs scaled by RVE count)"
     kern64 = {}
     for name, (tms, cnt) in R["fp64"]["prof"].items():
         avg = tms / max(cnt, 1)
@@ -432,6 +519,7 @@ def main():
                     "h2d_bytes_per_step": mx["h2d"], "d2h_bytes_per_step": mx["d2h"]}}
     if serving is not None:
         line["serving"] = serving
+    line.update(extra)
     if pool is not None:
         nproc = os.cpu_count() or 1
         idx = list(np.random.default_rng(1).choice(batch.nrve, size=args.cpu_sample, replace=False))

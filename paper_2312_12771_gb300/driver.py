@@ -71,8 +71,16 @@ class MonolithicFE2:
                     sigma_eff=sig.cpu().numpy().copy(), Cbar=Cb.cpu().numpy().copy(),
                     status=st.cpu().numpy().copy(), err=err.cpu().numpy().copy())
 
-    def load_step(self, Fk, step, tol_macro=1e-9, tol_micro=1e-9, maxit=25, log=None):
+    def load_step(self, Fk, step, tol_macro=1e-9, tol_micro=1e-9, maxit=25, log=None, F_prev=None):
+        """One load step.  The previous converged state is the start value
+        (Section 5.2); with ``F_prev`` given, the affine increment
+        (Fk - F_prev) X is added to every node first (affine predictor), so
+        that the Dirichlet increment does not distort only the boundary
+        elements of a fine macro mesh."""
         ctx = self.ctx
+        if F_prev is not None:
+            q = ctx.macro_get_positions() + self.X @ (np.asarray(Fk) - np.asarray(F_prev)).T
+            ctx.macro_set_positions(q)
         q_fixed = self.X @ np.asarray(Fk).T
         ctx.macro_set_positions(q_fixed, which=self.fixed)
         sig, Cb, st, err = self.outs
@@ -102,10 +110,12 @@ class MonolithicFE2:
             ctx.macro_step(self.ids, self.dFbar)
         raise RuntimeError("macro Newton did not converge")
 
-    def run(self, F_final, n_steps, **kw):
+    def run(self, F_final, n_steps, predictor=False, **kw):
         log = NewtonLog()
         F_final = np.asarray(F_final, float)
+        F_prev = np.eye(2)
         for k in range(1, n_steps + 1):
             Fk = np.eye(2) + (k / n_steps) * (F_final - np.eye(2))
-            self.load_step(Fk, k, log=log, **kw)
+            self.load_step(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)
+            F_prev = Fk
         return log

@@ -410,3 +410,23 @@ def test_hex8_config5_rve_sampled(torch):
     torch.cuda.synchronize()
     w = check3(b, sig, Cb, st, [0, 17, 31], TOL["mixed"])
     print(f"hex8 8^3 worst sampled rel err {w:.3e}")
+
+
+def test_monolithic_newton_affine_predictor(torch):
+    """With the affine predictor the converged state is the same fixed point
+    (the predictor only changes the start value of each load step)."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh
+    N = 6
+    X, conn, fixed = macro_mesh(2, 2)
+    b = W.inclusion_batch(16, N, stretch=1.0)
+    Ff = np.diag([1.1, 1.0])
+    states = []
+    for pred in (False, True):
+        ctx = ctx_for(torch, "fp64")
+        fe = MonolithicFE2(ctx, X, conn, fixed, b)
+        fe.run(Ff, 2, predictor=pred, tol_macro=1e-11, tol_micro=1e-11)
+        states.append(fe.state())
+        ctx.close()
+    for k in range(16):
+        assert O.rel_err(states[1]["Pbar"][k], states[0]["Pbar"][k]) <= 1e-9
+        assert O.rel_err(states[1]["Cbar"][k], states[0]["Cbar"][k]) <= 1e-9
