@@ -256,6 +256,15 @@ int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma,
                     double* latency_ms);
 int fe2_server_pending(const fe2_server* srv);
 
+/*
+ * Self-test of the bounded device waits used by the TMA streams of the solve
+ * kernels (no counterpart in the paper): one kernel waits on an mbarrier that
+ * nothing arrives on; after about a second (2^31 SM cycles) the wait gives up
+ * and status [device] int[1] receives FE2_ERR_TIMEOUT.  The context stays
+ * usable.  Failure detection is exercised this way without faulting the GPU.
+ */
+fe2_status fe2_selftest_wait_timeout(fe2_ctx* ctx, int* status);
+
 /* Number of kernel launches the context has issued so far. */
 long long fe2_launch_count(const fe2_ctx* ctx);
 

@@ -539,6 +539,12 @@ fe2_status fe2_sync(fe2_ctx* ctx) {
 
 long long fe2_launch_count(const fe2_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
+fe2_status fe2_selftest_wait_timeout(fe2_ctx* ctx, int* status) {
+    if (!ctx || !status) return FE2_ERR_ARG;
+    CK(launch_selftest_wait(status, ctx->stream));
+    return FE2_OK;
+}
+
 fe2_status fe2_profile(fe2_ctx* ctx, int enable) {
     if (!ctx) return FE2_ERR_ARG;
     drain_timing(ctx);

@@ -100,6 +100,7 @@ cudaError_t launch_factor_gw(const RveDev* tab, const int* ids, int n, Workspace
 size_t factor_gw_smem_bytes(int kd, int nr, bool fp64);
 size_t factor_smem_bytes(int kd, int nr, bool fp64);
 size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64);  // refinement solve (the larger one)
+cudaError_t launch_selftest_wait(int* status, cudaStream_t s);
 
 // macro problem (fe2_macro.cu)
 struct MacroDev {

@@ -430,3 +430,24 @@ def test_monolithic_newton_affine_predictor(torch):
     for k in range(16):
         assert O.rel_err(states[1]["Pbar"][k], states[0]["Pbar"][k]) <= 1e-9
         assert O.rel_err(states[1]["Cbar"][k], states[0]["Cbar"][k]) <= 1e-9
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(torch):
+    """A device wait that can never complete gives up with FE2_ERR_TIMEOUT
+    (no trap, no hang) and the context keeps working afterwards."""
+    from paper_2312_12771_gb300.fe2 import FE2_ERR_TIMEOUT
+    ctx = ctx_for(torch, "mixed")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert ctx.lib.fe2_selftest_wait_timeout(ctx.h, C_ptr(st)) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == FE2_ERR_TIMEOUT
+    b = W.fiber_batch(2, 8)
+    ids = ctx.register_batch(b)
+    _, _, s2, _ = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    assert (s2.cpu().numpy() == 0).all()
+
+
+def C_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
