@@ -71,6 +71,10 @@ def peaks():
         # plain-ALU peaks derived from unit counts x clock (no measured figure exists)
         "fp32_tflops": SM_COUNT * FP32_LANES * 2 * mhz * 1e6 / 1e12,
         "fp64_tflops": SM_COUNT * FP64_FMA_PER_SM * 2 * mhz * 1e6 / 1e12,
+        # dense TF32 tensor peak: the measured bf16 burst x the nominal tf32/bf16 ratio (1.1 / 2.25)
+        "tf32_tflops": float(p.get("bf16_tflops", 1900.0)) * 1.1 / 2.25,
+        "tf32_src": ("measured bf16 burst x nominal tf32/bf16 ratio 1.1/2.25" if "bf16_tflops" in p
+                     else "fallback bf16 1.9 PF x nominal tf32/bf16 ratio 1.1/2.25"),
     }
 
 
@@ -99,6 +103,7 @@ def work_per_rve(N, d=2):
     return {
         "assemble_reduce_linear": {"bytes": stencil_bytes + nn, "flops64": nn * 2 * (128 + 64 + 44 + 8)},
         "band_factor_fp32": {"flops": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
+        "band_factor_tc": {"flops_tc": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
         "band_backward_fp32": {"flops": nr * tri, "bytes": L_bytes + 4 * nr * nm + 8 * nr * nm},
         "band_refine_fp32": {"flops": 2 * nr * tri, "bytes": 2 * L_bytes + 8 * 3 * nr * nm},
         "residual_fp64": {"flops64": 2 * nr * nnz, "bytes": 9 * d * d * nn * 8 + 3 * nr * nm * 8},
@@ -113,6 +118,13 @@ def roofline_for(name, avg_ms, nrve, pk, N=N_MESH):
     if w is None or avg_ms <= 0:
         return None
     s = avg_ms * 1e-3
+    if "flops_tc" in w:
+        # trailing updates on the TF32 tensor cores (3 passes), panels on the FP32 pipes:
+        # algorithmic flops against the dense TF32 peak, and against the FP32 ALU peak for context
+        ach = w["flops_tc"] * nrve / s / 1e12
+        return {"bound": "tensor", "achieved": round(ach, 3), "peak": round(pk["tf32_tflops"], 1),
+                "unit": "TFLOP/s", "frac": round(ach / pk["tf32_tflops"], 4), "peak_src": pk["tf32_src"],
+                "frac_of_fp32_alu": round(ach / pk["fp32_tflops"], 4)}
     if "flops" in w:
         ach = w["flops"] * nrve / s / 1e12
         return {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 2),
@@ -243,8 +255,11 @@ def run_gpu(args, rank, world, dist):
 
     results = {}
     F = torch.tensor(batch.Fbar, device=dev)
-    for prec in ("mixed", "fp64"):
-        ctx = Fe2Context(dim=2, precision=prec, max_refine=args.refine)
+    legs = ("mixed", "tensor_core", "fp64") if not args.no_tc else ("mixed", "fp64")
+    for prec in legs:
+        # "tensor_core": the mixed path with the tcgen05 (3xTF32) band factor
+        ctx = Fe2Context(dim=2, precision="fp64" if prec == "fp64" else "mixed", max_refine=args.refine,
+                         factor="tensor_core" if prec == "tensor_core" else "auto")
         ids = ctx.register_batch(batch)
         outs = ctx._outs(nrve)
         steps = args.steps if prec == "mixed" else max(2, min(args.steps, 3))
@@ -411,6 +426,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the Hex8 and NH-Newton legs")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core factor leg")
     ap.add_argument("--hex8-rves", type=int, default=4096)
     ap.add_argument("--nh-macro", type=int, default=32)
     ap.add_argument("--nh-steps", type=int, default=10)
@@ -480,6 +496,7 @@ def main():
     ms = max_over_ranks(mx["ms"], dist)
     ms64 = max_over_ranks(R["fp64"]["ms"], dist)
     e2e_ms = max_over_ranks(mx["e2e_ms"], dist)
+    ms_tc = max_over_ranks(R["tensor_core"]["ms"], dist) if "tensor_core" in R else None
     total = args.rves * world
     value = total * mx["steps"] / (ms * 1e-3)
     value64 = total * R["fp64"]["steps"] / (ms64 * 1e-3)
@@ -499,6 +516,19 @@ def main():
         roof["kernel"] = dom
         roof["traffic"] = factor_traffic(args.rves) if dom == "band_factor_fp32" else None
         roof["traffic_unit"] = "bytes per launch (ncu capture of 304 RVEs scaled by RVE count)"
+    tc_leg = None
+    if "tensor_core" in R:
+        tc = R["tensor_core"]
+        ktc = {}
+        for name, (tms, cnt) in tc["prof"].items():
+            avg = tms / max(cnt, 1)
+            ktc[name] = {"avg_ms": round(avg, 4), "roofline": roofline_for(name, avg, args.rves, pk, args.N)}
+        tc_leg = {"value": round(total * tc["steps"] / (ms_tc * 1e-3), 1), "unit": UNIT,
+                  "ms_per_step": round(ms_tc / tc["steps"], 4), "steps": tc["steps"],
+                  "factor_kernel": "band_factor_tc (tcgen05 kind::tf32, 3xTF32 split, fp32 accumulation in TMEM)",
+                  "max_rel_err_vs_fp64_gpu": rel_errs(tc["Cbar"], R["fp64"]["Cbar"], tc["sigma"], R["fp64"]["sigma"],
+                                                      batch.Fbar),
+                  "status_nonzero": int((tc["status"] != 0).sum()), "kernels": ktc}
     kern64 = {}
     for name, (tms, cnt) in R["fp64"]["prof"].items():
         avg = tms / max(cnt, 1)
@@ -511,6 +541,7 @@ def main():
             "precision_path": "mixed", "gpu_launches": mx["launches"],
             "fp64_path": {"value": round(value64, 1), "ms_per_step": round(ms64 / R["fp64"]["steps"], 3),
                           "steps": R["fp64"]["steps"], "kernels": kern64},
+            "tensor_core_path": tc_leg,
             "speedup_mixed_vs_fp64": round(value / value64, 2),
             "max_rel_err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
             "status_nonzero": int((mx["status"] != 0).sum()),

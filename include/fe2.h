@@ -59,6 +59,15 @@ typedef enum {
 enum { FE2_ELEM_Q4 = 0, FE2_ELEM_HEX8 = 1 };
 enum { FE2_PREC_FP64 = 0, FE2_PREC_MIXED = 1 };
 enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1 };
+/* FP32 band factor of the mixed path (Section 4: K_mm factorised once per
+ * RVE and Newton iteration).  FE2_FACTOR_CUDA_CORE: shared-memory band
+ * Cholesky on the FP32 pipes, two RVEs per SM.  FE2_FACTOR_TENSOR_CORE: the
+ * dense trailing updates as tcgen05 MMAs (3xTF32, fp32 accumulation in tensor
+ * memory), one RVE per SM, for 2D bands with 32 + kd + d*d+1 <= 192 whose
+ * shared memory fits; other bands take the CUDA-core kernel.  FE2_FACTOR_AUTO
+ * is the library's choice, currently the CUDA-core kernel (measured faster on
+ * GB300 for these bands: the panel chain, not the update, bounds both). */
+enum { FE2_FACTOR_AUTO = 0, FE2_FACTOR_CUDA_CORE = 1, FE2_FACTOR_TENSOR_CORE = 2 };
 
 typedef struct {
     int dim;                 /* 2 or 3                                            */
@@ -68,6 +77,7 @@ typedef struct {
     void* cuda_stream;       /* cudaStream_t the work is queued on; NULL = default */
     double refine_tol;       /* mixed path: accepted relative error estimate      */
     int max_refine;          /* mixed path: FP64-residual refinement sweeps (>=0) */
+    int factor_kernel;       /* FE2_FACTOR_AUTO, _CUDA_CORE or _TENSOR_CORE       */
 } fe2_config;
 
 /* Create a context on the current CUDA device.  Allocates nothing large. */

@@ -196,6 +196,13 @@ static bool use_smem_factor(int kd, int nr, bool fp64, int max_smem, int d) {
     return d == 2 && kd + nr + 32 <= FACT_THREADS && (int)factor_smem_bytes(kd, nr, fp64) <= max_smem;
 }
 
+// Mixed path: the tensor-core FP32 factor when the context asks for it and
+// the band fits it; the CUDA-core kernel otherwise (and by default).
+static bool use_tc_factor(const fe2_ctx* ctx, int maxkd, int maxnr) {
+    return ctx->cfg.factor_kernel == FE2_FACTOR_TENSOR_CORE &&
+           factor_tc_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem);
+}
+
 static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64, int max_smem, int d) {
     const size_t es = fp64 ? 8 : 4;
     WsLayout l;
@@ -450,6 +457,8 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
             int* redo = ctx->cfg.max_refine > 0 ? ctx->d_redo : nullptr;
             if (l.gw)
                 TIMED("band_factor_fp32_gw", launch_factor_gw<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            else if (use_tc_factor(ctx, b.maxkd, b.maxnr))
+                TIMED("band_factor_tc", launch_factor_tc(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else
                 TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp32",
@@ -489,6 +498,7 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     if ((cfg->dim == 2) != (cfg->elem == FE2_ELEM_Q4)) return FE2_ERR_ARG;
     if (cfg->precision != FE2_PREC_FP64 && cfg->precision != FE2_PREC_MIXED) return FE2_ERR_ARG;
     if (cfg->max_refine < 0 || cfg->max_refine > 16) return FE2_ERR_ARG;
+    if (cfg->factor_kernel < FE2_FACTOR_AUTO || cfg->factor_kernel > FE2_FACTOR_TENSOR_CORE) return FE2_ERR_ARG;
     ctx = new fe2_ctx();
     ctx->cfg = *cfg;
     if (!(ctx->cfg.refine_tol > 0.0)) ctx->cfg.refine_tol = 1e-10;
@@ -1165,6 +1175,8 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
     } else {
         if (l.gw)
             CK(launch_factor_gw<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        else if (use_tc_factor(ctx, b.maxkd, b.maxnr))
+            CK(launch_factor_tc(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else
             CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<float>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));

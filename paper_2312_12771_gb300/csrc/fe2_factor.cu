@@ -610,21 +610,6 @@ __global__ void __launch_bounds__(256) k_residual2(const RveDev* __restrict__ ta
     }
 }
 
-// Self-test of the bounded device wait: an mbarrier that nothing ever arrives
-// on; the wait gives up after ~2^31 cycles and the kernel reports a timeout.
-__global__ void k_selftest_wait(int* status) {
-    __shared__ __align__(8) uint64_t bar;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    __shared__ int to;
-    if (threadIdx.x == 0) to = mbar_wait_bounded(&bar, 0) ? 0 : 1;
-    __syncthreads();
-    if (threadIdx.x == 0) *status = to ? FE2_ERR_TIMEOUT : FE2_OK;
-}
-
 template <typename K>
 cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -669,11 +654,6 @@ cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace 
                             cudaStream_t s) {
     dim3 grid((maxnn + 255) / 256, n);
     k_residual2<<<grid, 256, 0, s>>>(tab, ids, ws, active);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_selftest_wait(int* status, cudaStream_t s) {
-    k_selftest_wait<<<1, 32, 0, s>>>(status);
     return cudaGetLastError();
 }
 

@@ -67,6 +67,11 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
 template <typename T>
 cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws, int* status,
                           int maxkd, int maxnr, cudaStream_t s);
+// tensor-core FP32 band factor (2D): eligibility, shared memory, launch
+bool factor_tc_eligible(int kd, int nr, int d, int max_smem);
+size_t factor_tc_smem_bytes(int kd, int nr);
+cudaError_t launch_factor_tc(const RveDev* tab, const int* ids, int n, Workspace ws, int* status,
+                             int maxkd, int maxnr, cudaStream_t s);
 template <typename T>
 cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate,
                             int maxkd, int maxnr, int maxnm_pad, int* status, cudaStream_t s);

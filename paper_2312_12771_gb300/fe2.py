@@ -22,6 +22,8 @@ FE2_OK, FE2_ERR_ARG, FE2_ERR_CUDA, FE2_ERR_BUDGET = 0, 1, 2, 3
 FE2_ERR_NOT_PD, FE2_ERR_NAN, FE2_ERR_NO_CONV, FE2_ERR_TIMEOUT = 4, 5, 6, 7
 FE2_ELEM_Q4, FE2_ELEM_HEX8 = 0, 1
 FE2_PREC_FP64, FE2_PREC_MIXED = 0, 1
+FE2_FACTOR_AUTO, FE2_FACTOR_CUDA_CORE, FE2_FACTOR_TENSOR_CORE = 0, 1, 2
+FACTOR_KERNELS = {"auto": FE2_FACTOR_AUTO, "cuda_core": FE2_FACTOR_CUDA_CORE, "tensor_core": FE2_FACTOR_TENSOR_CORE}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_BUDGET", 4: "NOT_PD", 5: "NAN",
                 6: "NO_CONV", 7: "TIMEOUT"}
 
@@ -29,7 +31,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_BUDGET", 4: "NOT_P
 class fe2_config(C.Structure):
     _fields_ = [("dim", C.c_int), ("elem", C.c_int), ("precision", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("cuda_stream", C.c_void_p),
-                ("refine_tol", C.c_double), ("max_refine", C.c_int)]
+                ("refine_tol", C.c_double), ("max_refine", C.c_int),
+                ("factor_kernel", C.c_int)]
 
 
 class Fe2Error(RuntimeError):
@@ -154,7 +157,7 @@ class Fe2Context:
     """A libfe2 context on the current CUDA device and stream."""
 
     def __init__(self, dim=2, precision="mixed", hbm_budget_bytes=0, refine_tol=1e-10, max_refine=1,
-                 stream=None):
+                 stream=None, factor="auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libfe2 needs a CUDA GPU (GB300, sm_103a)")
@@ -165,7 +168,7 @@ class Fe2Context:
         cfg = fe2_config(dim, FE2_ELEM_Q4 if dim == 2 else FE2_ELEM_HEX8,
                          FE2_PREC_MIXED if precision == "mixed" else FE2_PREC_FP64,
                          int(hbm_budget_bytes), C.c_void_p(self.stream.cuda_stream), float(refine_tol),
-                         int(max_refine))
+                         int(max_refine), FACTOR_KERNELS[factor])
         self.cfg = cfg
         self.h = fe2_create(cfg)
         self.lib = load()

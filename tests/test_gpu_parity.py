@@ -451,3 +451,28 @@ def test_bounded_wait_reports_timeout_and_context_survives(torch):
 def C_ptr(t):
     import ctypes
     return ctypes.c_void_p(t.data_ptr())
+
+
+@pytest.mark.parametrize("N", [3, 8, 24, 30, 32])
+def test_tensor_core_factor_parity(torch, N):
+    """Mixed path with the tcgen05 (3xTF32) band factor against the oracle and
+    against the CUDA-core FP32 factor.  N spans the operand shapes: one
+    128-row tile (N <= 24), two row tiles without (N = 30) and with (N = 32)
+    the corner tile beyond column 128."""
+    b = W.fiber_batch(4, N, dF_scale=2e-3)
+    out = {}
+    for kern in ("tensor_core", "cuda_core"):
+        ctx = ctx_for(torch, "mixed", factor=kern)
+        ids = ctx.register_batch(b)
+        ctx.profile(True)
+        sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+        torch.cuda.synchronize()
+        names = ctx.profile_read()
+        assert ("band_factor_tc" in names) == (kern == "tensor_core"), names
+        out[kern] = (sig.clone(), Cb.clone(), st.clone())
+    idx = list(range(b.nrve))
+    refs = oracle_batch(b, idx)
+    for kern, (sig, Cb, st) in out.items():
+        check(b, sig, Cb, st, refs, idx, TOL["mixed"])
+    dC = (out["tensor_core"][1] - out["cuda_core"][1]).abs().max().item()
+    assert dC <= 1e-8 * out["cuda_core"][1].abs().max().item()
