@@ -397,6 +397,42 @@ def run_nh_newton(args):
     return out
 
 
+def run_schemes(args):
+    """Section 4.1 vs 4.2 on the config-3 problem: the classical staggered
+    scheme and the monolithic scheme over a sweep of load-step counts n_l
+    (Table-1 style robustness): converged or not, macro Newton iterations,
+    inner micro Newton updates, batched RVE-solve calls and wall time."""
+    import torch
+    from paper_2312_12771_gb300.driver import MonolithicFE2, NewtonLog, macro_mesh
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    nx = args.nh_macro
+    X, conn, fixed = macro_mesh(nx, nx)
+    b = W.inclusion_batch(4 * nx * nx, 32, stretch=1.0)
+    out = {"workload": f"macro {nx}x{nx} Q4 x 4 Gauss = {4 * nx * nx} NH RVEs 32x32 (random inclusions), stretch 1.2 "
+                       "in n_l load steps, affine predictor per step, tol 1e-8 (macro) / 1e-8 (micro)",
+           "runs": []}
+    for n_l in [int(x) for x in args.scheme_steps.split(",") if x]:
+        for scheme in ("monolithic", "staggered"):
+            ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+            fe = MonolithicFE2(ctx, X, conn, fixed, b)
+            log = NewtonLog()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            err = None
+            try:
+                fe.run(np.diag([1.2, 1.0]), n_l, predictor=True, scheme=scheme, log=log, tol_macro=1e-8,
+                       tol_micro=1e-8)
+            except RuntimeError as exc:
+                err = str(exc)[:120]
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            out["runs"].append({"scheme": scheme, "n_l": n_l, "converged": err is None, "error": err,
+                                "macro_iterations": log.iters, "micro_updates": log.micro_iters,
+                                "rve_solve_calls": log.rve_solve_calls, "wall_s": round(wall, 3)})
+            ctx.close()
+    return out
+
+
 def max_over_ranks(v, dist):
     if not dist:
         return v
@@ -427,6 +463,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the Hex8 and NH-Newton legs")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core factor leg")
+    ap.add_argument("--scheme-steps", default="1,2,5,10",
+                    help="load-step counts of the staggered vs monolithic sweep ('' to skip)")
     ap.add_argument("--hex8-rves", type=int, default=4096)
     ap.add_argument("--nh-macro", type=int, default=32)
     ap.add_argument("--nh-steps", type=int, default=10)
@@ -483,7 +521,7 @@ def main():
     batch, R, pk = run_gpu(args, rank, world, dist)
     extra = {}
     if rank == 0 and not args.no_extra:
-        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton)):
+        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton), ("schemes", run_schemes)):
             try:
                 extra[key] = fn(args)
             except Exception as exc:  # reported, not fatal: the headline leg is already measured

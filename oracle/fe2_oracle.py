@@ -20,6 +20,8 @@ What it computes (Hesch, Schmidt & Schuss, arXiv 2312.12771):
 * Section 4, Eqs. (discreteSys_K), (discreteSys_D), (discreteSys_L): the
   Hessian blocks, here per RVE: K_MM = int A, K_mM = int grad(R)^T A,
   K_mm = int grad(R)^T A grad(R).
+* Section 4.1: the classical staggered (nested) FE^2 scheme, with an inner
+  micro Newton to equilibrium in every macro iteration (staggered_fe2).
 * Section 4.2, Eq. (solution2) and the update of w~ below it: the condensed
   (null-space reduced) tangent Cbar = (K_MM - K_Mm K_mm^-1 K_mM)/|Omega|, the
   effective stress sigma_eff = (Pint - K_Mm K_mm^-1 r_m)/|Omega| and
@@ -387,6 +389,69 @@ def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e
         Fb, s = sols[b]
         out.append(dict(Fbar=Fb, Pbar=s["Pbar"], Cbar=s["Cbar"], sigma_eff=s["sigma_eff"], w=ws[b]))
     return out, iters, q
+
+
+def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-12,
+                  maxit=25, maxit_micro=50, record=None):
+    """Classical (staggered, nested) FE^2 of Section 4.1 on the same macro
+    problem as ``monolithic_fe2``: in every macro Newton iteration each RVE is
+    first brought to micro equilibrium r_m = 0 at its current Fbar by an inner
+    Newton (starting from its last state), then Pbar and the condensed tangent
+    Cbar = (K_MM - K_Mm K_mm^-1 K_mM)/|Omega| at that equilibrium give the
+    macro residual and stiffness.  The macro update moves only the macro
+    nodes; the micro states are re-equilibrated in the next iteration.
+    Returns the converged per-Gauss-point states, the macro iteration count
+    of every load step, the total number of inner micro iterations and q."""
+    X, conn, bnd = macro
+    grads, etas, _ = macro_gauss(X, conn)
+    nb = len(etas)
+    nnode = len(X)
+    q = X.copy()
+    ws = [np.zeros(2 * (r["N"] ** 2 - 1)) for r in rves]
+    free = np.ones(2 * nnode, bool)
+    for n in bnd:
+        free[2 * n:2 * n + 2] = False
+    iters, micro_total = [], 0
+    for k in range(1, n_steps + 1):
+        Fk = np.eye(2) + (k / n_steps) * (np.asarray(F_final) - np.eye(2))
+        q[bnd] = X[bnd] @ Fk.T
+        for it in range(maxit):
+            Kg = np.zeros((2 * nnode, 2 * nnode))
+            Rg = np.zeros(2 * nnode)
+            sols = []
+            for b in range(nb):
+                e = b // 4
+                Fb = q[conn[e]].T @ grads[b]
+                r = rves[b]
+                ws[b], mit = micro_equilibrate(r["N"], 2, r["phase"], r["mat"], Fb, ws[b], tol=tol_micro,
+                                               maxit=maxit_micro)
+                micro_total += mit
+                s = rve_solve(r["N"], 2, r["phase"], r["mat"], Fb, ws[b])
+                sols.append((Fb, s))
+                Bm = np.zeros((4, 8))
+                for A_ in range(4):
+                    for i in range(2):
+                        for J in range(2):
+                            Bm[2 * i + J, 2 * A_ + i] = grads[b][A_, J]
+                dofs = np.array([[2 * conn[e][A_], 2 * conn[e][A_] + 1] for A_ in range(4)]).ravel()
+                Kg[np.ix_(dofs, dofs)] += etas[b] * Bm.T @ s["Cbar"] @ Bm
+                Rg[dofs] += etas[b] * Bm.T @ s["Pbar"].ravel()
+            rnorm = np.linalg.norm(Rg[free])
+            if record is not None:
+                record.append((k, it, rnorm))
+            if rnorm < tol_macro:
+                iters.append(it)
+                break
+            dq = np.zeros(2 * nnode)
+            dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rg[free])
+            q = q + dq.reshape(nnode, 2)
+        else:
+            raise RuntimeError("macro Newton did not converge")
+    out = []
+    for b in range(nb):
+        Fb, s = sols[b]
+        out.append(dict(Fbar=Fb, Pbar=s["Pbar"], Cbar=s["Cbar"], sigma_eff=s["sigma_eff"], w=ws[b]))
+    return out, iters, micro_total, q
 
 
 # ---------------------------------------------------------------------------

@@ -1,9 +1,12 @@
-"""Monolithic FE^2 Newton driver (Section 4.2, Eq. (solution2)) over the C ABI.
+"""FE^2 Newton drivers over the C ABI: the monolithic scheme (Section 4.2,
+Eq. (solution2)) and the classical staggered scheme (Section 4.1).
 
 The loop control lives here; every arithmetic step is a libfe2 kernel:
 macro gradients, the fused RVE solve (S1-S6), the volume-averaged stress and
 micro residual norms, the macro assembly + band solve (S7) and the
-fluctuation update w~ <- w~ - (x_r + X_M : dFbar).  Load stepping follows
+fluctuation update w~ <- w~ - (x_r + X_M : dFbar).  The staggered scheme
+instead brings every RVE to micro equilibrium (inner Newton: the same update
+with dFbar = 0) before each macro iteration.  Load stepping follows
 Section 5.2: the Dirichlet data are applied in n_l increments and each load
 step starts from the previous converged state.  A step fails when the macro
 residual exceeds 1e10 (the failure criterion of Section 5.2).
@@ -37,6 +40,8 @@ class NewtonLog:
     iters: list = field(default_factory=list)      # Newton iterations per load step
     history: list = field(default_factory=list)    # (step, it, ||R_macro||, max ||r_m||)
     failed: bool = False
+    micro_iters: int = 0                           # staggered: inner micro Newton updates (all RVEs at once)
+    rve_solve_calls: int = 0                       # batched fe2_rve_solve calls
 
 
 class MonolithicFE2:
@@ -62,6 +67,7 @@ class MonolithicFE2:
         self.rn = torch.zeros(2, dtype=f64, device=dev)
         self.rnm = torch.zeros(ngp, dtype=f64, device=dev)
         self.mstatus = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.zero_dF = torch.zeros_like(self.Fbar)
         self.ngp = ngp
 
     def state(self):
@@ -87,6 +93,8 @@ class MonolithicFE2:
         for it in range(maxit):
             ctx.macro_gradients(self.Fbar)
             ctx.rve_solve(self.ids, self.Fbar, out=self.outs)
+            if log is not None:
+                log.rve_solve_calls += 1
             ctx.rve_average_stress(self.ids, self.Pbar)
             ctx.macro_residual(self.Pbar, self.rn[0:1])
             ctx.rve_residual_norm(self.ids, self.rnm)
@@ -110,12 +118,76 @@ class MonolithicFE2:
             ctx.macro_step(self.ids, self.dFbar)
         raise RuntimeError("macro Newton did not converge")
 
-    def run(self, F_final, n_steps, predictor=False, **kw):
-        log = NewtonLog()
+    def load_step_staggered(self, Fk, step, tol_macro=1e-9, tol_micro=1e-11, maxit=25, maxit_micro=30, log=None,
+                            F_prev=None):
+        """One load step of the classical staggered scheme (Section 4.1): in
+        every macro iteration all RVEs are first brought to micro equilibrium
+        at their current Fbar (inner Newton w~ <- w~ - x_r, i.e. the micro
+        update with dFbar = 0, until max ||r_m|| < tol_micro); Pbar and the
+        condensed tangent at that equilibrium then give the macro residual and
+        stiffness, and the macro step moves only the macro nodes."""
+        ctx = self.ctx
+        if F_prev is not None:
+            q = ctx.macro_get_positions() + self.X @ (np.asarray(Fk) - np.asarray(F_prev)).T
+            ctx.macro_set_positions(q)
+        ctx.macro_set_positions(self.X @ np.asarray(Fk).T, which=self.fixed)
+        sig, Cb, st, err = self.outs
+        for it in range(maxit):
+            ctx.macro_gradients(self.Fbar)
+            for mit in range(maxit_micro):
+                ctx.rve_solve(self.ids, self.Fbar, out=self.outs)
+                ctx.rve_residual_norm(self.ids, self.rnm)
+                self.t.cuda.current_stream().synchronize()
+                if log is not None:
+                    log.rve_solve_calls += 1
+                bad = int((st != 0).sum().item())
+                if bad:
+                    if log is not None:
+                        log.failed = True
+                    raise RuntimeError(f"{bad} RVEs failed (status {np.unique(st.cpu().numpy())})")
+                rmic = float(self.rnm.max().item())
+                if rmic < tol_micro:
+                    break
+                if not np.isfinite(rmic) or rmic > 1e10:
+                    if log is not None:
+                        log.failed = True
+                    raise RuntimeError(f"micro residual {rmic:.3e}: inner Newton diverged")
+                ctx.macro_step(self.ids, self.zero_dF)
+                if log is not None:
+                    log.micro_iters += 1
+            else:
+                if log is not None:
+                    log.failed = True
+                raise RuntimeError("micro Newton did not converge")
+            ctx.rve_average_stress(self.ids, self.Pbar)
+            ctx.macro_residual(self.Pbar, self.rn[0:1])
+            self.t.cuda.current_stream().synchronize()
+            rmac = float(self.rn[0].item())
+            if log is not None:
+                log.history.append((step, it, rmac, rmic))
+            if rmac < tol_macro:
+                if log is not None:
+                    log.iters.append(it)
+                return it
+            if rmac > 1e10 or not np.isfinite(rmac):
+                if log is not None:
+                    log.failed = True
+                raise RuntimeError(f"macro residual {rmac:.3e}: Newton diverged")
+            ctx.macro_solve(sig, Cb, self.dFbar, self.rn[1:2], self.mstatus)
+        if log is not None:
+            log.failed = True
+        raise RuntimeError("macro Newton did not converge")
+
+    def run(self, F_final, n_steps, predictor=False, scheme="monolithic", log=None, **kw):
+        """Load-stepped solve; ``scheme`` is "monolithic" (Section 4.2) or
+        "staggered" (Section 4.1).  A failing step raises; ``log`` (if given)
+        keeps what was recorded up to the failure."""
+        log = NewtonLog() if log is None else log
+        step_fn = self.load_step if scheme == "monolithic" else self.load_step_staggered
         F_final = np.asarray(F_final, float)
         F_prev = np.eye(2)
         for k in range(1, n_steps + 1):
             Fk = np.eye(2) + (k / n_steps) * (F_final - np.eye(2))
-            self.load_step(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)
+            step_fn(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)
             F_prev = Fk
         return log

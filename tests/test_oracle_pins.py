@@ -366,3 +366,31 @@ def test_monolithic_newton_converges_quadratically():
     for o, r in zip(out, rves):
         s = O.rve_solve(4, 2, r["phase"], r["mat"], o["Fbar"], o["w"])
         assert np.linalg.norm(s["r_m"]) < 1e-9
+
+
+def test_staggered_and_monolithic_reach_the_same_equilibrium():
+    """Section 4.1 vs 4.2: both schemes solve the same discrete equations
+    (macro equilibrium with micro equilibrium at every Gauss point), so their
+    converged states agree; the staggered states are micro-equilibrated to
+    its inner tolerance and its macro Newton converges quadratically."""
+    macro = O.macro_mesh(2, 1)
+    rves = []
+    for b in range(8):
+        c, r = W.random_inclusions(W.GLOBAL_SEED, 100 + b)
+        rves.append(dict(N=4, phase=W.inclusion_phase(4, 2, c, r),
+                         mat=W.neohooke_mat(1.0, 10.0, 20.0, 200.0)))
+    F = np.diag([1.15, 1.0]) + np.array([[0.0, 0.03], [0.0, 0.0]])
+    mono, it_m, q_m = O.monolithic_fe2(macro, rves, F, n_steps=2, tol_macro=1e-11, tol_micro=1e-11)
+    rec = []
+    stag, it_s, micro, q_s = O.staggered_fe2(macro, rves, F, n_steps=2, tol_macro=1e-11, tol_micro=1e-12,
+                                             record=rec)
+    assert np.abs(q_m - q_s).max() < 1e-10
+    for a, b in zip(mono, stag):
+        assert O.rel_err(b["Cbar"], a["Cbar"]) < 1e-9
+        assert O.rel_err(b["Pbar"], a["Pbar"]) < 1e-9
+    assert micro > 0 and max(it_s) <= 6
+    # quadratic decay of the macro residual within the last load step
+    res = [r for (k, it, r) in rec if k == 2]
+    for r0, r1 in zip(res[1:-1], res[2:]):
+        if r0 < 1e-3:
+            assert r1 < 10.0 * r0 * r0 + 1e-11
