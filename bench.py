@@ -433,6 +433,49 @@ def run_schemes(args):
     return out
 
 
+def run_cook(args):
+    """Section 5.2 Cook's membrane (Table 1 style): macro 20x20 Q4 x 2x2
+    Gauss = 1600 RVEs of 30x30 with the Mooney-Rivlin cross microstructure,
+    clamped left edge, traction (-5, 10) on the right edge in n_l load steps;
+    generalized (monolithic) and classical (staggered) Newton, tolerances as
+    in Section 5.2 (macro 1e-9; classical micro 1e-13)."""
+    import torch
+    from paper_2312_12771_gb300.driver import MonolithicFE2, NewtonLog, edge_load
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    nx = args.cook_macro
+    X, conn, left, right = W.cook_mesh(nx, nx)
+    fixed = np.zeros(2 * len(X), np.uint8)
+    for n in left:
+        fixed[2 * n:2 * n + 2] = 1
+    b = W.cook_batch(4 * len(conn), args.cook_N)
+    fext = edge_load(X, right, W.MEMBRANE_TRACTION)
+    out = {"workload": f"Cook's membrane, macro {nx}x{nx} Q4 x 4 Gauss = {b.nrve} Mooney-Rivlin cross RVEs "
+                       f"{args.cook_N}x{args.cook_N}, traction (-5,10) in n_l steps",
+           "runs": []}
+    for n_l in [int(x) for x in args.cook_steps.split(",") if x]:
+        for scheme in ("monolithic", "staggered"):
+            ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+            fe = MonolithicFE2(ctx, X, conn, fixed, b)
+            log = NewtonLog()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            err = None
+            try:
+                fe.run(np.eye(2), n_l, scheme=scheme, log=log, fext=fext, tol_macro=1e-9,
+                       tol_micro=1e-13 if scheme == "staggered" else 1e-9)
+            except RuntimeError as exc:
+                err = str(exc)[:120]
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            tip = (fe.ctx.macro_get_positions()[right[-1]] - X[right[-1]]).tolist() if err is None else None
+            out["runs"].append({"scheme": scheme, "n_l": n_l, "converged": err is None, "error": err,
+                                "iterations_per_step": log.iters, "micro_updates": log.micro_iters,
+                                "rve_solve_calls": log.rve_solve_calls, "wall_s": round(wall, 3),
+                                "tip_displacement": tip})
+            ctx.close()
+    return out
+
+
 def max_over_ranks(v, dist):
     if not dist:
         return v
@@ -463,6 +506,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the Hex8 and NH-Newton legs")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core factor leg")
+    ap.add_argument("--cook-macro", type=int, default=20)
+    ap.add_argument("--cook-N", type=int, default=30)
+    ap.add_argument("--cook-steps", default="1,2,12,22", help="load-step counts of the Cook's membrane sweep")
     ap.add_argument("--scheme-steps", default="1,2,5,10",
                     help="load-step counts of the staggered vs monolithic sweep ('' to skip)")
     ap.add_argument("--hex8-rves", type=int, default=4096)
@@ -521,7 +567,8 @@ def main():
     batch, R, pk = run_gpu(args, rank, world, dist)
     extra = {}
     if rank == 0 and not args.no_extra:
-        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton), ("schemes", run_schemes)):
+        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton), ("schemes", run_schemes),
+                        ("cook", run_cook)):
             try:
                 extra[key] = fn(args)
             except Exception as exc:  # reported, not fatal: the headline leg is already measured

@@ -23,7 +23,11 @@
  *  - Materials per RVE and phase: double[4] = (model, p1, p2, p3):
  *    FE2_MODEL_LINEAR (p1 = E, p2 = nu, plane strain in 2D, strain
  *    sym(F - I)); FE2_MODEL_NEOHOOKE (p1 = mu, p2 = kappa; energy
- *    mu/2 (F:F - 3) - mu ln J + kappa/2 (J-1)^2, Eq. (MR) with beta = 0).
+ *    mu/2 (F:F - 3) - mu ln J + kappa/2 (J-1)^2, Eq. (MR) with beta = 0);
+ *    FE2_MODEL_MOONEY_RIVLIN (p1 = alpha, p2 = beta, p3 = kappa; energy
+ *    alpha (F:F - 3) + beta (H:H - 3) + kappa/2 (J-1)^2 - 2 (alpha + 2 beta) ln J,
+ *    Eq. (MR) with the f(J) of the Section 5.2 membrane; plane strain, 2D only,
+ *    where H:H = F:F + J^2).
  *  - Pointers marked [device] are CUDA device pointers, borrowed for the
  *    duration of the work queued on the context's stream; [host] pointers are
  *    read before the call returns.  rve_ids are always [host].
@@ -58,7 +62,7 @@ typedef enum {
 
 enum { FE2_ELEM_Q4 = 0, FE2_ELEM_HEX8 = 1 };
 enum { FE2_PREC_FP64 = 0, FE2_PREC_MIXED = 1 };
-enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1 };
+enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1, FE2_MODEL_MOONEY_RIVLIN = 2 };
 /* FP32 band factor of the mixed path (Section 4: K_mm factorised once per
  * RVE and Newton iteration).  FE2_FACTOR_CUDA_CORE: shared-memory band
  * Cholesky on the FP32 pipes, two RVEs per SM.  FE2_FACTOR_TENSOR_CORE: the
@@ -174,6 +178,12 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
 fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which);
 /* Copy the current nodal positions to q_host [host] double[nnode][2].  Synchronises. */
 fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host);
+/* Nodal external forces of the current load, fext_host [host] double[nnode][2]
+ * (the surface-load term of Eq. (weakMech), e.g. the Section 5.2 membrane
+ * traction scaled to the load step; NULL = no load).  fe2_macro_residual and
+ * fe2_macro_solve then use R = (internal) - fext on the free DOFs.  Returns
+ * FE2_ERR_NAN for a non-finite entry.  Synchronises. */
+fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host);
 /* Fbar_b = sum_A q_A (x) grad N^A(X_b) into Fbar [device] double[4 nelem][2][2];
  * eta [device] double[4 nelem] receives the quadrature weights (may be NULL). */
 fe2_status fe2_macro_gradients(fe2_ctx* ctx, double* Fbar, double* eta);

@@ -8,8 +8,9 @@ What it computes (Hesch, Schmidt & Schuss, arXiv 2312.12771):
 
 * Section 2.1, cofactor and determinant equations: H = 1/2 F x F (tensor cross
   product with Levi-Civita symbols), J = 1/6 F : (F x F).
-* Section 2.1, Eq. (MR) with beta = 0 and the P formula below it: the
-  compressible Neo-Hooke law used here,
+* Section 2.1, Eq. (MR) and the P formula below it: the compressible
+  Mooney-Rivlin law with the f(J) of the Section 5.2 membrane materials
+  (mooney_rivlin), and with beta = 0 the compressible Neo-Hooke law,
   Psi = mu/2 (F:F - 3) - mu ln J + kappa/2 (J-1)^2 (3D; plane strain embeds
   F with F33 = 1), P = dPsi/dF, A = dP/dF.
 * Section 2.2, Eqs. (microdefo), (microGrad): F~ = Fbar + grad w~.
@@ -101,6 +102,40 @@ def neohooke(F, mu, kappa, d):
     return P[..., :d, :d], A[..., :d, :d, :d, :d]
 
 
+def mooney_rivlin_energy(F, alpha, beta, kappa, d):
+    """Psi = alpha (F:F - 3) + beta (H:H - 3) + kappa/2 (J-1)^2 - 2 (alpha + 2 beta) ln J:
+    Eq. (MR) with the f(J) of the Section 5.2 membrane materials (stress free
+    at F = I).  For d = 2 the plane-strain embedding gives H:H = F:F + J^2,
+    which is the two-dimensional energy printed in Section 5.2."""
+    F3 = embed3(F, d)
+    H = cofactor(F3)
+    J = jacobian(F3)
+    return alpha * (np.einsum("...iJ,...iJ->...", F3, F3) - 3.0) + beta * (np.einsum("...iJ,...iJ->...", H, H) - 3.0) \
+        + 0.5 * kappa * (J - 1.0) ** 2 - 2.0 * (alpha + 2.0 * beta) * np.log(J)
+
+
+def mooney_rivlin(F, alpha, beta, kappa, d):
+    """P = dPsi/dF + dPsi/dH x F + dPsi/dJ H (Section 2.1, P formula) with
+    dPsi/dF = 2 alpha F, dPsi/dH = 2 beta H, dPsi/dJ = kappa (J-1) - 2 (alpha + 2 beta)/J.
+    A = dP/dF from dH : dF = F x dF:
+      A:dF = 2 alpha dF + 2 beta ((F x dF) x F + H x dF) + f''(J) (H:dF) H + f'(J) F x dF."""
+    F3 = embed3(F, d)
+    H = cofactor(F3)
+    J = jacobian(F3)
+    s = kappa * (J - 1.0) - 2.0 * (alpha + 2.0 * beta) / J          # f'(J)
+    c = kappa + 2.0 * (alpha + 2.0 * beta) / J ** 2                 # f''(J)
+    P = 2.0 * alpha * F3 + 2.0 * beta * tensor_cross(H, F3) + s[..., None, None] * H
+    I4 = np.einsum("ik,JL->iJkL", np.eye(3), np.eye(3))
+    dHdF = np.einsum("ijk,JML,...jM->...iJkL", _EPS, _EPS, F3)        # (F x dF)_iJ = dHdF_iJkL dF_kL
+    HxdF = np.einsum("ijk,JML,...jM->...iJkL", _EPS, _EPS, H)        # (H x dF)_iJ
+    # ((F x dF) x F)_iJ = eps_ijk eps_JMN (F x dF)_jM F_kN
+    FdFxF = np.einsum("ijk,JMN,...jMbD,...kN->...iJbD", _EPS, _EPS, dHdF, F3)
+    A = 2.0 * alpha * I4 + 2.0 * beta * (FdFxF + HxdF) \
+        + c[..., None, None, None, None] * np.einsum("...iJ,...kL->...iJkL", H, H) \
+        + s[..., None, None, None, None] * dHdF
+    return P[..., :d, :d], A[..., :d, :d, :d, :d]
+
+
 def lame(E, nu):
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
@@ -135,6 +170,8 @@ def material(F, m, d):
         return linear_elastic(F, m[1], m[2], d)
     if model == 1:
         return neohooke(F, m[1], m[2], d)
+    if model == 2:
+        return mooney_rivlin(F, m[1], m[2], m[3], d)
     raise ValueError(f"unknown material model {model}")
 
 
@@ -142,6 +179,8 @@ def energy(F, m, d):
     model = int(m[0])
     if model == 0:
         return linear_energy(F, m[1], m[2], d)
+    if model == 2:
+        return mooney_rivlin_energy(F, m[1], m[2], m[3], d)
     return neohooke_energy(F, m[1], m[2], d)
 
 
@@ -327,13 +366,28 @@ def macro_gauss(X, conn):
     return np.array(grads), np.array(etas), np.array(pts)
 
 
+def traction_load(X, edge_nodes, T):
+    """Nodal external forces of a constant surface load T on a boundary polyline
+    of bilinear-element edges (the Neumann term of Eq. (weakMech)): every
+    segment of length L between consecutive nodes gives T L / 2 to each end."""
+    f = np.zeros_like(np.asarray(X, dtype=np.float64))
+    T = np.asarray(T, dtype=np.float64)
+    for a, b in zip(edge_nodes[:-1], edge_nodes[1:]):
+        L = np.linalg.norm(X[b] - X[a])
+        f[a] += 0.5 * L * T
+        f[b] += 0.5 * L * T
+    return f
+
+
 def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-9,
-                   maxit=25, record=None):
+                   maxit=25, record=None, fext=None):
     """Load-stepped monolithic Newton (Section 4.2, Eq. (solution2)) on a Q4
     macro mesh with affine Dirichlet data u = (F_k - I) X on all boundary
-    nodes, F_k = I + k/n (F_final - I).  ``rves`` is a list (one per macro
-    Gauss point) of dicts with N, d, phase, mat.  Returns per Gauss point the
-    converged Fbar, sigma (= Pbar), Cbar and w~, plus iteration counts."""
+    nodes, F_k = I + k/n (F_final - I), and with ``fext`` (nodal forces
+    [nnode][2] of a surface load, Eq. (weakMech)) the load k/n fext in step k.
+    ``rves`` is a list (one per macro Gauss point) of dicts with N, d, phase,
+    mat.  Returns per Gauss point the converged Fbar, sigma (= Pbar), Cbar and
+    w~, plus iteration counts.  A step fails when ||R_macro|| > 1e10 (Section 5.2)."""
     X, conn, bnd = macro
     grads, etas, _ = macro_gauss(X, conn)
     nb = len(etas)
@@ -368,12 +422,17 @@ def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e
                 Kg[np.ix_(dofs, dofs)] += etas[b] * Bm.T @ s["Cbar"] @ Bm
                 Rg[dofs] += etas[b] * Bm.T @ s["Pbar"].ravel()
                 Rc[dofs] += etas[b] * Bm.T @ s["sigma_eff"].ravel()
+            if fext is not None:
+                Rg -= (k / n_steps) * np.asarray(fext).ravel()
+                Rc -= (k / n_steps) * np.asarray(fext).ravel()
             rnorm = np.linalg.norm(Rg[free])
             if record is not None:
                 record.append((k, it, rnorm, rmic))
             if rnorm < tol_macro and rmic < tol_micro:
                 iters.append(it)
                 break
+            if not rnorm < 1e10:
+                raise RuntimeError("macro residual above 1e10: Newton diverged")
             dq = np.zeros(2 * nnode)
             dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rc[free])
             q = q + dq.reshape(nnode, 2)
@@ -392,7 +451,7 @@ def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e
 
 
 def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-12,
-                  maxit=25, maxit_micro=50, record=None):
+                  maxit=25, maxit_micro=50, record=None, fext=None):
     """Classical (staggered, nested) FE^2 of Section 4.1 on the same macro
     problem as ``monolithic_fe2``: in every macro Newton iteration each RVE is
     first brought to micro equilibrium r_m = 0 at its current Fbar by an inner
@@ -400,8 +459,9 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
     Cbar = (K_MM - K_Mm K_mm^-1 K_mM)/|Omega| at that equilibrium give the
     macro residual and stiffness.  The macro update moves only the macro
     nodes; the micro states are re-equilibrated in the next iteration.
-    Returns the converged per-Gauss-point states, the macro iteration count
-    of every load step, the total number of inner micro iterations and q."""
+    ``fext`` as in monolithic_fe2.  Returns the converged per-Gauss-point
+    states, the macro iteration count of every load step, the total number of
+    inner micro iterations and q."""
     X, conn, bnd = macro
     grads, etas, _ = macro_gauss(X, conn)
     nb = len(etas)
@@ -436,12 +496,16 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
                 dofs = np.array([[2 * conn[e][A_], 2 * conn[e][A_] + 1] for A_ in range(4)]).ravel()
                 Kg[np.ix_(dofs, dofs)] += etas[b] * Bm.T @ s["Cbar"] @ Bm
                 Rg[dofs] += etas[b] * Bm.T @ s["Pbar"].ravel()
+            if fext is not None:
+                Rg -= (k / n_steps) * np.asarray(fext).ravel()
             rnorm = np.linalg.norm(Rg[free])
             if record is not None:
                 record.append((k, it, rnorm))
             if rnorm < tol_macro:
                 iters.append(it)
                 break
+            if not rnorm < 1e10:
+                raise RuntimeError("macro residual above 1e10: Newton diverged")
             dq = np.zeros(2 * nnode)
             dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rg[free])
             q = q + dq.reshape(nnode, 2)

@@ -2,6 +2,7 @@
 // HBM-budget admission, id-list cache, transient workspace, and the launch
 // sequences of the assemble / reduce / condense / macro-step calls.
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <cstdarg>
 #include <deque>
@@ -615,8 +616,10 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         for (int p = 0; p < nphase; ++p) {
             const double* m = mat + ((size_t)k * nphase + p) * 4;
             const int model = (int)m[0];
-            if (model != FE2_MODEL_LINEAR && model != FE2_MODEL_NEOHOOKE)
+            if (model != FE2_MODEL_LINEAR && model != FE2_MODEL_NEOHOOKE && model != FE2_MODEL_MOONEY_RIVLIN)
                 return fail(ctx, FE2_ERR_ARG, "rve %d phase %d: unknown material model %g", k, p, m[0]);
+            if (model == FE2_MODEL_MOONEY_RIVLIN && d != 2)
+                return fail(ctx, FE2_ERR_ARG, "rve %d phase %d: the Mooney-Rivlin model is 2D only", k, p);
         }
         for (int e = 0; e < nn; ++e)
             if (phase[phase_off + e] >= nphase) return fail(ctx, FE2_ERR_ARG, "rve %d: phase index out of range", k);
@@ -1005,6 +1008,9 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
     if ((st = upload_vec(ctx, std::vector<double>((size_t)nfree * (kd + 1)), &dK))) return st;
     if ((st = upload_vec(ctx, std::vector<double>(nfree), &dR))) return st;
     if ((st = upload_vec(ctx, std::vector<double>(2 * nnode), &ddq))) return st;
+    double* dfext;
+    if ((st = upload_vec(ctx, std::vector<double>(2 * nnode), &dfext))) return st;
+    M.fext = dfext;
     M.conn = dconn;
     M.dof2free = dd2f;
     M.grads = dgr;
@@ -1031,6 +1037,19 @@ fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uin
     for (int t = 0; t < nd; ++t)
         if (!which || which[t]) q[t] = q_host[t];
     CK(cudaMemcpy(ctx->macro.q, q.data(), sizeof(double) * nd, cudaMemcpyHostToDevice));
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready) return fail(ctx, FE2_ERR_ARG, "no macro problem");
+    const int nd = 2 * ctx->macro.nnode;
+    std::vector<double> f(nd, 0.0);
+    if (fext_host) f.assign(fext_host, fext_host + nd);
+    for (int t = 0; t < nd; ++t)
+        if (!std::isfinite(f[t])) return fail(ctx, FE2_ERR_NAN, "external force %d is not finite", t);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(const_cast<double*>(ctx->macro.fext), f.data(), sizeof(double) * nd, cudaMemcpyHostToDevice));
     return FE2_OK;
 }
 

@@ -56,12 +56,25 @@ __device__ void consti2(const double* m, const double F[2][2], double P[2][2],
                         A[i][J][k][L] = (i == J && k == L ? lam : 0.0) +
                                         mu * ((i == k && J == L ? 1.0 : 0.0) + (i == L && J == k ? 1.0 : 0.0));
     } else {
-        const double mu = m[1], kappa = m[2];
-        // plane-strain cofactor of the in-plane block and J = det F
+        // hyperelastic laws of the form Psi = a/2 F:F + g(J) in plane strain (H = cof F of
+        // the in-plane block, J = det F): P = a F + g'(J) H, A = a I + g''(J) H (x) H + g'(J) dH/dF.
+        //   Neo-Hooke:      a = mu,             g' = kappa (J-1) - mu/J
+        //   Mooney-Rivlin:  a = 2 (alpha+beta), g' = 2 beta J + kappa (J-1) - 2 (alpha + 2 beta)/J
+        //                   (beta H:H = beta (F:F + J^2) for the plane-strain embedding)
         const double H[2][2] = {{F[1][1], -F[1][0]}, {-F[0][1], F[0][0]}};
         const double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
-        const double s = kappa * (J - 1.0) - mu / J;          // dPsi/dJ
-        const double c = mu / (J * J) + kappa;                // d^2Psi/dJ^2
+        double mu, s, c;
+        if (model == FE2_MODEL_MOONEY_RIVLIN) {
+            const double al = m[1], be = m[2], kappa = m[3], q = 2.0 * (al + 2.0 * be);
+            mu = 2.0 * (al + be);
+            s = 2.0 * be * J + kappa * (J - 1.0) - q / J;
+            c = 2.0 * be + kappa + q / (J * J);
+        } else {
+            const double kappa = m[2];
+            mu = m[1];
+            s = kappa * (J - 1.0) - mu / J;  // dPsi/dJ
+            c = mu / (J * J) + kappa;        // d^2Psi/dJ^2
+        }
         for (int i = 0; i < 2; ++i)
             for (int K = 0; K < 2; ++K) P[i][K] = mu * F[i][K] + s * H[i][K];
         for (int i = 0; i < 2; ++i)

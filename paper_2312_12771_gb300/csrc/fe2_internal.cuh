@@ -120,6 +120,7 @@ struct MacroDev {
     double* K;            // [nfree][kd+1] lower band, column-major
     double* R;            // [nfree]
     double* dq;           // [2 nnode]
+    const double* fext;   // [2 nnode] nodal external forces of the current load (zero unless set)
 };
 cudaError_t launch_macro_gradients(const MacroDev& M, double* Fbar, double* eta, cudaStream_t s);
 cudaError_t launch_macro_residual(const MacroDev& M, const double* stress, double* rnorm, cudaStream_t s);

@@ -64,7 +64,7 @@ __global__ void k_macro_assemble(MacroDev M, const double* __restrict__ stress, 
             }
         }
     }
-    M.R[i] = r;
+    M.R[i] = r - M.fext[t];  // internal minus external virtual work (Eq. (weakMech))
 }
 
 // One CTA: ||R||_2 of the free residual (deterministic tree).

@@ -35,6 +35,19 @@ def macro_mesh(nx, ny, Lx=1.0, Ly=1.0):
     return X, conn, fixed
 
 
+def edge_load(X, edge_nodes, T):
+    """Nodal forces of a constant surface load T on a boundary polyline of
+    bilinear-element edges (Neumann term of Eq. (weakMech)): T L/2 per end
+    node of every segment of length L."""
+    X = np.asarray(X, dtype=np.float64)
+    f = np.zeros_like(X)
+    for a, b in zip(edge_nodes[:-1], edge_nodes[1:]):
+        L = float(np.hypot(*(X[b] - X[a])))
+        f[a] += 0.5 * L * np.asarray(T, dtype=np.float64)
+        f[b] += 0.5 * L * np.asarray(T, dtype=np.float64)
+    return f
+
+
 @dataclass
 class NewtonLog:
     iters: list = field(default_factory=list)      # Newton iterations per load step
@@ -76,6 +89,10 @@ class MonolithicFE2:
         return dict(Fbar=self.Fbar.cpu().numpy().copy(), Pbar=self.Pbar.cpu().numpy().copy(),
                     sigma_eff=sig.cpu().numpy().copy(), Cbar=Cb.cpu().numpy().copy(),
                     status=st.cpu().numpy().copy(), err=err.cpu().numpy().copy())
+
+    def set_load(self, fext):
+        """Nodal external forces of the current load step (Eq. (weakMech))."""
+        self.ctx.macro_set_load(fext)
 
     def load_step(self, Fk, step, tol_macro=1e-9, tol_micro=1e-9, maxit=25, log=None, F_prev=None):
         """One load step.  The previous converged state is the start value
@@ -178,16 +195,21 @@ class MonolithicFE2:
             log.failed = True
         raise RuntimeError("macro Newton did not converge")
 
-    def run(self, F_final, n_steps, predictor=False, scheme="monolithic", log=None, **kw):
+    def run(self, F_final, n_steps, predictor=False, scheme="monolithic", log=None, fext=None, **kw):
         """Load-stepped solve; ``scheme`` is "monolithic" (Section 4.2) or
-        "staggered" (Section 4.1).  A failing step raises; ``log`` (if given)
-        keeps what was recorded up to the failure."""
+        "staggered" (Section 4.1).  Step k applies the Dirichlet data of
+        F_k = I + k/n (F_final - I) and, with ``fext`` (nodal forces [nnode][2]
+        of a surface load), the load k/n fext (Section 5.2: T_k = k T / n_l).
+        A failing step raises; ``log`` (if given) keeps what was recorded up
+        to the failure."""
         log = NewtonLog() if log is None else log
         step_fn = self.load_step if scheme == "monolithic" else self.load_step_staggered
         F_final = np.asarray(F_final, float)
         F_prev = np.eye(2)
         for k in range(1, n_steps + 1):
             Fk = np.eye(2) + (k / n_steps) * (F_final - np.eye(2))
+            if fext is not None:
+                self.set_load((k / n_steps) * np.asarray(fext, dtype=np.float64))
             step_fn(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)
             F_prev = Fk
         return log

@@ -63,6 +63,7 @@ _SIGS = {
     "fe2_macro_setup": (_I, [_P, _I, _DP, _I, _IP, C.POINTER(C.c_uint8)]),
     "fe2_macro_set_positions": (_I, [_P, _DP, C.POINTER(C.c_uint8)]),
     "fe2_macro_get_positions": (_I, [_P, _DP]),
+    "fe2_macro_set_load": (_I, [_P, _DP]),
     "fe2_macro_gradients": (_I, [_P, _P, _P]),
     "fe2_macro_residual": (_I, [_P, _P, _P]),
     "fe2_macro_solve": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -271,6 +272,14 @@ class Fe2Context:
         q = np.zeros((self.macro_nnode, 2))
         self._check(self.lib.fe2_macro_get_positions(self.h, q.ctypes.data_as(_DP)), "fe2_macro_get_positions")
         return q
+
+    def macro_set_load(self, fext):
+        """Nodal external forces [nnode][2] of the current load (None = no load)."""
+        if fext is None:
+            self._check(self.lib.fe2_macro_set_load(self.h, None), "fe2_macro_set_load")
+            return
+        f = np.ascontiguousarray(np.asarray(fext, dtype=np.float64).reshape(self.macro_nnode, 2))
+        self._check(self.lib.fe2_macro_set_load(self.h, f.ctypes.data_as(_DP)), "fe2_macro_set_load")
 
     def macro_gradients(self, Fbar):
         self._check(self.lib.fe2_macro_gradients(self.h, _ptr(Fbar), None), "fe2_macro_gradients")

@@ -31,6 +31,7 @@ MASK64 = (1 << 64) - 1
 
 MODEL_LINEAR = 0
 MODEL_NEOHOOKE = 1
+MODEL_MOONEY_RIVLIN = 2
 
 
 # --------------------------------------------------------------------------
@@ -108,6 +109,15 @@ def sphere_phase(N: int, vf: float = 0.2) -> np.ndarray:
     return inclusion_phase(N, 3, [(0.5, 0.5, 0.5)], [r])
 
 
+def cross_phase(N: int, width: float = 1.0 / 3.0) -> np.ndarray:
+    """Centred cross of the given width (fraction of the cell side) in phase 1,
+    the rest phase 0 -- the membrane RVE of Section 5.2 ((-3,3)^2 mm with a
+    2 mm cross: width 1/3), element phase by centroid."""
+    pts = _centroids(N, 2)
+    inside = (np.abs(pts[:, 0] - 0.5) < 0.5 * width) | (np.abs(pts[:, 1] - 0.5) < 0.5 * width)
+    return inside.astype(np.uint8)
+
+
 def random_inclusions(seed: int, rve: int, d: int = 2, nmin: int = 1, nmax: int = 6,
                       rmin: float = 0.05, rmax: float = 0.15, max_tries: int = 10000):
     """1..6 non-overlapping periodic circles: count U{nmin..nmax}, radius
@@ -144,6 +154,43 @@ def neohooke_mat(mu0: float, kappa0: float, mu1: float, kappa1: float) -> np.nda
     return np.array([[MODEL_NEOHOOKE, mu0, kappa0, 0.0], [MODEL_NEOHOOKE, mu1, kappa1, 0.0]])
 
 
+def mooney_rivlin_mat(p0, p1) -> np.ndarray:
+    """Two Mooney-Rivlin phases, p = (alpha, beta, kappa)."""
+    return np.array([[MODEL_MOONEY_RIVLIN, *p0], [MODEL_MOONEY_RIVLIN, *p1]], dtype=np.float64)
+
+
+# the two membrane materials of Section 5.2: (alpha, beta, kappa)
+MEMBRANE_MATERIAL_1 = (27.0, 18.0, 60.0)
+MEMBRANE_MATERIAL_2 = (13.5, 6.5, 30.0)
+MEMBRANE_TRACTION = (-5.0, 10.0)
+
+
+def cook_mesh(nx: int, ny: int):
+    """Cook's membrane of Section 5.2: the quadrilateral with corners (0,0),
+    (480,440), (480,600), (0,440), meshed by nx x ny bilinear elements
+    (straight lines between corresponding points of the bottom and top
+    edges).  Node n = ix + (nx+1) iy, element nodes ordered
+    (ix,iy), (ix+1,iy), (ix,iy+1), (ix+1,iy+1).  Returns X [nnode][2],
+    conn [nelem][4], the left-edge nodes (clamped) and the right-edge nodes
+    (loaded), bottom to top."""
+    xs = np.linspace(0.0, 480.0, nx + 1)
+    X = np.zeros(((nx + 1) * (ny + 1), 2))
+    for iy in range(ny + 1):
+        t = iy / ny
+        for ix in range(nx + 1):
+            x = xs[ix]
+            lo, hi = 11.0 / 12.0 * x, x / 3.0 + 440.0
+            X[ix + (nx + 1) * iy] = (x, lo + t * (hi - lo))
+    conn = []
+    for iy in range(ny):
+        for ix in range(nx):
+            n0 = ix + (nx + 1) * iy
+            conn.append([n0, n0 + 1, n0 + nx + 1, n0 + nx + 2])
+    left = np.array([(nx + 1) * iy for iy in range(ny + 1)])
+    right = np.array([nx + (nx + 1) * iy for iy in range(ny + 1)])
+    return X, np.array(conn, dtype=np.int32), left, right
+
+
 # --------------------------------------------------------------------------
 # batches
 # --------------------------------------------------------------------------
@@ -177,6 +224,16 @@ def laminate_batch(nrve: int = 64, N: int = 8, strain: float = 1e-3) -> RveBatch
     F = np.repeat((np.eye(2) + np.diag([strain, 0.0]))[None], nrve, axis=0)
     return RveBatch(2, np.full(nrve, N, np.int32), [ph] * nrve, mat, F,
                     {"workload": f"laminate {N}x{N} Q4, {nrve} RVEs"})
+
+
+def cook_batch(nrve: int, N: int = 30) -> RveBatch:
+    """Membrane RVEs of Section 5.2: the cross microstructure (phase 1 = the
+    second material) at every macro Gauss point, Fbar = I."""
+    ph = cross_phase(N)
+    mat = np.broadcast_to(mooney_rivlin_mat(MEMBRANE_MATERIAL_1, MEMBRANE_MATERIAL_2), (nrve, 2, 4)).copy()
+    F = np.broadcast_to(np.eye(2), (nrve, 2, 2)).copy()
+    return RveBatch(2, np.full(nrve, N, np.int32), [ph] * nrve, mat, F,
+                    meta={"kind": "cook membrane cross", "N": N})
 
 
 def fiber_batch(nrve: int = 4096, N: int = 32, seed: int = GLOBAL_SEED, strain: float = 1e-3,

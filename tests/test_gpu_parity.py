@@ -523,3 +523,60 @@ def test_staggered_scheme_matches_oracle_and_monolithic(torch, precision):
     fs2 = MonolithicFE2(ctx4, X, conn, fixed, b)
     with pytest.raises(RuntimeError):
         fs2.run(Ff, 2, scheme="staggered", tol_macro=1e-10, tol_micro=1e-11)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [6, 12])
+def test_mooney_rivlin_cross_rve_parity(torch, precision, N):
+    """Section 5.2 membrane RVE: the cross microstructure of the two
+    Mooney-Rivlin materials at finite, non-symmetric Fbar."""
+    b = W.cook_batch(5, N)
+    rng = np.random.default_rng(7)
+    b.Fbar = np.eye(2)[None] + 0.12 * rng.standard_normal((5, 2, 2))
+    ctx = ctx_for(torch, precision)
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    idx = list(range(b.nrve))
+    check(b, sig, Cb, st, oracle_batch(b, idx), idx, TOL[precision])
+
+
+def test_mooney_rivlin_is_2d_only(torch):
+    from paper_2312_12771_gb300.fe2 import Fe2Context, Fe2Error
+    ctx = Fe2Context(dim=3, precision="fp64")
+    b = W.sphere_batch(1, 3)
+    b.mat[:] = W.mooney_rivlin_mat(W.MEMBRANE_MATERIAL_1, W.MEMBRANE_MATERIAL_2)
+    with pytest.raises(Fe2Error):
+        ctx.register_batch(b)
+
+
+@pytest.mark.parametrize("scheme", ["monolithic", "staggered"])
+def test_cook_membrane_matches_oracle(torch, scheme):
+    """Section 5.2 Cook's membrane on a 2x2 macro mesh with 6x6 cross RVEs:
+    clamped left edge, traction (-5, 10) on the right edge in n_l = 2 load
+    steps.  Newton iteration counts, tip position and converged Pbar, Cbar
+    equal the oracle's (FP64 path)."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, edge_load
+    X, conn, left, right = W.cook_mesh(2, 2)
+    fixed = np.zeros(2 * len(X), np.uint8)
+    for n in left:
+        fixed[2 * n:2 * n + 2] = 1
+    b = W.cook_batch(4 * len(conn), 6)
+    ctx = ctx_for(torch, "fp64")
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    fext = edge_load(X, right, W.MEMBRANE_TRACTION)
+    kw = dict(tol_macro=1e-9, tol_micro=1e-11) if scheme == "staggered" else dict(tol_macro=1e-9, tol_micro=1e-9)
+    log = fe.run(np.eye(2), 2, scheme=scheme, fext=fext, **kw)
+    st = fe.state()
+    q = fe.ctx.macro_get_positions()
+    rves = [dict(N=6, phase=b.phase[k], mat=b.mat[k]) for k in range(b.nrve)]
+    fo = O.traction_load(X, right, W.MEMBRANE_TRACTION)
+    if scheme == "monolithic":
+        out, iters, q_ref = O.monolithic_fe2((X, conn, left), rves, np.eye(2), n_steps=2, fext=fo, **kw)
+    else:
+        out, iters, _, q_ref = O.staggered_fe2((X, conn, left), rves, np.eye(2), n_steps=2, fext=fo, **kw)
+    assert log.iters == iters
+    assert np.abs(q - q_ref).max() <= 1e-8 * np.abs(q_ref).max()
+    for k in range(b.nrve):
+        assert O.rel_err(st["Pbar"][k], out[k]["Pbar"]) <= 1e-9
+        assert O.rel_err(st["Cbar"][k], out[k]["Cbar"]) <= 1e-9

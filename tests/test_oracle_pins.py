@@ -89,14 +89,16 @@ def test_laminate_any_layer_width(rows):
 
 
 @pytest.mark.parametrize("d,N", [(2, 3), (2, 4), (3, 2)])
-@pytest.mark.parametrize("model", ["linear", "nh"])
+@pytest.mark.parametrize("model", ["linear", "nh", "mr"])
 def test_homogeneous_rve_recovers_local_law(d, N, model):
     rng = np.random.default_rng(3)
     F = np.eye(d) + 0.15 * rng.standard_normal((d, d))
     if model == "linear":
         m = np.array([0, 3.0, 0.3, 0])
-    else:
+    elif model == "nh":
         m = np.array([1, 1.5, 12.0, 0])
+    else:
+        m = np.array([2, 27.0, 18.0, 60.0])
     mat = np.stack([m, m])
     ph = (rng.random(N ** d) < 0.5).astype(np.uint8)
     s = O.rve_solve(N, d, ph, mat, F)
@@ -126,12 +128,12 @@ def test_neohooke_at_identity_equals_linear(d, N):
 
 
 @pytest.mark.parametrize("d", [2, 3])
-@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("model", [0, 1, 2])
 def test_stress_and_tangent_are_energy_derivatives(d, model):
     """Complex-step derivatives of the energy give P; of P give A."""
     rng = np.random.default_rng(11 + d)
     F = np.eye(d) + 0.2 * rng.standard_normal((d, d))
-    m = np.array([model, 2.0, 0.3 if model == 0 else 9.0, 0])
+    m = {0: np.array([0, 2.0, 0.3, 0]), 1: np.array([1, 2.0, 9.0, 0]), 2: np.array([2, 13.5, 6.5, 30.0])}[model]
     P, A = O.material(F[None], m, d)
     hcs = 1e-30
     Pc = np.zeros((d, d))
@@ -394,3 +396,45 @@ def test_staggered_and_monolithic_reach_the_same_equilibrium():
     for r0, r1 in zip(res[1:-1], res[2:]):
         if r0 < 1e-3:
             assert r1 < 10.0 * r0 * r0 + 1e-11
+
+
+def test_mooney_rivlin_membrane_form_and_limits():
+    """Section 5.2: the printed two-dimensional membrane energy
+    alpha (F:F - 2) + beta (F:F + J^2 - 3) + kappa/2 (J-1)^2 - 2 (alpha+2beta) ln J
+    equals Eq. (MR) with the plane-strain embedding; it is stress free at F = I;
+    beta = 0 gives the compressible Neo-Hooke law with mu = 2 alpha; at F = I
+    the tangent is the plane-strain Lame tensor with mu = 2(alpha+beta),
+    lambda = kappa + 4 beta."""
+    rng = np.random.default_rng(21)
+    al, be, ka = W.MEMBRANE_MATERIAL_1
+    for _ in range(5):
+        F = np.eye(2) + 0.25 * rng.standard_normal((2, 2))
+        J = np.linalg.det(F)
+        if J <= 0.1:
+            continue
+        printed = al * ((F * F).sum() - 2) + be * ((F * F).sum() + J ** 2 - 3) + ka / 2 * (J - 1) ** 2 \
+            - 2 * (al + 2 * be) * np.log(J)
+        assert abs(O.mooney_rivlin_energy(F[None], al, be, ka, 2)[0] - printed) < 1e-12 * abs(printed)
+        P0, A0 = O.mooney_rivlin(F[None], al, 0.0, ka, 2)
+        Pn, An = O.neohooke(F[None], 2 * al, ka, 2)
+        assert np.allclose(P0, Pn, atol=1e-12) and np.allclose(A0, An, atol=1e-12)
+    P, A = O.mooney_rivlin(np.eye(2)[None], al, be, ka, 2)
+    assert np.abs(P).max() < 1e-13
+    mu, lam = 2 * (al + be), ka + 4 * be
+    I = np.eye(2)
+    lame = lam * np.einsum("iJ,kL->iJkL", I, I) + mu * (np.einsum("ik,JL->iJkL", I, I) + np.einsum("iL,Jk->iJkL", I, I))
+    assert np.allclose(A[0], lame, atol=1e-12)
+
+
+def test_traction_load_is_the_surface_integral():
+    """Nodal forces of a constant traction sum to T times the edge length,
+    and their first moment is the exact moment of the uniform load."""
+    X, conn, left, right = W.cook_mesh(6, 5)
+    T = np.array(W.MEMBRANE_TRACTION)
+    f = O.traction_load(X, right, T)
+    L = np.linalg.norm(X[right[-1]] - X[right[0]])
+    assert np.allclose(f.sum(axis=0), T * L)
+    mid = 0.5 * (X[right[-1]] + X[right[0]])
+    m_nodes = np.sum(X[:, 0] * f[:, 1] - X[:, 1] * f[:, 0])
+    m_exact = (mid[0] * T[1] - mid[1] * T[0]) * L
+    assert abs(m_nodes - m_exact) < 1e-9 * abs(m_exact)
