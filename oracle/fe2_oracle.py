@@ -457,8 +457,9 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
     first brought to micro equilibrium r_m = 0 at its current Fbar by an inner
     Newton (starting from its last state), then Pbar and the condensed tangent
     Cbar = (K_MM - K_Mm K_mm^-1 K_mM)/|Omega| at that equilibrium give the
-    macro residual and stiffness.  The macro update moves only the macro
-    nodes; the micro states are re-equilibrated in the next iteration.
+    macro residual and stiffness (Eq. (solution1)).  After the macro update
+    the micro states follow Eq. (reduction), dw~ = -L^-1 E dq = -X_M : dFbar,
+    and are re-equilibrated in the next iteration.
     ``fext`` as in monolithic_fe2.  Returns the converged per-Gauss-point
     states, the macro iteration count of every load step, the total number of
     inner micro iterations and q."""
@@ -509,6 +510,11 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
             dq = np.zeros(2 * nnode)
             dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rg[free])
             q = q + dq.reshape(nnode, 2)
+            # Eq. (reduction): dw~ = -L^-1 E dq, i.e. -X_M : dFbar per Gauss point
+            for b in range(nb):
+                e = b // 4
+                dF = dq.reshape(nnode, 2)[conn[e]].T @ grads[b]
+                ws[b] = ws[b] - sols[b][1]["X_M"] @ dF.ravel()
         else:
             raise RuntimeError("macro Newton did not converge")
     out = []

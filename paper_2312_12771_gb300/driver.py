@@ -142,7 +142,8 @@ class MonolithicFE2:
         at their current Fbar (inner Newton w~ <- w~ - x_r, i.e. the micro
         update with dFbar = 0, until max ||r_m|| < tol_micro); Pbar and the
         condensed tangent at that equilibrium then give the macro residual and
-        stiffness, and the macro step moves only the macro nodes."""
+        stiffness (Eq. (solution1)); after the macro step the micro states follow
+        Eq. (reduction), dw~ = -X_M : dFbar, before they are re-equilibrated."""
         ctx = self.ctx
         if F_prev is not None:
             q = ctx.macro_get_positions() + self.X @ (np.asarray(Fk) - np.asarray(F_prev)).T
@@ -191,6 +192,8 @@ class MonolithicFE2:
                     log.failed = True
                 raise RuntimeError(f"macro residual {rmac:.3e}: Newton diverged")
             ctx.macro_solve(sig, Cb, self.dFbar, self.rn[1:2], self.mstatus)
+            # Eq. (reduction): dw~ = -X_M : dFbar (x_r vanishes at micro equilibrium)
+            ctx.macro_step(self.ids, self.dFbar)
         if log is not None:
             log.failed = True
         raise RuntimeError("macro Newton did not converge")
