@@ -72,6 +72,16 @@ enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1, FE2_MODEL_MOONEY_RIVLIN = 2
  * is the library's choice, currently the CUDA-core kernel (measured faster on
  * GB300 for these bands: the panel chain, not the update, bounds both). */
 enum { FE2_FACTOR_AUTO = 0, FE2_FACTOR_CUDA_CORE = 1, FE2_FACTOR_TENSOR_CORE = 2 };
+/* Macro interpolation of the fluctuation w~ (Section 3).  FE2_BASIS_DIRAC: Dirac
+ * pulses at the macro Gauss points, one RVE per Gauss point (Eqs.
+ * (fluctVaria_dirac), (fluctSolution)).  FE2_BASIS_CONST: piecewise constant
+ * per macro element, one RVE per element whose micro residual and stiffness
+ * are integrated over the element's nq = 4 macro Gauss points (Eqs.
+ * (constSolution1), (constSolution2)); 2D only.  With FE2_BASIS_CONST every
+ * per-RVE array below that has a Gauss-point dimension carries nq of them:
+ * Fbar/dFbar [n][nq][d][d], sigma_eff and Pbar [n][nq][d*d],
+ * Cbar [n][nq*d*d][nq*d*d] with Cbar[(q,iJ)][(q',kL)] = d sigma_{q,iJ} / d Fbar_{q',kL}. */
+enum { FE2_BASIS_DIRAC = 0, FE2_BASIS_CONST = 1 };
 
 typedef struct {
     int dim;                 /* 2 or 3                                            */
@@ -82,6 +92,7 @@ typedef struct {
     double refine_tol;       /* mixed path: accepted relative error estimate      */
     int max_refine;          /* mixed path: FP64-residual refinement sweeps (>=0) */
     int factor_kernel;       /* FE2_FACTOR_AUTO, _CUDA_CORE or _TENSOR_CORE       */
+    int macro_basis;         /* FE2_BASIS_DIRAC or FE2_BASIS_CONST                */
 } fe2_config;
 
 /* Create a context on the current CUDA device.  Allocates nothing large. */
@@ -176,6 +187,11 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
  * only those with which[t] != 0 when `which` [host] is not NULL (e.g. the
  * Dirichlet DOFs at the start of a load step).  Synchronises. */
 fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which);
+/* FE2_BASIS_CONST: the weights of the nq macro Gauss points of each element
+ * RVE, wq [host] double[n][nq] (eta_q / sum_q eta_q of its macro element, see
+ * fe2_macro_gradients; they sum to 1).  Registration sets 1/nq.  Returns
+ * FE2_ERR_ARG with the Dirac basis or for weights that are not positive. */
+fe2_status fe2_rve_set_quad_weights(fe2_ctx* ctx, int n, const int* rve_ids, const double* wq);
 /* Copy the current nodal positions to q_host [host] double[nnode][2].  Synchronises. */
 fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host);
 /* Nodal external forces of the current load, fext_host [host] double[nnode][2]
@@ -237,15 +253,19 @@ fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w);
  * (about 1.7 MB per RVE at N = 32, i.e. 37 RVEs; 0.45 MB at N = 16); larger
  * requests return FE2_ERR_BUDGET without running anything.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current, so make the first call on each device before any
- * stream capture.  Every call reuses the same array and leaves the previous
- * call's data in it: calls that overlap on the GPU (other streams, other host
+ * that device current, waits for its stream once and reads the set-up
+ * descriptors back to check them (FE2_ERR_CUDA if they are not as written), so
+ * make the first call on each device before any stream capture.  Every call
+ * reuses the same array and leaves the previous call's data in it: calls that overlap on the GPU (other streams, other host
  * threads) race and corrupt each other -- serialise them.
  */
 #define FE2_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint8_t* phase, const double* mat,
                                  const double* Fbar, double* sigma_eff, double* Cbar, int* rve_status,
                                  double* err_est, void* cuda_stream);
+/* Reason of the last failed fe2_rve_solve_noalloc call on any thread ("" after
+ * a call that succeeded); the string is owned by the library. */
+const char* fe2_noalloc_last_error(void);
 
 /*
  * Serving: continuous batching of RVE solve requests (S1 - S6 per request) as

@@ -21,6 +21,8 @@ What it computes (Hesch, Schmidt & Schuss, arXiv 2312.12771):
 * Section 4, Eqs. (discreteSys_K), (discreteSys_D), (discreteSys_L): the
   Hessian blocks, here per RVE: K_MM = int A, K_mM = int grad(R)^T A,
   K_mm = int grad(R)^T A grad(R).
+* Section 3, Eqs. (constSolution1), (constSolution2): the piecewise-constant
+  macro basis for w~, one RVE per macro element (rve_solve_elem).
 * Section 4.1: the classical staggered (nested) FE^2 scheme, with an inner
   micro Newton to equilibrium in every macro iteration (staggered_fe2).
 * Section 4.2, Eq. (solution2) and the update of w~ below it: the condensed
@@ -314,6 +316,56 @@ def rve_solve(N, d, phase, mat, Fbar, w=None, L=1.0):
     return out
 
 
+def rve_solve_elem(N, d, phase, mat, Fbars, wq, w=None, L=1.0):
+    """Piecewise-constant macro basis for w~ (Section 3, Eqs. (constSolution1),
+    (constSolution2)): one fluctuation w~ per macro element, whose micro
+    residual and stiffness are integrated over the element's macro Gauss
+    points q (deformation gradients Fbars[q], weights wq normalised to sum 1):
+      K_mm = sum_q wq K_mm(Fbar_q),  r_m = sum_q wq r_m(Fbar_q),  K_mM,q = K_mM(Fbar_q).
+    Condensing dw~ = -K_mm^-1 (r_m + sum_q wq K_mM,q : dFbar_q) gives per pair
+    of Gauss points (q, q') the d^2 x d^2 block
+      Cbar[q][q'] = (K_MM,q delta_qq' - K_Mm,q K_mm^-1 K_mM,q' wq')/|Omega|
+    and sigma_eff,q = (Pint_q - K_Mm,q K_mm^-1 r_m)/|Omega|.  With one Gauss
+    point this is rve_solve."""
+    nq = len(Fbars)
+    wq = np.asarray(wq, dtype=np.float64)
+    parts = []
+    for q in range(nq):
+        ints = rve_integrals(N, d, np.asarray(phase), np.asarray(mat), np.asarray(Fbars[q], float), w, L)
+        K_q, r_q, KmM_q = reduce_periodic(ints)
+        parts.append((K_q, r_q, KmM_q, ints["K_MM"], ints["Pint"], ints["vol"]))
+    K_mm = sum(wq[q] * parts[q][0] for q in range(nq))
+    r_m = sum(wq[q] * parts[q][1] for q in range(nq))
+    vol = parts[0][5]
+    cf = scipy.linalg.cho_factor(K_mm, lower=True)
+    X = [scipy.linalg.cho_solve(cf, parts[q][2]) for q in range(nq)]
+    x_r = scipy.linalg.cho_solve(cf, r_m)
+    dd = d * d
+    Cbar = np.zeros((nq * dd, nq * dd))
+    for q in range(nq):
+        for q2 in range(nq):
+            blk = -wq[q2] * parts[q][2].T @ X[q2]
+            if q == q2:
+                blk = blk + parts[q][3]
+            Cbar[q * dd:(q + 1) * dd, q2 * dd:(q2 + 1) * dd] = blk / vol
+    sigma = np.array([(parts[q][4] - parts[q][2].T @ x_r) / vol for q in range(nq)])
+    return dict(Cbar=Cbar, sigma_eff=sigma, X_M=X, x_r=x_r, r_m=r_m, K_mm=K_mm,
+                Pbar=np.array([parts[q][4] / vol for q in range(nq)]))
+
+
+def micro_equilibrate_elem(N, d, phase, mat, Fbars, wq, w=None, tol=1e-13, maxit=50, L=1.0):
+    """Inner Newton on one element RVE (piecewise-constant basis) at fixed
+    Fbars until ||r_m|| < tol, r_m = sum_q wq r_m(Fbar_q)."""
+    nm = d * (N ** d - 1)
+    w = np.zeros(nm) if w is None else np.array(w, dtype=np.float64)
+    for it in range(maxit):
+        s = rve_solve_elem(N, d, phase, mat, Fbars, wq, w, L)
+        if np.linalg.norm(s["r_m"]) < tol:
+            return w, it
+        w = w - s["x_r"]
+    raise RuntimeError("micro Newton did not converge")
+
+
 def micro_equilibrate(N, d, phase, mat, Fbar, w=None, tol=1e-13, maxit=50, L=1.0):
     """Classical inner Newton on one RVE at fixed Fbar (Section 4.1) until
     ||r_m|| < tol; returns the equilibrium fluctuation and iteration count."""
@@ -447,6 +499,87 @@ def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e
     for b in range(nb):
         Fb, s = sols[b]
         out.append(dict(Fbar=Fb, Pbar=s["Pbar"], Cbar=s["Cbar"], sigma_eff=s["sigma_eff"], w=ws[b]))
+    return out, iters, q
+
+
+def monolithic_fe2_const(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-9,
+                         maxit=25, record=None, fext=None):
+    """The monolithic Newton of monolithic_fe2 with the piecewise-constant
+    macro basis for w~ (Section 3, Eqs. (constSolution1), (constSolution2)):
+    ``rves`` holds one RVE per macro element; its solve (rve_solve_elem) uses
+    the Fbar of the element's four Gauss points with weights eta_q / sum eta.
+    Macro stiffness sum_q sum_q' eta_q B_q^T Cbar[q][q'] B_q', residual
+    sum_q eta_q B_q^T Pbar_q, update dw~ = -(x_r + sum_q w_q X_M,q : dFbar_q)."""
+    X, conn, bnd = macro
+    grads, etas, _ = macro_gauss(X, conn)
+    nel = len(conn)
+    nnode = len(X)
+    q = X.copy()
+    ws = [np.zeros(2 * (r["N"] ** 2 - 1)) for r in rves]
+    free = np.ones(2 * nnode, bool)
+    for n in bnd:
+        free[2 * n:2 * n + 2] = False
+
+    def Bmat(b):
+        Bm = np.zeros((4, 8))
+        for A_ in range(4):
+            for i in range(2):
+                for J in range(2):
+                    Bm[2 * i + J, 2 * A_ + i] = grads[b][A_, J]
+        return Bm
+
+    iters = []
+    for k in range(1, n_steps + 1):
+        Fk = np.eye(2) + (k / n_steps) * (np.asarray(F_final) - np.eye(2))
+        q[bnd] = X[bnd] @ Fk.T
+        for it in range(maxit):
+            Kg = np.zeros((2 * nnode, 2 * nnode))
+            Rg = np.zeros(2 * nnode)
+            Rc = np.zeros(2 * nnode)
+            sols, rmic = [], 0.0
+            for e in range(nel):
+                bs = [4 * e + g for g in range(4)]
+                Fbs = [q[conn[e]].T @ grads[b] for b in bs]
+                wq = etas[bs] / etas[bs].sum()
+                r = rves[e]
+                s = rve_solve_elem(r["N"], 2, r["phase"], r["mat"], Fbs, wq, ws[e])
+                sols.append((Fbs, wq, s))
+                rmic = max(rmic, np.linalg.norm(s["r_m"]))
+                dofs = np.array([[2 * conn[e][A_], 2 * conn[e][A_] + 1] for A_ in range(4)]).ravel()
+                for g in range(4):
+                    Bg = Bmat(bs[g])
+                    Rg[dofs] += etas[bs[g]] * Bg.T @ s["Pbar"][g].ravel()
+                    Rc[dofs] += etas[bs[g]] * Bg.T @ s["sigma_eff"][g].ravel()
+                    for g2 in range(4):
+                        blk = s["Cbar"][4 * g:4 * g + 4, 4 * g2:4 * g2 + 4]
+                        Kg[np.ix_(dofs, dofs)] += etas[bs[g]] * Bg.T @ blk @ Bmat(bs[g2])
+            if fext is not None:
+                Rg -= (k / n_steps) * np.asarray(fext).ravel()
+                Rc -= (k / n_steps) * np.asarray(fext).ravel()
+            rnorm = np.linalg.norm(Rg[free])
+            if record is not None:
+                record.append((k, it, rnorm, rmic))
+            if rnorm < tol_macro and rmic < tol_micro:
+                iters.append(it)
+                break
+            if not rnorm < 1e10:
+                raise RuntimeError("macro residual above 1e10: Newton diverged")
+            dq = np.zeros(2 * nnode)
+            dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rc[free])
+            q = q + dq.reshape(nnode, 2)
+            for e in range(nel):
+                Fbs, wq, s = sols[e]
+                upd = s["x_r"].copy()
+                for g in range(4):
+                    dF = dq.reshape(nnode, 2)[conn[e]].T @ grads[4 * e + g]
+                    upd += wq[g] * (s["X_M"][g] @ dF.ravel())
+                ws[e] = ws[e] - upd
+        else:
+            raise RuntimeError("macro Newton did not converge")
+    out = []
+    for e in range(nel):
+        Fbs, wq, s = sols[e]
+        out.append(dict(Fbar=np.array(Fbs), Pbar=s["Pbar"], Cbar=s["Cbar"], sigma_eff=s["sigma_eff"], w=ws[e]))
     return out, iters, q
 
 

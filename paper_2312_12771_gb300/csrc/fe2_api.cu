@@ -173,8 +173,8 @@ static const int* nbr_table(fe2_ctx* ctx, int N, int d) {
     return dptr;
 }
 
-static size_t persistent_bytes_of(int N, int d, int nphase) {
-    const int nn = nodes_of(N, d), nm = d * (nn - 1), nr = d * d + 1;
+static size_t persistent_bytes_of(int N, int d, int nphase, int nq = 1) {
+    const int nn = nodes_of(N, d), nm = d * (nn - 1), nr = d * d * nq + 1;
     const int nst = (d == 2 ? 9 : 27) * d * d;
     size_t b = 0;
     b += align256(nn);                               // phase
@@ -182,9 +182,12 @@ static size_t persistent_bytes_of(int N, int d, int nphase) {
     b += align256((size_t)nm * 8);                   // w
     b += align256((size_t)nst * nn * 8);             // stencil
     b += 2 * align256((size_t)nr * nm * 8);          // rhs, X
-    b += align256((size_t)(d * d * d * d + d * d) * 8);  // KMM, Pint
+    b += align256((size_t)(d * d * d * d + d * d) * nq * 8);  // KMM, Pint per macro Gauss point
     return b;
 }
+
+// macro Gauss points per RVE: 1 (Dirac basis) or 4 (element RVE, piecewise-constant basis)
+static int nq_of(const fe2_ctx* ctx) { return ctx->cfg.macro_basis == FE2_BASIS_CONST ? MAX_NQ : 1; }
 
 struct WsLayout {
     size_t offY, offR, offD, offWin, stride;
@@ -418,16 +421,20 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
     if (st != FE2_OK) return st;
     if (reset_status) CK(cudaMemsetAsync(status, 0, sizeof(int) * n, ctx->stream));
     Workspace ws{ctx->ws, l.stride, l.offY, l.offR, l.offD, l.offWin};
-    const int dd = ctx->cfg.dim * ctx->cfg.dim;
-    const bool d3 = ctx->cfg.dim == 3;
+    // per-RVE output sizes: sigma [nq][d^2], Cbar [nq d^2][nq d^2]
+    const int dd = ctx->cfg.dim * ctx->cfg.dim * nq_of(ctx);
+    const bool d3 = ctx->cfg.dim == 3, elem = nq_of(ctx) > 1;
     auto residual = [&](const int* di, int m, const int* active) {
-        return d3 ? launch_residual3(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream)
-                  : launch_residual(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream);
+        return d3     ? launch_residual3(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream)
+               : elem ? launch_residual_elem(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream)
+                      : launch_residual(ctx->d_tab, di, m, ws, b.maxnn, active, ctx->stream);
     };
     auto schur = [&](const int* di, int m, int corrected, double* sg, double* cb, int* stp, double* er,
                      const double* tol, int* redo, int sweep) {
-        return d3 ? launch_schur3(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep)
-                  : launch_schur(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep);
+        return d3     ? launch_schur3(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep)
+               : elem ? launch_schur_elem(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream,
+                                          sweep)
+                      : launch_schur(ctx->d_tab, di, m, ws, corrected, sg, cb, stp, er, tol, redo, ctx->stream, sweep);
     };
     for (int c0 = 0; c0 < n; c0 += cap) {
         const int m = std::min(cap, n - c0);
@@ -500,6 +507,8 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     if (cfg->precision != FE2_PREC_FP64 && cfg->precision != FE2_PREC_MIXED) return FE2_ERR_ARG;
     if (cfg->max_refine < 0 || cfg->max_refine > 16) return FE2_ERR_ARG;
     if (cfg->factor_kernel < FE2_FACTOR_AUTO || cfg->factor_kernel > FE2_FACTOR_TENSOR_CORE) return FE2_ERR_ARG;
+    if (cfg->macro_basis != FE2_BASIS_DIRAC && cfg->macro_basis != FE2_BASIS_CONST) return FE2_ERR_ARG;
+    if (cfg->macro_basis == FE2_BASIS_CONST && cfg->dim != 2) return FE2_ERR_ARG;
     ctx = new fe2_ctx();
     ctx->cfg = *cfg;
     if (!(ctx->cfg.refine_tol > 0.0)) ctx->cfg.refine_tol = 1e-10;
@@ -586,8 +595,9 @@ size_t fe2_rve_bytes(const fe2_ctx* ctx, int N) {
     const int d = ctx->cfg.dim;
     const int kd = compute_kd(const_cast<fe2_ctx*>(ctx), N, d);
     const int nn = nodes_of(N, d), nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
-    const WsLayout l = ws_layout(kd, d * d + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64, ctx->max_smem, d);
-    return persistent_bytes_of(N, d, 2) + l.stride;
+    const int nq = nq_of(ctx);
+    const WsLayout l = ws_layout(kd, d * d * nq + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64, ctx->max_smem, d);
+    return persistent_bytes_of(N, d, 2, nq) + l.stride;
 }
 
 fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase, int nphase,
@@ -603,12 +613,14 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
     for (int k = 0; k < nrve; ++k) {
         if (N[k] < 3 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range (N >= 3)", N[k]);
         const int kd = compute_kd(ctx, N[k], d);
-        const int nr = d * d + 1;
+        const int nr = d * d * nq_of(ctx) + 1;
+        if (nr > MAX_NR) return fail(ctx, FE2_ERR_ARG, "%d right-hand sides exceed the solver limit %d", nr, MAX_NR);
         {
+            // the FP64 path never runs the refinement solve (which keeps y in shared memory)
             const int nmk = d * (nodes_of(N[k], d) - 1), nmpk = (nmk + NB - 1) / NB * NB;
             if ((!use_smem_factor(kd, nr, fp64, ctx->max_smem, d) &&
                  (int)factor_gw_smem_bytes(kd, nr, fp64) > ctx->max_smem) ||
-                (int)solve_smem_bytes(kd, nr, nmpk, fp64) > ctx->max_smem)
+                (int)solve_smem_bytes(kd, nr, fp64 ? 0 : nmpk, fp64) > ctx->max_smem)
                 return fail(ctx, FE2_ERR_ARG, "N=%d: band of half width %d is too wide for the %s path", N[k], kd,
                             fp64 ? "FP64" : "mixed");
         }
@@ -625,7 +637,7 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
             if (phase[phase_off + e] >= nphase) return fail(ctx, FE2_ERR_ARG, "rve %d: phase index out of range", k);
         phase_off += nn;
         offs[k] = total;
-        total += persistent_bytes_of(N[k], d, nphase);
+        total += persistent_bytes_of(N[k], d, nphase, nq_of(ctx));
         const int nm = d * (nn - 1), nmp = (nm + NB - 1) / NB * NB;
         ws_need = std::max(ws_need, ws_layout(kd, nr, nm, nmp, fp64, ctx->max_smem, d).stride);
     }
@@ -688,7 +700,8 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
     std::vector<unsigned char> stage(total, 0);
     phase_off = 0;
     for (int k = 0; k < nrve; ++k) {
-        const int nn = nodes_of(N[k], d), nm = d * (nn - 1), nr = d * d + 1;
+        const int nq = nq_of(ctx);
+        const int nn = nodes_of(N[k], d), nm = d * (nn - 1), nr = d * d * nq + 1;
         const int nst = (d == 2 ? 9 : 27) * d * d;
         char* base = (char*)ch.dev + offs[k];
         unsigned char* hb = stage.data() + offs[k];
@@ -716,8 +729,10 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         o += align256((size_t)nr * nm * 8);
         r.X = (double*)(base + o);
         o += align256((size_t)nr * nm * 8);
-        r.KMM = (double*)(base + o);
-        r.Pint = r.KMM + d * d * d * d;
+        r.KMM = (double*)(base + o);                 // [nq][d^4], then Pint [nq][d^2]
+        r.Pint = r.KMM + d * d * d * d * nq;
+        r.nq = nq;
+        for (int g = 0; g < MAX_NQ; ++g) r.wq[g] = g < nq ? 1.0 / nq : 0.0;
         r.elem = nullptr;
         r.nbr = nbr_table(ctx, N[k], d);
         if (!r.nbr) return fail(ctx, FE2_ERR_CUDA, "neighbour table allocation failed");
@@ -760,7 +775,7 @@ fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids) {
         if (!h.active) continue;
         h.active = false;
         const RveDev& r = ctx->mirror[id];
-        ctx->persistent_bytes -= persistent_bytes_of(r.N, r.d, r.nphase);
+        ctx->persistent_bytes -= persistent_bytes_of(r.N, r.d, r.nphase, r.nq > 0 ? r.nq : 1);
         Chunk& c = ctx->chunks[h.chunk];
         if (--c.refs == 0) {
             CK(cudaFree(c.dev));
@@ -774,6 +789,8 @@ fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids) {
 
 fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar) {
     if (!ctx) return FE2_ERR_ARG;
+    if (ctx->cfg.macro_basis == FE2_BASIS_CONST)
+        return fail(ctx, FE2_ERR_ARG, "element RVEs (piecewise-constant basis) use the fused fe2_rve_solve");
     if (!Fbar) return fail(ctx, FE2_ERR_ARG, "Fbar is NULL");
     const int* d_ids = nullptr;
     fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
@@ -807,6 +824,8 @@ fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const dou
 
 fe2_status fe2_nullspace_reduce(fe2_ctx* ctx, int n, const int* rve_ids) {
     if (!ctx) return FE2_ERR_ARG;
+    if (ctx->cfg.macro_basis == FE2_BASIS_CONST)
+        return fail(ctx, FE2_ERR_ARG, "element RVEs (piecewise-constant basis) use the fused fe2_rve_solve");
     const int* d_ids = nullptr;
     fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
     if (st != FE2_OK) return st;
@@ -848,6 +867,11 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
         if (st != FE2_OK) return st;
         return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
     }
+    if (nq_of(ctx) > 1) {
+        TIMED("check_fbar", launch_check_fbar_dd(Fbar, n, 4 * nq_of(ctx), rve_status, ctx->stream));
+        TIMED("assemble_reduce_elem", launch_assemble_fused_elem(ctx->d_tab, d_ids, n, Fbar, ctx->stream));
+        return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
+    }
     TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));
     TIMED(b.all_linear ? "assemble_reduce_linear" : "assemble_reduce_general",
           launch_assemble_fused(ctx->d_tab, d_ids, n, Fbar, ctx->cfg.dim, b.maxN, b.all_linear ? 1 : 0, ctx->stream));
@@ -861,7 +885,10 @@ fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double*
     fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
     if (st != FE2_OK) return st;
     const BatchInfo b = batch_info(ctx, n, rve_ids);
-    TIMED("macro_update", launch_macro_update(ctx->d_tab, d_ids, n, dFbar, b.maxnm, ctx->stream));
+    if (nq_of(ctx) > 1)
+        TIMED("macro_update", launch_macro_update_elem(ctx->d_tab, d_ids, n, dFbar, b.maxnm, ctx->stream));
+    else
+        TIMED("macro_update", launch_macro_update(ctx->d_tab, d_ids, n, dFbar, b.maxnm, ctx->stream));
     for (int k = 0; k < n; ++k) ctx->mirror[rve_ids[k]].zero_w = 0;
     return FE2_OK;
 }
@@ -1081,8 +1108,12 @@ fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready || !sigma || !Cbar || !dFbar || !rnorm)
         return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
-    TIMED("macro_solve", launch_macro_solve(ctx->macro, sigma, Cbar, dFbar, rnorm,
-                                            status ? status : ctx->d_macro_status, ctx->stream));
+    if (nq_of(ctx) > 1)
+        TIMED("macro_solve", launch_macro_solve_elem(ctx->macro, sigma, Cbar, dFbar, rnorm,
+                                                     status ? status : ctx->d_macro_status, ctx->stream));
+    else
+        TIMED("macro_solve", launch_macro_solve(ctx->macro, sigma, Cbar, dFbar, rnorm,
+                                                status ? status : ctx->d_macro_status, ctx->stream));
     ctx->launches += 6;
     return FE2_OK;
 }
@@ -1093,8 +1124,28 @@ fe2_status fe2_rve_average_stress(fe2_ctx* ctx, int n, const int* rve_ids, doubl
     const int* d_ids = nullptr;
     fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
     if (st != FE2_OK) return st;
-    TIMED("rve_average_stress", launch_rve_avg_stress(ctx->d_tab, d_ids, n, Pbar, ctx->stream));
+    if (nq_of(ctx) > 1)
+        TIMED("rve_average_stress", launch_rve_avg_stress_elem(ctx->d_tab, d_ids, n, Pbar, ctx->stream));
+    else
+        TIMED("rve_average_stress", launch_rve_avg_stress(ctx->d_tab, d_ids, n, Pbar, ctx->stream));
     return FE2_OK;
+}
+
+fe2_status fe2_rve_set_quad_weights(fe2_ctx* ctx, int n, const int* rve_ids, const double* wq) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (nq_of(ctx) == 1) return fail(ctx, FE2_ERR_ARG, "quadrature weights belong to element RVEs (FE2_BASIS_CONST)");
+    if (n < 0 || (n > 0 && (!rve_ids || !wq))) return fail(ctx, FE2_ERR_ARG, "bad weight arguments");
+    const int nq = nq_of(ctx);
+    for (int k = 0; k < n; ++k) {
+        const int id = rve_ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        for (int g = 0; g < nq; ++g)
+            if (!(wq[(size_t)k * nq + g] > 0.0)) return fail(ctx, FE2_ERR_ARG, "weight %d of rve %d is not positive", g, id);
+    }
+    for (int k = 0; k < n; ++k)
+        for (int g = 0; g < nq; ++g) ctx->mirror[rve_ids[k]].wq[g] = wq[(size_t)k * nq + g];
+    return upload_all(ctx);
 }
 
 fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double* rnorm) {
@@ -1226,6 +1277,7 @@ fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server
     *out = nullptr;
     if (max_batch < 1 || nlanes < 1 || nlanes > 8) return fail(ctx, FE2_ERR_ARG, "bad server sizes");
     if (ctx->cfg.dim != 2) return fail(ctx, FE2_ERR_ARG, "the server batches 2D (Q4) RVEs");
+    if (nq_of(ctx) > 1) return fail(ctx, FE2_ERR_ARG, "the server batches Dirac-basis RVEs");
     fe2_server* srv = new fe2_server();
     srv->ctx = ctx;
     srv->max_batch = max_batch;

@@ -227,6 +227,65 @@ __global__ void __launch_bounds__(256) k_assemble_fused_general2(const RveDev* _
     else if (threadIdx.x < 20) r.Pint[threadIdx.x - 16] = tot[threadIdx.x];
 }
 
+// Element RVE (piecewise-constant macro basis, Eqs. (constSolution1), (constSolution2)):
+// one CTA per RVE, one thread per node row.  For each of the nq macro Gauss points g
+// (Fbar[(slot*nq + g)*4 ..]) the rows are integrated at (Fbar_g, w~); the stencil and
+// r_m are the wq_g-weighted sums (accumulated in the thread's own rows, g in order),
+// the K_mM rows of g go to rhs columns 4g..4g+3, r_m to column 4 nq, and K_MM, Pint
+// of g to KMM[16 g ..], Pint[4 g ..].
+__global__ void __launch_bounds__(256) k_assemble_fused_elem2(const RveDev* __restrict__ tab,
+                                                              const int* __restrict__ ids,
+                                                              const double* __restrict__ Fbar) {
+    __shared__ double red[256];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N, nq = r.nq, nn = r.nn, nm = r.nm;
+    for (int g = 0; g < nq; ++g) {
+        double Fb[4];
+        for (int k = 0; k < 4; ++k) Fb[k] = Fbar[(size_t)(blockIdx.x * nq + g) * 4 + k];
+        const double wg = r.wq[g];
+        double mm[20];
+        for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+        for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+            const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+            double st[9][2][2] = {};
+            double f[2] = {0.0, 0.0}, kM[2][4] = {};
+            for (int a = 0; a < 4; ++a) {
+                const int ax = a & 1, ay = a >> 1;
+                const int ex = (i - ax + N) % N, ey = (j - ay + N) % N;
+                Rows2 rw;
+                elem_rows2(r, ex, ey, a, Fb, rw, a == 0 ? mm : nullptr);
+                for (int b = 0; b < 4; ++b) {
+                    const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                    for (int c = 0; c < 2; ++c)
+                        for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += rw.kr[b][c][c2];
+                }
+                for (int c = 0; c < 2; ++c) {
+                    f[c] += rw.f[c];
+                    for (int kL = 0; kL < 4; ++kL) kM[c][kL] += rw.kM[c][kL];
+                }
+            }
+            for (int off = 0; off < 9; ++off)
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2) {
+                        double* p = r.stencil + (size_t)((off * 2 + c) * 2 + c2) * nn + q;
+                        *p = (g == 0 ? 0.0 : *p) + wg * st[off][c][c2];
+                    }
+            if (q == 0) continue;  // pinned corner: no reduced DOF
+            for (int c = 0; c < 2; ++c) {
+                const int dof = 2 * (q - 1) + c;
+                for (int kL = 0; kL < 4; ++kL) r.rhs[(size_t)(4 * g + kL) * nm + dof] = kM[c][kL];
+                double* pr = r.rhs + (size_t)(4 * nq) * nm + dof;
+                *pr = (g == 0 ? 0.0 : *pr) + wg * f[c];
+            }
+        }
+        double tot[20];
+        block_sum<20>(mm, red, tot);
+        if (threadIdx.x < 16) r.KMM[16 * g + threadIdx.x] = tot[threadIdx.x];
+        else if (threadIdx.x < 20) r.Pint[4 * g + threadIdx.x - 16] = tot[threadIdx.x];
+        __syncthreads();
+    }
+}
+
 // Split S1 + S2: one thread per (element, local node a).
 __global__ void __launch_bounds__(128) k_assemble_elems2(const RveDev* __restrict__ tab,
                                                          const int* __restrict__ ids,
@@ -422,6 +481,16 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
         k_assemble_fused_linear2<<<n, 256, 0, s>>>(tab, ids, Fbar);
     else
         k_assemble_fused_general2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, cudaStream_t s) {
+    k_assemble_fused_elem2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_fbar_dd(const double* Fbar, int n, int dd, int* status, cudaStream_t s) {
+    k_check_fbar<<<(n + 255) / 256, 256, 0, s>>>(Fbar, n, dd, status);
     return cudaGetLastError();
 }
 

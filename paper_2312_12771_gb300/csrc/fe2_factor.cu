@@ -423,7 +423,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                               T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to) {
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ T tv[16][NB];
+    __shared__ T tv[MAX_NR][NB];
     for (int k = tid; k < nr * 2 * S; k += blockDim.x) xr[k] = T(0);
     const int nblk = nmp / NB;
     ls.issue(k0, nmp - NB);
@@ -661,11 +661,11 @@ size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64) {
     if (fp64) {
         SolveLayout<double> l;
         l.init(kd, nr, nmp, true);
-        return l.total + 16 * NB * sizeof(double);
+        return l.total + MAX_NR * NB * sizeof(double);
     }
     SolveLayout<float> l;
     l.init(kd, nr, nmp, true);
-    return l.total + 16 * NB * sizeof(float);
+    return l.total + MAX_NR * NB * sizeof(float);
 }
 
 size_t factor_smem_bytes(int kd, int nr, bool fp64) {

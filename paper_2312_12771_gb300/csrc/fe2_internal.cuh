@@ -29,7 +29,8 @@ struct RveDev {
     double* elem;               // split path: element workspace [ncomp][nn] (or null)
     const int* nbr;             // [nn][3^d] folded index of each node's neighbours (shared per N)
     int zero_w;                 // 1 while w is known to be exactly zero
-    int pad_;
+    int nq;                     // macro Gauss points per RVE: 1 (Dirac basis) or 4 (element RVE)
+    double wq[4];               // element RVE: normalised weights of its macro Gauss points
 };
 
 // Transient per-launch workspace: slot s of a launch owns
@@ -56,6 +57,9 @@ __host__ __device__ constexpr int elem_row_comps(int d) {
 __host__ __device__ constexpr int elem_comps(int d) {
     return (1 << d) * elem_row_comps(d) + d * d * d * d + d * d;
 }
+
+constexpr int MAX_NQ = 4;      // macro Gauss points of an element RVE (2D Q4)
+constexpr int MAX_NR = 4 * MAX_NQ + 1;  // right-hand sides of the band solves (2D element RVE: 17)
 
 // ---------------------------------------------------------------- launchers
 // every launcher returns cudaGetLastError() of its launch(es)
@@ -127,6 +131,20 @@ cudaError_t launch_macro_residual(const MacroDev& M, const double* stress, doubl
 cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
                                double* rnorm, int* status, cudaStream_t s);
 cudaError_t launch_rve_avg_stress(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
+
+// element RVEs (piecewise-constant macro basis, 2D, nq = 4, nr = 17)
+cudaError_t launch_check_fbar_dd(const double* Fbar, int n, int dd, int* status, cudaStream_t s);
+cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, cudaStream_t s);
+cudaError_t launch_residual_elem(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
+                                 const int* active, cudaStream_t s);
+cudaError_t launch_schur_elem(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
+                              double* Cbar, int* status, double* err, const double* tol, int* redo, cudaStream_t s,
+                              int refine_sweep);
+cudaError_t launch_macro_update_elem(const RveDev* tab, const int* ids, int n, const double* dF, int maxnm,
+                                     cudaStream_t s);
+cudaError_t launch_rve_avg_stress_elem(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
+cudaError_t launch_macro_solve_elem(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
+                                    double* rnorm, int* status, cudaStream_t s);
 cudaError_t launch_rve_rnorm(const RveDev* tab, const int* ids, int n, double* out, cudaStream_t s);
 
 }  // namespace fe2

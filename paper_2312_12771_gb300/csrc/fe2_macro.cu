@@ -67,6 +67,46 @@ __global__ void k_macro_assemble(MacroDev M, const double* __restrict__ stress, 
     M.R[i] = r - M.fext[t];  // internal minus external virtual work (Eq. (weakMech))
 }
 
+// Element RVEs (piecewise-constant basis): the condensed tangent couples the
+// four Gauss points of an element, Cbar_e[(4g + iJ)][(4g' + kL)] (16 x 16), so
+// K_AB = sum_e sum_g sum_g' eta_g B_g(A)^T Cbar_e[g][g'] B_g'(B).  R as above.
+__global__ void k_macro_assemble_elem(MacroDev M, const double* __restrict__ stress, const double* __restrict__ Cbar) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * M.nnode) return;
+    const int i = M.dof2free[t];
+    if (i < 0) return;
+    const int A = t >> 1, c = t & 1;
+    const int LD = M.kd + 1;
+    double r = 0.0;
+    for (int p = M.adj_ptr[A]; p < M.adj_ptr[A + 1]; ++p) {
+        const int e = M.adj[p] >> 2, a = M.adj[p] & 3;
+        const double* Ce = Cbar + (size_t)e * 256;
+        for (int g = 0; g < 4; ++g) {
+            const int b = 4 * e + g;
+            const double* G = M.grads + (size_t)b * 8;
+            const double eta = M.eta[b];
+            r += eta * (stress[4 * b + 2 * c] * G[2 * a] + stress[4 * b + 2 * c + 1] * G[2 * a + 1]);
+            for (int g2 = 0; g2 < 4; ++g2) {
+                const double* G2 = M.grads + (size_t)(4 * e + g2) * 8;
+                // tk_kL = sum_J G_aJ Cbar_e[(g, c, J)][(g2, kL)]
+                double tk[4];
+                for (int kL = 0; kL < 4; ++kL)
+                    tk[kL] = G[2 * a] * Ce[(4 * g + 2 * c) * 16 + 4 * g2 + kL] +
+                             G[2 * a + 1] * Ce[(4 * g + 2 * c + 1) * 16 + 4 * g2 + kL];
+                for (int Bn = 0; Bn < 4; ++Bn) {
+                    const int nb = M.conn[4 * e + Bn];
+                    for (int k = 0; k < 2; ++k) {
+                        const int j = M.dof2free[2 * nb + k];
+                        if (j < 0 || j > i) continue;
+                        M.K[(size_t)j * LD + (i - j)] += eta * (tk[2 * k] * G2[2 * Bn] + tk[2 * k + 1] * G2[2 * Bn + 1]);
+                    }
+                }
+            }
+        }
+    }
+    M.R[i] = r - M.fext[t];
+}
+
 // One CTA: ||R||_2 of the free residual (deterministic tree).
 __global__ void k_macro_norm(MacroDev M, double* __restrict__ out) {
     __shared__ double red[1024];
@@ -213,6 +253,19 @@ cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const do
     cudaError_t e = cudaMemsetAsync(M.K, 0, sizeof(double) * (size_t)M.nfree * (M.kd + 1), s);
     if (e != cudaSuccess) return e;
     k_macro_assemble<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M, stress, Cbar, 1);
+    k_macro_norm<<<1, 1024, 0, s>>>(M, rnorm);
+    k_macro_chol_solve<<<1, 1024, 0, s>>>(M, status);
+    k_macro_apply<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M, dFbar);
+    k_macro_apply2<<<(M.ngp + 127) / 128, 128, 0, s>>>(M, dFbar);
+    k_macro_apply3<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_solve_elem(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
+                                    double* rnorm, int* status, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(M.K, 0, sizeof(double) * (size_t)M.nfree * (M.kd + 1), s);
+    if (e != cudaSuccess) return e;
+    k_macro_assemble_elem<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M, stress, Cbar);
     k_macro_norm<<<1, 1024, 0, s>>>(M, rnorm);
     k_macro_chol_solve<<<1, 1024, 0, s>>>(M, status);
     k_macro_apply<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M, dFbar);

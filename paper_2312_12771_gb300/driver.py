@@ -58,7 +58,10 @@ class NewtonLog:
 
 
 class MonolithicFE2:
-    """Macro Q4 problem with one RVE per macro Gauss point (b = 4 e + q)."""
+    """Macro Q4 problem with one RVE per macro Gauss point (b = 4 e + q), or,
+    on a context with the piecewise-constant basis, one element RVE per macro
+    element (Eqs. (constSolution1), (constSolution2)) whose four Gauss points
+    are weighted by eta_q / sum eta."""
 
     def __init__(self, ctx, X, conn, fixed, batch):
         import torch
@@ -67,8 +70,10 @@ class MonolithicFE2:
         self.X = np.asarray(X, float)
         self.fixed = np.asarray(fixed, np.uint8)
         ngp = 4 * len(conn)
-        if batch.nrve != ngp:
-            raise ValueError(f"need one RVE per macro Gauss point ({ngp}), got {batch.nrve}")
+        nrve = ngp // getattr(ctx, "nq", 1)
+        if batch.nrve != nrve:
+            raise ValueError(f"need {nrve} RVEs ({'macro elements' if nrve != ngp else 'macro Gauss points'}), "
+                             f"got {batch.nrve}")
         ctx.macro_setup(self.X, conn, self.fixed)
         self.ids = ctx.register_batch(batch)
         dev = "cuda"
@@ -76,9 +81,14 @@ class MonolithicFE2:
         self.Fbar = torch.zeros((ngp, 2, 2), dtype=f64, device=dev)
         self.dFbar = torch.zeros_like(self.Fbar)
         self.Pbar = torch.zeros((ngp, 4), dtype=f64, device=dev)
-        self.outs = ctx._outs(ngp)
+        self.outs = ctx._outs(nrve)
         self.rn = torch.zeros(2, dtype=f64, device=dev)
-        self.rnm = torch.zeros(ngp, dtype=f64, device=dev)
+        self.rnm = torch.zeros(nrve, dtype=f64, device=dev)
+        if nrve != ngp:
+            eta = torch.zeros(ngp, dtype=f64, device=dev)
+            ctx.macro_gradients(self.Fbar, eta)
+            e = eta.cpu().numpy().reshape(nrve, 4)
+            ctx.rve_set_quad_weights(self.ids, e / e.sum(axis=1, keepdims=True))
         self.mstatus = torch.zeros(1, dtype=torch.int32, device=dev)
         self.zero_dF = torch.zeros_like(self.Fbar)
         self.ngp = ngp

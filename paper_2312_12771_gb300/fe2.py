@@ -24,6 +24,8 @@ FE2_ELEM_Q4, FE2_ELEM_HEX8 = 0, 1
 FE2_PREC_FP64, FE2_PREC_MIXED = 0, 1
 FE2_FACTOR_AUTO, FE2_FACTOR_CUDA_CORE, FE2_FACTOR_TENSOR_CORE = 0, 1, 2
 FACTOR_KERNELS = {"auto": FE2_FACTOR_AUTO, "cuda_core": FE2_FACTOR_CUDA_CORE, "tensor_core": FE2_FACTOR_TENSOR_CORE}
+FE2_BASIS_DIRAC, FE2_BASIS_CONST = 0, 1
+MACRO_BASES = {"dirac": FE2_BASIS_DIRAC, "const": FE2_BASIS_CONST}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_BUDGET", 4: "NOT_PD", 5: "NAN",
                 6: "NO_CONV", 7: "TIMEOUT"}
 
@@ -32,7 +34,7 @@ class fe2_config(C.Structure):
     _fields_ = [("dim", C.c_int), ("elem", C.c_int), ("precision", C.c_int),
                 ("hbm_budget_bytes", C.c_size_t), ("cuda_stream", C.c_void_p),
                 ("refine_tol", C.c_double), ("max_refine", C.c_int),
-                ("factor_kernel", C.c_int)]
+                ("factor_kernel", C.c_int), ("macro_basis", C.c_int)]
 
 
 class Fe2Error(RuntimeError):
@@ -64,6 +66,7 @@ _SIGS = {
     "fe2_macro_set_positions": (_I, [_P, _DP, C.POINTER(C.c_uint8)]),
     "fe2_macro_get_positions": (_I, [_P, _DP]),
     "fe2_macro_set_load": (_I, [_P, _DP]),
+    "fe2_rve_set_quad_weights": (_I, [_P, _I, _IP, _DP]),
     "fe2_macro_gradients": (_I, [_P, _P, _P]),
     "fe2_macro_residual": (_I, [_P, _P, _P]),
     "fe2_macro_solve": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -73,6 +76,7 @@ _SIGS = {
     "fe2_rve_set_w": (_I, [_P, _I, _DP]),
     "fe2_launch_count": (C.c_longlong, [_P]),
     "fe2_rve_solve_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "fe2_noalloc_last_error": (C.c_char_p, []),
     "fe2_server_create": (_I, [_P, _I, _I, C.POINTER(_P)]),
     "fe2_server_destroy": (None, [_P]),
     "fe2_server_submit": (_I, [_P, _I, _IP, _DP, C.POINTER(C.c_longlong)]),
@@ -150,7 +154,8 @@ def rve_solve_noalloc(N, phase, mat, Fbar, out, stream=None):
     code = load().fe2_rve_solve_noalloc(int(N), int(n), int(nphase), _ptr(phase), _ptr(mat), _ptr(Fbar),
                                         _ptr(sig), _ptr(Cb), _ptr(st), _ptr(err), C.c_void_p(s.cuda_stream))
     if code != FE2_OK:
-        raise Fe2Error(code, f"fe2_rve_solve_noalloc(N={N}, n={n}) failed")
+        why = load().fe2_noalloc_last_error().decode()
+        raise Fe2Error(code, f"fe2_rve_solve_noalloc(N={N}, n={n}) failed: {why}")
     return out
 
 
@@ -158,7 +163,7 @@ class Fe2Context:
     """A libfe2 context on the current CUDA device and stream."""
 
     def __init__(self, dim=2, precision="mixed", hbm_budget_bytes=0, refine_tol=1e-10, max_refine=1,
-                 stream=None, factor="auto"):
+                 stream=None, factor="auto", basis="dirac"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libfe2 needs a CUDA GPU (GB300, sm_103a)")
@@ -169,7 +174,9 @@ class Fe2Context:
         cfg = fe2_config(dim, FE2_ELEM_Q4 if dim == 2 else FE2_ELEM_HEX8,
                          FE2_PREC_MIXED if precision == "mixed" else FE2_PREC_FP64,
                          int(hbm_budget_bytes), C.c_void_p(self.stream.cuda_stream), float(refine_tol),
-                         int(max_refine), FACTOR_KERNELS[factor])
+                         int(max_refine), FACTOR_KERNELS[factor], MACRO_BASES[basis])
+        self.basis = basis
+        self.nq = 4 if basis == "const" else 1
         self.cfg = cfg
         self.h = fe2_create(cfg)
         self.lib = load()
@@ -214,8 +221,9 @@ class Fe2Context:
 
     # -- the hot path ------------------------------------------------------------
     def _outs(self, n):
+        """(sigma_eff [n, nq*d*d], Cbar [n, nq*d*d, nq*d*d], status [n], err [n])."""
         t = self.torch
-        dd = self.dim * self.dim
+        dd = self.dim * self.dim * self.nq
         dev = "cuda"
         return (t.empty((n, dd), dtype=t.float64, device=dev), t.empty((n, dd, dd), dtype=t.float64, device=dev),
                 t.empty(n, dtype=t.int32, device=dev), t.empty(n, dtype=t.float64, device=dev))
@@ -273,6 +281,13 @@ class Fe2Context:
         self._check(self.lib.fe2_macro_get_positions(self.h, q.ctypes.data_as(_DP)), "fe2_macro_get_positions")
         return q
 
+    def rve_set_quad_weights(self, ids, wq):
+        """Element RVEs: normalised weights [n][nq] of their macro Gauss points."""
+        a, p = _ids(ids)
+        w = np.ascontiguousarray(np.asarray(wq, dtype=np.float64).reshape(len(a), self.nq))
+        self._check(self.lib.fe2_rve_set_quad_weights(self.h, len(a), p, w.ctypes.data_as(_DP)),
+                    "fe2_rve_set_quad_weights")
+
     def macro_set_load(self, fext):
         """Nodal external forces [nnode][2] of the current load (None = no load)."""
         if fext is None:
@@ -281,8 +296,10 @@ class Fe2Context:
         f = np.ascontiguousarray(np.asarray(fext, dtype=np.float64).reshape(self.macro_nnode, 2))
         self._check(self.lib.fe2_macro_set_load(self.h, f.ctypes.data_as(_DP)), "fe2_macro_set_load")
 
-    def macro_gradients(self, Fbar):
-        self._check(self.lib.fe2_macro_gradients(self.h, _ptr(Fbar), None), "fe2_macro_gradients")
+    def macro_gradients(self, Fbar, eta=None):
+        """Fbar_b of every macro Gauss point; eta (optional) receives the weights."""
+        self._check(self.lib.fe2_macro_gradients(self.h, _ptr(Fbar), None if eta is None else _ptr(eta)),
+                    "fe2_macro_gradients")
 
     def macro_residual(self, stress, rnorm):
         self._check(self.lib.fe2_macro_residual(self.h, _ptr(stress), _ptr(rnorm)), "fe2_macro_residual")

@@ -570,3 +570,57 @@ def test_cook_membrane_matches_oracle(torch, scheme):
     for k in range(b.nrve):
         assert O.rel_err(st["Pbar"][k], out[k]["Pbar"]) <= 1e-9
         assert O.rel_err(st["Cbar"][k], out[k]["Cbar"]) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_element_rve_piecewise_constant_basis_parity(torch, precision):
+    """Eqs. (constSolution1), (constSolution2): element RVEs with four macro
+    Gauss points (different Fbar, non-uniform weights) against the oracle's
+    rve_solve_elem: the 16x16 coupled tangent and the four stresses."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    n, N = 6, 6
+    b = W.inclusion_batch(n, N, stretch=1.0)
+    rng = np.random.default_rng(13)
+    F = np.eye(2)[None, None] + 0.06 * rng.standard_normal((n, 4, 2, 2))
+    wq = rng.uniform(0.5, 1.5, (n, 4))
+    wq /= wq.sum(axis=1, keepdims=True)
+    ctx = Fe2Context(dim=2, precision=precision, basis="const")
+    ids = ctx.register_batch(b)
+    ctx.rve_set_quad_weights(ids, wq)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(F, device="cuda"))
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    sig = sig.cpu().numpy().reshape(n, 4, 4)
+    Cb = Cb.cpu().numpy()
+    tol = TOL[precision]
+    for k in range(n):
+        ref = O.rve_solve_elem(N, 2, b.phase[k], b.mat[k], list(F[k]), wq[k])
+        assert O.rel_err(Cb[k], ref["Cbar"]) <= tol
+        floor = np.linalg.norm(ref["Cbar"]) * np.linalg.norm(F[k] - np.eye(2)[None])
+        assert O.rel_err(sig[k], ref["sigma_eff"], floor) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_piecewise_constant_basis_newton_matches_oracle(torch, precision):
+    """Monolithic Newton with one element RVE per macro element (macro 2x2
+    Q4, NH inclusion RVEs 6x6, stretch 1.1 in 2 steps): iteration counts,
+    nodal positions and converged Pbar, Cbar equal the oracle's."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    N = 6
+    X, conn, fixed = macro_mesh(2, 2)
+    b = W.inclusion_batch(len(conn), N, stretch=1.0)
+    ctx = Fe2Context(dim=2, precision=precision, basis="const", refine_tol=1e-14, max_refine=2)
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    Ff = np.diag([1.1, 1.0])
+    log = fe.run(Ff, 2, tol_macro=1e-10, tol_micro=1e-10)
+    st = fe.state()
+    rves = [dict(N=N, phase=b.phase[k], mat=b.mat[k]) for k in range(len(conn))]
+    out, iters, q = O.monolithic_fe2_const(O.macro_mesh(2, 2), rves, Ff, n_steps=2, tol_macro=1e-10,
+                                           tol_micro=1e-10)
+    assert log.iters == iters
+    tol = TOL[precision]
+    for e in range(len(conn)):
+        assert O.rel_err(st["Pbar"][4 * e:4 * e + 4], out[e]["Pbar"]) <= tol
+        assert O.rel_err(st["Cbar"][e], out[e]["Cbar"]) <= tol
+    assert np.abs(fe.ctx.macro_get_positions() - q).max() <= 1e-11

@@ -438,3 +438,75 @@ def test_traction_load_is_the_surface_integral():
     m_nodes = np.sum(X[:, 0] * f[:, 1] - X[:, 1] * f[:, 0])
     m_exact = (mid[0] * T[1] - mid[1] * T[0]) * L
     assert abs(m_nodes - m_exact) < 1e-9 * abs(m_exact)
+
+
+def test_element_rve_piecewise_constant_basis():
+    """Eqs. (constSolution1), (constSolution2): one w~ per macro element.
+    With one Gauss point it is the Dirac RVE solve; the 16x16 condensed
+    tangent is the central-difference derivative of the equilibrium Pbar_q
+    with respect to Fbar_q' (the element RVE re-equilibrated); it is
+    symmetric after weighting; uniform dFbar over the element reproduces the
+    Dirac tangent when all Gauss points share Fbar."""
+    rng = np.random.default_rng(1)
+    N = 4
+    c, r = W.random_inclusions(W.GLOBAL_SEED, 3)
+    ph = W.inclusion_phase(N, 2, c, r)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    Fs = [np.eye(2) + 0.05 * rng.standard_normal((2, 2)) for _ in range(4)]
+    wq = np.array([0.2, 0.3, 0.1, 0.4])
+    a = O.rve_solve_elem(N, 2, ph, mat, [Fs[0]], [1.0])
+    b = O.rve_solve(N, 2, ph, mat, Fs[0])
+    assert np.abs(a["Cbar"] - b["Cbar"]).max() < 1e-14 * np.abs(b["Cbar"]).max()
+    w, _ = O.micro_equilibrate_elem(N, 2, ph, mat, Fs, wq, tol=1e-13)
+    s = O.rve_solve_elem(N, 2, ph, mat, Fs, wq, w)
+    h = 1e-6
+    C_fd = np.zeros((16, 16))
+    for q2 in range(4):
+        for kL in range(4):
+            Fp = [F.copy() for F in Fs]
+            Fm = [F.copy() for F in Fs]
+            Fp[q2].flat[kL] += h
+            Fm[q2].flat[kL] -= h
+            wp, _ = O.micro_equilibrate_elem(N, 2, ph, mat, Fp, wq, w, tol=1e-13)
+            wm, _ = O.micro_equilibrate_elem(N, 2, ph, mat, Fm, wq, w, tol=1e-13)
+            Pp = O.rve_solve_elem(N, 2, ph, mat, Fp, wq, wp)["Pbar"]
+            Pm = O.rve_solve_elem(N, 2, ph, mat, Fm, wq, wm)["Pbar"]
+            C_fd[:, 4 * q2 + kL] = ((Pp - Pm) / (2 * h)).ravel()
+    assert np.abs(C_fd - s["Cbar"]).max() < 1e-7 * np.abs(s["Cbar"]).max()
+    M = np.kron(np.diag(wq), np.eye(4)) @ s["Cbar"]
+    assert np.abs(M - M.T).max() < 1e-12 * np.abs(M).max()
+    Fc = [Fs[0]] * 4
+    e = O.rve_solve_elem(N, 2, ph, mat, Fc, wq)
+    d = O.rve_solve(N, 2, ph, mat, Fs[0])
+    for g in range(4):
+        uni = sum(e["Cbar"][4 * g:4 * g + 4, 4 * g2:4 * g2 + 4] for g2 in range(4))
+        assert np.abs(uni - d["Cbar"]).max() < 1e-12 * np.abs(d["Cbar"]).max()
+
+
+def test_piecewise_constant_basis_patch_test_and_convergence():
+    """Element RVEs in the monolithic Newton: homogeneous microstructure and
+    affine Dirichlet data give the affine macro solution; a heterogeneous
+    problem converges quadratically and its converged state is micro
+    equilibrated per element."""
+    X, conn, bnd = O.macro_mesh(2, 2)
+    m = W.neohooke_mat(1.0, 10.0, 1.0, 10.0)
+    rves = [dict(N=4, phase=np.zeros(16, np.uint8), mat=m) for _ in range(len(conn))]
+    F = np.diag([1.1, 0.95]) + np.array([[0.0, 0.02], [0.01, 0.0]])
+    out, iters, q = O.monolithic_fe2_const((X, conn, bnd), rves, F, n_steps=1, tol_macro=1e-11, tol_micro=1e-11)
+    assert np.abs(q - X @ F.T).max() < 1e-10
+    for o in out:
+        assert np.abs(o["Fbar"] - F[None]).max() < 1e-10
+    rves = []
+    for e in range(len(conn)):
+        c, r = W.random_inclusions(W.GLOBAL_SEED, 200 + e)
+        rves.append(dict(N=4, phase=W.inclusion_phase(4, 2, c, r), mat=W.neohooke_mat(1.0, 10.0, 20.0, 200.0)))
+    rec = []
+    out, iters, q = O.monolithic_fe2_const((X, conn, bnd), rves, np.diag([1.15, 1.0]), n_steps=2,
+                                           tol_macro=1e-11, tol_micro=1e-11, record=rec)
+    assert max(iters) <= 6
+    grads, etas, _ = O.macro_gauss(X, conn)
+    for e, (o, r) in enumerate(zip(out, rves)):
+        bs = [4 * e + g for g in range(4)]
+        wq = etas[bs] / etas[bs].sum()
+        s = O.rve_solve_elem(4, 2, r["phase"], r["mat"], o["Fbar"], wq, o["w"])
+        assert np.linalg.norm(s["r_m"]) < 1e-10
