@@ -42,7 +42,7 @@ SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
 # DRAM bytes per RVE of the FP32 band factor from one ncu capture (304 RVEs,
 # profiles/band_factor_fp32_fiber32_304rves.md); valid only for the kernel
 # source it was taken on (sha1 prefix), else the bench reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "4b0037a9bfe8", "bytes": 406.0e6 / 304}
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "852c2cf5ce4d", "bytes": (113854720 + 291457792) / 304}
 
 
 def factor_traffic(nrve):
@@ -433,6 +433,68 @@ def run_schemes(args):
     return out
 
 
+def run_basis(args):
+    """Section 3: Dirac macro basis (one RVE per macro Gauss point) against the
+    piecewise-constant basis (one element RVE per macro element, its Gauss
+    points weighted by eta) on the config-3 problem: monolithic Newton, stretch
+    1.2 in n_l steps with the affine predictor.  Per basis: iterations, RVEs,
+    wall time, per-kernel time of one batched RVE solve at the converged state,
+    the final homogenised response and the distance between the two solutions."""
+    import torch
+    from paper_2312_12771_gb300.driver import MonolithicFE2, NewtonLog, macro_mesh
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    nx = args.nh_macro
+    X, conn, fixed = macro_mesh(nx, nx)
+    out = {"workload": f"macro {nx}x{nx} Q4, NH RVEs 32x32 (random inclusions, one microstructure per macro "
+                       f"element), stretch 1.2 in {args.nh_steps} steps, affine predictor, tol 1e-8; Dirac: one RVE "
+                       "per Gauss point, const: one element RVE per macro element",
+           "runs": []}
+    q = {}
+    # one microstructure per macro element; the Dirac basis gives it to all four Gauss points
+    be = W.inclusion_batch(nx * nx, 32, stretch=1.0)
+    bd = be.subset(np.repeat(np.arange(nx * nx), 4))
+    for basis, b in (("dirac", bd), ("const", be)):
+        nrve = b.nrve
+        ctx = Fe2Context(dim=2, precision="mixed", max_refine=1, basis=basis)
+        fe = MonolithicFE2(ctx, X, conn, fixed, b)
+        log = NewtonLog()
+        # warm-up outside the timed region: one RVE solve at the reference state
+        ctx.macro_gradients(fe.Fbar)
+        ctx.rve_solve(fe.ids, fe.Fbar, out=fe.outs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        err = None
+        try:
+            fe.run(np.diag([1.2, 1.0]), args.nh_steps, predictor=True, log=log, tol_macro=1e-8, tol_micro=1e-8)
+        except RuntimeError as exc:
+            err = str(exc)[:120]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        run = {"basis": basis, "rves": nrve, "converged": err is None, "error": err,
+               "iterations_per_step": log.iters, "rve_solve_calls": log.rve_solve_calls, "wall_s": round(wall, 3)}
+        if err is None:
+            q[basis] = fe.ctx.macro_get_positions()
+            st = fe.state()
+            run["mean_Pbar"] = np.asarray(st["Pbar"]).reshape(-1, 4).mean(axis=0).round(9).tolist()
+            ctx.profile(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            for _ in range(3):
+                ctx.rve_solve(fe.ids, fe.Fbar, out=fe.outs)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 3
+            prof = ctx.profile_read()
+            run["rve_solve_ms"] = round(ms, 3)
+            run["kernels_ms"] = {k: round(v[0] / v[1], 3) for k, v in prof.items()}
+        out["runs"].append(run)
+        ctx.close()
+    if len(q) == 2:
+        u = np.abs(q["dirac"] - X).max()
+        out["max_position_difference_rel"] = float(np.abs(q["dirac"] - q["const"]).max() / u)
+    return out
+
+
 def run_cook(args):
     """Section 5.2 Cook's membrane (Table 1 style): macro 20x20 Q4 x 2x2
     Gauss = 1600 RVEs of 30x30 with the Mooney-Rivlin cross microstructure,
@@ -568,7 +630,7 @@ def main():
     extra = {}
     if rank == 0 and not args.no_extra:
         for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton), ("schemes", run_schemes),
-                        ("cook", run_cook)):
+                        ("cook", run_cook), ("basis", run_basis)):
             try:
                 extra[key] = fn(args)
             except Exception as exc:  # reported, not fatal: the headline leg is already measured
