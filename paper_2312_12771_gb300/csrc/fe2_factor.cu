@@ -137,13 +137,76 @@ __device__ __forceinline__ void prefetch_columns(T* __restrict__ Stg, T* __restr
     if (c0 >= nm) return;
     const int qa = c0 / 2 + 1;
     const int nq = min(STG_NODES, nn - qa);
-    for (int k = t0; k < STG_COMPS * STG_NODES; k += nt) {
-        const int comp = k / STG_NODES, t = k - comp * STG_NODES;
-        Stg[k] = (t < nq) ? (T)sten[(size_t)comp * nn + qa + t] : T(0);
+    const int ns = STG_COMPS * STG_NODES, ntot = ns + nr * NB;
+    // four loads in flight per thread before the converted values are stored
+    for (int k0 = t0; k0 < ntot; k0 += 4 * nt) {
+        double v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i * nt;
+            v[i] = 0.0;
+            if (k < ns) {
+                const int comp = k / STG_NODES, t = k - comp * STG_NODES;
+                if (t < nq) v[i] = sten[(size_t)comp * nn + qa + t];
+            } else if (k < ntot) {
+                const int q = k - ns, rr = q / NB, c = q - rr * NB;
+                if (c0 + c < nm) v[i] = rhs[(size_t)rr * nm + c0 + c];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = k0 + i * nt;
+            if (k < ns)
+                Stg[k] = (T)v[i];
+            else if (k < ntot)
+                Bstg[k - ns] = (T)v[i];
+        }
     }
-    for (int k = t0; k < nr * NB; k += nt) {
-        const int rr = k / NB, c = k - rr * NB;
-        Bstg[k] = (c0 + c < nm) ? (T)rhs[(size_t)rr * nm + c0 + c] : T(0);
+}
+
+// Block b (32 x 32 rows x columns of the window, from the block list) of the
+// rank-NB update of the panel whose first column sits in ring slot pb:
+// W(t1, t2) -= sum_c Pn[c][t1] Pn[c][t2] for kd > t2, KR > t1 >= t2 (rows t1 >= kd
+// are right-hand-side rows, in Bw).  One warp, 8 x 4 outputs per lane.
+template <typename T>
+__device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, int b, const T* __restrict__ Pn,
+                                             T* __restrict__ W, T* __restrict__ Bw, int pb, int S, int LDW, int KP,
+                                             int kd, int KR, int lane) {
+    const int rg = lane >> 3, cg = lane & 7;
+    const unsigned bv = blk[b];
+    const int I = bv & 0xffff, K = bv >> 16;
+    const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
+    T acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+    for (int c = 0; c < NB; ++c) {
+        const T* pc = Pn + c * KP;
+        T a[8], bb[4];
+        Vec4<T>::load(pc + r0, a);
+        Vec4<T>::load(pc + r0 + 4, a + 4);
+        Vec4<T>::load(pc + q0, bb);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
+    }
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int t2 = q0 + w;
+        if (t2 >= kd) continue;
+        const int slot = wrapS(pb + NB + t2, S);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t1 = r0 + u;
+            if (t1 < t2 || t1 >= KR) continue;
+            if (t1 < kd)
+                W[(size_t)slot * LDW + (t1 - t2)] -= acc[u][w];
+            else
+                Bw[(t1 - kd) * S + slot] -= acc[u][w];
+        }
     }
 }
 
@@ -208,10 +271,19 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     }
     __syncthreads();
 
-    int base = 0;  // ring slot of column j0
+    // Look-ahead schedule per panel j (columns [j0, j0+NB), ring slot base):
+    //   1: warp 0 factors the diagonal block; warps 1.. bring in the entering columns,
+    //      prefetch the next ones and run the update blocks of panel j-1 that were left
+    //      over (column blocks K >= 1, which do not touch panel j's columns);
+    //   2: panel rows (L21 and y) by warps 0 .. ceil(KR/32)-1;
+    //   3: the first nwarps update blocks of panel j (all K = 0 blocks, which the next
+    //      diagonal block and panel rows need), L and y of panel j written out.
+    // Pn holds panel j from phase 2 of panel j until phase 2 of panel j+1.
+    const int nfirst = min(lay.nblk, nwarps);
+    int base = 0;   // ring slot of column j0
+    int pbase = 0;  // ring slot of the previous panel's first column
     for (int j0 = 0; j0 < nmp; j0 += NB) {
-        // ---- 1: warp 0 factors the diagonal block in registers (lane = row);
-        //         the other warps bring columns [j0+kd, j0+kd+NB) into the ring
+        // ---- 1
         if (warp == 0) {
             T a[NB];
 #pragma unroll
@@ -255,9 +327,14 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                 const int rr = p / NB, x = p - rr * NB;
                 Bw[rr * S + wrapS(base + kd + x, S)] = (c0 + x < nm) ? Bstg[p] : T(0);
             }
+            bar_sync_named(1, nt);  // the staged columns are consumed: stage the next ones
+            prefetch_columns<T>(Stg, Bstg, sten, r.rhs, j0 + S, nm, nn, nr, t0, nt);
+            if (j0 > 0)
+                for (int b = nfirst + warp - 1; b < lay.nblk; b += nwarps - 1)
+                    update_block<T>(blk, b, Pn, W, Bw, pbase, S, LDW, KP, kd, KR, lane);
         }
         __syncthreads();
-        // ---- 2: panel rows (L21 and y) / prefetch of the next entering columns
+        // ---- 2: panel rows (L21 and y)
         if (tid < KR) {
             T v[NB];
             if (tid < kd) {
@@ -285,50 +362,12 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) Bp[wrapS(base + c, S)] = v[c];
             }
-        } else {
-            prefetch_columns<T>(Stg, Bstg, sten, r.rhs, j0 + S, nm, nn, nr, tid - KR, blockDim.x - KR);
         }
         __syncthreads();
-        // ---- 3: rank-NB update of the window and RHS rows, 32x32 blocks per warp
+        // ---- 3: the first update blocks of this panel; L and y out
+        for (int b = warp; b < nfirst; b += nwarps)
+            update_block<T>(blk, b, Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
         {
-            const int rg = lane >> 3, cg = lane & 7;
-            for (int b = warp; b < lay.nblk; b += nwarps) {
-                const unsigned bv = blk[b];
-                const int I = bv & 0xffff, K = bv >> 16;
-                const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
-                T acc[8][4];
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
-#pragma unroll 4
-                for (int c = 0; c < NB; ++c) {
-                    const T* pc = Pn + c * KP;
-                    T a[8], bb[4];
-                    Vec4<T>::load(pc + r0, a);
-                    Vec4<T>::load(pc + r0 + 4, a + 4);
-                    Vec4<T>::load(pc + q0, bb);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
-                }
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int t2 = q0 + w;
-                    if (t2 >= kd) continue;
-                    const int slot = wrapS(base + NB + t2, S);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int t1 = r0 + u;
-                        if (t1 < t2 || t1 >= KR) continue;
-                        if (t1 < kd)
-                            W[(size_t)slot * LDW + (t1 - t2)] -= acc[u][w];
-                        else
-                            Bw[(t1 - kd) * S + slot] -= acc[u][w];
-                    }
-                }
-            }
             const int LDL = kd + 1;
             for (int c = warp; c < NB; c += nwarps) {
                 const T* Wc = W + (size_t)wrapS(base + c, S) * LDW;
@@ -341,6 +380,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             }
         }
         __syncthreads();
+        pbase = base;
         base = wrapS(base + NB, S);
     }
     if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
