@@ -167,7 +167,12 @@ __device__ __forceinline__ void prefetch_columns(T* __restrict__ Stg, T* __restr
 // Block b (32 x 32 rows x columns of the window, from the block list) of the
 // rank-NB update of the panel whose first column sits in ring slot pb:
 // W(t1, t2) -= sum_c Pn[c][t1] Pn[c][t2] for kd > t2, KR > t1 >= t2 (rows t1 >= kd
-// are right-hand-side rows, in Bw).  One warp, 8 x 4 outputs per lane.
+// are right-hand-side rows, in Bw).  One warp; lane (rg, cg) owns the 8 contiguous
+// rows 32I + 8rg + u and the 4 columns 32K + cg + 8w.  With the window's column
+// stride LDW = kd + 1 and kd odd, one (u, w) step of the write-back then touches 32
+// distinct banks.  Lanes whose 32 entries all lie in the window below the diagonal
+// take a write-back without predicates (one base index per column, all old values
+// loaded before any store); the others predicate each entry.
 template <typename T>
 __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, int b, const T* __restrict__ Pn,
                                              T* __restrict__ W, T* __restrict__ Bw, int pb, int S, int LDW, int KP,
@@ -175,7 +180,7 @@ __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, i
     const int rg = lane >> 3, cg = lane & 7;
     const unsigned bv = blk[b];
     const int I = bv & 0xffff, K = bv >> 16;
-    const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
+    const int r0 = 32 * I + 8 * rg, q0 = 32 * K + cg;
     T acc[8][4];
 #pragma unroll
     for (int u = 0; u < 8; ++u)
@@ -187,25 +192,44 @@ __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, i
         T a[8], bb[4];
         Vec4<T>::load(pc + r0, a);
         Vec4<T>::load(pc + r0 + 4, a + 4);
-        Vec4<T>::load(pc + q0, bb);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + 8 * w];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
 #pragma unroll
             for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
     }
+    if (I > K && r0 + 8 <= kd && q0 + 24 < kd) {
+        T old[4][8];
+        int cb[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int t2 = q0 + 8 * w;
+            cb[w] = wrapS(pb + NB + t2, S) * LDW + r0 - t2;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) old[w][u] = W[cb[w] + u];
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) W[cb[w] + u] = old[w][u] - acc[u][w];
+        return;
+    }
+    // general lanes: entries on or above the diagonal, beyond column kd or in the
+    // right-hand-side rows; one predicated update per entry through one index into
+    // the shared array
+    const int boff = (int)(Bw - W);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
-        const int t2 = q0 + w;
-        if (t2 >= kd) continue;
+        const int t2 = q0 + 8 * w;
         const int slot = wrapS(pb + NB + t2, S);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int t1 = r0 + u;
-            if (t1 < t2 || t1 >= KR) continue;
-            if (t1 < kd)
-                W[(size_t)slot * LDW + (t1 - t2)] -= acc[u][w];
-            else
-                Bw[(t1 - kd) * S + slot] -= acc[u][w];
+            const int ix = t1 < kd ? slot * LDW + (t1 - t2) : boff + (t1 - kd) * S + slot;
+            if (t2 < kd && t1 >= t2 && t1 < KR) W[ix] -= acc[u][w];
         }
     }
 }
