@@ -234,6 +234,24 @@ __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, i
     }
 }
 
+// Columns [j0, j0+NB) of L (ring slots pb ..) and their y rows to global memory,
+// by warps w0, w0+nw, ... (columns) and threads t0, t0+nt, ... (y).
+template <typename T>
+__device__ __forceinline__ void write_panel(const T* __restrict__ W, const T* __restrict__ Bw, T* __restrict__ Lg,
+                                            T* __restrict__ Yg, int pb, int j0, int S, int LDW, int kd, int nr,
+                                            int nmp, int w0, int nw, int t0, int nt, int lane) {
+    const int LDL = kd + 1;
+    for (int c = w0; c < NB; c += nw) {
+        const T* Wc = W + (size_t)wrapS(pb + c, S) * LDW;
+        T* dst = Lg + (size_t)(j0 + c) * LDL;
+        for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
+    }
+    for (int k = t0; k < nr * NB; k += nt) {
+        const int rr = k / NB, c = k - rr * NB;
+        Yg[(size_t)rr * nmp + j0 + c] = Bw[rr * S + wrapS(pb + c, S)];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_factor(const RveDev* __restrict__ tab,
                                                                                       const int* __restrict__ ids,
@@ -301,7 +319,9 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     //      over (column blocks K >= 1, which do not touch panel j's columns);
     //   2: panel rows (L21 and y) by warps 0 .. ceil(KR/32)-1;
     //   3: the first nwarps update blocks of panel j (all K = 0 blocks, which the next
-    //      diagonal block and panel rows need), L and y of panel j written out.
+    //      diagonal block and panel rows need).
+    // L and y of panel j go out at the start of phase 1 of panel j+1 (warps 1..), before
+    // the entering columns reuse its ring slots; those of the last panel after the loop.
     // Pn holds panel j from phase 2 of panel j until phase 2 of panel j+1.
     const int nfirst = min(lay.nblk, nwarps);
     int base = 0;   // ring slot of column j0
@@ -323,6 +343,11 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             Dg[j0 + lane] = dinv[lane];
         } else {
             const int t0 = tid - 32, nt = blockDim.x - 32;
+            if (j0 > 0) {  // L and y of the previous panel out, before its slots are reused
+                write_panel<T>(W, Bw, Lg, Yg, pbase, j0 - NB, S, LDW, kd, nr, nmp, warp - 1, nwarps - 1, t0, nt,
+                               lane);
+                bar_sync_named(1, nt);
+            }
             const int c0 = j0 + kd;  // first entering column; its slot is base + kd (mod S)
             for (int c = warp - 1; c < NB; c += nwarps - 1) {
                 T* Wc = W + (size_t)wrapS(base + kd + c, S) * LDW;
@@ -388,25 +413,15 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             }
         }
         __syncthreads();
-        // ---- 3: the first update blocks of this panel; L and y out
+        // ---- 3: the first update blocks of this panel (its L and y go out in the
+        //         next panel's phase 1)
         for (int b = warp; b < nfirst; b += nwarps)
             update_block<T>(blk, b, Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
-        {
-            const int LDL = kd + 1;
-            for (int c = warp; c < NB; c += nwarps) {
-                const T* Wc = W + (size_t)wrapS(base + c, S) * LDW;
-                T* dst = Lg + (size_t)(j0 + c) * LDL;
-                for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
-            }
-            for (int k = tid; k < nr * NB; k += blockDim.x) {
-                const int rr = k / NB, c = k - rr * NB;
-                Yg[(size_t)rr * nmp + j0 + c] = Bw[rr * S + wrapS(base + c, S)];
-            }
-        }
         __syncthreads();
         pbase = base;
         base = wrapS(base + NB, S);
     }
+    write_panel<T>(W, Bw, Lg, Yg, pbase, nmp - NB, S, LDW, kd, nr, nmp, warp, nwarps, tid, blockDim.x, lane);
     if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
 }
 
