@@ -86,7 +86,9 @@ struct Vec4<double> {
 
 // Column K of the register-resident Cholesky of the NB x NB diagonal block
 // (lane r holds row r in a[]); template recursion keeps every index static so
-// the block never leaves registers.
+// the block never leaves registers.  Entries a[c] with c > lane (above the
+// diagonal) are updated without a predicate: nothing reads them (a shuffle of
+// column K reads lanes >= K only, and the caller stores c <= lane only).
 template <typename T, int K>
 __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __restrict__ dinv, int& bad) {
     if constexpr (K < NB) {
@@ -110,17 +112,17 @@ __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __rest
 }
 
 // Step C of the right-looking solve of one panel row v against L11 (rows of
-// L11 read as broadcasts from the ring window).
+// L11 read as broadcasts from the ring window).  The half bandwidth is at least
+// NB (the registration clamps it), so every entry of L11 lies in the band.
 template <typename T, int C>
 __device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict__ W, int base, int S, int LDW,
-                                                int kd, const T* __restrict__ dinv) {
+                                                const T* __restrict__ dinv) {
     if constexpr (C < NB) {
         const T* Lc = W + (size_t)(base + C >= S ? base + C - S : base + C) * LDW;
         v[C] *= dinv[C];
 #pragma unroll
-        for (int c2 = C + 1; c2 < NB; ++c2)
-            if (c2 - C <= kd) v[c2] -= v[C] * Lc[c2 - C];
-        panel_row_steps<T, C + 1>(v, W, base, S, LDW, kd, dinv);
+        for (int c2 = C + 1; c2 < NB; ++c2) v[c2] -= v[C] * Lc[c2 - C];
+        panel_row_steps<T, C + 1>(v, W, base, S, LDW, dinv);
     }
 }
 
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) v[c] = Bp[wrapS(base + c, S)];
             }
-            panel_row_steps<T, 0>(v, W, base, S, LDW, kd, dinv);
+            panel_row_steps<T, 0>(v, W, base, S, LDW, dinv);
 #pragma unroll
             for (int c = 0; c < NB; ++c) Pn[c * KP + tid] = v[c];
             if (tid < kd) {
