@@ -42,7 +42,7 @@ SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
 # DRAM bytes per RVE of the FP32 band factor from one ncu capture (304 RVEs,
 # profiles/band_factor_fp32_fiber32_304rves.md); valid only for the kernel
 # source it was taken on (sha1 prefix), else the bench reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "852c2cf5ce4d", "bytes": (113854720 + 291457792) / 304}
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "6725e9f92746", "bytes": (114210048 + 288662272) / 304}
 
 
 def factor_traffic(nrve):
