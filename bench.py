@@ -101,7 +101,8 @@ def work_per_rve(N, d=2):
     stencil_bytes = 9 * d * d * nn * 8 + nr * nm * 8  # FP64 node-row stencil + [K_mM | r_m]
     L_bytes = 4 * nm * (kd + 1)
     return {
-        "assemble_reduce_linear": {"bytes": stencil_bytes + nn, "flops64": nn * 2 * (128 + 64 + 44 + 8)},
+        # rows tabulated per phase combination: the kernel streams the stencil and [K_mM | r_m] out
+        "assemble_reduce_linear": {"hbm_bytes": stencil_bytes + nn},
         "band_factor_fp32": {"flops": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
         "band_factor_tc": {"flops_tc": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
         "band_backward_fp32": {"flops": nr * tri, "bytes": L_bytes + 4 * nr * nm + 8 * nr * nm},
@@ -118,6 +119,10 @@ def roofline_for(name, avg_ms, nrve, pk, N=N_MESH):
     if w is None or avg_ms <= 0:
         return None
     s = avg_ms * 1e-3
+    if "hbm_bytes" in w:
+        ach = w["hbm_bytes"] * nrve / s / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": round(pk["hbm_gbs"], 1), "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "peak_src": pk.get("hbm_src", "MEASURED_PEAKS.json")}
     if "flops_tc" in w:
         # trailing updates on the TF32 tensor cores (3 passes), panels on the FP32 pipes:
         # algorithmic flops against the dense TF32 peak, and against the FP32 ALU peak for context

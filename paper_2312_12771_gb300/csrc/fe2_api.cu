@@ -317,8 +317,11 @@ static void drop_cached_lists_with(fe2_ctx* ctx, const std::vector<int>& release
 }
 
 struct BatchInfo {
-    int maxN = 0, maxkd = 0, maxnr = 0, maxnm = 0, maxnmp = 0, maxnn = 0;
+    int maxN = 0, maxkd = 0, maxnr = 0, maxnm = 0, maxnmp = 0, maxnn = 0, maxnphase = 0;
     bool all_linear = true;
+    // assembly kernel selector: 0 general, 1 linear, 2 linear with node rows tabulated
+    // by phase combination (at most 3 phases per RVE)
+    int linear_mode() const { return all_linear ? (maxnphase <= 3 ? 2 : 1) : 0; }
 };
 
 static BatchInfo batch_info(const fe2_ctx* ctx, int n, const int* ids) {
@@ -327,6 +330,7 @@ static BatchInfo batch_info(const fe2_ctx* ctx, int n, const int* ids) {
         const RveDev& r = ctx->mirror[ids[k]];
         b.maxN = std::max(b.maxN, r.N);
         b.maxkd = std::max(b.maxkd, r.kd);
+        b.maxnphase = std::max(b.maxnphase, r.nphase);
         b.maxnr = std::max(b.maxnr, r.nr);
         b.maxnm = std::max(b.maxnm, r.nm);
         b.maxnmp = std::max(b.maxnmp, r.nm_pad);
@@ -874,7 +878,7 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
     }
     TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));
     TIMED(b.all_linear ? "assemble_reduce_linear" : "assemble_reduce_general",
-          launch_assemble_fused(ctx->d_tab, d_ids, n, Fbar, ctx->cfg.dim, b.maxN, b.all_linear ? 1 : 0, ctx->stream));
+          launch_assemble_fused(ctx->d_tab, d_ids, n, Fbar, ctx->cfg.dim, b.maxN, b.linear_mode(), ctx->stream));
     return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
 }
 
@@ -1233,7 +1237,7 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
     CK(cudaMemcpyAsync(L.d_F, L.h_F, sizeof(double) * dd * n, cudaMemcpyHostToDevice, s));
     Workspace ws{L.ws, l.stride, l.offY, l.offR, l.offD, l.offWin};
     CK(launch_check_fbar(L.d_F, n, d, L.d_st, s));
-    CK(launch_assemble_fused(ctx->d_tab, L.d_ids, n, L.d_F, d, b.maxN, b.all_linear ? 1 : 0, s));
+    CK(launch_assemble_fused(ctx->d_tab, L.d_ids, n, L.d_F, d, b.maxN, b.linear_mode(), s));
     if (fp64) {
         if (l.gw)
             CK(launch_factor_gw<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));

@@ -355,10 +355,35 @@ __global__ void __launch_bounds__(256) k_reduce2(const RveDev* __restrict__ tab,
 // constant per element, so every element integral is lam * (table) + mu * (table)
 // with tables of the uniform grid (exact; linearity of the integrals in A).
 // r_m = K w + K_mM : H and Pint = K_MM : H + K_mM^T w follow from linearity.
+constexpr int MAX_COMBO = 81;  // node-row phase combinations tabulated per RVE (3 phases)
+
+// Stencil and K_mM rows of a node whose 4 elements (local node a = 0..3 of each)
+// have the phases of `combo` (digit a in base np, a = 0 least significant).
+__device__ __forceinline__ void linear_row(int combo, int np, const double* lamE, const double* muE,
+                                           const double (*Kl)[4][2][2], const double (*Km)[4][2][2],
+                                           const double (*kMl)[2][4], const double (*kMm)[2][4],
+                                           double (&st)[9][2][2], double (&kM)[2][4]) {
+    for (int a = 0; a < 4; ++a) {
+        const int ax = a & 1, ay = a >> 1;
+        const int ph = combo % np;
+        combo /= np;
+        const double lam = lamE[ph], mu = muE[ph];
+        for (int b = 0; b < 4; ++b) {
+            const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+            for (int c = 0; c < 2; ++c)
+                for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += lam * Kl[a][b][c][c2] + mu * Km[a][b][c][c2];
+        }
+        for (int c = 0; c < 2; ++c)
+            for (int kL = 0; kL < 4; ++kL) kM[c][kL] += lam * kMl[a][c][kL] + mu * kMm[a][c][kL];
+    }
+}
+
+template <bool TAB>
 __global__ void __launch_bounds__(256) k_assemble_fused_linear2(const RveDev* __restrict__ tab,
                                                                 const int* __restrict__ ids,
                                                                 const double* __restrict__ Fbar) {
     __shared__ double Kl[4][4][2][2], Km[4][4][2][2], kMl[4][2][4], kMm[4][2][4];
+    __shared__ double Tst[TAB ? MAX_COMBO : 1][9][2][2], TkM[TAB ? MAX_COMBO : 1][2][4];
     __shared__ double red[256];
     __shared__ double lamE[MAX_PHASES], muE[MAX_PHASES];
     const RveDev r = tab[ids[blockIdx.x]];
@@ -391,31 +416,74 @@ __global__ void __launch_bounds__(256) k_assemble_fused_linear2(const RveDev* __
         lame(r.mat[4 * p + 1], r.mat[4 * p + 2], lamE[p], muE[p]);
     }
     __syncthreads();
+    // TAB: a node row depends on the phases of its 4 elements only; with at most 3
+    // phases every combination's row (np^4 <= 81) is computed once here, by the
+    // same arithmetic in the same order as the per-node path, and the node loop
+    // copies it (the per-node path does the FP64 products for every node).
+    const int np = r.nphase;
+    if constexpr (TAB) {
+        for (int t = tid; t < np * np * np * np; t += blockDim.x) {
+            double st[9][2][2] = {};
+            double kM[2][4] = {};
+            linear_row(t, np, lamE, muE, Kl, Km, kMl, kMm, st, kM);
+            for (int off = 0; off < 9; ++off)
+                for (int c = 0; c < 2; ++c)
+                    for (int c2 = 0; c2 < 2; ++c2) Tst[t][off][c][c2] = st[off][c][c2];
+            for (int c = 0; c < 2; ++c)
+                for (int kL = 0; kL < 4; ++kL) TkM[t][c][kL] = kM[c][kL];
+        }
+        __syncthreads();
+    }
     double H[4];
     for (int k = 0; k < 4; ++k) H[k] = Fbar[4 * blockIdx.x + k] - ((k == 0 || k == 3) ? 1.0 : 0.0);
     double part[6];  // sum lam_e, sum mu_e, (K_mM^T w)[4]
     for (int k = 0; k < 6; ++k) part[k] = 0.0;
     for (int q = tid; q < r.nn; q += blockDim.x) {
         const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
+        int combo = 0;
+#pragma unroll
+        for (int a = 3; a >= 0; --a) {
+            const int ax = a & 1, ay = a >> 1;
+            const int ph = r.phase[(i - ax + N) % N + N * ((j - ay + N) % N)];
+            combo = combo * np + ph;
+            if (a == 0) {
+                part[0] += lamE[ph];
+                part[1] += muE[ph];
+            }
+        }
+        if constexpr (TAB) {
+            // the row straight from the table: r_m = K w + K_mM : H, stored as store_row does
+            const double* T = &Tst[combo][0][0][0];
+            const double* Tk = &TkM[combo][0][0];
+            double f[2];
+            for (int c = 0; c < 2; ++c)
+                f[c] = Tk[4 * c] * H[0] + Tk[4 * c + 1] * H[1] + Tk[4 * c + 2] * H[2] + Tk[4 * c + 3] * H[3];
+            if (!r.zero_w) {
+                for (int off = 0; off < 9; ++off) {
+                    const int qn = nbr_q(i, j, off, N);
+                    if (qn == 0) continue;
+                    const double w0 = r.w[2 * (qn - 1)], w1 = r.w[2 * (qn - 1) + 1];
+                    for (int c = 0; c < 2; ++c) f[c] += T[(off * 2 + c) * 2] * w0 + T[(off * 2 + c) * 2 + 1] * w1;
+                }
+                if (q != 0) {
+                    const double w0 = r.w[2 * (q - 1)], w1 = r.w[2 * (q - 1) + 1];
+                    for (int kL = 0; kL < 4; ++kL) part[2 + kL] += Tk[kL] * w0 + Tk[4 + kL] * w1;
+                }
+            }
+            const int nn = r.nn;
+#pragma unroll 4
+            for (int k = 0; k < 36; ++k) r.stencil[(size_t)k * nn + q] = T[k];
+            if (q != 0)
+                for (int c = 0; c < 2; ++c) {
+                    const int dof = 2 * (q - 1) + c;
+                    for (int kL = 0; kL < 4; ++kL) r.rhs[(size_t)kL * r.nm + dof] = Tk[4 * c + kL];
+                    r.rhs[(size_t)4 * r.nm + dof] = f[c];
+                }
+            continue;
+        }
         double st[9][2][2] = {};
         double kM[2][4] = {};
-        for (int a = 0; a < 4; ++a) {
-            const int ax = a & 1, ay = a >> 1;
-            const int e = (i - ax + N) % N + N * ((j - ay + N) % N);
-            const int ph = r.phase[e];
-            const double lam = lamE[ph], mu = muE[ph];
-            if (a == 0) {
-                part[0] += lam;
-                part[1] += mu;
-            }
-            for (int b = 0; b < 4; ++b) {
-                const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
-                for (int c = 0; c < 2; ++c)
-                    for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += lam * Kl[a][b][c][c2] + mu * Km[a][b][c][c2];
-            }
-            for (int c = 0; c < 2; ++c)
-                for (int kL = 0; kL < 4; ++kL) kM[c][kL] += lam * kMl[a][c][kL] + mu * kMm[a][c][kL];
-        }
+        linear_row(combo, np, lamE, muE, Kl, Km, kMl, kMm, st, kM);
         double f[2];
         for (int c = 0; c < 2; ++c) f[c] = kM[c][0] * H[0] + kM[c][1] * H[1] + kM[c][2] * H[2] + kM[c][3] * H[3];
         if (!r.zero_w) {
@@ -477,8 +545,11 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
                                   int maxN, int all_linear, cudaStream_t s) {
     (void)maxN;
     if (d != 2) return cudaErrorNotSupported;
-    if (all_linear)
-        k_assemble_fused_linear2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    // all_linear: 0 general, 1 linear, 2 linear with at most 3 phases per RVE (tabulated rows)
+    if (all_linear == 2)
+        k_assemble_fused_linear2<true><<<n, 256, 0, s>>>(tab, ids, Fbar);
+    else if (all_linear)
+        k_assemble_fused_linear2<false><<<n, 256, 0, s>>>(tab, ids, Fbar);
     else
         k_assemble_fused_general2<<<n, 256, 0, s>>>(tab, ids, Fbar);
     return cudaGetLastError();
