@@ -63,17 +63,18 @@ __device__ void consti2(const double* m, const double F[2][2], double P[2][2],
         //                   (beta H:H = beta (F:F + J^2) for the plane-strain embedding)
         const double H[2][2] = {{F[1][1], -F[1][0]}, {-F[0][1], F[0][0]}};
         const double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+        const double iJ = 1.0 / J;  // one FP64 division per Gauss point
         double mu, s, c;
         if (model == FE2_MODEL_MOONEY_RIVLIN) {
             const double al = m[1], be = m[2], kappa = m[3], q = 2.0 * (al + 2.0 * be);
             mu = 2.0 * (al + be);
-            s = 2.0 * be * J + kappa * (J - 1.0) - q / J;
-            c = 2.0 * be + kappa + q / (J * J);
+            s = 2.0 * be * J + kappa * (J - 1.0) - q * iJ;
+            c = 2.0 * be + kappa + q * iJ * iJ;
         } else {
             const double kappa = m[2];
             mu = m[1];
-            s = kappa * (J - 1.0) - mu / J;  // dPsi/dJ
-            c = mu / (J * J) + kappa;        // d^2Psi/dJ^2
+            s = kappa * (J - 1.0) - mu * iJ;  // dPsi/dJ
+            c = mu * iJ * iJ + kappa;         // d^2Psi/dJ^2
         }
         for (int i = 0; i < 2; ++i)
             for (int K = 0; K < 2; ++K) P[i][K] = mu * F[i][K] + s * H[i][K];
@@ -286,6 +287,209 @@ __global__ void __launch_bounds__(256) k_assemble_fused_elem2(const RveDev* __re
     }
 }
 
+// ---------------------------------------------------------------- element-centric general path
+// One thread integrates a whole element: the constitutive law runs once per Gauss
+// point (the per-(element, a) path above runs it once per local node), and only the
+// 10 blocks k_e(a, b), a <= b, are formed (k_e(b, a) = k_e(a, b)^T by the major
+// symmetry of A).  Compact per-element components (EC_COMP):
+//   [4 p + 2 i + k]        k_e block p = pair(a, b), entry (i, k), a <= b   (40)
+//   [40 + 2 a + i]         f_e rows of local node a                          (8)
+//   [48 + 8 a + 4 i + kL]  k_eM rows of local node a                         (32)
+// The fused kernel stages strips of element rows in shared memory and gathers the
+// node rows from them; the split path stores the same values in the per-element
+// layout of k_assemble_elems2 and gathers with k_reduce2.  Both sum in the same
+// order, so they agree bit for bit.
+constexpr int EC_COMP = 80;
+constexpr int EC_SMEM_MAX = 200 * 1024;
+constexpr int EC_NMAX = 160;  // larger meshes take the per-(element, a) path
+
+// element rows per strip: at most 256 elements, (R + 1) rows staged
+__host__ __device__ inline int ec_rows(int N) {
+    int R = 256 / N;
+    if (R > N) R = N;
+    while (R > 1 && (size_t)(R + 1) * EC_COMP * N * sizeof(double) > (size_t)EC_SMEM_MAX) --R;
+    return R;
+}
+
+__host__ __device__ inline size_t ec_smem_bytes(int maxN) {
+    size_t b = 0;
+    for (int N = 3; N <= maxN; ++N) {
+        const size_t x = (size_t)(ec_rows(N) + 1) * EC_COMP * N * sizeof(double);
+        b = x > b ? x : b;
+    }
+    return b;
+}
+
+__device__ __forceinline__ int ec_pair(int a, int b) {  // a <= b
+    return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
+}
+
+// All rows of element (ex, ey) at (Fbar, w~) into out[c * stride], c < EC_COMP,
+// summed over the Gauss points in order; mme = K_MM (16) and Pint (4) of the element.
+// Gt[(g * 4 + b) * 2 + J] = dN_b/dX_J at Gauss point g.
+__device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const double Fb[4],
+                                          const double* __restrict__ Gt, double* __restrict__ out, int stride,
+                                          double (&mme)[20]) {
+    const int N = r.N;
+    const double h = 1.0 / N, wq = 0.25 * h * h;
+    const double* m = r.mat + 4 * r.phase[ex + N * ey];
+    double we[4][2];
+    for (int b = 0; b < 4; ++b) {
+        const int i = (ex + (b & 1)) % N, j = (ey + (b >> 1)) % N;
+        const int q = fold_pos(i, N) + N * fold_pos(j, N);
+        for (int c = 0; c < 2; ++c) we[b][c] = (q == 0 || r.zero_w) ? 0.0 : r.w[2 * (q - 1) + c];
+    }
+#pragma unroll
+    for (int k = 0; k < 20; ++k) mme[k] = 0.0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const double* G = Gt + g * 8;
+        double F[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int J = 0; J < 2; ++J) {
+                double v = Fb[2 * i + J];
+                for (int b = 0; b < 4; ++b) v += we[b][i] * G[2 * b + J];
+                F[i][J] = v;
+            }
+        double P[2][2], A[2][2][2][2];
+        consti2(m, F, P, A);
+        for (int iJ = 0; iJ < 4; ++iJ) {
+            for (int kL = 0; kL < 4; ++kL) mme[4 * iJ + kL] += wq * A[iJ >> 1][iJ & 1][kL >> 1][kL & 1];
+            mme[16 + iJ] += wq * P[iJ >> 1][iJ & 1];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            double t[2][2][2];  // t[i][k][L] = sum_J G_aJ A_iJkL
+            for (int i = 0; i < 2; ++i)
+                for (int k = 0; k < 2; ++k)
+                    for (int L = 0; L < 2; ++L)
+                        t[i][k][L] = G[2 * a] * A[i][0][k][L] + G[2 * a + 1] * A[i][1][k][L];
+#pragma unroll
+            for (int b = a; b < 4; ++b) {
+                const int p = ec_pair(a, b);
+                for (int i = 0; i < 2; ++i)
+                    for (int k = 0; k < 2; ++k) {
+                        const double v = t[i][k][0] * G[2 * b] + t[i][k][1] * G[2 * b + 1];
+                        double* o = out + (4 * p + 2 * i + k) * stride;
+                        *o = g == 0 ? wq * v : __fma_rn(wq, v, *o);
+                    }
+            }
+            for (int i = 0; i < 2; ++i) {
+                const double v = P[i][0] * G[2 * a] + P[i][1] * G[2 * a + 1];
+                double* o = out + (40 + 2 * a + i) * stride;
+                *o = g == 0 ? wq * v : __fma_rn(wq, v, *o);
+                for (int k = 0; k < 2; ++k)
+                    for (int L = 0; L < 2; ++L) {
+                        double* o2 = out + (48 + 8 * a + 4 * i + 2 * k + L) * stride;
+                        *o2 = g == 0 ? wq * t[i][k][L] : __fma_rn(wq, t[i][k][L], *o2);
+                    }
+            }
+        }
+    }
+}
+
+// block (a, b) entry (c, c2) of an element from its compact components at E (stride)
+__device__ __forceinline__ double ec_kr(const double* E, int stride, int a, int b, int c, int c2) {
+    return a <= b ? E[(4 * ec_pair(a, b) + 2 * c + c2) * stride] : E[(4 * ec_pair(b, a) + 2 * c2 + c) * stride];
+}
+
+__device__ __forceinline__ void ec_gradients(double* Gt, int N) {
+    if (threadIdx.x < 32) {
+        const int t = threadIdx.x, g = t >> 3, b = (t >> 1) & 3, J = t & 1;
+        Gt[t] = grad2(g, b, J, 1.0 / N);
+    }
+}
+
+// Fused S1 - S3, element-centric: strips of R element rows are integrated into
+// shared memory (one thread per element), then the node rows they complete are
+// gathered (one thread per node).  Element row N-1 is integrated first as well,
+// for node row 0 (its K_MM / Pint count once, in the last strip).
+__global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __restrict__ tab,
+                                                            const int* __restrict__ ids,
+                                                            const double* __restrict__ Fbar) {
+    extern __shared__ __align__(16) double ebuf[];  // [(R + 1) slots][EC_COMP][N]
+    __shared__ double Gt[32];
+    __shared__ double red[256];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N, tid = threadIdx.x;
+    const int R = ec_rows(N), slots = R + 1, sl = EC_COMP * N;
+    ec_gradients(Gt, N);
+    double Fb[4];
+    for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.x + k];
+    double mm[20];
+    for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+    __syncthreads();
+    if (tid < N) {  // element row N - 1 as row u = -1 (slot 0)
+        double mme[20];
+        elem_all2(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
+    }
+    for (int s0 = 0; s0 < N; s0 += R) {
+        const int nrow = min(R, N - s0);
+        if (tid < nrow * N) {
+            const int du = tid / N, ex = tid - du * N, u = s0 + du;
+            double mme[20];
+            elem_all2(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
+            for (int k = 0; k < 20; ++k) mm[k] += mme[k];
+        }
+        __syncthreads();
+        for (int t = tid; t < nrow * N; t += blockDim.x) {
+            const int dj = t / N, i = t - dj * N, j = s0 + dj;
+            const int q = fold_pos(i, N) + N * fold_pos(j, N);
+            double st[9][2][2] = {};
+            double f[2] = {0.0, 0.0}, kM[2][4] = {};
+            for (int a = 0; a < 4; ++a) {
+                const int ax = a & 1, ay = a >> 1;
+                const int ex = (i - ax + N) % N, u = j - ay;
+                const double* E = ebuf + (size_t)((u + 1) % slots) * sl + ex;
+                for (int b = 0; b < 4; ++b) {
+                    const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                    for (int c = 0; c < 2; ++c)
+                        for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += ec_kr(E, N, a, b, c, c2);
+                }
+                for (int c = 0; c < 2; ++c) f[c] += E[(40 + 2 * a + c) * N];
+                for (int c = 0; c < 2; ++c)
+                    for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(48 + 8 * a + 4 * c + kL) * N];
+            }
+            store_row(r, q, st, f, kM);
+        }
+        __syncthreads();
+    }
+    double tot[20];
+    block_sum<20>(mm, red, tot);
+    if (tid < 16) r.KMM[tid] = tot[tid];
+    else if (tid < 20) r.Pint[tid - 16] = tot[tid];
+}
+
+// Split S1 + S2, element-centric: one thread per element, the values of
+// k_assemble_fused_ec2 stored in the per-element layout of k_assemble_elems2.
+__global__ void __launch_bounds__(128) k_assemble_elems_ec2(const RveDev* __restrict__ tab,
+                                                            const int* __restrict__ ids,
+                                                            const double* __restrict__ Fbar) {
+    __shared__ double Gt[32];
+    const RveDev r = tab[ids[blockIdx.y]];
+    ec_gradients(Gt, r.N);
+    __syncthreads();
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= r.nn) return;
+    const int N = r.N, ex = e % N, ey = e / N, nn = r.nn, RC = elem_row_comps(2);
+    double Fb[4];
+    for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.y + k];
+    double loc[EC_COMP];
+    double mme[20];
+    elem_all2(r, ex, ey, Fb, Gt, loc, 1, mme);
+    double* E = r.elem;
+    for (int a = 0; a < 4; ++a) {
+        int c0 = a * RC;
+        for (int b = 0; b < 4; ++b)
+            for (int c = 0; c < 2; ++c)
+                for (int c2 = 0; c2 < 2; ++c2) E[(size_t)(c0++) * nn + e] = ec_kr(loc, 1, a, b, c, c2);
+        for (int c = 0; c < 2; ++c) E[(size_t)(c0++) * nn + e] = loc[40 + 2 * a + c];
+        for (int c = 0; c < 2; ++c)
+            for (int kL = 0; kL < 4; ++kL) E[(size_t)(c0++) * nn + e] = loc[48 + 8 * a + 4 * c + kL];
+    }
+    for (int k = 0; k < 20; ++k) E[(size_t)(4 * RC + k) * nn + e] = mme[k];
+}
+
 // Split S1 + S2: one thread per (element, local node a).
 __global__ void __launch_bounds__(128) k_assemble_elems2(const RveDev* __restrict__ tab,
                                                          const int* __restrict__ ids,
@@ -314,7 +518,10 @@ __global__ void __launch_bounds__(128) k_assemble_elems2(const RveDev* __restric
         for (int k = 0; k < 20; ++k) E[(size_t)(4 * RC + k) * nn + e] = mm[k];
 }
 
-// Split S3: gather the element rows of each node through the periodic map.
+// Split S3: gather the element rows of each node through the periodic map.  EC:
+// K_MM and Pint of the elements are summed in the thread order of
+// k_assemble_fused_ec2 (else with the node gather, as k_assemble_fused_general2).
+template <bool EC>
 __global__ void __launch_bounds__(256) k_reduce2(const RveDev* __restrict__ tab,
                                                  const int* __restrict__ ids) {
     __shared__ double red[256];
@@ -339,10 +546,20 @@ __global__ void __launch_bounds__(256) k_reduce2(const RveDev* __restrict__ tab,
             for (int c = 0; c < 2; ++c) f[c] += E[(size_t)(c0++) * nn + e];
             for (int c = 0; c < 2; ++c)
                 for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
-            if (a == 0)
+            if (!EC && a == 0)
                 for (int k = 0; k < 20; ++k) mm[k] += E[(size_t)(4 * RC + k) * nn + e];
         }
         store_row(r, q, st, f, kM);
+    }
+    if (EC) {
+        const int R = ec_rows(N);
+        for (int s0 = 0; s0 < N; s0 += R) {
+            const int nrow = min(R, N - s0);
+            if ((int)threadIdx.x < nrow * N) {
+                const int du = threadIdx.x / N, e = (threadIdx.x - du * N) + N * (s0 + du);
+                for (int k = 0; k < 20; ++k) mm[k] += E[(size_t)(4 * RC + k) * nn + e];
+            }
+        }
     }
     double tot[20];
     block_sum<20>(mm, red, tot);
@@ -529,22 +746,36 @@ __global__ void k_check_fbar(const double* __restrict__ Fbar, int n, int dd, int
 cudaError_t launch_assemble_elems(const RveDev* tab, const int* ids, int n, const double* Fbar, int d,
                                   int maxN, cudaStream_t s) {
     if (d != 2) return cudaErrorNotSupported;
-    dim3 grid((4 * maxN * maxN + 127) / 128, n);
-    k_assemble_elems2<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    if (maxN <= EC_NMAX) {
+        dim3 grid((maxN * maxN + 127) / 128, n);
+        k_assemble_elems_ec2<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    } else {
+        dim3 grid((4 * maxN * maxN + 127) / 128, n);
+        k_assemble_elems2<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const RveDev* tab, const int* ids, int n, int d, int maxN, cudaStream_t s) {
-    (void)maxN;
     if (d != 2) return cudaErrorNotSupported;
-    k_reduce2<<<n, 256, 0, s>>>(tab, ids);
+    if (maxN <= EC_NMAX)
+        k_reduce2<true><<<n, 256, 0, s>>>(tab, ids);
+    else
+        k_reduce2<false><<<n, 256, 0, s>>>(tab, ids);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, const double* Fbar, int d,
                                   int maxN, int all_linear, cudaStream_t s) {
-    (void)maxN;
     if (d != 2) return cudaErrorNotSupported;
+    if (!all_linear && maxN <= EC_NMAX) {
+        const size_t smem = ec_smem_bytes(maxN);
+        cudaError_t e = cudaFuncSetAttribute(k_assemble_fused_ec2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_assemble_fused_ec2<<<n, 256, smem, s>>>(tab, ids, Fbar);
+        return cudaGetLastError();
+    }
     // all_linear: 0 general, 1 linear, 2 linear with at most 3 phases per RVE (tabulated rows)
     if (all_linear == 2)
         k_assemble_fused_linear2<true><<<n, 256, 0, s>>>(tab, ids, Fbar);
