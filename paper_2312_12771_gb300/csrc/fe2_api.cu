@@ -873,7 +873,7 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
     }
     if (nq_of(ctx) > 1) {
         TIMED("check_fbar", launch_check_fbar_dd(Fbar, n, 4 * nq_of(ctx), rve_status, ctx->stream));
-        TIMED("assemble_reduce_elem", launch_assemble_fused_elem(ctx->d_tab, d_ids, n, Fbar, ctx->stream));
+        TIMED("assemble_reduce_elem", launch_assemble_fused_elem(ctx->d_tab, d_ids, n, Fbar, b.maxN, ctx->stream));
         return condense_impl(ctx, n, rve_ids, d_ids, sigma_eff, Cbar, rve_status, err_est, false);
     }
     TIMED("check_fbar", launch_check_fbar(Fbar, n, ctx->cfg.dim, rve_status, ctx->stream));

@@ -490,6 +490,81 @@ __global__ void __launch_bounds__(128) k_assemble_elems_ec2(const RveDev* __rest
     for (int k = 0; k < 20; ++k) E[(size_t)(4 * RC + k) * nn + e] = mme[k];
 }
 
+// Element RVE, element-centric: the k_assemble_fused_ec2 pipeline once per macro
+// Gauss point g at Fbar_g, with the outputs of k_assemble_fused_elem2 (weighted
+// stencil and r_m, K_mM of g in rhs columns 4g.., K_MM / Pint of g).
+__global__ void __launch_bounds__(256) k_assemble_fused_elem_ec2(const RveDev* __restrict__ tab,
+                                                                 const int* __restrict__ ids,
+                                                                 const double* __restrict__ Fbar) {
+    extern __shared__ __align__(16) double ebuf[];  // [(R + 1) slots][EC_COMP][N]
+    __shared__ double Gt[32];
+    __shared__ double red[256];
+    const RveDev r = tab[ids[blockIdx.x]];
+    const int N = r.N, nq = r.nq, nn = r.nn, nm = r.nm, tid = threadIdx.x;
+    const int R = ec_rows(N), slots = R + 1, sl = EC_COMP * N;
+    ec_gradients(Gt, N);
+    __syncthreads();
+    for (int g = 0; g < nq; ++g) {
+        double Fb[4];
+        for (int k = 0; k < 4; ++k) Fb[k] = Fbar[(size_t)(blockIdx.x * nq + g) * 4 + k];
+        const double wg = r.wq[g];
+        double mm[20];
+        for (int k = 0; k < 20; ++k) mm[k] = 0.0;
+        if (tid < N) {
+            double mme[20];
+            elem_all2(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
+        }
+        for (int s0 = 0; s0 < N; s0 += R) {
+            const int nrow = min(R, N - s0);
+            if (tid < nrow * N) {
+                const int du = tid / N, ex = tid - du * N, u = s0 + du;
+                double mme[20];
+                elem_all2(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
+                for (int k = 0; k < 20; ++k) mm[k] += mme[k];
+            }
+            __syncthreads();
+            for (int t = tid; t < nrow * N; t += blockDim.x) {
+                const int dj = t / N, i = t - dj * N, j = s0 + dj;
+                const int q = fold_pos(i, N) + N * fold_pos(j, N);
+                double st[9][2][2] = {};
+                double f[2] = {0.0, 0.0}, kM[2][4] = {};
+                for (int a = 0; a < 4; ++a) {
+                    const int ax = a & 1, ay = a >> 1;
+                    const int ex = (i - ax + N) % N, u = j - ay;
+                    const double* E = ebuf + (size_t)((u + 1) % slots) * sl + ex;
+                    for (int b = 0; b < 4; ++b) {
+                        const int off = ((b & 1) - ax + 1) + 3 * ((b >> 1) - ay + 1);
+                        for (int c = 0; c < 2; ++c)
+                            for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += ec_kr(E, N, a, b, c, c2);
+                    }
+                    for (int c = 0; c < 2; ++c) f[c] += E[(40 + 2 * a + c) * N];
+                    for (int c = 0; c < 2; ++c)
+                        for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(48 + 8 * a + 4 * c + kL) * N];
+                }
+                for (int off = 0; off < 9; ++off)
+                    for (int c = 0; c < 2; ++c)
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            double* p = r.stencil + (size_t)((off * 2 + c) * 2 + c2) * nn + q;
+                            *p = (g == 0 ? 0.0 : *p) + wg * st[off][c][c2];
+                        }
+                if (q == 0) continue;  // pinned corner: no reduced DOF
+                for (int c = 0; c < 2; ++c) {
+                    const int dof = 2 * (q - 1) + c;
+                    for (int kL = 0; kL < 4; ++kL) r.rhs[(size_t)(4 * g + kL) * nm + dof] = kM[c][kL];
+                    double* pr = r.rhs + (size_t)(4 * nq) * nm + dof;
+                    *pr = (g == 0 ? 0.0 : *pr) + wg * f[c];
+                }
+            }
+            __syncthreads();
+        }
+        double tot[20];
+        block_sum<20>(mm, red, tot);
+        if (tid < 16) r.KMM[16 * g + tid] = tot[tid];
+        else if (tid < 20) r.Pint[4 * g + tid - 16] = tot[tid];
+        __syncthreads();
+    }
+}
+
 // Split S1 + S2: one thread per (element, local node a).
 __global__ void __launch_bounds__(128) k_assemble_elems2(const RveDev* __restrict__ tab,
                                                          const int* __restrict__ ids,
@@ -786,8 +861,17 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, cudaStream_t s) {
-    k_assemble_fused_elem2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
+                                       cudaStream_t s) {
+    if (maxN <= EC_NMAX) {
+        const size_t smem = ec_smem_bytes(maxN);
+        cudaError_t e = cudaFuncSetAttribute(k_assemble_fused_elem_ec2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_assemble_fused_elem_ec2<<<n, 256, smem, s>>>(tab, ids, Fbar);
+    } else {
+        k_assemble_fused_elem2<<<n, 256, 0, s>>>(tab, ids, Fbar);
+    }
     return cudaGetLastError();
 }
 

@@ -134,7 +134,8 @@ cudaError_t launch_rve_avg_stress(const RveDev* tab, const int* ids, int n, doub
 
 // element RVEs (piecewise-constant macro basis, 2D, nq = 4, nr = 17)
 cudaError_t launch_check_fbar_dd(const double* Fbar, int n, int dd, int* status, cudaStream_t s);
-cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, cudaStream_t s);
+cudaError_t launch_assemble_fused_elem(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
+                                       cudaStream_t s);
 cudaError_t launch_residual_elem(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
                                  const int* active, cudaStream_t s);
 cudaError_t launch_schur_elem(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
