@@ -78,75 +78,93 @@ __device__ void consti3(const double* m, const double F[3][3], double P[3][3], d
         }
 }
 
-// S1 + S2: one thread per (element, local node a); rows of a written to the
-// element workspace [comp][nn]: per a: kr[b][i][k] (72), f[i] (3), kM[i][kL] (27);
-// after the 8 row groups: K_MM (81) and Pint (9) of the element (a == 0 only).
-__global__ void __launch_bounds__(128) k_assemble_elems3(const RveDev* __restrict__ tab, const int* __restrict__ ids,
-                                                         const double* __restrict__ Fbar) {
+// S1 + S2: the rows of every (element, local node a) written to the element
+// workspace [comp][nn]: per a: kr[b][i][k] (72), f[i] (3), kM[i][kL] (27); after the
+// 8 row groups: K_MM (81) and Pint (9) of the element.  A CTA holds 16 elements.
+// Phase 1: the thread of each (element, Gauss point) evaluates the law once and
+// caches A (81) and P (9) in shared memory.  Phase 2: one thread per (element, a,
+// component i) integrates row i of node a (24 + 9 + 1 accumulators, in registers).
+constexpr int E3_ELEMS = 16;
+constexpr int E3_THREADS = 24 * E3_ELEMS;
+__global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __restrict__ tab,
+                                                                const int* __restrict__ ids,
+                                                                const double* __restrict__ Fbar) {
+    extern __shared__ __align__(16) double cache3[];  // [E3_ELEMS][8 GP][90]
+    __shared__ double Gt[8][8][3];                     // [GP][node][J]
     const RveDev r = tab[ids[blockIdx.y]];
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 8 * r.nn) return;
-    const int e = t >> 3, a = t & 7, N = r.N, nn = r.nn;
-    const int ex = e % N, ey = (e / N) % N, ez = e / (N * N);
+    const int N = r.N, nn = r.nn;
     const double h = 1.0 / N, wq = 0.125 * h * h * h;
-    const double* m = r.mat + 4 * r.phase[e];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < 8 * 8 * 3; k += blockDim.x) {
+        const int q = k / 24, b = (k / 3) % 8, J = k % 3;
+        Gt[q][b][J] = grad3(q, b, J, h);
+    }
     double Fb[9];
     for (int k = 0; k < 9; ++k) Fb[k] = Fbar[9 * blockIdx.y + k];
-    double we[8][3];
-    for (int b = 0; b < 8; ++b) {
-        const int i = (ex + (b & 1)) % N, j = (ey + ((b >> 1) & 1)) % N, k = (ez + (b >> 2)) % N;
-        const int q = fold_pos(i, N) + N * fold_pos(j, N) + N * N * fold_pos(k, N);
-        for (int c = 0; c < 3; ++c) we[b][c] = (q == 0 || r.zero_w) ? 0.0 : r.w[3 * (q - 1) + c];
-    }
-    double kr[8][3][3], f[3], kM[3][9], mm[90];
-    for (int b = 0; b < 8; ++b)
-        for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) kr[b][i][k] = 0.0;
-    for (int i = 0; i < 3; ++i) {
-        f[i] = 0.0;
-        for (int kL = 0; kL < 9; ++kL) kM[i][kL] = 0.0;
-    }
-    if (a == 0)
-        for (int k = 0; k < 90; ++k) mm[k] = 0.0;
-    for (int q = 0; q < 8; ++q) {
-        double G[8][3];
-        for (int b = 0; b < 8; ++b)
-            for (int J = 0; J < 3; ++J) G[b][J] = grad3(q, b, J, h);
-        double F[3][3];
-        for (int i = 0; i < 3; ++i)
-            for (int J = 0; J < 3; ++J) {
-                double v = Fb[3 * i + J];
-                for (int b = 0; b < 8; ++b) v += we[b][i] * G[b][J];
-                F[i][J] = v;
-            }
-        double P[3][3], A[3][3][3][3];
-        consti3(m, F, P, A);
-        for (int i = 0; i < 3; ++i) {
-            f[i] += wq * (P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2]);
-            for (int k = 0; k < 3; ++k)
-                for (int L = 0; L < 3; ++L) {
-                    const double tv = G[a][0] * A[i][0][k][L] + G[a][1] * A[i][1][k][L] + G[a][2] * A[i][2][k][L];
-                    kM[i][3 * k + L] += wq * tv;
-                    for (int b = 0; b < 8; ++b) kr[b][i][k] += wq * tv * G[b][L];
+    __syncthreads();
+    // phase 1: thread (el, q) evaluates the law of element el at Gauss point q
+    if (tid < 8 * E3_ELEMS) {
+        const int el = tid >> 3, q = tid & 7, e = blockIdx.x * E3_ELEMS + el;
+        if (e < nn) {
+            const int ex = e % N, ey = (e / N) % N, ez = e / (N * N);
+            double F[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int J = 0; J < 3; ++J) F[i][J] = Fb[3 * i + J];
+            for (int b = 0; b < 8; ++b) {
+                const int i = (ex + (b & 1)) % N, j = (ey + ((b >> 1) & 1)) % N, k = (ez + (b >> 2)) % N;
+                const int qn = fold_pos(i, N) + N * fold_pos(j, N) + N * N * fold_pos(k, N);
+                for (int c = 0; c < 3; ++c) {
+                    const double w = (qn == 0 || r.zero_w) ? 0.0 : r.w[3 * (qn - 1) + c];
+                    for (int J = 0; J < 3; ++J) F[c][J] += w * Gt[q][b][J];
                 }
+            }
+            double P[3][3], A[3][3][3][3];
+            consti3(r.mat + 4 * r.phase[e], F, P, A);
+            double* c = cache3 + (size_t)(el * 8 + q) * 90;
+            for (int k = 0; k < 81; ++k) c[k] = A[k / 27][(k / 9) % 3][(k / 3) % 3][k % 3];
+            for (int k = 0; k < 9; ++k) c[81 + k] = P[k / 3][k % 3];
         }
-        if (a == 0) {
-            for (int iJ = 0; iJ < 9; ++iJ)
-                for (int kL = 0; kL < 9; ++kL) mm[9 * iJ + kL] += wq * A[iJ / 3][iJ % 3][kL / 3][kL % 3];
-            for (int iJ = 0; iJ < 9; ++iJ) mm[81 + iJ] += wq * P[iJ / 3][iJ % 3];
-        }
+    }
+    __syncthreads();
+    // phase 2: thread (el, a, i)
+    const int el = tid / 24, rem = tid - 24 * el, a = rem / 3, i = rem - 3 * a;
+    const int e = blockIdx.x * E3_ELEMS + el;
+    if (e >= nn) return;
+    double kr[8][3], kM[9], f = 0.0;
+    for (int b = 0; b < 8; ++b)
+        for (int k = 0; k < 3; ++k) kr[b][k] = 0.0;
+    for (int kL = 0; kL < 9; ++kL) kM[kL] = 0.0;
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+        const double* c = cache3 + (size_t)(el * 8 + q) * 90;
+        const double(*G)[3] = Gt[q];
+        f += wq * (c[81 + 3 * i] * G[a][0] + c[81 + 3 * i + 1] * G[a][1] + c[81 + 3 * i + 2] * G[a][2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int L = 0; L < 3; ++L) {
+                const double tv = G[a][0] * c[27 * i + 3 * k + L] + G[a][1] * c[27 * i + 9 + 3 * k + L] +
+                                  G[a][2] * c[27 * i + 18 + 3 * k + L];
+                kM[3 * k + L] += wq * tv;
+#pragma unroll
+                for (int b = 0; b < 8; ++b) kr[b][k] += wq * tv * G[b][L];
+            }
     }
     const int RC = elem_row_comps(3);
     double* E = r.elem;
-    int c0 = a * RC;
+    const int c0 = a * RC;
     for (int b = 0; b < 8; ++b)
-        for (int i = 0; i < 3; ++i)
-            for (int k = 0; k < 3; ++k) E[(size_t)(c0++) * nn + e] = kr[b][i][k];
-    for (int i = 0; i < 3; ++i) E[(size_t)(c0++) * nn + e] = f[i];
-    for (int i = 0; i < 3; ++i)
-        for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0++) * nn + e] = kM[i][kL];
-    if (a == 0)
-        for (int k = 0; k < 90; ++k) E[(size_t)(8 * RC + k) * nn + e] = mm[k];
+        for (int k = 0; k < 3; ++k) E[(size_t)(c0 + 9 * b + 3 * i + k) * nn + e] = kr[b][k];
+    E[(size_t)(c0 + 72 + i) * nn + e] = f;
+    for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0 + 75 + 9 * i + kL) * nn + e] = kM[kL];
+    if (a == 0) {  // K_MM rows i and Pint row i of the element, Gauss points in order
+        for (int k = 0; k < 30; ++k) {
+            const int ck = k < 27 ? 27 * i + k : 81 + 3 * i + (k - 27);
+            double m = 0.0;
+            for (int q = 0; q < 8; ++q) m += wq * cache3[(size_t)(el * 8 + q) * 90 + ck];
+            E[(size_t)(8 * RC + ck) * nn + e] = m;
+        }
+    }
 }
 
 // S3: node-row gather through the periodic map (one CTA per RVE).  Each node row
@@ -525,8 +543,11 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
 
 cudaError_t launch_assemble_elems3(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
                                    cudaStream_t s) {
-    dim3 grid((8 * maxN * maxN * maxN + 127) / 128, n);
-    k_assemble_elems3<<<grid, 128, 0, s>>>(tab, ids, Fbar);
+    const size_t smem = (size_t)E3_ELEMS * 8 * 90 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_assemble_elems3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((maxN * maxN * maxN + E3_ELEMS - 1) / E3_ELEMS, n);
+    k_assemble_elems3<<<grid, E3_THREADS, smem, s>>>(tab, ids, Fbar);
     return cudaGetLastError();
 }
 
