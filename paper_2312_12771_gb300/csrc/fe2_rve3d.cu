@@ -296,6 +296,24 @@ __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, 
 
 __device__ __forceinline__ int wrapS3(int x, int S) { return x >= S ? x - S : x; }
 
+// four consecutive shared-memory values (16-byte aligned) in one or two vector loads
+template <typename T>
+struct Ld4;
+template <>
+struct Ld4<float> {
+    __device__ __forceinline__ static void load(const float* p, float* o) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+    }
+};
+template <>
+struct Ld4<double> {
+    __device__ __forceinline__ static void load(const double* p, double* o) {
+        const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+        o[0] = v0.x, o[1] = v0.y, o[2] = v1.x, o[3] = v1.y;
+    }
+};
+
 template <typename T>
 struct GwLayout {
     int kd, S, LDW, KR, KP, nr, nblk;
@@ -483,42 +501,46 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
         __syncthreads();
         // 3: rank-NB update (32x32 warp blocks) and stream out the finished panel
         {
-            const int rg = lane >> 3, cg = lane & 7;
+            // lane = row t1 = 32I + lane of the block, 32 columns t2 = 32K + w per lane:
+            // every write-back step is one coalesced 128-byte row segment of a window
+            // column in global memory; a warp loads all old values before storing any
             for (int b = warp; b < lay.nblk; b += nwarps) {
                 const unsigned bv = blk[b];
                 const int I = bv & 0xffff, K = bv >> 16;
-                const int r0 = 32 * I + 8 * rg, q0 = 32 * K + 4 * cg;
-                T acc[8][4];
+                const int t1 = 32 * I + lane, q0 = 32 * K;
+                T acc[32];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
-#pragma unroll 4
+                for (int w = 0; w < 32; ++w) acc[w] = T(0);
+#pragma unroll 2
                 for (int c = 0; c < NB; ++c) {
                     const T* pc = Pn + c * KP;
-                    T av[8], bb[4];
+                    const T av = pc[t1];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) av[u] = pc[r0 + u];
+                    for (int w4 = 0; w4 < 8; ++w4) {
+                        T bb[4];
+                        Ld4<T>::load(pc + q0 + 4 * w4, bb);
 #pragma unroll
-                    for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + w];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int w = 0; w < 4; ++w) acc[u][w] += av[u] * bb[w];
+                        for (int x = 0; x < 4; ++x) acc[4 * w4 + x] += av * bb[x];
+                    }
                 }
+                if (I > K && 32 * I + 32 <= kd && q0 + 32 <= kd) {
+                    T old[32];
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                    const int t2 = q0 + w;
-                    if (t2 >= kd) continue;
-                    const int sl = wrapS3(base + NB + t2, S);
+                    for (int w = 0; w < 32; ++w)
+                        old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int t1 = r0 + u;
-                        if (t1 < t2 || t1 >= KR) continue;
+                    for (int w = 0; w < 32; ++w)
+                        W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 32; ++w) {
+                        const int t2 = q0 + w;
+                        if (t2 >= kd || t1 < t2 || t1 >= KR) continue;
+                        const int sl = wrapS3(base + NB + t2, S);
                         if (t1 < kd)
-                            W[(size_t)sl * LDW + (t1 - t2)] -= acc[u][w];
+                            W[(size_t)sl * LDW + (t1 - t2)] -= acc[w];
                         else
-                            Bw[(t1 - kd) * S + sl] -= acc[u][w];
+                            Bw[(t1 - kd) * S + sl] -= acc[w];
                     }
                 }
             }
