@@ -376,12 +376,22 @@ __device__ __forceinline__ void gw_chol_steps(T (&a)[NB], int lane, T* __restric
     }
 }
 
-// Column c (< nm) of K_mm (rows >= c) from the node-row stencil (any dimension).
+// Columns [c0, c0 + ncol) of K_mm into the window slots sl(x) (x < ncol), one
+// (column, neighbour) pair per item, items t0, t0 + nt, ...; the slots must be
+// zero.  The neighbours of a node are distinct for N >= 3, so no two items write
+// the same entry.  Columns in [nm, nmp) get a unit diagonal.
 template <typename T>
-__device__ __forceinline__ void gw_load_column(T* __restrict__ Wc, int LDW, int c, const RveDev& r) {
-    const int d = r.d, ns = d == 2 ? 9 : 27, nn = r.nn;
-    const int q = c / d + 1, cc = c - d * (q - 1);
-    for (int off = 0; off < ns; ++off) {
+__device__ __forceinline__ void gw_load_columns(T* __restrict__ W, int LDW, int S, int base, int c0, int ncol,
+                                                int nmp, const RveDev& r, int t0, int nt) {
+    const int d = r.d, ns = d == 2 ? 9 : 27, nn = r.nn, nm = r.nm;
+    for (int p = t0; p < ncol * ns; p += nt) {
+        const int x = p / ns, off = p - x * ns, c = c0 + x;
+        T* Wc = W + (size_t)wrapS3(base + x, S) * LDW;
+        if (c >= nm) {
+            if (c < nmp && off == 0) Wc[0] = T(1);
+            continue;
+        }
+        const int q = c / d + 1, cc = c - d * (q - 1);
         const int qn = r.nbr[q * ns + off];
         if (qn == 0) continue;
         for (int c2 = 0; c2 < d; ++c2) {
@@ -426,13 +436,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
         Bw[k] = (c < nm && c < kd) ? (T)r.rhs[(size_t)rr * nm + c] : T(0);
     }
     __syncthreads();
-    for (int c = tid; c < min(kd, nmp); c += blockDim.x) {
-        T* Wc = W + (size_t)c * LDW;
-        if (c < nm)
-            gw_load_column<T>(Wc, LDW, c, r);
-        else
-            Wc[0] = T(1);
-    }
+    gw_load_columns<T>(W, LDW, S, 0, 0, min(kd, nmp), nmp, r, tid, blockDim.x);
     __syncthreads();
     int base = 0;
     for (int j0 = 0; j0 < nmp; j0 += NB) {
@@ -457,14 +461,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
                 for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
             }
             asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
-            for (int x = t0; x < NB; x += nt) {
-                const int cn = j0 + kd + x;
-                T* Wc = W + (size_t)wrapS3(base + kd + x, S) * LDW;
-                if (cn < nm)
-                    gw_load_column<T>(Wc, LDW, cn, r);
-                else if (cn < nmp)
-                    Wc[0] = T(1);
-            }
+            gw_load_columns<T>(W, LDW, S, wrapS3(base + kd, S), j0 + kd, NB, nmp, r, t0, nt);
             for (int p = t0; p < nr * NB; p += nt) {
                 const int rr = p / NB, x = p - rr * NB, cn = j0 + kd + x;
                 Bw[rr * S + wrapS3(base + kd + x, S)] = (cn < nm) ? (T)r.rhs[(size_t)rr * nm + cn] : T(0);
