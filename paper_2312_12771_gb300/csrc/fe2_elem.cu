@@ -39,16 +39,17 @@ __global__ void __launch_bounds__(128) k_residual2_elem(const RveDev* __restrict
         const double k10 = r.stencil[(size_t)(off * 4 + 2) * nn + q], k11 = r.stencil[(size_t)(off * 4 + 3) * nn + q];
 #pragma unroll
         for (int rr = 0; rr < NR_E; ++rr) {
-            const double x0 = r.X[(size_t)rr * nm + 2 * (qn - 1)], x1 = r.X[(size_t)rr * nm + 2 * (qn - 1) + 1];
-            acc[0][rr] += k00 * x0 + k01 * x1;
-            acc[1][rr] += k10 * x0 + k11 * x1;
+            // the two DOFs of a node are adjacent and 16-byte aligned (nm is even)
+            const double2 xv = *reinterpret_cast<const double2*>(r.X + (size_t)rr * nm + 2 * (qn - 1));
+            acc[0][rr] += k00 * xv.x + k01 * xv.y;
+            acc[1][rr] += k10 * xv.x + k11 * xv.y;
         }
     }
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-        const int dof = 2 * (q - 1) + c;
-#pragma unroll
-        for (int rr = 0; rr < NR_E; ++rr) R[(size_t)rr * nm + dof] = r.rhs[(size_t)rr * nm + dof] - acc[c][rr];
+    for (int rr = 0; rr < NR_E; ++rr) {
+        const size_t o = (size_t)rr * nm + 2 * (q - 1);
+        const double2 bv = *reinterpret_cast<const double2*>(r.rhs + o);
+        *reinterpret_cast<double2*>(R + o) = make_double2(bv.x - acc[0][rr], bv.y - acc[1][rr]);
     }
 }
 
