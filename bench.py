@@ -41,18 +41,25 @@ N_RVE, N_MESH = 4096, 32
 SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
 # DRAM bytes per RVE of the FP32 band factor from one ncu capture (304 RVEs,
 # profiles/band_factor_fp32_fiber32_304rves.md); valid only for the kernel
-# source it was taken on (sha1 prefix), else the bench reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "6725e9f92746", "bytes": (114210048 + 288662272) / 304}
+# source it was taken on: the sha1 prefix of the factor's part of fe2_factor.cu
+# (from STG_NODES to the solves), else the bench reports traffic = null.
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "1b5e1c2f01b7", "bytes": (114210048 + 288662272) / 304}
 
 
-def factor_traffic(nrve):
+def factor_source_sha1():
     import hashlib
     src = os.path.join(ROOT, "paper_2312_12771_gb300", "csrc", "fe2_factor.cu")
     try:
-        h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
-    except OSError:
+        t = open(src).read()
+        a = t.index("constexpr int STG_NODES")
+        b = t.index("// ------------------------------------------------------------------ solves")
+    except (OSError, ValueError):
         return None
-    if h != FACTOR_TRAFFIC_PER_RVE["sha1"]:
+    return hashlib.sha1(t[a:b].encode()).hexdigest()[:12]
+
+
+def factor_traffic(nrve):
+    if factor_source_sha1() != FACTOR_TRAFFIC_PER_RVE["sha1"]:
         return None
     return round(FACTOR_TRAFFIC_PER_RVE["bytes"] * nrve)
 
