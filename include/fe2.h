@@ -286,6 +286,12 @@ const char* fe2_noalloc_last_error(void);
  *   arrays: tickets, sigma [max][d*d], Cbar [max][d^4], status, latency_ms
  *   = completion - submission time); returns the number taken (-1 on error).
  * fe2_server_pending: requests queued or in flight.
+ * fe2_server_use_graphs: a lane captures its launch sequence (input copies,
+ *   S1 - S6 kernels, result copies) as a CUDA graph once per batch shape
+ *   (batch size and the batch's maximum mesh sizes) and replays it for later
+ *   batches of that shape; on by default, enable = 0 launches every kernel
+ *   from the host instead.  The results are the same either way.
+ * fe2_server_graph_stats: captures and replays so far ([host], may be NULL).
  */
 typedef struct fe2_server fe2_server;
 fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server** out);
@@ -295,6 +301,8 @@ fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes);
 int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma, double* Cbar, int* status,
                     double* latency_ms);
 int fe2_server_pending(const fe2_server* srv);
+fe2_status fe2_server_use_graphs(fe2_server* srv, int enable);
+fe2_status fe2_server_graph_stats(const fe2_server* srv, long long* captures, long long* replays);
 
 /*
  * Self-test of the bounded device waits used by the TMA streams of the solve

@@ -1187,6 +1187,22 @@ struct ServeDone {
     double lat_ms;
 };
 
+// What a lane's launch sequence depends on besides the contents of its buffers:
+// a captured graph is replayed only for an equal key.
+struct GraphKey {
+    int n, maxN, maxkd, maxnr, maxnm, maxnmp, maxnn, lin, tc;
+    const void* tab;
+    const void* ws;
+    bool operator<(const GraphKey& o) const {
+        const int a[9] = {n, maxN, maxkd, maxnr, maxnm, maxnmp, maxnn, lin, tc};
+        const int b[9] = {o.n, o.maxN, o.maxkd, o.maxnr, o.maxnm, o.maxnmp, o.maxnn, o.lin, o.tc};
+        for (int k = 0; k < 9; ++k)
+            if (a[k] != b[k]) return a[k] < b[k];
+        if (tab != o.tab) return tab < o.tab;
+        return ws < o.ws;
+    }
+};
+
 struct Lane {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
@@ -1197,19 +1213,28 @@ struct Lane {
     double *d_F = nullptr, *h_F = nullptr, *d_sig = nullptr, *h_sig = nullptr, *d_C = nullptr, *h_C = nullptr;
     double *d_err = nullptr;
     std::vector<ServeReq> batch;
+    std::map<GraphKey, cudaGraphExec_t> graphs;  // launch sequences captured per batch shape
+    std::deque<GraphKey> graph_order;            // insertion order, for eviction
 };
+
+constexpr int kMaxLaneGraphs = 64;
 
 }  // namespace
 
 struct fe2_server {
     fe2_ctx* ctx = nullptr;
     int max_batch = 0;
+    bool use_graphs = true;
+    long long graph_captures = 0, graph_replays = 0;
     std::vector<Lane> lanes;
     std::deque<ServeReq> queue;
     std::deque<ServeDone> done;
     std::unordered_set<int> inflight;
     long long next_ticket = 1;
 };
+
+static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo& b, const WsLayout& l, bool tc,
+                               bool record = true);
 
 static fe2_status lane_launch(fe2_server* srv, Lane& L) {
     fe2_ctx* ctx = srv->ctx;
@@ -1233,6 +1258,56 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
         L.ws_bytes = l.stride * (size_t)n;
     }
     cudaStream_t s = L.s;
+    const bool tc = !fp64 && !l.gw && use_tc_factor(ctx, b.maxkd, b.maxnr);
+    if (!srv->use_graphs) return lane_enqueue(srv, L, n, b, l, tc);
+    const GraphKey key{n, b.maxN, b.maxkd, b.maxnr, b.maxnm, b.maxnmp, b.maxnn, b.linear_mode(), tc ? 1 : 0,
+                       ctx->d_tab, L.ws};
+    auto it = L.graphs.find(key);
+    if (it == L.graphs.end()) {
+        // capture the sequence once for this batch shape (the kernels read ids and Fbar
+        // from the lane's fixed buffers, so the graph serves every batch of the shape)
+        if ((int)L.graphs.size() >= kMaxLaneGraphs) {
+            auto old = L.graphs.find(L.graph_order.front());
+            if (old != L.graphs.end()) {
+                CK(cudaStreamSynchronize(s));
+                cudaGraphExecDestroy(old->second);
+                L.graphs.erase(old);
+            }
+            L.graph_order.pop_front();
+        }
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        const fe2_status st = lane_enqueue(srv, L, n, b, l, tc, false);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s, &g);
+        if (st != FE2_OK || ec != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            return st != FE2_OK ? st : fail(ctx, FE2_ERR_CUDA, "lane graph capture: %s", cudaGetErrorString(ec));
+        }
+        cudaGraphExec_t x = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&x, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return fail(ctx, FE2_ERR_CUDA, "lane graph instantiate: %s", cudaGetErrorString(ei));
+        it = L.graphs.emplace(key, x).first;
+        L.graph_order.push_back(key);
+        ++srv->graph_captures;
+    } else {
+        ++srv->graph_replays;
+    }
+    CK(cudaGraphLaunch(it->second, s));
+    ctx->launches += fp64 ? 5 : 6 + 3 * ctx->cfg.max_refine;
+    CK(cudaEventRecord(L.ev, s));
+    L.busy = true;
+    return FE2_OK;
+}
+
+// The lane's launch sequence: inputs in, S1 - S6, results out (and, unless it is
+// being captured into a graph, the completion event).
+static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo& b, const WsLayout& l, bool tc,
+                               bool record) {
+    fe2_ctx* ctx = srv->ctx;
+    const int d = ctx->cfg.dim, dd = d * d;
+    const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
+    cudaStream_t s = L.s;
     CK(cudaMemcpyAsync(L.d_ids, L.h_ids, sizeof(int) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(L.d_F, L.h_F, sizeof(double) * dd * n, cudaMemcpyHostToDevice, s));
     Workspace ws{L.ws, l.stride, l.offY, l.offR, l.offD, l.offWin};
@@ -1245,11 +1320,11 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
             CK(launch_factor<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<double>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
         CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 0, L.d_sig, L.d_C, L.d_st, L.d_err, nullptr, nullptr, s));
-        ctx->launches += 5;
+        if (record) ctx->launches += 5;
     } else {
         if (l.gw)
             CK(launch_factor_gw<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
-        else if (use_tc_factor(ctx, b.maxkd, b.maxnr))
+        else if (tc)
             CK(launch_factor_tc(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else
             CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
@@ -1264,13 +1339,15 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
             CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, L.d_redo, s,
                             it + 1 == ctx->cfg.max_refine ? 2 : 1));
         }
-        ctx->launches += 6 + 3 * ctx->cfg.max_refine;
+        if (record) ctx->launches += 6 + 3 * ctx->cfg.max_refine;
     }
     CK(cudaMemcpyAsync(L.h_sig, L.d_sig, sizeof(double) * dd * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(L.h_C, L.d_C, sizeof(double) * dd * dd * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(L.h_st, L.d_st, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaEventRecord(L.ev, s));
-    L.busy = true;
+    if (record) {
+        CK(cudaEventRecord(L.ev, s));
+        L.busy = true;
+    }
     return FE2_OK;
 }
 
@@ -1315,6 +1392,7 @@ void fe2_server_destroy(fe2_server* srv) {
     if (!srv) return;
     for (auto& L : srv->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
+        for (auto& g : L.graphs) cudaGraphExecDestroy(g.second);
         cudaFree(L.ws);
         cudaFree(L.d_ids);
         cudaFree(L.d_st);
@@ -1429,6 +1507,19 @@ int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma,
         ++k;
     }
     return k;
+}
+
+fe2_status fe2_server_use_graphs(fe2_server* srv, int enable) {
+    if (!srv) return FE2_ERR_ARG;
+    srv->use_graphs = enable != 0;
+    return FE2_OK;
+}
+
+fe2_status fe2_server_graph_stats(const fe2_server* srv, long long* captures, long long* replays) {
+    if (!srv) return FE2_ERR_ARG;
+    if (captures) *captures = srv->graph_captures;
+    if (replays) *replays = srv->graph_replays;
+    return FE2_OK;
 }
 
 int fe2_server_pending(const fe2_server* srv) {

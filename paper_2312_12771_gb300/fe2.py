@@ -83,6 +83,8 @@ _SIGS = {
     "fe2_server_pump": (_I, [_P, _IP]),
     "fe2_server_take": (_I, [_P, _I, C.POINTER(C.c_longlong), _DP, _DP, _IP, _DP]),
     "fe2_server_pending": (_I, [_P]),
+    "fe2_server_use_graphs": (_I, [_P, _I]),
+    "fe2_server_graph_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "fe2_selftest_wait_timeout": (_I, [_P, _P]),
     "fe2_profile": (_I, [_P, _I]),
     "fe2_profile_read": (_I, [_P, _I, C.c_char_p, _DP, C.POINTER(C.c_longlong)]),

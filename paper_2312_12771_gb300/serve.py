@@ -18,14 +18,21 @@ from .fe2 import Fe2Error, FE2_OK, _DP, _IP, fe2_last_error
 
 
 class Server:
-    def __init__(self, ctx, max_batch=1024, lanes=2):
+    def __init__(self, ctx, max_batch=1024, lanes=2, graphs=True):
         self.ctx = ctx
         self.lib = ctx.lib
         self.h = C.c_void_p()
         st = self.lib.fe2_server_create(ctx.h, int(max_batch), int(lanes), C.byref(self.h))
         if st != FE2_OK:
             raise Fe2Error(st, f"fe2_server_create: {fe2_last_error(ctx.h)}")
+        self.lib.fe2_server_use_graphs(self.h, 1 if graphs else 0)
         self.dd = ctx.dim * ctx.dim
+
+    def graph_stats(self):
+        """(graphs captured, graph replays) of the lanes so far."""
+        c, r = C.c_longlong(0), C.c_longlong(0)
+        self.lib.fe2_server_graph_stats(self.h, C.byref(c), C.byref(r))
+        return c.value, r.value
 
     def close(self):
         if self.h:

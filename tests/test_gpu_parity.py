@@ -347,6 +347,39 @@ def test_serving_results_equal_alone_and_in_the_mix(torch):
     srv.close()
 
 
+def test_serving_graph_replay_equals_direct_launches(torch):
+    """A lane replays its captured CUDA graph for a batch shape it has seen
+    before; the replayed batches give bit-identical sigma/Cbar to the same
+    requests launched kernel by kernel."""
+    from paper_2312_12771_gb300.serve import Server
+    sizes = W.serving_sizes(5, 32)
+    b = W.inclusion_batch(32, sizes, stretch=1.03)
+    ctx = ctx_for(torch, "mixed")
+    ids = np.asarray(ctx.register_batch(b))
+    out = {}
+    for graphs in (True, False):
+        srv = Server(ctx, max_batch=8, lanes=2, graphs=graphs)
+        got = []
+        for _ in range(3):                     # the same burst three times
+            tk = srv.submit(ids, b.Fbar)
+            t, sig, Cb, st, _ = srv.drain()
+            assert (st == 0).all() and len(t) == len(ids)
+            pos = {int(x): j for j, x in enumerate(tk)}
+            order = np.argsort([pos[int(x)] for x in t])
+            got.append((sig[order], Cb[order]))
+        cap, rep = srv.graph_stats()
+        if graphs:
+            assert cap > 0 and rep > 0, (cap, rep)
+        else:
+            assert cap == 0 and rep == 0
+        srv.close()
+        for s, c in got[1:]:
+            assert np.array_equal(s, got[0][0]) and np.array_equal(c, got[0][1])
+        out[graphs] = got[0]
+    assert np.array_equal(out[True][0], out[False][0])
+    assert np.array_equal(out[True][1], out[False][1])
+
+
 def ctx3(torch, precision, **kw):
     from paper_2312_12771_gb300.fe2 import Fe2Context
     return Fe2Context(dim=3, precision=precision, **kw)
