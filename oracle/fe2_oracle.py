@@ -398,24 +398,80 @@ def macro_mesh(nx, ny, Lx=1.0, Ly=1.0):
     return X, conn, bnd
 
 
+def macro_mesh3(nx, ny, nz, Lx=1.0, Ly=1.0, Lz=1.0):
+    """Hex8 macro mesh of the box: nodes x fastest, then y, then z; local node
+    a = a_x + 2 a_y + 4 a_z; returns (X, conn, boundary nodes)."""
+    xs, ys, zs = np.linspace(0.0, Lx, nx + 1), np.linspace(0.0, Ly, ny + 1), np.linspace(0.0, Lz, nz + 1)
+    X = np.array([[x, y, z] for z in zs for y in ys for x in xs])
+    offs = local_nodes(3)
+    conn = []
+    for ez in range(nz):
+        for ey in range(ny):
+            for ex in range(nx):
+                conn.append([(ex + o[0]) + (nx + 1) * ((ey + o[1]) + (ny + 1) * (ez + o[2])) for o in offs])
+    conn = np.array(conn)
+    L = (Lx, Ly, Lz)
+    bnd = np.array([i for i, x in enumerate(X) if any(abs(x[k]) < 1e-12 or abs(x[k] - L[k]) < 1e-12
+                                                       for k in range(3))])
+    return X, conn, bnd
+
+
 def macro_gauss(X, conn):
-    """Per macro Gauss point b = 4 e + q: grad N^A(X_b) [4][2] and weight eta_b."""
+    """Per macro Gauss point b = 2^d e + q (q = q_x + 2 q_y [+ 4 q_z], 2^d Gauss
+    points on the isoparametric Q4 / Hex8): grad N^A(X_b) [2^d][d], weight
+    eta_b = det(dX/dxi) and the point X_b."""
+    X = np.asarray(X, float)
+    d = X.shape[1]
     g = 1.0 / math.sqrt(3.0)
-    offs = local_nodes(2)
+    offs = local_nodes(d)
     s = 2.0 * offs - 1.0
+    na = 2 ** d
     grads, etas, pts = [], [], []
     for e in range(len(conn)):
         xe = X[conn[e]]
         for bits in offs:
             xi = g * (2.0 * bits - 1.0)
-            dN = np.array([[0.25 * s[a, 0] * (1 + s[a, 1] * xi[1]),
-                            0.25 * s[a, 1] * (1 + s[a, 0] * xi[0])] for a in range(4)])
+            # N_a = prod_k (1 + s_ak xi_k)/2, dN_a/dxi_J = s_aJ/2 prod_{k != J} (1 + s_ak xi_k)/2
+            fac = 0.5 * (1.0 + s * xi[None, :])          # [na][d]
+            Nv = np.prod(fac, axis=1)
+            dN = np.zeros((na, d))
+            for a in range(na):
+                for J in range(d):
+                    dN[a, J] = 0.5 * s[a, J] * np.prod([fac[a, k] for k in range(d) if k != J])
             Jm = xe.T @ dN                                  # dX/dxi
             grads.append(dN @ np.linalg.inv(Jm))
             etas.append(np.linalg.det(Jm))
-            Nv = np.array([0.25 * (1 + s[a, 0] * xi[0]) * (1 + s[a, 1] * xi[1]) for a in range(4)])
             pts.append(Nv @ xe)
     return np.array(grads), np.array(etas), np.array(pts)
+
+
+def macro_B(grad, d):
+    """dFbar_iJ / dq_(A,k) of F_iJ = sum_A q_Ai dN_A/dX_J at one Gauss point:
+    row iJ = d i + J, column d A + k."""
+    na = grad.shape[0]
+    Bm = np.zeros((d * d, d * na))
+    for A_ in range(na):
+        for i in range(d):
+            for J in range(d):
+                Bm[d * i + J, d * A_ + i] = grad[A_, J]
+    return Bm
+
+
+def macro_system(conn, grads, etas, stress, Cbar, d):
+    """Macro tangent and residual of Section 3, Eq. (linSys2) with the condensed
+    RVE tangents of Section 4.2, Eq. (solution2):
+    K = sum_b eta_b B_b^T Cbar_b B_b,  R = sum_b eta_b B_b^T s_b (dense, all DOFs)."""
+    na = 2 ** d
+    nnode = int(np.max(conn)) + 1
+    Kg = np.zeros((d * nnode, d * nnode))
+    Rg = np.zeros(d * nnode)
+    for b in range(len(etas)):
+        e = b // na
+        Bm = macro_B(grads[b], d)
+        dofs = (d * np.asarray(conn[e])[:, None] + np.arange(d)[None, :]).ravel()
+        Kg[np.ix_(dofs, dofs)] += etas[b] * Bm.T @ np.asarray(Cbar[b]).reshape(d * d, d * d) @ Bm
+        Rg[dofs] += etas[b] * Bm.T @ np.asarray(stress[b]).ravel()
+    return Kg, Rg
 
 
 def traction_load(X, edge_nodes, T):
@@ -434,46 +490,41 @@ def traction_load(X, edge_nodes, T):
 def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-9,
                    maxit=25, record=None, fext=None):
     """Load-stepped monolithic Newton (Section 4.2, Eq. (solution2)) on a Q4
-    macro mesh with affine Dirichlet data u = (F_k - I) X on all boundary
-    nodes, F_k = I + k/n (F_final - I), and with ``fext`` (nodal forces
-    [nnode][2] of a surface load, Eq. (weakMech)) the load k/n fext in step k.
-    ``rves`` is a list (one per macro Gauss point) of dicts with N, d, phase,
-    mat.  Returns per Gauss point the converged Fbar, sigma (= Pbar), Cbar and
-    w~, plus iteration counts.  A step fails when ||R_macro|| > 1e10 (Section 5.2)."""
+    (d = 2) or Hex8 (d = 3) macro mesh with affine Dirichlet data
+    u = (F_k - I) X on the nodes ``bnd``, F_k = I + k/n (F_final - I), and
+    with ``fext`` (nodal forces [nnode][d] of a surface load, Eq. (weakMech))
+    the load k/n fext in step k.  ``rves`` is a list (one per macro Gauss
+    point, b = 2^d e + q) of dicts with N, phase, mat.  Returns per Gauss point
+    the converged Fbar, sigma (= Pbar), Cbar and w~, plus iteration counts.  A
+    step fails when ||R_macro|| > 1e10 (Section 5.2)."""
     X, conn, bnd = macro
+    X = np.asarray(X, float)
+    d = X.shape[1]
+    na = 2 ** d
     grads, etas, _ = macro_gauss(X, conn)
     nb = len(etas)
     nnode = len(X)
     q = X.copy()
-    ws = [np.zeros(2 * (r["N"] ** 2 - 1)) for r in rves]
-    free = np.ones(2 * nnode, bool)
+    ws = [np.zeros(d * (r["N"] ** d - 1)) for r in rves]
+    free = np.ones(d * nnode, bool)
     for n in bnd:
-        free[2 * n:2 * n + 2] = False
+        free[d * n:d * n + d] = False
     iters = []
     for k in range(1, n_steps + 1):
-        Fk = np.eye(2) + (k / n_steps) * (np.asarray(F_final) - np.eye(2))
+        Fk = np.eye(d) + (k / n_steps) * (np.asarray(F_final) - np.eye(d))
         q[bnd] = X[bnd] @ Fk.T
         for it in range(maxit):
-            Kg = np.zeros((2 * nnode, 2 * nnode))
-            Rg = np.zeros(2 * nnode)        # R_macro (uses Pbar)
-            Rc = np.zeros(2 * nnode)        # condensed RHS (uses sigma_eff)
             sols, rmic = [], 0.0
             for b in range(nb):
-                e = b // 4
+                e = b // na
                 Fb = q[conn[e]].T @ grads[b]
                 r = rves[b]
-                s = rve_solve(r["N"], 2, r["phase"], r["mat"], Fb, ws[b])
+                s = rve_solve(r["N"], d, r["phase"], r["mat"], Fb, ws[b])
                 sols.append((Fb, s))
                 rmic = max(rmic, np.linalg.norm(s["r_m"]))
-                Bm = np.zeros((4, 8))          # dF_iJ / dq_(A,k): F_iJ = sum_A q_Ai dN_A/dX_J
-                for A_ in range(4):
-                    for i in range(2):
-                        for J in range(2):
-                            Bm[2 * i + J, 2 * A_ + i] = grads[b][A_, J]
-                dofs = np.array([[2 * conn[e][A_], 2 * conn[e][A_] + 1] for A_ in range(4)]).ravel()
-                Kg[np.ix_(dofs, dofs)] += etas[b] * Bm.T @ s["Cbar"] @ Bm
-                Rg[dofs] += etas[b] * Bm.T @ s["Pbar"].ravel()
-                Rc[dofs] += etas[b] * Bm.T @ s["sigma_eff"].ravel()
+            Cb = [s["Cbar"] for _, s in sols]
+            Kg, Rg = macro_system(conn, grads, etas, [s["Pbar"] for _, s in sols], Cb, d)     # R_macro
+            _, Rc = macro_system(conn, grads, etas, [s["sigma_eff"] for _, s in sols], Cb, d)  # condensed RHS
             if fext is not None:
                 Rg -= (k / n_steps) * np.asarray(fext).ravel()
                 Rc -= (k / n_steps) * np.asarray(fext).ravel()
@@ -485,12 +536,12 @@ def monolithic_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e
                 break
             if not rnorm < 1e10:
                 raise RuntimeError("macro residual above 1e10: Newton diverged")
-            dq = np.zeros(2 * nnode)
+            dq = np.zeros(d * nnode)
             dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rc[free])
-            q = q + dq.reshape(nnode, 2)
+            q = q + dq.reshape(nnode, d)
             for b in range(nb):
-                e = b // 4
-                dF = dq.reshape(nnode, 2)[conn[e]].T @ grads[b]
+                e = b // na
+                dF = dq.reshape(nnode, d)[conn[e]].T @ grads[b]
                 s = sols[b][1]
                 ws[b] = ws[b] - (s["x_r"] + s["X_M"] @ dF.ravel())
         else:

@@ -351,6 +351,100 @@ def test_macro_patch_test():
     assert np.abs(q - X @ Ff.T).max() < 1e-12
 
 
+def _distorted_hex_mesh(n, seed=7):
+    """Hex8 mesh of the unit cube with interior nodes moved by up to 0.15 h
+    (elements stay convex), then mapped by a fixed affine map x -> A x + c."""
+    X, conn, bnd = O.macro_mesh3(n, n, n)
+    rng = np.random.default_rng(seed)
+    inner = np.setdiff1d(np.arange(len(X)), bnd)
+    X = X.copy()
+    X[inner] += rng.uniform(-0.15, 0.15, (len(inner), 3)) / n
+    A = np.array([[1.2, 0.1, 0.0], [0.05, 0.9, 0.2], [0.0, -0.1, 1.1]])
+    return X @ A.T + np.array([0.3, -0.2, 0.1]), conn, bnd, A
+
+
+def test_macro_hex8_gauss_geometry():
+    """Isoparametric Hex8 at the 2x2x2 Gauss points: the gradients sum to zero
+    (partition of unity), any linear field x = B X + c is reproduced exactly
+    (sum_A x_A (x) grad N^A = B), and the weights sum to the volume of the
+    box image, det A (the Jacobian is degree <= 2 per direction, which the
+    2-point rule integrates exactly; the interior distortion leaves the
+    total volume unchanged)."""
+    X, conn, bnd, A = _distorted_hex_mesh(3)
+    grads, etas, pts = O.macro_gauss(X, conn)
+    assert grads.shape == (8 * 27, 8, 3)
+    assert np.abs(grads.sum(axis=1)).max() < 1e-12
+    B = np.array([[0.3, -1.0, 2.0], [0.5, 0.25, 0.0], [-0.7, 0.1, 1.5]])
+    x = X @ B.T + 1.0
+    for b in range(len(etas)):
+        e = b // 8
+        assert np.abs(x[conn[e]].T @ grads[b] - B).max() < 1e-12
+    assert abs(etas.sum() - np.linalg.det(A)) < 1e-12
+    assert (etas > 0).all()
+    # the Gauss points of a cube element sit at (1 +- 1/sqrt 3)/2 of its edges
+    X0, conn0, _ = O.macro_mesh3(1, 1, 1)
+    _, e0, p0 = O.macro_gauss(X0, conn0)
+    g = 0.5 * (1.0 - 1.0 / math.sqrt(3.0))
+    assert np.abs(np.sort(np.unique(np.round(p0, 14))) - np.array([g, 1.0 - g])).max() < 1e-14
+    assert np.abs(e0 - 0.125).max() < 1e-15
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_macro_system_virtual_work_and_tangent(d):
+    """R . dq equals sum_b eta_b s_b : dFbar_b with dFbar_b taken directly from
+    the nodal increments (Eq. (linSys2)), and for a linear law s_b = C_b : Fbar_b
+    the tangent is exact: K dq = R(q + dq) - R(q)."""
+    rng = np.random.default_rng(11 + d)
+    if d == 2:
+        X, conn, _ = O.macro_mesh(3, 2)
+        X = X + rng.uniform(-0.05, 0.05, X.shape)
+    else:
+        X, conn, _, _ = _distorted_hex_mesh(2)
+    grads, etas, _ = O.macro_gauss(X, conn)
+    na, nb, dd = 2 ** d, len(etas), d * d
+    C = []
+    for _ in range(nb):
+        M = rng.standard_normal((dd, dd))
+        C.append(M @ M.T + dd * np.eye(dd))
+    q = X + rng.uniform(-0.05, 0.05, X.shape)
+    dq = rng.uniform(-0.05, 0.05, X.shape)
+
+    def F_of(qq):
+        return [qq[conn[b // na]].T @ grads[b] for b in range(nb)]
+
+    def stress(qq):
+        return [(C[b] @ F.ravel()).reshape(d, d) for b, F in enumerate(F_of(qq))]
+
+    s = stress(q)
+    K, R = O.macro_system(conn, grads, etas, s, C, d)
+    dF = F_of(dq)   # Fbar is linear in q
+    vw = sum(etas[b] * np.sum(s[b] * dF[b]) for b in range(nb))
+    assert abs(R @ dq.ravel() - vw) < 1e-12 * max(1.0, abs(vw))
+    _, R1 = O.macro_system(conn, grads, etas, stress(q + dq), C, d)
+    assert np.abs(K @ dq.ravel() - (R1 - R)).max() < 1e-11 * np.abs(R1 - R).max()
+    assert np.abs(K - K.T).max() < 1e-12 * np.abs(K).max()
+
+
+def test_macro_hex8_patch_test():
+    """Hex8 macro mesh, identical heterogeneous RVEs (a centred inclusion on a
+    3^3 grid) and affine Dirichlet data on the boundary: the homogenised
+    material is uniform, so the macro solution is affine, every Gauss point
+    sees Fbar = F_final, and all converged states are equal."""
+    macro = O.macro_mesh3(2, 2, 2)
+    ph = np.zeros(27, np.uint8)
+    ph[13] = 1                                         # centre element of 3^3
+    mat = W.neohooke_mat(1.0, 10.0, 10.0, 100.0)
+    rves = [dict(N=3, phase=ph, mat=mat) for _ in range(64)]
+    Ff = np.array([[1.0, 0.06, 0.0], [0.0, 1.0, 0.0], [0.02, 0.0, 0.97]])
+    out, iters, q = O.monolithic_fe2(macro, rves, Ff, n_steps=2, tol_macro=1e-11, tol_micro=1e-11)
+    assert max(iters) <= 5
+    assert np.abs(q - macro[0] @ Ff.T).max() < 1e-11
+    for o in out:
+        assert np.abs(o["Fbar"] - Ff).max() < 1e-11
+        assert O.rel_err(o["Pbar"], out[0]["Pbar"]) < 1e-10
+        assert O.rel_err(o["Cbar"], out[0]["Cbar"]) < 1e-10
+
+
 def test_monolithic_newton_converges_quadratically():
     """Heterogeneous RVEs: the monolithic scheme converges in a few iterations
     with a quadratically falling residual (Section 4.2, Table 2 pattern), and
