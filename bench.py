@@ -406,6 +406,46 @@ def run_hex8(args):
     return out
 
 
+def run_config5(args):
+    """Config-5 style: macro n^3 Hex8 x 2x2x2 Gauss points = 8 n^3 RVEs of 8^3
+    Hex8 (centred sphere vf 0.2, mu_i/mu_m = 10, kappa = 10 mu), simple shear
+    Fbar = I + gamma e1 (x) e2 on the whole boundary, gamma -> 0.1 in 5 load
+    steps, 3D monolithic Newton (affine predictor per step), mixed path."""
+    import torch
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh3
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    nx = args.c5_macro
+    X, conn, fixed = macro_mesh3(nx, nx, nx)
+    b = W.sphere_batch(8 * nx ** 3, 8)
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=1)
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    # warm-up outside the timed region: one RVE solve at the reference state
+    ctx.macro_gradients(fe.Fbar)
+    ctx.rve_solve(fe.ids, fe.Fbar, out=fe.outs)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    F = np.eye(3)
+    F[0, 1] = 0.1
+    t0 = time.perf_counter()
+    log = fe.run(F, args.c5_steps, predictor=True, tol_macro=1e-8, tol_micro=1e-8)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = ctx.profile_read()
+    solves = sum(it + 1 for it in log.iters) * fe.ngp
+    nfree = int((fixed == 0).sum())
+    out = {"workload": f"macro {nx}^3 Hex8 x 8 Gauss = {fe.ngp} RVEs 8^3 (sphere vf 0.2, mu_i/mu_m = 10), "
+                       f"simple shear gamma -> 0.1 in {args.c5_steps} steps (affine predictor)",
+           "macro_dofs": 3 * len(X), "macro_free_dofs": nfree,
+           "newton_iterations_per_step": log.iters, "rve_solves": solves, "wall_s": round(wall, 3),
+           "solves_per_s": round(solves / wall, 1),
+           "final_macro_residual": log.history[-1][2], "final_max_micro_residual": log.history[-1][3],
+           "kernels_ms_total": {k: round(v[0], 2) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])[:8]},
+           "macro_solve_ms_per_call": round(prof["macro_solve"][0] / max(prof["macro_solve"][1], 1), 3)
+           if "macro_solve" in prof else None}
+    ctx.close()
+    return out
+
+
 def run_nh_newton(args):
     """Config-3 style: macro 32x32 Q4 x 2x2 Gauss = 4096 NH RVEs (32x32, 1-6 random
     inclusions, mu_i/mu_m = 20, kappa = 10 mu), stretch diag(1.2, 1) in 10 load
@@ -606,7 +646,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the Hex8 and NH-Newton legs")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Hex8, Newton, scheme, Cook and basis legs")
+    ap.add_argument("--legs", default="all",
+                    help="comma list of extra legs (hex8, hex8_newton, nh_newton, schemes, cook, basis)")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core factor leg")
     ap.add_argument("--cook-macro", type=int, default=20)
     ap.add_argument("--cook-N", type=int, default=30)
@@ -614,6 +656,8 @@ def main():
     ap.add_argument("--scheme-steps", default="1,2,5,10",
                     help="load-step counts of the staggered vs monolithic sweep ('' to skip)")
     ap.add_argument("--hex8-rves", type=int, default=4096)
+    ap.add_argument("--c5-macro", type=int, default=16, help="macro Hex8 mesh n^3 of the 3D Newton leg")
+    ap.add_argument("--c5-steps", type=int, default=5)
     ap.add_argument("--nh-macro", type=int, default=32)
     ap.add_argument("--nh-steps", type=int, default=10)
     ap.add_argument("--serve-nreq", default="2048,8192,32768,65536",
@@ -671,8 +715,12 @@ def main():
     batch, R, pk = run_gpu(args, rank, world, dist)
     extra = {}
     if rank == 0 and not args.no_extra:
-        for key, fn in (("hex8", run_hex8), ("nh_newton", run_nh_newton), ("schemes", run_schemes),
-                        ("cook", run_cook), ("basis", run_basis)):
+        legs = (("hex8", run_hex8), ("hex8_newton", run_config5), ("nh_newton", run_nh_newton),
+                ("schemes", run_schemes), ("cook", run_cook), ("basis", run_basis))
+        chosen = None if args.legs == "all" else set(args.legs.split(","))
+        for key, fn in legs:
+            if chosen is not None and key not in chosen:
+                continue
             try:
                 extra[key] = fn(args)
             except Exception as exc:  # reported, not fatal: the headline leg is already measured

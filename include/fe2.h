@@ -167,23 +167,26 @@ fe2_status fe2_rve_solve(fe2_ctx* ctx, int n, const int* rve_ids, const double* 
 fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double* dFbar);
 
 /*
- * Macro Q4 problem of Section 3, Eq. (linSys2), solved with the condensed
- * tangent of Section 4.2, Eq. (solution2):
+ * Macro Q4 (dim 2) or Hex8 (dim 3) problem of Section 3, Eq. (linSys2),
+ * solved with the condensed tangent of Section 4.2, Eq. (solution2):
  *   K = sum_b eta_b B_b^T Cbar_b B_b,   R = sum_b eta_b B_b^T s_b,
- * over the macro Gauss points b = 4 e + q (q = qx + 2 qy, 2x2 Gauss), with
- * B_b dq = sum_A dq_A (x) grad N^A(X_b).  Dirichlet DOFs are held at their
- * prescribed positions; the free block is factorised by a band Cholesky on the
- * device.  The macro state (nodal positions q, starting at X) is owned by the
- * context.
+ * over the macro Gauss points b = 2^d e + q (q = qx + 2 qy [+ 4 qz], 2^d Gauss
+ * points), with B_b dq = sum_A dq_A (x) grad N^A(X_b).  Dirichlet DOFs are held
+ * at their prescribed positions; the free block (natural DOF order, half
+ * bandwidth from the element couplings) is factorised on the device by a
+ * blocked FP64 band Cholesky (32-column panels: diagonal block, panel rows,
+ * trailing update as separate kernels).  The macro state (nodal positions q,
+ * starting at X) is owned by the context.  Element RVEs (FE2_BASIS_CONST) are
+ * 2D only.
  *
- * fe2_macro_setup [host]: nodes X[nnode][2], connectivity conn[nelem][4]
- * (local node a = ax + 2 ay on the reference square, counter-clockwise
- * elements), fixed[2*nnode] (1 = prescribed DOF).  Returns FE2_ERR_ARG for an
+ * fe2_macro_setup [host]: nodes X[nnode][d], connectivity conn[nelem][2^d]
+ * (local node a = ax + 2 ay [+ 4 az] on the reference square / cube, positive
+ * Jacobian), fixed[d*nnode] (1 = prescribed DOF).  Returns FE2_ERR_ARG for an
  * inverted element.
  */
 fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, const int* conn,
                            const uint8_t* fixed);
-/* Overwrite nodal positions from q_host [host] double[nnode][2]: every DOF, or
+/* Overwrite nodal positions from q_host [host] double[nnode][d]: every DOF, or
  * only those with which[t] != 0 when `which` [host] is not NULL (e.g. the
  * Dirichlet DOFs at the start of a load step).  Synchronises. */
 fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which);
@@ -192,24 +195,25 @@ fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uin
  * fe2_macro_gradients; they sum to 1).  Registration sets 1/nq.  Returns
  * FE2_ERR_ARG with the Dirac basis or for weights that are not positive. */
 fe2_status fe2_rve_set_quad_weights(fe2_ctx* ctx, int n, const int* rve_ids, const double* wq);
-/* Copy the current nodal positions to q_host [host] double[nnode][2].  Synchronises. */
+/* Copy the current nodal positions to q_host [host] double[nnode][d].  Synchronises. */
 fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host);
-/* Nodal external forces of the current load, fext_host [host] double[nnode][2]
+/* Nodal external forces of the current load, fext_host [host] double[nnode][d]
  * (the surface-load term of Eq. (weakMech), e.g. the Section 5.2 membrane
  * traction scaled to the load step; NULL = no load).  fe2_macro_residual and
  * fe2_macro_solve then use R = (internal) - fext on the free DOFs.  Returns
  * FE2_ERR_NAN for a non-finite entry.  Synchronises. */
 fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host);
-/* Fbar_b = sum_A q_A (x) grad N^A(X_b) into Fbar [device] double[4 nelem][2][2];
- * eta [device] double[4 nelem] receives the quadrature weights (may be NULL). */
+/* Fbar_b = sum_A q_A (x) grad N^A(X_b) into Fbar [device] double[2^d nelem][d][d];
+ * eta [device] double[2^d nelem] receives the quadrature weights (may be NULL). */
 fe2_status fe2_macro_gradients(fe2_ctx* ctx, double* Fbar, double* eta);
 /* R_macro on the free DOFs for the stress s_b = stress [device]
- * double[4 nelem][2][2] (Pbar for the equilibrium residual); rnorm [device]
+ * double[2^d nelem][d][d] (Pbar for the equilibrium residual); rnorm [device]
  * double[1] = ||R_free||_2. */
 fe2_status fe2_macro_residual(fe2_ctx* ctx, const double* stress, double* rnorm);
-/* One monolithic macro update: assemble K from Cbar [device] double[4 nelem][4][4]
- * and R from sigma [device] (sigma_eff: condensed right-hand side), solve
- * K dq = -R, update q += dq and write dFbar [device] double[4 nelem][2][2] = B_b dq,
+/* One monolithic macro update: assemble K from Cbar [device]
+ * double[2^d nelem][d*d][d*d] (element RVEs: double[nelem][16][16]) and R from
+ * sigma [device] (sigma_eff: condensed right-hand side), solve K dq = -R,
+ * update q += dq and write dFbar [device] double[2^d nelem][d][d] = B_b dq,
  * rnorm [device] double[1] = ||R_free||, status [device] int[1] (may be NULL):
  * FE2_ERR_NOT_PD if the macro tangent had a non-positive pivot. */
 fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dFbar, double* rnorm,

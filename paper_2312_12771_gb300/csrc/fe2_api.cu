@@ -966,62 +966,95 @@ fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* out) {
 fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, const int* conn,
                            const uint8_t* fixed) {
     if (!ctx) return FE2_ERR_ARG;
-    if (ctx->cfg.dim != 2) return fail(ctx, FE2_ERR_ARG, "the macro problem is 2D (Q4)");
+    const int d = ctx->cfg.dim, nen = 1 << d;
+    if (d == 3 && nq_of(ctx) > 1) return fail(ctx, FE2_ERR_ARG, "element RVEs are 2D");
     if (nnode <= 0 || nelem <= 0 || !X || !conn || !fixed) return fail(ctx, FE2_ERR_ARG, "bad macro mesh");
     CK(cudaStreamSynchronize(ctx->stream));
     for (void* p : ctx->macro_bufs) cudaFree(p);
     ctx->macro_bufs.clear();
     ctx->macro_ready = false;
-    const int ngp = 4 * nelem;
-    std::vector<int> cn(conn, conn + 4 * nelem);
+    const int ngp = nen * nelem;
+    std::vector<int> cn(conn, conn + (size_t)nen * nelem);
     for (int v : cn)
         if (v < 0 || v >= nnode) return fail(ctx, FE2_ERR_ARG, "connectivity references node %d", v);
     // free DOFs in natural order; band width from the element couplings
-    std::vector<int> d2f(2 * nnode, -1);
+    std::vector<int> d2f((size_t)d * nnode, -1);
     int nfree = 0;
-    for (int t = 0; t < 2 * nnode; ++t)
+    for (int t = 0; t < d * nnode; ++t)
         if (!fixed[t]) d2f[t] = nfree++;
     if (nfree == 0) return fail(ctx, FE2_ERR_ARG, "no free macro DOFs");
     int kd = 0;
     for (int e = 0; e < nelem; ++e)
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b)
-                for (int c = 0; c < 2; ++c)
-                    for (int k = 0; k < 2; ++k) {
-                        const int i = d2f[2 * cn[4 * e + a] + c], j = d2f[2 * cn[4 * e + b] + k];
+        for (int a = 0; a < nen; ++a)
+            for (int b = 0; b < nen; ++b)
+                for (int c = 0; c < d; ++c)
+                    for (int k = 0; k < d; ++k) {
+                        const int i = d2f[d * cn[nen * e + a] + c], j = d2f[d * cn[nen * e + b] + k];
                         if (i >= 0 && j >= 0) kd = std::max(kd, std::abs(i - j));
                     }
-    // Gauss-point gradients and weights (2x2 Gauss on the isoparametric Q4)
-    std::vector<double> grads((size_t)ngp * 8), eta(ngp);
+    // Gauss-point gradients and weights (2^d Gauss points on the isoparametric
+    // Q4 / Hex8): N_a = prod_k (1 + s_ak xi_k) / 2, s_ak = +-1 from the bits of a
+    std::vector<double> grads((size_t)ngp * nen * d), eta(ngp);
     const double g = 0.57735026918962576451;
     for (int e = 0; e < nelem; ++e)
-        for (int q = 0; q < 4; ++q) {
-            const double xi[2] = {(q & 1) ? g : -g, (q & 2) ? g : -g};
-            double dN[4][2], Jm[2][2] = {{0, 0}, {0, 0}};
-            for (int a = 0; a < 4; ++a) {
-                const double s0 = (a & 1) ? 1.0 : -1.0, s1 = (a & 2) ? 1.0 : -1.0;
-                dN[a][0] = 0.25 * s0 * (1.0 + s1 * xi[1]);
-                dN[a][1] = 0.25 * s1 * (1.0 + s0 * xi[0]);
-                for (int i = 0; i < 2; ++i)
-                    for (int k = 0; k < 2; ++k) Jm[i][k] += X[2 * cn[4 * e + a] + i] * dN[a][k];
+        for (int q = 0; q < nen; ++q) {
+            double xi[3], dN[8][3], Jm[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+            for (int k = 0; k < d; ++k) xi[k] = ((q >> k) & 1) ? g : -g;
+            for (int a = 0; a < nen; ++a) {
+                double sgn[3], fac[3];
+                for (int k = 0; k < d; ++k) {
+                    sgn[k] = ((a >> k) & 1) ? 1.0 : -1.0;
+                    fac[k] = 0.5 * (1.0 + sgn[k] * xi[k]);
+                }
+                for (int J = 0; J < d; ++J) {
+                    double v = 0.5 * sgn[J];
+                    for (int k = 0; k < d; ++k)
+                        if (k != J) v *= fac[k];
+                    dN[a][J] = v;
+                }
+                for (int i = 0; i < d; ++i)
+                    for (int k = 0; k < d; ++k) Jm[i][k] += X[(size_t)d * cn[nen * e + a] + i] * dN[a][k];
             }
-            const double det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+            double inv[3][3], det;
+            if (d == 2) {
+                det = Jm[0][0] * Jm[1][1] - Jm[0][1] * Jm[1][0];
+                inv[0][0] = Jm[1][1] / det;
+                inv[0][1] = -Jm[0][1] / det;
+                inv[1][0] = -Jm[1][0] / det;
+                inv[1][1] = Jm[0][0] / det;
+            } else {
+                // inverse by cofactors: inv[k][i] = cof[i][k] / det
+                double cof[3][3];
+                for (int i = 0; i < 3; ++i)
+                    for (int k = 0; k < 3; ++k) {
+                        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+                        cof[i][k] = Jm[i1][k1] * Jm[i2][k2] - Jm[i1][k2] * Jm[i2][k1];
+                    }
+                det = Jm[0][0] * cof[0][0] + Jm[0][1] * cof[0][1] + Jm[0][2] * cof[0][2];
+                for (int i = 0; i < 3; ++i)
+                    for (int k = 0; k < 3; ++k) inv[k][i] = cof[i][k] / det;
+            }
             if (!(det > 0.0)) return fail(ctx, FE2_ERR_ARG, "macro element %d is inverted", e);
-            const double inv[2][2] = {{Jm[1][1] / det, -Jm[0][1] / det}, {-Jm[1][0] / det, Jm[0][0] / det}};
-            const int b = 4 * e + q;
-            for (int a = 0; a < 4; ++a)
-                for (int J = 0; J < 2; ++J) grads[(size_t)(b * 4 + a) * 2 + J] = dN[a][0] * inv[0][J] + dN[a][1] * inv[1][J];
+            const int b = nen * e + q;
+            // grad N_a = dN/dxi (dX/dxi)^-1
+            for (int a = 0; a < nen; ++a)
+                for (int J = 0; J < d; ++J) {
+                    double v = 0.0;
+                    for (int k = 0; k < d; ++k) v += dN[a][k] * inv[k][J];
+                    grads[((size_t)b * nen + a) * d + J] = v;
+                }
             eta[b] = det;
         }
     std::vector<int> adj_ptr(nnode + 1, 0), adj;
     for (int e = 0; e < nelem; ++e)
-        for (int a = 0; a < 4; ++a) ++adj_ptr[cn[4 * e + a] + 1];
+        for (int a = 0; a < nen; ++a) ++adj_ptr[cn[nen * e + a] + 1];
     for (int n = 0; n < nnode; ++n) adj_ptr[n + 1] += adj_ptr[n];
     adj.assign(adj_ptr[nnode], 0);
     std::vector<int> fill(adj_ptr.begin(), adj_ptr.end() - 1);
     for (int e = 0; e < nelem; ++e)
-        for (int a = 0; a < 4; ++a) adj[fill[cn[4 * e + a]]++] = 4 * e + a;
+        for (int a = 0; a < nen; ++a) adj[fill[cn[nen * e + a]]++] = nen * e + a;
     MacroDev M{};
+    M.d = d;
     M.nnode = nnode;
     M.nelem = nelem;
     M.nfree = nfree;
@@ -1034,13 +1067,13 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
         (st = upload_vec(ctx, grads, &dgr)) || (st = upload_vec(ctx, eta, &deta)) ||
         (st = upload_vec(ctx, adj_ptr, &dadjp)) || (st = upload_vec(ctx, adj, &dadj)))
         return st;
-    std::vector<double> q0(X, X + 2 * nnode);
+    std::vector<double> q0(X, X + (size_t)d * nnode);
     if ((st = upload_vec(ctx, q0, &dq))) return st;
     if ((st = upload_vec(ctx, std::vector<double>((size_t)nfree * (kd + 1)), &dK))) return st;
     if ((st = upload_vec(ctx, std::vector<double>(nfree), &dR))) return st;
-    if ((st = upload_vec(ctx, std::vector<double>(2 * nnode), &ddq))) return st;
+    if ((st = upload_vec(ctx, std::vector<double>((size_t)d * nnode), &ddq))) return st;
     double* dfext;
-    if ((st = upload_vec(ctx, std::vector<double>(2 * nnode), &dfext))) return st;
+    if ((st = upload_vec(ctx, std::vector<double>((size_t)d * nnode), &dfext))) return st;
     M.fext = dfext;
     M.conn = dconn;
     M.dof2free = dd2f;
@@ -1061,7 +1094,7 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
 fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uint8_t* which) {
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready || !q_host) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL positions");
-    const int nd = 2 * ctx->macro.nnode;
+    const int nd = ctx->macro.d * ctx->macro.nnode;
     std::vector<double> q(nd);
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(q.data(), ctx->macro.q, sizeof(double) * nd, cudaMemcpyDeviceToHost));
@@ -1074,7 +1107,7 @@ fe2_status fe2_macro_set_positions(fe2_ctx* ctx, const double* q_host, const uin
 fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host) {
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready) return fail(ctx, FE2_ERR_ARG, "no macro problem");
-    const int nd = 2 * ctx->macro.nnode;
+    const int nd = ctx->macro.d * ctx->macro.nnode;
     std::vector<double> f(nd, 0.0);
     if (fext_host) f.assign(fext_host, fext_host + nd);
     for (int t = 0; t < nd; ++t)
@@ -1088,7 +1121,7 @@ fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host) {
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready || !q_host) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL output");
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(q_host, ctx->macro.q, sizeof(double) * 2 * ctx->macro.nnode, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(q_host, ctx->macro.q, sizeof(double) * ctx->macro.d * ctx->macro.nnode, cudaMemcpyDeviceToHost));
     return FE2_OK;
 }
 
@@ -1112,13 +1145,14 @@ fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready || !sigma || !Cbar || !dFbar || !rnorm)
         return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    int nl = 0;
     if (nq_of(ctx) > 1)
         TIMED("macro_solve", launch_macro_solve_elem(ctx->macro, sigma, Cbar, dFbar, rnorm,
-                                                     status ? status : ctx->d_macro_status, ctx->stream));
+                                                     status ? status : ctx->d_macro_status, ctx->stream, &nl));
     else
         TIMED("macro_solve", launch_macro_solve(ctx->macro, sigma, Cbar, dFbar, rnorm,
-                                                status ? status : ctx->d_macro_status, ctx->stream));
-    ctx->launches += 6;
+                                                status ? status : ctx->d_macro_status, ctx->stream, &nl));
+    ctx->launches += nl;
     return FE2_OK;
 }
 

@@ -113,23 +113,23 @@ cudaError_t launch_selftest_wait(int* status, cudaStream_t s);
 
 // macro problem (fe2_macro.cu)
 struct MacroDev {
-    int nnode, nelem, nfree, kd, ngp;
-    const int* conn;      // [nelem][4]
-    const int* dof2free;  // [2 nnode] -> free index or -1
-    const double* grads;  // [ngp][4][2]
+    int d, nnode, nelem, nfree, kd, ngp;  // d = 2 (Q4) or 3 (Hex8); ngp = 2^d nelem
+    const int* conn;      // [nelem][2^d]
+    const int* dof2free;  // [d nnode] -> free index or -1
+    const double* grads;  // [ngp][2^d][d]
     const double* eta;    // [ngp]
-    const int* adj_ptr;   // [nnode+1] CSR: node -> (elem * 4 + local) entries
+    const int* adj_ptr;   // [nnode+1] CSR: node -> (elem * 2^d + local) entries
     const int* adj;       //
-    double* q;            // [nnode][2] current nodal positions
+    double* q;            // [nnode][d] current nodal positions
     double* K;            // [nfree][kd+1] lower band, column-major
     double* R;            // [nfree]
-    double* dq;           // [2 nnode]
-    const double* fext;   // [2 nnode] nodal external forces of the current load (zero unless set)
+    double* dq;           // [d nnode]
+    const double* fext;   // [d nnode] nodal external forces of the current load (zero unless set)
 };
 cudaError_t launch_macro_gradients(const MacroDev& M, double* Fbar, double* eta, cudaStream_t s);
 cudaError_t launch_macro_residual(const MacroDev& M, const double* stress, double* rnorm, cudaStream_t s);
 cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
-                               double* rnorm, int* status, cudaStream_t s);
+                               double* rnorm, int* status, cudaStream_t s, int* launches);
 cudaError_t launch_rve_avg_stress(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
 
 // element RVEs (piecewise-constant macro basis, 2D, nq = 4, nr = 17)
@@ -145,7 +145,7 @@ cudaError_t launch_macro_update_elem(const RveDev* tab, const int* ids, int n, c
                                      cudaStream_t s);
 cudaError_t launch_rve_avg_stress_elem(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
 cudaError_t launch_macro_solve_elem(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
-                                    double* rnorm, int* status, cudaStream_t s);
+                                    double* rnorm, int* status, cudaStream_t s, int* launches);
 cudaError_t launch_rve_rnorm(const RveDev* tab, const int* ids, int n, double* out, cudaStream_t s);
 
 }  // namespace fe2

@@ -35,6 +35,22 @@ def macro_mesh(nx, ny, Lx=1.0, Ly=1.0):
     return X, conn, fixed
 
 
+def macro_mesh3(nx, ny, nz, Lx=1.0, Ly=1.0, Lz=1.0):
+    """Structured Hex8 mesh of [0,Lx]x[0,Ly]x[0,Lz] (nodes x fastest, local node
+    a = a_x + 2 a_y + 4 a_z); boundary nodes flagged as Dirichlet."""
+    g = np.meshgrid(np.linspace(0.0, Lx, nx + 1), np.linspace(0.0, Ly, ny + 1), np.linspace(0.0, Lz, nz + 1),
+                    indexing="ij")
+    X = np.stack([g[0].ravel(order="F"), g[1].ravel(order="F"), g[2].ravel(order="F")], axis=1)
+    ex, ey, ez = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ex, ey, ez = ex.ravel(order="F"), ey.ravel(order="F"), ez.ravel(order="F")
+    conn = np.stack([(ex + (a & 1)) + (nx + 1) * ((ey + ((a >> 1) & 1)) + (ny + 1) * (ez + ((a >> 2) & 1)))
+                     for a in range(8)], axis=1).astype(np.int32)
+    L = np.array([Lx, Ly, Lz])
+    on_bnd = ((np.abs(X) < 1e-12) | (np.abs(X - L) < 1e-12)).any(axis=1)
+    fixed = np.repeat(on_bnd, 3).astype(np.uint8)
+    return X, conn, fixed
+
+
 def edge_load(X, edge_nodes, T):
     """Nodal forces of a constant surface load T on a boundary polyline of
     bilinear-element edges (Neumann term of Eq. (weakMech)): T L/2 per end
@@ -58,10 +74,10 @@ class NewtonLog:
 
 
 class MonolithicFE2:
-    """Macro Q4 problem with one RVE per macro Gauss point (b = 4 e + q), or,
-    on a context with the piecewise-constant basis, one element RVE per macro
-    element (Eqs. (constSolution1), (constSolution2)) whose four Gauss points
-    are weighted by eta_q / sum eta."""
+    """Macro Q4 (2D) or Hex8 (3D) problem with one RVE per macro Gauss point
+    (b = 2^d e + q), or, on a 2D context with the piecewise-constant basis, one
+    element RVE per macro element (Eqs. (constSolution1), (constSolution2))
+    whose four Gauss points are weighted by eta_q / sum eta."""
 
     def __init__(self, ctx, X, conn, fixed, batch):
         import torch
@@ -69,7 +85,9 @@ class MonolithicFE2:
         self.ctx = ctx
         self.X = np.asarray(X, float)
         self.fixed = np.asarray(fixed, np.uint8)
-        ngp = 4 * len(conn)
+        d = ctx.dim
+        self.d = d
+        ngp = (1 << d) * len(conn)
         nrve = ngp // getattr(ctx, "nq", 1)
         if batch.nrve != nrve:
             raise ValueError(f"need {nrve} RVEs ({'macro elements' if nrve != ngp else 'macro Gauss points'}), "
@@ -78,9 +96,9 @@ class MonolithicFE2:
         self.ids = ctx.register_batch(batch)
         dev = "cuda"
         f64 = torch.float64
-        self.Fbar = torch.zeros((ngp, 2, 2), dtype=f64, device=dev)
+        self.Fbar = torch.zeros((ngp, d, d), dtype=f64, device=dev)
         self.dFbar = torch.zeros_like(self.Fbar)
-        self.Pbar = torch.zeros((ngp, 4), dtype=f64, device=dev)
+        self.Pbar = torch.zeros((ngp, d * d), dtype=f64, device=dev)
         self.outs = ctx._outs(nrve)
         self.rn = torch.zeros(2, dtype=f64, device=dev)
         self.rnm = torch.zeros(nrve, dtype=f64, device=dev)
@@ -218,9 +236,10 @@ class MonolithicFE2:
         log = NewtonLog() if log is None else log
         step_fn = self.load_step if scheme == "monolithic" else self.load_step_staggered
         F_final = np.asarray(F_final, float)
-        F_prev = np.eye(2)
+        I = np.eye(self.d)
+        F_prev = I
         for k in range(1, n_steps + 1):
-            Fk = np.eye(2) + (k / n_steps) * (F_final - np.eye(2))
+            Fk = I + (k / n_steps) * (F_final - I)
             if fext is not None:
                 self.set_load((k / n_steps) * np.asarray(fext, dtype=np.float64))
             step_fn(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)

@@ -269,7 +269,7 @@ class Fe2Context:
         self._check(self.lib.fe2_macro_setup(self.h, len(X), X.ctypes.data_as(_DP), len(conn),
                                              conn.ctypes.data_as(_IP), fixed.ctypes.data_as(C.POINTER(C.c_uint8))),
                     "fe2_macro_setup")
-        self.macro_nnode, self.macro_ngp = len(X), 4 * len(conn)
+        self.macro_nnode, self.macro_ngp = len(X), (1 << self.dim) * len(conn)
 
     def macro_set_positions(self, q, which=None):
         q = np.ascontiguousarray(np.asarray(q, dtype=np.float64))
@@ -279,7 +279,7 @@ class Fe2Context:
                     "fe2_macro_set_positions")
 
     def macro_get_positions(self):
-        q = np.zeros((self.macro_nnode, 2))
+        q = np.zeros((self.macro_nnode, self.dim))
         self._check(self.lib.fe2_macro_get_positions(self.h, q.ctypes.data_as(_DP)), "fe2_macro_get_positions")
         return q
 
@@ -291,11 +291,11 @@ class Fe2Context:
                     "fe2_rve_set_quad_weights")
 
     def macro_set_load(self, fext):
-        """Nodal external forces [nnode][2] of the current load (None = no load)."""
+        """Nodal external forces [nnode][d] of the current load (None = no load)."""
         if fext is None:
             self._check(self.lib.fe2_macro_set_load(self.h, None), "fe2_macro_set_load")
             return
-        f = np.ascontiguousarray(np.asarray(fext, dtype=np.float64).reshape(self.macro_nnode, 2))
+        f = np.ascontiguousarray(np.asarray(fext, dtype=np.float64).reshape(self.macro_nnode, self.dim))
         self._check(self.lib.fe2_macro_set_load(self.h, f.ctypes.data_as(_DP)), "fe2_macro_set_load")
 
     def macro_gradients(self, Fbar, eta=None):

@@ -445,6 +445,99 @@ def test_hex8_config5_rve_sampled(torch):
     print(f"hex8 8^3 worst sampled rel err {w:.3e}")
 
 
+def _macro_problem(d, shape, seed):
+    """Structured Q4 / Hex8 macro mesh with its interior nodes moved by up to
+    0.2 h, boundary nodes fixed."""
+    from paper_2312_12771_gb300.driver import macro_mesh, macro_mesh3
+    X, conn, fixed = macro_mesh(*shape) if d == 2 else macro_mesh3(*shape)
+    rng = np.random.default_rng(seed)
+    inner = fixed.reshape(-1, d)[:, 0] == 0
+    X = X.copy()
+    X[inner] += rng.uniform(-0.2, 0.2, (int(inner.sum()), d)) / max(shape)
+    return X, conn, fixed, rng
+
+
+@pytest.mark.parametrize("d,shape", [(2, (5, 5)), (2, (40, 30)), (3, (3, 3, 3)), (3, (6, 6, 5)),
+                                     (3, (12, 12, 12))])
+def test_macro_solve_matches_oracle(torch, d, shape):
+    """One macro update (S7) for given sigma_eff and Cbar (random; Cbar SPD per
+    Gauss point): dq from the blocked band Cholesky, dFbar_b = B_b dq and
+    ||R_free|| equal a dense FP64 solve of the oracle's assembled system.  The
+    cases cover a band narrower than one 32-column panel, many panels with a
+    ragged last one, and (12^3 Hex8, 3993 DOFs, kd = 401) a trailing update of
+    91 tiles."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    X, conn, fixed, rng = _macro_problem(d, shape, 5 + d)
+    ctx = Fe2Context(dim=d, precision="fp64")
+    ctx.macro_setup(X, conn, fixed)
+    na, dd = 2 ** d, d * d
+    ngp = na * len(conn)
+    sig = rng.standard_normal((ngp, d, d))
+    M = rng.standard_normal((ngp, dd, dd))
+    Cb = np.einsum("bij,bkj->bik", M, M) + dd * np.eye(dd)[None]
+    dF = torch.zeros((ngp, d, d), dtype=torch.float64, device="cuda")
+    rn = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = torch.ones(1, dtype=torch.int32, device="cuda")
+    ctx.macro_solve(torch.tensor(sig, device="cuda"), torch.tensor(Cb, device="cuda"), dF, rn, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    dq = ctx.macro_get_positions() - X
+    grads, etas, _ = O.macro_gauss(X, conn)
+    K, R = O.macro_system(conn, grads, etas, sig, Cb, d)
+    free = fixed == 0
+    ref = np.zeros(len(free))
+    ref[free] = np.linalg.solve(K[np.ix_(free, free)], -R[free])
+    ref = ref.reshape(-1, d)
+    assert np.abs(dq - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert abs(float(rn.item()) - np.linalg.norm(R[free])) <= 1e-12 * np.linalg.norm(R[free])
+    dFh = dF.cpu().numpy()
+    dFr = np.stack([ref[conn[b // na]].T @ grads[b] for b in range(ngp)])
+    assert np.abs(dFh - dFr).max() <= 1e-10 * np.abs(dFr).max()
+    # a tangent that is not positive definite is reported, not factorised silently
+    ctx.macro_solve(torch.tensor(sig, device="cuda"), torch.tensor(-Cb, device="cuda"), dF, rn, st)
+    torch.cuda.synchronize()
+    from paper_2312_12771_gb300.fe2 import FE2_ERR_NOT_PD
+    assert int(st.item()) == FE2_ERR_NOT_PD
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hex8_monolithic_newton_matches_oracle(torch, precision):
+    """3D monolithic Newton (macro 2x2x2 Hex8, 64 NH RVEs of 3^3 with random
+    inclusions; the faces x = 0 and x = 1 carry the affine Dirichlet data
+    F = I + 0.04 e1 (x) e1 + 0.03 e2 (x) e1 in 2 load steps, the other boundary
+    nodes are free, so the macro field is not affine): converged Pbar, Cbar,
+    positions and iteration counts match the oracle.  (A load that compresses
+    the elements next to a face, started from w~ = 0 without a predictor,
+    makes some heterogeneous 3^3 micro Hessians indefinite at the first
+    iterate, on both sides.)"""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh3
+    X, conn, fixed = macro_mesh3(2, 2, 2)
+    onx = (np.abs(X[:, 0]) < 1e-12) | (np.abs(X[:, 0] - 1.0) < 1e-12)
+    fixed = np.repeat(onx, 3).astype(np.uint8)
+    N = 3
+    b = W.inclusion_batch(64, N, d=3)
+    ctx = ctx3(torch, precision, refine_tol=1e-14, max_refine=2)
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    Ff = np.eye(3)
+    Ff[0, 0] += 0.04
+    Ff[1, 0] = 0.03
+    log = fe.run(Ff, 2, tol_macro=1e-10, tol_micro=1e-10)
+    st = fe.state()
+    rves = [dict(N=N, phase=b.phase[k], mat=b.mat[k]) for k in range(64)]
+    out, iters, q = O.monolithic_fe2((X, conn, np.nonzero(onx)[0]), rves, Ff, n_steps=2,
+                                     tol_macro=1e-10, tol_micro=1e-10)
+    assert log.iters == iters
+    tol = TOL[precision]
+    for k in range(64):
+        assert O.rel_err(st["Pbar"][k], out[k]["Pbar"]) <= tol
+        assert O.rel_err(st["Cbar"][k], out[k]["Cbar"]) <= tol
+    assert np.abs(fe.ctx.macro_get_positions() - q).max() <= 1e-11
+    # the free faces moved: the solution is not the affine map of the Dirichlet data
+    assert np.abs(q - X @ Ff.T).max() > 1e-4
+    ctx.close()
+
+
 def test_monolithic_newton_affine_predictor(torch):
     """With the affine predictor the converged state is the same fixed point
     (the predictor only changes the start value of each load step)."""
