@@ -43,7 +43,7 @@ SM_COUNT, FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 152, 128, 2, 2070.0
 # profiles/band_factor_fp32_fiber32_304rves.md); valid only for the kernel
 # source it was taken on: the sha1 prefix of the factor's part of fe2_factor.cu
 # (from STG_NODES to the solves), else the bench reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "1b5e1c2f01b7", "bytes": (114210048 + 288662272) / 304}
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "48f254217286", "bytes": (113871104 + 288247808) / 304}
 
 
 def factor_source_sha1():

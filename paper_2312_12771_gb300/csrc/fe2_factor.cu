@@ -39,7 +39,7 @@ struct FactLayout {
         kd = kd_;
         nr = nr_;
         S = kd + NB;
-        LDW = kd + 1;
+        LDW = (kd + 2) & ~1;  // even: aligned pairs in a column, conflict-free update write-back
         KR = kd + nr;
         KP = (KR + 31) & ~31;
         const int RB = KP / 32, CB = (kd + 31) / 32;
@@ -53,7 +53,7 @@ struct FactLayout {
         o += (size_t)nr * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offDinv = o;
-        o += NB * sizeof(T);
+        o += 2 * NB * sizeof(T);  // dinv, then one column of the diagonal block (col = dinv + NB)
         o = (o + 15) & ~(size_t)15;
         offBlk = o;
         o += (size_t)nblk * 4;
@@ -86,9 +86,11 @@ struct Vec4<double> {
 
 // Column K of the register-resident Cholesky of the NB x NB diagonal block
 // (lane r holds row r in a[]); template recursion keeps every index static so
-// the block never leaves registers.  Entries a[c] with c > lane (above the
-// diagonal) are updated without a predicate: nothing reads them (a shuffle of
-// column K reads lanes >= K only, and the caller stores c <= lane only).
+// the block never leaves registers.  The scaled column goes through the NB
+// entries after dinv (16-byte aligned shared memory) and comes back as 16-byte
+// broadcasts: one store and at most NB/4 vector loads per column instead of one
+// shuffle per entry.  Lanes below K hold zeros in a[K] (the block's upper
+// triangle), so their entries are zero and are never read (only c >= K+1 are).
 template <typename T, int K>
 __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __restrict__ dinv, int& bad) {
     if constexpr (K < NB) {
@@ -102,10 +104,21 @@ __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __rest
             a[K] *= dk;
         if (lane == 0) dinv[K] = dk;
         bad |= badk;
+        if constexpr (K + 1 < NB) {
+            T* col = dinv + NB;
+            col[lane] = a[K];
+            __syncwarp();
 #pragma unroll
-        for (int c = K + 1; c < NB; ++c) {
-            const T lck = __shfl_sync(0xffffffffu, a[K], c);
-            if (lane >= c) a[c] -= a[K] * lck;
+            for (int g = (K + 1) / 4; g < NB / 4; ++g) {
+                T lc[4];
+                Vec4<T>::load(col + 4 * g, lc);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = 4 * g + u;
+                    if (c >= K + 1 && lane >= c) a[c] -= a[K] * lc[u];
+                }
+            }
+            __syncwarp();  // the column is rewritten by the next step
         }
         chol_block_steps<T, K + 1>(a, lane, dinv, bad);
     }
@@ -171,7 +184,7 @@ __device__ __forceinline__ void prefetch_columns(T* __restrict__ Stg, T* __restr
 // W(t1, t2) -= sum_c Pn[c][t1] Pn[c][t2] for kd > t2, KR > t1 >= t2 (rows t1 >= kd
 // are right-hand-side rows, in Bw).  One warp; lane (rg, cg) owns the 8 contiguous
 // rows 32I + 8rg + u and the 4 columns 32K + cg + 8w.  With the window's column
-// stride LDW = kd + 1 and kd odd, one (u, w) step of the write-back then touches 32
+// stride LDW even (LDW - 1 odd), one (u, w) step of the write-back then touches 32
 // distinct banks.  Lanes whose 32 entries all lie in the window below the diagonal
 // take a write-back without predicates (one base index per column, all old values
 // loaded before any store); the others predicate each entry.
