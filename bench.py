@@ -728,7 +728,10 @@ def main():
     serving = None
     if rank == 0 and not args.no_serve:
         import torch
-        serving = run_serving(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+        try:
+            serving = run_serving(args, torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+        except Exception as exc:  # reported, not fatal: the headline leg is already measured
+            serving = {"error": f"{type(exc).__name__}: {exc}"}
     mx = R["mixed"]
     ms = max_over_ranks(mx["ms"], dist)
     ms64 = max_over_ranks(R["fp64"]["ms"], dist)
