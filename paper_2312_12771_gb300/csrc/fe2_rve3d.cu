@@ -11,8 +11,11 @@
 // k_band_factor_gw: the band Cholesky of S4 for bands too wide for a
 // shared-memory window (3D: kd = 3 (2N^2 + 2N + 2) + 2, i.e. 440 at N = 8):
 // the sliding window lives in the launch slot's global workspace (L2), the
-// panel and the right-hand-side rows stay in shared memory.  Same panel
-// algorithm as the shared-memory kernel, any dimension.
+// panel, the diagonal block and the right-hand-side rows stay in shared memory.
+// Same panel algorithm as the shared-memory kernel, any dimension.  The FP32
+// kernel is bounded to 128 registers so that two CTAs share an SM: the update's
+// global read-modify-write latency is the limit, and a second RVE per SM hides
+// part of it.
 #include "fe2_internal.cuh"
 
 namespace fe2 {
@@ -317,7 +320,7 @@ struct Ld4<double> {
 template <typename T>
 struct GwLayout {
     int kd, S, LDW, KR, KP, nr, nblk;
-    size_t offBw, offDinv, offBlk, total;
+    size_t offBw, offDinv, offBlk, offL11, total;
     __host__ __device__ void init(int kd_, int nr_) {
         kd = kd_;
         nr = nr_;
@@ -337,20 +340,23 @@ struct GwLayout {
         o = (o + 15) & ~(size_t)15;
         offBlk = o;
         o += (size_t)nblk * 4;
+        o = (o + 15) & ~(size_t)15;
+        offL11 = o;
+        o += (size_t)NB * (NB + 1) * sizeof(T);
         total = (o + 15) & ~(size_t)15;
     }
 };
 
+// Step C of the solve of one panel row v against L11, staged in shared memory
+// as L11s[c][r] = L(r, c) with stride NB + 1 (the half bandwidth is at least NB)
 template <typename T, int C>
-__device__ __forceinline__ void gw_row_steps(T (&v)[NB], const T* __restrict__ W, int base, int S, int LDW, int kd,
-                                             const T* __restrict__ dinv) {
+__device__ __forceinline__ void gw_row_steps_s(T (&v)[NB], const T* __restrict__ L11s, const T* __restrict__ dinv) {
     if constexpr (C < NB) {
-        const T* Lc = W + (size_t)(base + C >= S ? base + C - S : base + C) * LDW;
+        const T* Lc = L11s + C * (NB + 1);
         v[C] *= dinv[C];
 #pragma unroll
-        for (int c2 = C + 1; c2 < NB; ++c2)
-            if (c2 - C <= kd) v[c2] -= v[C] * Lc[c2 - C];
-        gw_row_steps<T, C + 1>(v, W, base, S, LDW, kd, dinv);
+        for (int c2 = C + 1; c2 < NB; ++c2) v[c2] -= v[C] * Lc[c2];
+        gw_row_steps_s<T, C + 1>(v, L11s, dinv);
     }
 }
 
@@ -402,7 +408,7 @@ __device__ __forceinline__ void gw_load_columns(T* __restrict__ W, int LDW, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* __restrict__ tab,
+__global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_factor_gw(const RveDev* __restrict__ tab,
                                                                  const int* __restrict__ ids, Workspace ws,
                                                                  int* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -415,6 +421,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
     T* Bw = (T*)(smem + lay.offBw);
     T* dinv = (T*)(smem + lay.offDinv);
     unsigned* blk = (unsigned*)(smem + lay.offBlk);
+    T* L11s = (T*)(smem + lay.offL11);
     __shared__ int s_bad;
     char* slot = ws.base + blockIdx.x * ws.stride;
     T* Lg = (T*)slot;
@@ -451,8 +458,10 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
             if (lane == 0 && badb) s_bad = 1;
             __syncwarp();
 #pragma unroll
-            for (int c = 0; c < NB; ++c)
+            for (int c = 0; c < NB; ++c) {
                 if (c <= lane && lane - c <= kd) W[(size_t)wrapS3(base + c, S) * LDW + (lane - c)] = a[c];
+                L11s[c * (NB + 1) + lane] = (c <= lane && lane - c <= kd) ? a[c] : T(0);
+            }
             Dg[j0 + lane] = dinv[lane];
         } else {
             const int nt = blockDim.x - 32, t0 = tid - 32;
@@ -481,7 +490,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_factor_gw(const RveDev* _
 #pragma unroll
                 for (int c = 0; c < NB; ++c) v[c] = Bw[(t - kd) * S + wrapS3(base + c, S)];
             }
-            gw_row_steps<T, 0>(v, W, base, S, LDW, kd, dinv);
+            gw_row_steps_s<T, 0>(v, L11s, dinv);
 #pragma unroll
             for (int c = 0; c < NB; ++c) Pn[c * KP + t] = v[c];
             if (t < kd) {
