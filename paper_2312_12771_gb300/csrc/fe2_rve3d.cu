@@ -17,12 +17,14 @@
 // global read-modify-write latency is the limit, and a second RVE per SM hides
 // part of it.
 #include "fe2_internal.cuh"
+#include "fe2_ptx.cuh"
 
 namespace fe2 {
 
 namespace {
 
 constexpr double kG = 0.57735026918962576451;  // 1/sqrt(3)
+constexpr int GW_PRE = 24;  // update-block columns whose old values are staged in shared memory (FP32)
 
 // dN_a/dX_J at Gauss point q of a cube element of side h (a, q = bx + 2 by + 4 bz)
 __device__ __forceinline__ double grad3(int q, int a, int J, double h) {
@@ -320,7 +322,7 @@ struct Ld4<double> {
 template <typename T>
 struct GwLayout {
     int kd, S, LDW, KR, KP, nr, nblk;
-    size_t offBw, offDinv, offBlk, offL11, total;
+    size_t offBw, offDinv, offBlk, offL11, offOld, total;
     __host__ __device__ void init(int kd_, int nr_) {
         kd = kd_;
         nr = nr_;
@@ -343,6 +345,9 @@ struct GwLayout {
         o = (o + 15) & ~(size_t)15;
         offL11 = o;
         o += (size_t)NB * (NB + 1) * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offOld = o;  // FP32: per warp, old window values of GW_PRE columns of its update block
+        if (sizeof(T) == 4) o += (size_t)(FACT_THREADS / 32) * GW_PRE * NB * sizeof(T);
         total = (o + 15) & ~(size_t)15;
     }
 };
@@ -429,6 +434,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     T* Dg = (T*)(slot + ws.offD);
     T* W = (T*)(slot + ws.offWin);  // the sliding window, [S][LDW], in global memory
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    T* Old = (T*)(smem + lay.offOld) + (size_t)warp * GW_PRE * NB;  // FP32 only: [column w][lane]
     if (tid == 0) {
         s_bad = 0;
         const int RB = KP / 32, CB = (kd + 31) / 32;
@@ -514,6 +520,22 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                 const unsigned bv = blk[b];
                 const int I = bv & 0xffff, K = bv >> 16;
                 const int t1 = 32 * I + lane, q0 = 32 * K;
+                const bool fast = I > K && 32 * I + 32 <= kd && q0 + 32 <= kd;
+                T oldr[NB - GW_PRE];
+                if constexpr (sizeof(T) == 4) {
+                    // the old values travel while the products accumulate: GW_PRE columns
+                    // to shared memory, the rest to registers
+                    if (fast) {
+#pragma unroll 8
+                        for (int w = 0; w < GW_PRE; ++w)
+                            cp_async4(Old + w * NB + lane,
+                                      W + (size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w)));
+                        cp_async_commit();
+#pragma unroll
+                        for (int w = GW_PRE; w < NB; ++w)
+                            oldr[w - GW_PRE] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+                    }
+                }
                 T acc[32];
 #pragma unroll
                 for (int w = 0; w < 32; ++w) acc[w] = T(0);
@@ -529,14 +551,24 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                         for (int x = 0; x < 4; ++x) acc[4 * w4 + x] += av * bb[x];
                     }
                 }
-                if (I > K && 32 * I + 32 <= kd && q0 + 32 <= kd) {
-                    T old[32];
+                if (fast) {
+                    if constexpr (sizeof(T) == 4) {
+                        cp_async_wait_all();  // this lane's own copies: no exchange between lanes
 #pragma unroll
-                    for (int w = 0; w < 32; ++w)
-                        old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+                        for (int w = 0; w < GW_PRE; ++w)
+                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = Old[w * NB + lane] - acc[w];
 #pragma unroll
-                    for (int w = 0; w < 32; ++w)
-                        W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
+                        for (int w = GW_PRE; w < NB; ++w)
+                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = oldr[w - GW_PRE] - acc[w];
+                    } else {
+                        T old[32];
+#pragma unroll
+                        for (int w = 0; w < 32; ++w)
+                            old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+#pragma unroll
+                        for (int w = 0; w < 32; ++w)
+                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
+                    }
                 } else {
 #pragma unroll
                     for (int w = 0; w < 32; ++w) {
