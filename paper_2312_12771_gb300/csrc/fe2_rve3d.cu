@@ -523,17 +523,21 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                 const bool fast = I > K && 32 * I + 32 <= kd && q0 + 32 <= kd;
                 T oldr[NB - GW_PRE];
                 if constexpr (sizeof(T) == 4) {
-                    // the old values travel while the products accumulate: GW_PRE columns
-                    // to shared memory, the rest to registers
-                    if (fast) {
+                    // the old window values of this lane's entries (row t1 < kd, column
+                    // t2 <= t1, t2 < kd) travel while the products accumulate: GW_PRE
+                    // columns to shared memory, the rest to registers
 #pragma unroll 8
-                        for (int w = 0; w < GW_PRE; ++w)
-                            cp_async4(Old + w * NB + lane,
-                                      W + (size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w)));
-                        cp_async_commit();
+                    for (int w = 0; w < GW_PRE; ++w) {
+                        const int t2 = q0 + w;
+                        if (t2 < kd && t1 >= t2 && t1 < kd)
+                            cp_async4(Old + w * NB + lane, W + (size_t)(wrapS3(base + NB + t2, S) * LDW + t1 - t2));
+                    }
+                    cp_async_commit();
 #pragma unroll
-                        for (int w = GW_PRE; w < NB; ++w)
-                            oldr[w - GW_PRE] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+                    for (int w = GW_PRE; w < NB; ++w) {
+                        const int t2 = q0 + w;
+                        oldr[w - GW_PRE] =
+                            (t2 < kd && t1 >= t2 && t1 < kd) ? W[(size_t)(wrapS3(base + NB + t2, S) * LDW + t1 - t2)] : T(0);
                     }
                 }
                 T acc[32];
@@ -551,24 +555,26 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                         for (int x = 0; x < 4; ++x) acc[4 * w4 + x] += av * bb[x];
                     }
                 }
-                if (fast) {
-                    if constexpr (sizeof(T) == 4) {
-                        cp_async_wait_all();  // this lane's own copies: no exchange between lanes
+                if constexpr (sizeof(T) == 4) {
+                    cp_async_wait_all();  // this lane's own copies: no exchange between lanes
 #pragma unroll
-                        for (int w = 0; w < GW_PRE; ++w)
-                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = Old[w * NB + lane] - acc[w];
-#pragma unroll
-                        for (int w = GW_PRE; w < NB; ++w)
-                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = oldr[w - GW_PRE] - acc[w];
-                    } else {
-                        T old[32];
-#pragma unroll
-                        for (int w = 0; w < 32; ++w)
-                            old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
-#pragma unroll
-                        for (int w = 0; w < 32; ++w)
-                            W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
+                    for (int w = 0; w < NB; ++w) {
+                        const int t2 = q0 + w;
+                        if (t2 >= kd || t1 < t2 || t1 >= KR) continue;
+                        const int sl = wrapS3(base + NB + t2, S);
+                        if (t1 < kd)
+                            W[(size_t)sl * LDW + (t1 - t2)] = (w < GW_PRE ? Old[w * NB + lane] : oldr[w - GW_PRE]) - acc[w];
+                        else
+                            Bw[(t1 - kd) * S + sl] -= acc[w];
                     }
+                } else if (fast) {
+                    T old[32];
+#pragma unroll
+                    for (int w = 0; w < 32; ++w)
+                        old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+#pragma unroll
+                    for (int w = 0; w < 32; ++w)
+                        W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
                 } else {
 #pragma unroll
                     for (int w = 0; w < 32; ++w) {
