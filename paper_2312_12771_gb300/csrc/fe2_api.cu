@@ -218,8 +218,7 @@ static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64
     o += align256((size_t)maxnr * maxnm * 8);
     l.offD = o;
     o += align256((size_t)maxnmp * es);
-    l.offWin = o;
-    if (l.gw) o += align256((size_t)(maxkd + NB) * (maxkd + 1) * es);
+    l.offWin = o;  // unused: the wide-band factor works in L itself
     l.stride = o;
     return l;
 }

@@ -38,7 +38,7 @@ struct RveDev {
 //   Y  at base + s*stride + offY   (T[nr][nm_pad], forward-solve result)
 //   R  at base + s*stride + offR   (double[nr][nm], FP64 residuals)
 //   D  at base + s*stride + offD   (T[nm_pad], reciprocal diagonal of L)
-//   Win at base + s*stride + offWin (T[kd+NB][kd+1], band window of the wide-band factor)
+//   offWin: no longer used (the wide-band factor's window is a sliding view of L)
 struct Workspace {
     char* base;
     size_t stride, offY, offR, offD, offWin;

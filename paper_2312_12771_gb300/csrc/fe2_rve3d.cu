@@ -10,8 +10,10 @@
 //
 // k_band_factor_gw: the band Cholesky of S4 for bands too wide for a
 // shared-memory window (3D: kd = 3 (2N^2 + 2N + 2) + 2, i.e. 440 at N = 8):
-// the sliding window lives in the launch slot's global workspace (L2), the
-// panel, the diagonal block and the right-hand-side rows stay in shared memory.
+// the sliding window is L itself (columns j0 .. j0 + kd + 31 of the factor's
+// output, stride kd + 1, in the launch slot's workspace, mostly in L2), so a
+// finished panel needs no copy; the panel, the diagonal block and the
+// right-hand-side rows (a ring of kd + 32 slots) stay in shared memory.
 // Same panel algorithm as the shared-memory kernel, any dimension.  The FP32
 // kernel is bounded to 128 registers so that two CTAs share an SM: the update's
 // global read-modify-write latency is the limit, and a second RVE per SM hides
@@ -387,19 +389,20 @@ __device__ __forceinline__ void gw_chol_steps(T (&a)[NB], int lane, T* __restric
     }
 }
 
-// Columns [c0, c0 + ncol) of K_mm into the window slots sl(x) (x < ncol), one
-// (column, neighbour) pair per item, items t0, t0 + nt, ...; the slots must be
+// Columns [c0, c0 + ncol) of K_mm into their columns of L (stride LDW), one
+// (column, neighbour) pair per item, items t0, t0 + nt, ...; the columns must be
 // zero.  The neighbours of a node are distinct for N >= 3, so no two items write
-// the same entry.  Columns in [nm, nmp) get a unit diagonal.
+// the same entry.  Columns in [nm, nmp) get a unit diagonal; none exist beyond.
 template <typename T>
-__device__ __forceinline__ void gw_load_columns(T* __restrict__ W, int LDW, int S, int base, int c0, int ncol,
-                                                int nmp, const RveDev& r, int t0, int nt) {
+__device__ __forceinline__ void gw_load_columns(T* __restrict__ Lw, int LDW, int c0, int ncol, int nmp,
+                                                const RveDev& r, int t0, int nt) {
     const int d = r.d, ns = d == 2 ? 9 : 27, nn = r.nn, nm = r.nm;
     for (int p = t0; p < ncol * ns; p += nt) {
         const int x = p / ns, off = p - x * ns, c = c0 + x;
-        T* Wc = W + (size_t)wrapS3(base + x, S) * LDW;
+        if (c >= nmp) continue;
+        T* Wc = Lw + (size_t)c * LDW;
         if (c >= nm) {
-            if (c < nmp && off == 0) Wc[0] = T(1);
+            if (off == 0) Wc[0] = T(1);
             continue;
         }
         const int q = c / d + 1, cc = c - d * (q - 1);
@@ -432,7 +435,6 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     T* Lg = (T*)slot;
     T* Yg = (T*)(slot + ws.offY);
     T* Dg = (T*)(slot + ws.offD);
-    T* W = (T*)(slot + ws.offWin);  // the sliding window, [S][LDW], in global memory
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     T* Old = (T*)(smem + lay.offOld) + (size_t)warp * GW_PRE * NB;  // FP32 only: [column w][lane]
     if (tid == 0) {
@@ -443,13 +445,13 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             for (int I = K; I < RB; ++I) blk[x++] = (unsigned)I | ((unsigned)K << 16);
     }
     for (int k = tid; k < NB * KP; k += blockDim.x) Pn[k] = T(0);
-    for (size_t k = tid; k < (size_t)S * LDW; k += blockDim.x) W[k] = T(0);
+    for (size_t k = tid; k < (size_t)min(S, nmp) * LDW; k += blockDim.x) Lg[k] = T(0);
     for (int k = tid; k < nr * S; k += blockDim.x) {
         const int rr = k / S, c = k - rr * S;
         Bw[k] = (c < nm && c < kd) ? (T)r.rhs[(size_t)rr * nm + c] : T(0);
     }
     __syncthreads();
-    gw_load_columns<T>(W, LDW, S, 0, 0, min(kd, nmp), nmp, r, tid, blockDim.x);
+    gw_load_columns<T>(Lg, LDW, 0, min(kd, nmp), nmp, r, tid, blockDim.x);
     __syncthreads();
     int base = 0;
     for (int j0 = 0; j0 < nmp; j0 += NB) {
@@ -458,25 +460,26 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             T a[NB];
 #pragma unroll
             for (int c = 0; c < NB; ++c)
-                a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS3(base + c, S) * LDW + (lane - c)] : T(0);
+                a[c] = (c <= lane && lane - c <= kd) ? Lg[(size_t)(j0 + c) * LDW + (lane - c)] : T(0);
             int badb = 0;
             gw_chol_steps<T, 0>(a, lane, dinv, badb);
             if (lane == 0 && badb) s_bad = 1;
             __syncwarp();
 #pragma unroll
             for (int c = 0; c < NB; ++c) {
-                if (c <= lane && lane - c <= kd) W[(size_t)wrapS3(base + c, S) * LDW + (lane - c)] = a[c];
+                if (c <= lane && lane - c <= kd) Lg[(size_t)(j0 + c) * LDW + (lane - c)] = a[c];
                 L11s[c * (NB + 1) + lane] = (c <= lane && lane - c <= kd) ? a[c] : T(0);
             }
             Dg[j0 + lane] = dinv[lane];
         } else {
             const int nt = blockDim.x - 32, t0 = tid - 32;
             for (int x = warp - 1; x < NB; x += nwarps - 1) {
-                T* Wc = W + (size_t)wrapS3(base + kd + x, S) * LDW;
+                if (j0 + kd + x >= nmp) break;
+                T* Wc = Lg + (size_t)(j0 + kd + x) * LDW;
                 for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
             }
             asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
-            gw_load_columns<T>(W, LDW, S, wrapS3(base + kd, S), j0 + kd, NB, nmp, r, t0, nt);
+            gw_load_columns<T>(Lg, LDW, j0 + kd, NB, nmp, r, t0, nt);
             for (int p = t0; p < nr * NB; p += nt) {
                 const int rr = p / NB, x = p - rr * NB, cn = j0 + kd + x;
                 Bw[rr * S + wrapS3(base + kd + x, S)] = (cn < nm) ? (T)r.rhs[(size_t)rr * nm + cn] : T(0);
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) {
                     const int off = NB + t - c;
-                    v[c] = (off <= kd) ? W[(size_t)wrapS3(base + c, S) * LDW + off] : T(0);
+                    v[c] = (off <= kd) ? Lg[(size_t)(j0 + c) * LDW + off] : T(0);
                 }
             } else {
 #pragma unroll
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) {
                     const int off = NB + t - c;
-                    if (off <= kd) W[(size_t)wrapS3(base + c, S) * LDW + off] = v[c];
+                    if (off <= kd) Lg[(size_t)(j0 + c) * LDW + off] = v[c];
                 }
             } else {
 #pragma unroll
@@ -520,7 +523,8 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                 const unsigned bv = blk[b];
                 const int I = bv & 0xffff, K = bv >> 16;
                 const int t1 = 32 * I + lane, q0 = 32 * K;
-                const bool fast = I > K && 32 * I + 32 <= kd && q0 + 32 <= kd;
+                const bool fast = I > K && 32 * I + 32 <= kd && q0 + 32 <= kd && j0 + NB + q0 + 32 <= nmp;
+                T* Lq = Lg + (size_t)(j0 + NB + q0) * LDW;  // column t2 = q0 + w at Lq + w LDW
                 T oldr[NB - GW_PRE];
                 if constexpr (sizeof(T) == 4) {
                     // the old window values of this lane's entries (row t1 < kd, column
@@ -529,15 +533,15 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll 8
                     for (int w = 0; w < GW_PRE; ++w) {
                         const int t2 = q0 + w;
-                        if (t2 < kd && t1 >= t2 && t1 < kd)
-                            cp_async4(Old + w * NB + lane, W + (size_t)(wrapS3(base + NB + t2, S) * LDW + t1 - t2));
+                        if (t2 < kd && t1 >= t2 && t1 < kd && j0 + NB + t2 < nmp)
+                            cp_async4(Old + w * NB + lane, Lq + (size_t)w * LDW + (t1 - t2));
                     }
                     cp_async_commit();
 #pragma unroll
                     for (int w = GW_PRE; w < NB; ++w) {
                         const int t2 = q0 + w;
-                        oldr[w - GW_PRE] =
-                            (t2 < kd && t1 >= t2 && t1 < kd) ? W[(size_t)(wrapS3(base + NB + t2, S) * LDW + t1 - t2)] : T(0);
+                        oldr[w - GW_PRE] = (t2 < kd && t1 >= t2 && t1 < kd && j0 + NB + t2 < nmp)
+                                               ? Lq[(size_t)w * LDW + (t1 - t2)] : T(0);
                     }
                 }
                 T acc[32];
@@ -561,38 +565,31 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                     for (int w = 0; w < NB; ++w) {
                         const int t2 = q0 + w;
                         if (t2 >= kd || t1 < t2 || t1 >= KR) continue;
-                        const int sl = wrapS3(base + NB + t2, S);
-                        if (t1 < kd)
-                            W[(size_t)sl * LDW + (t1 - t2)] = (w < GW_PRE ? Old[w * NB + lane] : oldr[w - GW_PRE]) - acc[w];
-                        else
-                            Bw[(t1 - kd) * S + sl] -= acc[w];
+                        if (t1 < kd) {
+                            if (j0 + NB + t2 < nmp)
+                                Lq[(size_t)w * LDW + (t1 - t2)] = (w < GW_PRE ? Old[w * NB + lane] : oldr[w - GW_PRE]) - acc[w];
+                        } else {
+                            Bw[(t1 - kd) * S + wrapS3(base + NB + t2, S)] -= acc[w];
+                        }
                     }
                 } else if (fast) {
                     T old[32];
 #pragma unroll
-                    for (int w = 0; w < 32; ++w)
-                        old[w] = W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))];
+                    for (int w = 0; w < 32; ++w) old[w] = Lq[(size_t)w * LDW + (t1 - (q0 + w))];
 #pragma unroll
-                    for (int w = 0; w < 32; ++w)
-                        W[(size_t)(wrapS3(base + NB + q0 + w, S) * LDW + t1 - (q0 + w))] = old[w] - acc[w];
+                    for (int w = 0; w < 32; ++w) Lq[(size_t)w * LDW + (t1 - (q0 + w))] = old[w] - acc[w];
                 } else {
 #pragma unroll
                     for (int w = 0; w < 32; ++w) {
                         const int t2 = q0 + w;
                         if (t2 >= kd || t1 < t2 || t1 >= KR) continue;
-                        const int sl = wrapS3(base + NB + t2, S);
-                        if (t1 < kd)
-                            W[(size_t)sl * LDW + (t1 - t2)] -= acc[w];
-                        else
-                            Bw[(t1 - kd) * S + sl] -= acc[w];
+                        if (t1 < kd) {
+                            if (j0 + NB + t2 < nmp) Lq[(size_t)w * LDW + (t1 - t2)] -= acc[w];
+                        } else {
+                            Bw[(t1 - kd) * S + wrapS3(base + NB + t2, S)] -= acc[w];
+                        }
                     }
                 }
-            }
-            const int LDL = kd + 1;
-            for (int c = warp; c < NB; c += nwarps) {
-                const T* Wc = W + (size_t)wrapS3(base + c, S) * LDW;
-                T* dst = Lg + (size_t)(j0 + c) * LDL;
-                for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
             }
             for (int k = tid; k < nr * NB; k += blockDim.x) {
                 const int rr = k / NB, c = k - rr * NB;
