@@ -1,0 +1,39 @@
+"""Host-side logic of the product package, checked on the CPU against the
+oracle's own, independently written, mesh generators and against invariants
+of the bench's bookkeeping."""
+import numpy as np
+import pytest
+
+from oracle import fe2_oracle as O
+from paper_2312_12771_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 2), (5, 4)])
+def test_q4_macro_mesh_matches_the_oracle(shape):
+    from paper_2312_12771_gb300.driver import macro_mesh
+    X, conn, fixed = macro_mesh(*shape)
+    Xo, co, bo = O.macro_mesh(*shape)
+    assert np.array_equal(X, Xo) and np.array_equal(conn, co)
+    assert np.array_equal(np.nonzero(fixed[::2])[0], bo)
+    assert np.array_equal(fixed[::2], fixed[1::2])
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 4), (4, 4, 4)])
+def test_hex8_macro_mesh_matches_the_oracle(shape):
+    from paper_2312_12771_gb300.driver import macro_mesh3
+    X, conn, fixed = macro_mesh3(*shape)
+    Xo, co, bo = O.macro_mesh3(*shape)
+    assert np.array_equal(X, Xo) and np.array_equal(conn, co)
+    assert np.array_equal(np.nonzero(fixed[::3])[0], bo)
+    # positive Jacobian at every macro Gauss point, volume of the box
+    _, etas, _ = O.macro_gauss(X, conn)
+    assert (etas > 0).all() and abs(etas.sum() - 1.0) < 1e-12
+
+
+def test_serving_sizes_and_arrivals_are_seeded_and_well_formed():
+    s1, s2 = W.serving_sizes(3, 500), W.serving_sizes(3, 500)
+    assert np.array_equal(s1, s2) and set(np.unique(s1)) <= {16, 24, 32, 48}
+    a = W.poisson_arrivals(3, 2000, rate=1000.0)
+    assert (np.diff(a) > 0).all()
+    # mean inter-arrival time of a Poisson process of rate 1000 / s
+    assert abs(np.diff(a).mean() - 1e-3) < 1e-4
