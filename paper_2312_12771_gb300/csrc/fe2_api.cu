@@ -1135,7 +1135,7 @@ fe2_status fe2_macro_residual(fe2_ctx* ctx, const double* stress, double* rnorm)
     if (!ctx) return FE2_ERR_ARG;
     if (!ctx->macro_ready || !stress || !rnorm) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
     TIMED("macro_residual", launch_macro_residual(ctx->macro, stress, rnorm, ctx->stream));
-    ctx->launches += 1;
+    ctx->launches += 2;  // assembly of R, its norm
     return FE2_OK;
 }
 
