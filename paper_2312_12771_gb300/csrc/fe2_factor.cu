@@ -512,7 +512,42 @@ struct LStream {
 // Backward substitution x = L^-T y over the band, blocks from the bottom.
 // `k0` is the running block counter of the stream (continues across passes).
 // Result written to X (accumulate = 0) or added to X (accumulate = 1) in FP64.
-template <typename T>
+constexpr int BW_WIDE = 256;  // half bandwidths above this take the lane-split panel dot products
+
+// The panel's dot products of the backward solve: tv[rr][c] = y(j0 + c) -
+// sum_{off = NB - c .. kd} L(j0 + c + off, j0 + c) x(j0 + c + off) for every
+// right-hand side rr < nr (NRT >= nr, compile-time when it equals nr).  Warp w
+// takes columns c = w, w + nwarps, ..; lane l the offsets NB - c + l + 32k; the
+// lanes' partial sums meet in a butterfly (a fixed order: deterministic).
+template <typename T, int NRT>
+__device__ __forceinline__ void panel_dots(const T* __restrict__ Lb, const T* __restrict__ xr,
+                                           const T* __restrict__ ysrc, T (*tv)[NB], int s0, int j0, int kd, int S,
+                                           int LDL, int nr, int nmp, int warp, int lane) {
+    const int nw = blockDim.x >> 5;
+    for (int c = warp; c < NB; c += nw) {
+        const T* Lc = Lb + c * LDL;
+        const T* xc = xr + s0 + c - NB;  // x(j0 + c + off) of right-hand side rr: xc[rr 2S + off]
+        T acc[NRT];
+#pragma unroll
+        for (int rr = 0; rr < NRT; ++rr) acc[rr] = T(0);
+        for (int off = NB - c + lane; off <= kd; off += 32) {
+            const T l = Lc[off];
+#pragma unroll
+            for (int rr = 0; rr < NRT; ++rr)
+                if (rr < nr) acc[rr] += l * xc[rr * 2 * S + off];
+        }
+#pragma unroll
+        for (int rr = 0; rr < NRT; ++rr) {
+            if (rr >= nr) break;
+            T v = acc[rr];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - v;
+        }
+    }
+}
+
+template <typename T, bool WIDE>
 __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout<T>& lay, LStream<T>& ls, int& k0,
                               T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to) {
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
@@ -533,21 +568,32 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
         const T* Lb = ls.buf(k);
         const T* db = ls.dinv(k);
         const int s0 = wrapS(jb + NB, S);
-        // t = y_b - sum_{i >= j0+NB} L(i, c) x(i)
-        for (int t = tid; t < NB * nr; t += blockDim.x) {
-            const int c = t % NB, rr = t / NB;
-            const T* Lc = Lb + c * LDL;
-            const T* xp = xr + rr * 2 * S + s0 + c - NB;   // x(j0 + c + off) = xp[off]
-            T s0a = T(0), s1a = T(0), s2a = T(0), s3a = T(0);
-            int off = NB - c;
-            for (; off + 3 <= kd; off += 4) {
-                s0a += Lc[off] * xp[off];
-                s1a += Lc[off + 1] * xp[off + 1];
-                s2a += Lc[off + 2] * xp[off + 2];
-                s3a += Lc[off + 3] * xp[off + 3];
+        // t = y_b - sum_{i >= j0+NB} L(i, c) x(i).  WIDE (launches whose widest band
+        // exceeds BW_WIDE): warp w takes columns w, w + nw, .., its lanes split the rows,
+        // and every L entry loaded serves all nr right-hand sides.  Otherwise one thread
+        // per (c, rr), whose dot product is short (the lane split would be dominated by
+        // its reductions).  Both compute the same sums.
+        if constexpr (WIDE) {
+            if (nr == 10)
+                panel_dots<T, 10>(Lb, xr, ysrc, tv, s0, j0, kd, S, LDL, nr, nmp, warp, lane);
+            else
+                panel_dots<T, MAX_NR>(Lb, xr, ysrc, tv, s0, j0, kd, S, LDL, nr, nmp, warp, lane);
+        } else {
+            for (int t = tid; t < NB * nr; t += blockDim.x) {
+                const int c = t % NB, rr = t / NB;
+                const T* Lc = Lb + c * LDL;
+                const T* xp = xr + rr * 2 * S + s0 + c - NB;  // x(j0 + c + off) = xp[off]
+                T s0a = T(0), s1a = T(0), s2a = T(0), s3a = T(0);
+                int off = NB - c;
+                for (; off + 3 <= kd; off += 4) {
+                    s0a += Lc[off] * xp[off];
+                    s1a += Lc[off + 1] * xp[off + 1];
+                    s2a += Lc[off + 2] * xp[off + 2];
+                    s3a += Lc[off + 3] * xp[off + 3];
+                }
+                for (; off <= kd; ++off) s0a += Lc[off] * xp[off];
+                tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - ((s0a + s1a) + (s2a + s3a));
             }
-            for (; off <= kd; ++off) s0a += Lc[off] * xp[off];
-            tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - ((s0a + s1a) + (s2a + s3a));
         }
         __syncthreads();
         // NB x NB triangle L11^T x = t: warp rr handles RHS rr, lane c owns x_c
@@ -575,7 +621,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
     return true;
 }
 
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __restrict__ tab,
                                                                 const int* __restrict__ ids, Workspace ws,
                                                                 int accumulate, int* __restrict__ status) {
@@ -591,12 +637,12 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
     T* xr = (T*)(smem + lay.offX);
     const T* Yg = (const T*)(ws.base + blockIdx.x * ws.stride + ws.offY);
     int k0 = 0;
-    if (!backward_pass<T>(r, lay, ls, k0, xr, Yg, accumulate, &s_to) && threadIdx.x == 0)
+    if (!backward_pass<T, WIDE>(r, lay, ls, k0, xr, Yg, accumulate, &s_to) && threadIdx.x == 0)
         status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
 // Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx.
-template <typename T>
+template <typename T, bool WIDE>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDev* __restrict__ tab,
                                                                      const int* __restrict__ ids, Workspace ws,
                                                                      int* __restrict__ status,
@@ -666,7 +712,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
         jb = wrapS(jb + NB, S);
     }
     int k0 = nblk;
-    if (!backward_pass<T>(r, lay, ls, k0, bw, ys, 1, &s_to) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
+    if (!backward_pass<T, WIDE>(r, lay, ls, k0, bw, ys, 1, &s_to) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
 // FP64 residual R = [K_mM | r_m] - K_mm X from the node-row stencil.
@@ -728,9 +774,10 @@ cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace 
                             int maxnr, int maxnm_pad, int* status, cudaStream_t s) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, false);
-    cudaError_t e = set_smem(k_band_backward<T>, lay.total);
+    auto kern = maxkd > BW_WIDE ? k_band_backward<T, true> : k_band_backward<T, false>;
+    cudaError_t e = set_smem(kern, lay.total);
     if (e != cudaSuccess) return e;
-    k_band_backward<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, accumulate, status);
+    kern<<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, accumulate, status);
     return cudaGetLastError();
 }
 
@@ -739,9 +786,10 @@ cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Works
                                  int maxnm_pad, int* status, const int* active, cudaStream_t s) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, true);
-    cudaError_t e = set_smem(k_band_solve_correct<T>, lay.total);
+    auto kern = maxkd > BW_WIDE ? k_band_solve_correct<T, true> : k_band_solve_correct<T, false>;
+    cudaError_t e = set_smem(kern, lay.total);
     if (e != cudaSuccess) return e;
-    k_band_solve_correct<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status, active);
+    kern<<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status, active);
     return cudaGetLastError();
 }
 
