@@ -335,6 +335,34 @@ def test_shift_and_rotation_invariance():
     assert a["Cbar"].shape == (4, 4)
 
 
+def test_shift_and_rotation_invariance_3d():
+    """Hex8 RVE: a whole-element periodic shift of the phase array leaves the
+    equilibrated Pbar and Cbar unchanged; a rotation of the microstructure by
+    90 degrees about z (X' = R X) with F' = R F R^T rotates Pbar and Cbar."""
+    N = 3
+    rng = np.random.default_rng(21)
+    ph = (rng.random(N ** 3) < 0.4).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.04, 0.03, 0.0], [0.01, 0.98, 0.02], [0.0, -0.02, 1.01]])
+    w, _ = O.micro_equilibrate(N, 3, ph, mat, F)
+    a = O.rve_solve(N, 3, ph, mat, F, w)
+    grid = ph.reshape(N, N, N)                   # [ez][ey][ex]
+    shifted = np.roll(np.roll(np.roll(grid, 1, axis=0), 2, axis=1), -1, axis=2).ravel()
+    ws, _ = O.micro_equilibrate(N, 3, shifted, mat, F)
+    b = O.rve_solve(N, 3, shifted, mat, F, ws)
+    assert O.rel_err(b["Cbar"], a["Cbar"]) < 1e-10
+    assert O.rel_err(b["Pbar"], a["Pbar"]) < 1e-12
+    R = np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    rot = np.rot90(grid, -1, axes=(1, 2)).ravel()  # element (ex, ey) -> (N-1-ey, ex): X' = R X
+    Fr = R @ F @ R.T
+    wr, _ = O.micro_equilibrate(N, 3, rot, mat, Fr)
+    c = O.rve_solve(N, 3, rot, mat, Fr, wr)
+    C4 = a["Cbar"].reshape(3, 3, 3, 3)
+    Crot = np.einsum("ia,Jb,kc,Ld,abcd->iJkL", R, R, R, R, C4).reshape(9, 9)
+    assert O.rel_err(c["Cbar"], Crot) < 1e-10
+    assert O.rel_err(c["Pbar"], (R @ a["Pbar"].reshape(3, 3) @ R.T).ravel()) < 1e-12
+
+
 def test_macro_patch_test():
     """Homogeneous RVEs + affine Dirichlet data: the macro solution is affine,
     every Gauss point sees Fbar = F_final and Pbar = P(F_final)."""
