@@ -445,6 +445,46 @@ def test_hex8_config5_rve_sampled(torch):
     print(f"hex8 8^3 worst sampled rel err {w:.3e}")
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hex8_uneven_sizes_in_one_batch(torch, precision):
+    """One launch over Hex8 RVEs of 8^3 (kd = 440, wide-band factor, lane-split
+    backward dot products) and of 3^3 and 4^3 (kd = 80, 128): every RVE matches
+    the oracle, so the narrow bands are also correct on the wide code path."""
+    a = W.sphere_batch(1, 8, gamma=0.03)
+    rng = np.random.default_rng(4)
+    Ns = [8, 3, 4, 3]
+    phases = [a.phase[0]] + [(rng.random(n ** 3) < 0.4).astype(np.uint8) for n in Ns[1:]]
+    b = W.RveBatch(3, np.array(Ns, np.int32), phases, np.repeat(a.mat[:1], 4, 0),
+                   np.repeat(a.Fbar[:1], 4, 0))
+    b.Fbar = W.perturbed_F(b, 6, 2e-3)
+    ctx = ctx3(torch, precision)
+    ids = ctx.register_batch(b)
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    check3(b, sig, Cb, st, range(4), TOL[precision])
+    ctx.close()
+
+
+def test_hex8_macro_patch_test_on_gpu(torch):
+    """Hex8 macro mesh 6^3 (375 free DOFs, 12 panels of the blocked macro factor)
+    with identical homogeneous RVEs and affine Dirichlet data: every Gauss point
+    converges to Fbar = F_final and the nodal positions are affine."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, macro_mesh3
+    X, conn, fixed = macro_mesh3(6, 6, 6)
+    n = 8 * len(conn)
+    m = np.array([[1, 1.0, 10.0, 0], [1, 1.0, 10.0, 0]])
+    b = W.RveBatch(3, np.full(n, 3, np.int32), [np.zeros(27, np.uint8)] * n, np.repeat(m[None], n, 0),
+                   np.repeat(np.eye(3)[None], n, 0))
+    ctx = ctx3(torch, "mixed")
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    Ff = np.array([[1.05, 0.02, 0.0], [0.0, 0.97, 0.01], [0.03, 0.0, 1.02]])
+    fe.run(Ff, 2, tol_macro=1e-11, tol_micro=1e-11)
+    st = fe.state()
+    assert np.abs(st["Fbar"] - Ff[None]).max() < 1e-12
+    assert np.abs(fe.ctx.macro_get_positions() - X @ Ff.T).max() < 1e-12
+    ctx.close()
+
+
 def _macro_problem(d, shape, seed):
     """Structured Q4 / Hex8 macro mesh with its interior nodes moved by up to
     0.2 h, boundary nodes fixed."""
