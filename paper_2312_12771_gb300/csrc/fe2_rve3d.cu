@@ -91,17 +91,69 @@ __device__ void consti3(const double* m, const double F[3][3], double P[3][3], d
 // Phase 1: the thread of each (element, Gauss point) evaluates the law once and
 // caches A (81) and P (9) in shared memory.  Phase 2: one thread per (element, a,
 // component i) integrates row i of node a (24 + 9 + 1 accumulators, in registers).
-constexpr int E3_ELEMS = 16;
-constexpr int E3_THREADS = 24 * E3_ELEMS;
+constexpr int E3_ELEMS = 32;  // elements per CTA of the Hex8 assembly (one per lane)
+constexpr int E3_THREADS = 8 * 32;  // phase 1: warp = Gauss point; phase 2: warp = element row node
+// Row a of the element matrices of one element per lane (warp-uniform a): the
+// rows (a, i), i = 0..2, in turn, each integrated over the 8 Gauss points from
+// the cached law, and only the blocks k_e(a, b), b >= a (major symmetry of A:
+// the gather reads k_e(a, b), b < a, as the transpose of k_e(b, a)).  Loop
+// order (q, k, L, b) as in the full form.
+template <int A>
+__device__ __forceinline__ void elem3_row(const double* __restrict__ cache, const double (*Gt)[8][3], int el, int e,
+                                          int nn, double wq, double* __restrict__ E) {
+    constexpr int RC = elem_row_comps(3);
+    const int c0 = A * RC;
+#pragma unroll 1
+    for (int i = 0; i < 3; ++i) {
+        double kr[8 - A][3], kM[9], f = 0.0;
+#pragma unroll
+        for (int b = 0; b < 8 - A; ++b)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) kr[b][k] = 0.0;
+#pragma unroll
+        for (int kL = 0; kL < 9; ++kL) kM[kL] = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            const double* c = cache + (size_t)q * 90 * E3_ELEMS + el;  // c[k * E3_ELEMS]: entry k of (q, el)
+            const double(*G)[3] = Gt[q];
+            f += wq * (c[(81 + 3 * i) * E3_ELEMS] * G[A][0] + c[(81 + 3 * i + 1) * E3_ELEMS] * G[A][1] +
+                       c[(81 + 3 * i + 2) * E3_ELEMS] * G[A][2]);
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int L = 0; L < 3; ++L) {
+                    const double tv = G[A][0] * c[(27 * i + 3 * k + L) * E3_ELEMS] +
+                                      G[A][1] * c[(27 * i + 9 + 3 * k + L) * E3_ELEMS] +
+                                      G[A][2] * c[(27 * i + 18 + 3 * k + L) * E3_ELEMS];
+                    kM[3 * k + L] += wq * tv;
+#pragma unroll
+                    for (int b = A; b < 8; ++b) kr[b - A][k] += wq * tv * G[b][L];
+                }
+        }
+#pragma unroll
+        for (int b = A; b < 8; ++b)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) E[(size_t)(c0 + 9 * b + 3 * i + k) * nn + e] = kr[b - A][k];
+        E[(size_t)(c0 + 72 + i) * nn + e] = f;
+#pragma unroll
+        for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0 + 75 + 9 * i + kL) * nn + e] = kM[kL];
+    }
+}
+
+// S1-S2 for Hex8 RVEs: a CTA takes E3_ELEMS (32) elements.  Phase 1: warp q,
+// lane = element, evaluates the law at Gauss point q into shared memory
+// (element fastest).  Phase 2: warp a, lane = element, integrates the element
+// matrix rows of node a (elem3_row).  K_MM and Pint of the element: the 90
+// components split over the warps, Gauss points summed in order.
 __global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __restrict__ tab,
                                                                 const int* __restrict__ ids,
                                                                 const double* __restrict__ Fbar) {
-    extern __shared__ __align__(16) double cache3[];  // [E3_ELEMS][8 GP][90]
+    extern __shared__ __align__(16) double cache3[];  // [8 GP][90][E3_ELEMS]
     __shared__ double Gt[8][8][3];                     // [GP][node][J]
     const RveDev r = tab[ids[blockIdx.y]];
     const int N = r.N, nn = r.nn;
     const double h = 1.0 / N, wq = 0.125 * h * h * h;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int k = tid; k < 8 * 8 * 3; k += blockDim.x) {
         const int q = k / 24, b = (k / 3) % 8, J = k % 3;
         Gt[q][b][J] = grad3(q, b, J, h);
@@ -109,68 +161,47 @@ __global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __
     double Fb[9];
     for (int k = 0; k < 9; ++k) Fb[k] = Fbar[9 * blockIdx.y + k];
     __syncthreads();
-    // phase 1: thread (el, q) evaluates the law of element el at Gauss point q
-    if (tid < 8 * E3_ELEMS) {
-        const int el = tid >> 3, q = tid & 7, e = blockIdx.x * E3_ELEMS + el;
-        if (e < nn) {
-            const int ex = e % N, ey = (e / N) % N, ez = e / (N * N);
-            double F[3][3];
-            for (int i = 0; i < 3; ++i)
-                for (int J = 0; J < 3; ++J) F[i][J] = Fb[3 * i + J];
-            for (int b = 0; b < 8; ++b) {
-                const int i = (ex + (b & 1)) % N, j = (ey + ((b >> 1) & 1)) % N, k = (ez + (b >> 2)) % N;
-                const int qn = fold_pos(i, N) + N * fold_pos(j, N) + N * N * fold_pos(k, N);
-                for (int c = 0; c < 3; ++c) {
-                    const double w = (qn == 0 || r.zero_w) ? 0.0 : r.w[3 * (qn - 1) + c];
-                    for (int J = 0; J < 3; ++J) F[c][J] += w * Gt[q][b][J];
-                }
+    const int el = lane, e = blockIdx.x * E3_ELEMS + el;
+    // phase 1: the law of element el at Gauss point q = warp
+    if (e < nn) {
+        const int q = warp;
+        const int ex = e % N, ey = (e / N) % N, ez = e / (N * N);
+        double F[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int J = 0; J < 3; ++J) F[i][J] = Fb[3 * i + J];
+        for (int b = 0; b < 8; ++b) {
+            const int i = (ex + (b & 1)) % N, j = (ey + ((b >> 1) & 1)) % N, k = (ez + (b >> 2)) % N;
+            const int qn = fold_pos(i, N) + N * fold_pos(j, N) + N * N * fold_pos(k, N);
+            for (int c = 0; c < 3; ++c) {
+                const double w = (qn == 0 || r.zero_w) ? 0.0 : r.w[3 * (qn - 1) + c];
+                for (int J = 0; J < 3; ++J) F[c][J] += w * Gt[q][b][J];
             }
-            double P[3][3], A[3][3][3][3];
-            consti3(r.mat + 4 * r.phase[e], F, P, A);
-            double* c = cache3 + (size_t)(el * 8 + q) * 90;
-            for (int k = 0; k < 81; ++k) c[k] = A[k / 27][(k / 9) % 3][(k / 3) % 3][k % 3];
-            for (int k = 0; k < 9; ++k) c[81 + k] = P[k / 3][k % 3];
         }
+        double P[3][3], A[3][3][3][3];
+        consti3(r.mat + 4 * r.phase[e], F, P, A);
+        double* c = cache3 + (size_t)q * 90 * E3_ELEMS + el;
+        for (int k = 0; k < 81; ++k) c[k * E3_ELEMS] = A[k / 27][(k / 9) % 3][(k / 3) % 3][k % 3];
+        for (int k = 0; k < 9; ++k) c[(81 + k) * E3_ELEMS] = P[k / 3][k % 3];
     }
     __syncthreads();
-    // phase 2: thread (el, a, i)
-    const int el = tid / 24, rem = tid - 24 * el, a = rem / 3, i = rem - 3 * a;
-    const int e = blockIdx.x * E3_ELEMS + el;
     if (e >= nn) return;
-    double kr[8][3], kM[9], f = 0.0;
-    for (int b = 0; b < 8; ++b)
-        for (int k = 0; k < 3; ++k) kr[b][k] = 0.0;
-    for (int kL = 0; kL < 9; ++kL) kM[kL] = 0.0;
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-        const double* c = cache3 + (size_t)(el * 8 + q) * 90;
-        const double(*G)[3] = Gt[q];
-        f += wq * (c[81 + 3 * i] * G[a][0] + c[81 + 3 * i + 1] * G[a][1] + c[81 + 3 * i + 2] * G[a][2]);
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int L = 0; L < 3; ++L) {
-                const double tv = G[a][0] * c[27 * i + 3 * k + L] + G[a][1] * c[27 * i + 9 + 3 * k + L] +
-                                  G[a][2] * c[27 * i + 18 + 3 * k + L];
-                kM[3 * k + L] += wq * tv;
-#pragma unroll
-                for (int b = 0; b < 8; ++b) kr[b][k] += wq * tv * G[b][L];
-            }
-    }
-    const int RC = elem_row_comps(3);
     double* E = r.elem;
-    const int c0 = a * RC;
-    for (int b = 0; b < 8; ++b)
-        for (int k = 0; k < 3; ++k) E[(size_t)(c0 + 9 * b + 3 * i + k) * nn + e] = kr[b][k];
-    E[(size_t)(c0 + 72 + i) * nn + e] = f;
-    for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0 + 75 + 9 * i + kL) * nn + e] = kM[kL];
-    if (a == 0) {  // K_MM rows i and Pint row i of the element, Gauss points in order
-        for (int k = 0; k < 30; ++k) {
-            const int ck = k < 27 ? 27 * i + k : 81 + 3 * i + (k - 27);
-            double m = 0.0;
-            for (int q = 0; q < 8; ++q) m += wq * cache3[(size_t)(el * 8 + q) * 90 + ck];
-            E[(size_t)(8 * RC + ck) * nn + e] = m;
-        }
+    switch (warp) {  // warp-uniform
+        case 0: elem3_row<0>(cache3, Gt, el, e, nn, wq, E); break;
+        case 1: elem3_row<1>(cache3, Gt, el, e, nn, wq, E); break;
+        case 2: elem3_row<2>(cache3, Gt, el, e, nn, wq, E); break;
+        case 3: elem3_row<3>(cache3, Gt, el, e, nn, wq, E); break;
+        case 4: elem3_row<4>(cache3, Gt, el, e, nn, wq, E); break;
+        case 5: elem3_row<5>(cache3, Gt, el, e, nn, wq, E); break;
+        case 6: elem3_row<6>(cache3, Gt, el, e, nn, wq, E); break;
+        default: elem3_row<7>(cache3, Gt, el, e, nn, wq, E); break;
+    }
+    // K_MM (81) and Pint (9) of the element: components ck = warp, warp + 8, ..
+    constexpr int RC = elem_row_comps(3);
+    for (int ck = warp; ck < 90; ck += 8) {
+        double m = 0.0;
+        for (int q = 0; q < 8; ++q) m += wq * cache3[((size_t)q * 90 + ck) * E3_ELEMS + el];
+        E[(size_t)(8 * RC + ck) * nn + e] = m;
     }
 }
 
@@ -191,12 +222,16 @@ __global__ void __launch_bounds__(256) k_reduce3(const RveDev* __restrict__ tab,
         for (int a = 0; a < 8; ++a) {
             const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
             const int e = (i - ax + N) % N + N * ((j - ay + N) % N) + N * N * ((k - az + N) % N);
-            int c0 = a * RC;
+            // block k_e(a, b): stored for b >= a, read as the transpose of k_e(b, a) below
             for (int b = 0; b < 8; ++b) {
                 const int off = ((b & 1) - ax + 1) + 3 * (((b >> 1) & 1) - ay + 1) + 9 * ((b >> 2) - az + 1);
                 for (int c = 0; c < 3; ++c)
-                    for (int c2 = 0; c2 < 3; ++c2) st[(size_t)((off * 3 + c) * 3 + c2) * nn + q] += E[(size_t)(c0++) * nn + e];
+                    for (int c2 = 0; c2 < 3; ++c2) {
+                        const int comp = b >= a ? a * RC + 9 * b + 3 * c + c2 : b * RC + 9 * a + 3 * c2 + c;
+                        st[(size_t)((off * 3 + c) * 3 + c2) * nn + q] += E[(size_t)comp * nn + e];
+                    }
             }
+            int c0 = a * RC + 72;
             for (int c = 0; c < 3; ++c) f[c] += E[(size_t)(c0++) * nn + e];
             for (int c = 0; c < 3; ++c)
                 for (int kL = 0; kL < 9; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
