@@ -37,3 +37,26 @@ def test_serving_sizes_and_arrivals_are_seeded_and_well_formed():
     assert (np.diff(a) > 0).all()
     # mean inter-arrival time of a Poisson process of rate 1000 / s
     assert abs(np.diff(a).mean() - 1e-3) < 1e-4
+
+
+def test_reference_arm_prints_the_contract_line():
+    """``bench.py --impl reference`` (the FP64 oracle on the host cores) prints one
+    JSON line with the keys of the bench contract, on a small workload."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "3", "--rves", "64", "--N", "8", "--cpu-sample", "8"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["warmup"] >= 3
+    assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["config"]["N"] == 8 and d["config"]["rves_per_gpu"] == 64
