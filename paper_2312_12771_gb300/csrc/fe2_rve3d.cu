@@ -206,37 +206,55 @@ __global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __
 }
 
 // S3: node-row gather through the periodic map (one CTA per RVE).  Each node row
-// is owned by one thread (deterministic order); K_MM and Pint are summed over
-// elements by one thread per component.
+// is owned by one thread (deterministic order): per neighbour block off, the 9
+// entries are summed over the elements around the node in the order of their
+// local node a (k_e(a, b) with b < a read as the transpose of k_e(b, a)) and
+// stored once.  K_MM and Pint are summed over elements by one thread per component.
 __global__ void __launch_bounds__(256) k_reduce3(const RveDev* __restrict__ tab, const int* __restrict__ ids) {
     const RveDev r = tab[ids[blockIdx.x]];
     const int N = r.N, nn = r.nn, RC = elem_row_comps(3);
-    const double* E = r.elem;
+    const double* __restrict__ E = r.elem;
+    double* __restrict__ st = r.stencil;
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
         const int i = unfold_pos(q % N, N), j = unfold_pos((q / N) % N, N), k = unfold_pos(q / (N * N), N);
-        double* st = r.stencil;
-        for (int comp = 0; comp < 243; ++comp) st[(size_t)comp * nn + q] = 0.0;
-        double f[3] = {0.0, 0.0, 0.0}, kM[3][9];
-        for (int c = 0; c < 3; ++c)
-            for (int kL = 0; kL < 9; ++kL) kM[c][kL] = 0.0;
+        int ea[8];  // the element whose local node a is node q
+#pragma unroll
         for (int a = 0; a < 8; ++a) {
             const int ax = a & 1, ay = (a >> 1) & 1, az = a >> 2;
-            const int e = (i - ax + N) % N + N * ((j - ay + N) % N) + N * N * ((k - az + N) % N);
-            // block k_e(a, b): stored for b >= a, read as the transpose of k_e(b, a) below
-            for (int b = 0; b < 8; ++b) {
-                const int off = ((b & 1) - ax + 1) + 3 * (((b >> 1) & 1) - ay + 1) + 9 * ((b >> 2) - az + 1);
+            ea[a] = (i - ax + N) % N + N * ((j - ay + N) % N) + N * N * ((k - az + N) % N);
+        }
+        for (int off = 0; off < 27; ++off) {
+            const int ox = off % 3 - 1, oy = (off / 3) % 3 - 1, oz = off / 9 - 1;  // b - a per direction
+            double acc[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const int bx = (a & 1) + ox, by = ((a >> 1) & 1) + oy, bz = (a >> 2) + oz;
+                if (bx < 0 || bx > 1 || by < 0 || by > 1 || bz < 0 || bz > 1) continue;
+                const int b = bx + 2 * by + 4 * bz, e = ea[a];
+#pragma unroll
                 for (int c = 0; c < 3; ++c)
+#pragma unroll
                     for (int c2 = 0; c2 < 3; ++c2) {
                         const int comp = b >= a ? a * RC + 9 * b + 3 * c + c2 : b * RC + 9 * a + 3 * c2 + c;
-                        st[(size_t)((off * 3 + c) * 3 + c2) * nn + q] += E[(size_t)comp * nn + e];
+                        acc[3 * c + c2] += E[(size_t)comp * nn + e];
                     }
             }
-            int c0 = a * RC + 72;
-            for (int c = 0; c < 3; ++c) f[c] += E[(size_t)(c0++) * nn + e];
-            for (int c = 0; c < 3; ++c)
-                for (int kL = 0; kL < 9; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) st[(size_t)(off * 9 + t) * nn + q] = acc[t];
         }
         if (q != 0) {
+            double f[3] = {0.0, 0.0, 0.0}, kM[3][9];
+            for (int c = 0; c < 3; ++c)
+                for (int kL = 0; kL < 9; ++kL) kM[c][kL] = 0.0;
+            for (int a = 0; a < 8; ++a) {
+                const int e = ea[a];
+                int c0 = a * RC + 72;
+                for (int c = 0; c < 3; ++c) f[c] += E[(size_t)(c0++) * nn + e];
+                for (int c = 0; c < 3; ++c)
+                    for (int kL = 0; kL < 9; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
+            }
             for (int c = 0; c < 3; ++c) {
                 const int dof = 3 * (q - 1) + c;
                 for (int kL = 0; kL < 9; ++kL) r.rhs[(size_t)kL * r.nm + dof] = kM[c][kL];
