@@ -291,6 +291,49 @@ def test_hill_mandel_at_equilibrium():
     assert abs(lhs - rhs) < 1e-11
 
 
+def test_cbar_is_derivative_of_equilibrium_stress_3d():
+    """Hex8: Cbar = d Pbar / d Fbar along the equilibrium path (central FD, 9 x 9)."""
+    N, d = 3, 3
+    rng = np.random.default_rng(12)
+    ph = (rng.random(N ** 3) < 0.4).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.06, 0.04, 0.0], [-0.02, 0.97, 0.03], [0.01, 0.0, 1.02]])
+    w, _ = O.micro_equilibrate(N, d, ph, mat, F)
+    s = O.rve_solve(N, d, ph, mat, F, w)
+    assert O.rel_err(s["sigma_eff"], s["Pbar"]) < 1e-12
+    h = 1e-5
+    Cfd = np.zeros((9, 9))
+    for kL in range(9):
+        dF = np.zeros(9)
+        dF[kL] = h
+        wp, _ = O.micro_equilibrate(N, d, ph, mat, F + dF.reshape(3, 3), w)
+        wm, _ = O.micro_equilibrate(N, d, ph, mat, F - dF.reshape(3, 3), w)
+        Pp = O.rve_solve(N, d, ph, mat, F + dF.reshape(3, 3), wp)["Pbar"].ravel()
+        Pm = O.rve_solve(N, d, ph, mat, F - dF.reshape(3, 3), wm)["Pbar"].ravel()
+        Cfd[:, kL] = (Pp - Pm) / (2 * h)
+    assert O.rel_err(s["Cbar"], Cfd) < 1e-8
+    assert np.abs(s["Cbar"] - s["Cbar"].T).max() < 1e-10 * np.abs(s["Cbar"]).max()
+
+
+def test_hill_mandel_at_equilibrium_3d():
+    """Hex8: <P~ : dF~> = Pbar : dFbar for any periodic virtual fluctuation."""
+    N, d = 3, 3
+    rng = np.random.default_rng(14)
+    ph = (rng.random(N ** 3) < 0.5).astype(np.uint8)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    F = np.array([[1.1, 0.05, 0.0], [0.0, 0.96, 0.02], [0.03, 0.0, 1.01]])
+    w, _ = O.micro_equilibrate(N, d, ph, mat, F)
+    ints = O.rve_integrals(N, d, ph, mat, F, w)
+    dFbar = rng.standard_normal((3, 3))
+    dw = rng.standard_normal(3 * (N ** 3 - 1))
+    conn, nnode = O.full_grid(N, d)
+    dwe = (ints["T"] @ dw).reshape(nnode, d)[conn]
+    dFt = dFbar[None, None] + np.einsum("eai,qaJ->eqiJ", dwe, ints["G"])
+    lhs = np.einsum("eqiJ,eqiJ->", ints["P"], dFt) * ints["wq"] / ints["vol"]
+    rhs = np.sum(ints["Pint"].reshape(3, 3) / ints["vol"] * dFbar)
+    assert abs(lhs - rhs) < 1e-11
+
+
 def test_voigt_reuss_bounds_and_symmetry():
     N = 8
     ph = W.fiber_phase(N)
