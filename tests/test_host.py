@@ -60,3 +60,20 @@ def test_reference_arm_prints_the_contract_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["warmup"] >= 3
     assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
     assert d["config"]["N"] == 8 and d["config"]["rves_per_gpu"] == 64
+
+
+def test_clock_sampler_summary_reports_median_and_throttle_reasons():
+    """The bench's clock record: median SM clock under load, max clock, and the
+    throttle reasons seen as Active in any sample (parsed from nvidia-smi CSV)."""
+    import bench
+    cs = bench.ClockSampler()
+    rows = ["0, 2070, 2070, 150.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 180.4, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 170.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line"]
+    cs.f.write("\n".join(rows) + "\n")
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"] and abs(s["power_w_max"] - 180.4) < 1e-9
+    empty = bench.ClockSampler()
+    assert empty.summary()["reasons"] == ["nvidia-smi unavailable"]
