@@ -33,6 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2312_12771_gb300 import workcount as WC  # noqa: E402
 from paper_2312_12771_gb300 import workloads as W  # noqa: E402
 
 METRIC = "RVE solves/s (sigma_eff + Cbar per macro Gauss point)"
@@ -90,20 +91,16 @@ def workload(n=N_RVE, N=N_MESH, seed=W.GLOBAL_SEED):
 
 
 # ------------------------------------------------------------------ algorithmic work
-def band_counts(nm, kd):
-    c = np.minimum(kd, nm - 1 - np.arange(nm)).astype(np.float64)
-    return c
-
-
 def work_per_rve(N, d=2):
     """Algorithmic flops / bytes per RVE for every kernel of the step (2D Q4)."""
     nn = N * N
     nm = d * (nn - 1)
     kd = 4 * N + 5
     nr = d * d + 1
-    c = band_counts(nm, kd)
-    chol = float(np.sum(c * c + 2 * c + 1))          # sqrt, scale, rank-1 update
-    tri = float(np.sum(2 * c + 1))                   # one triangular solve, one RHS
+    # column counts of L from the symbolic factorisation (entries of the band that stay
+    # zero are not work): sqrt, scale and rank-1 update per column; one triangular solve
+    fl, tri = WC.factor_flops(N, d, nr)
+    chol = fl - nr * tri
     nnz = 18 * nm                                    # 9 node blocks of 2x2 per reduced row
     stencil_bytes = 9 * d * d * nn * 8 + nr * nm * 8  # FP64 node-row stencil + [K_mM | r_m]
     L_bytes = 4 * nm * (kd + 1)

@@ -77,3 +77,38 @@ def test_clock_sampler_summary_reports_median_and_throttle_reasons():
     assert s["reasons"] == ["sw_power_cap"] and abs(s["power_w_max"] - 180.4) < 1e-9
     empty = bench.ClockSampler()
     assert empty.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+@pytest.mark.parametrize("d,N", [(2, 6), (2, 8), (2, 9), (3, 3), (3, 4)])
+def test_symbolic_column_counts_match_the_oracle_factor(d, N):
+    """The work count of the band factor: the symbolic factorisation of K_mm in the
+    folded periodic ordering against the nonzero pattern of the Cholesky factor of
+    the oracle's K_mm (natural order, permuted).  Every numeric nonzero lies in the
+    symbolic pattern, the half bandwidth is 4N + 5 in 2D, and the counts agree up
+    to the rare entries that cancel exactly."""
+    from paper_2312_12771_gb300 import workcount as WC
+    rng = np.random.default_rng(N)
+    ph = (rng.random(N ** d) < 0.4).astype(np.uint8)
+    mat = W.linear_mat(1.0, 0.3, 10.0, 0.3)
+    K = O.rve_solve(N, d, ph, mat, np.eye(d))["K_mm"]
+    nm = K.shape[0]
+    perm = np.zeros(nm, int)
+    for p in range(1, N ** d):
+        g = [(p // N ** k) % N for k in range(d)]
+        q = sum(WC.fold_pos(g[k], N) * N ** k for k in range(d))
+        for c in range(d):
+            perm[d * (p - 1) + c] = d * (q - 1) + c
+    Kf = np.zeros_like(K)
+    Kf[np.ix_(perm, perm)] = K
+    L = np.linalg.cholesky(Kf)
+    sym = WC.column_structures(N, d)
+    num_total = 0
+    for j in range(nm):
+        rows = np.nonzero(L[j + 1:, j])[0] + j + 1
+        assert set(rows.tolist()) <= set(sym[j].tolist()), j
+        num_total += len(rows)
+    sym_total = int(WC.column_counts(N, d).sum())
+    assert num_total <= sym_total <= 1.01 * num_total
+    kd = max(int(c[-1]) - j for j, c in enumerate(sym) if len(c))
+    if d == 2:
+        assert kd == 4 * N + 5
