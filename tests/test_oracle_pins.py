@@ -496,6 +496,42 @@ def test_macro_system_virtual_work_and_tangent(d):
     assert np.abs(K - K.T).max() < 1e-12 * np.abs(K).max()
 
 
+def test_condensed_macro_tangent_is_the_equilibrium_derivative_3d():
+    """One Hex8 macro element with eight heterogeneous 3^3 RVEs, all of them at
+    micro equilibrium: K = sum_b eta_b B_b^T Cbar_b B_b (Section 4.2, Eq.
+    (solution2)) equals the central difference of the macro residual
+    R(q) = sum_b eta_b B_b^T Pbar_b(Fbar_b(q)) with every RVE re-equilibrated."""
+    X, conn, _ = O.macro_mesh3(1, 1, 1)
+    rng = np.random.default_rng(31)
+    X = X + rng.uniform(-0.05, 0.05, X.shape)
+    grads, etas, _ = O.macro_gauss(X, conn)
+    mat = W.neohooke_mat(1.0, 10.0, 20.0, 200.0)
+    phases = [(rng.random(27) < 0.4).astype(np.uint8) for _ in range(8)]
+    q0 = X @ np.array([[1.03, 0.02, 0.0], [0.0, 0.98, 0.01], [0.01, 0.0, 1.0]]).T
+    q0 = q0 + rng.uniform(-0.01, 0.01, q0.shape)
+
+    def state(q, ws=None):
+        out = []
+        for b in range(8):
+            Fb = q[conn[0]].T @ grads[b]
+            w, _ = O.micro_equilibrate(3, 3, phases[b], mat, Fb, None if ws is None else ws[b])
+            out.append((w, O.rve_solve(3, 3, phases[b], mat, Fb, w)))
+        return out
+
+    st0 = state(q0)
+    K, R0 = O.macro_system(conn, grads, etas, [s["Pbar"] for _, s in st0], [s["Cbar"] for _, s in st0], 3)
+    ws0 = [w for w, _ in st0]
+    h = 1e-6
+    for col in (0, 5, 13, 22):
+        dq = np.zeros(24)
+        dq[col] = h
+        sp, sm = state(q0 + dq.reshape(8, 3), ws0), state(q0 - dq.reshape(8, 3), ws0)
+        _, Rp = O.macro_system(conn, grads, etas, [s["Pbar"] for _, s in sp], [s["Cbar"] for _, s in sp], 3)
+        _, Rm = O.macro_system(conn, grads, etas, [s["Pbar"] for _, s in sm], [s["Cbar"] for _, s in sm], 3)
+        fd = (Rp - Rm) / (2 * h)
+        assert np.abs(K[:, col] - fd).max() <= 1e-6 * np.abs(K[:, col]).max()
+
+
 def test_macro_hex8_patch_test():
     """Hex8 macro mesh, identical heterogeneous RVEs (a centred inclusion on a
     3^3 grid) and affine Dirichlet data on the boundary: the homogenised
