@@ -207,6 +207,16 @@ fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host);
  * fe2_macro_solve then use R = (internal) - fext on the free DOFs.  Returns
  * FE2_ERR_NAN for a non-finite entry.  Synchronises. */
 fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host);
+/* The same surface load from a constant traction T [host] double[2] on the
+ * polyline of macro boundary nodes nodes [host] int[n] (n >= 2, consecutive
+ * nodes joined by straight bilinear element edges; 2D only), multiplied by
+ * `scale` (the load-step factor k / n_l of Section 5.2): every edge of length l
+ * gives T l scale / 2 to each of its two nodes (the consistent nodal forces of
+ * the Neumann term of Eq. (weakMech) for linear edge shape functions).  It
+ * replaces the current load.  FE2_ERR_ARG for a node out of range, a 3D
+ * context or no macro problem; FE2_ERR_NAN for a non-finite T or scale.
+ * Synchronises. */
+fe2_status fe2_macro_set_edge_load(fe2_ctx* ctx, int n, const int* nodes, const double* T, double scale);
 /* Fbar_b = sum_A q_A (x) grad N^A(X_b) into Fbar [device] double[2^d nelem][d][d];
  * eta [device] double[2^d nelem] receives the quadrature weights (may be NULL). */
 fe2_status fe2_macro_gradients(fe2_ctx* ctx, double* Fbar, double* eta);
@@ -254,18 +264,24 @@ fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w);
  * Fbar double[n][2][2].  Outputs [device]: sigma_eff double[n][4],
  * Cbar double[n][4][4], rve_status int[n], err_est double[n] (may be NULL).
  * Work is queued on cuda_stream (NULL = default stream); no context is used.
+ * The inputs are checked on the device: an RVE with a phase index >= nphase,
+ * an unknown material model or a non-finite material parameter gets
+ * rve_status FE2_ERR_ARG (a non-finite Fbar FE2_ERR_NAN) and meaningless
+ * outputs, and no kernel reads beyond its rows of phase and mat.
  *
  * All intermediate data live in one library-owned __device__ array of
  * FE2_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
- * until the process exits.  Limits: N >= 3, and the n RVEs must fit the array
- * (about 1.7 MB per RVE at N = 32, i.e. 37 RVEs; 0.45 MB at N = 16); larger
- * requests return FE2_ERR_BUDGET without running anything.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current, waits for its stream once and reads the set-up
+ * until the process exits.  Limits: N >= 3, 1 <= nphase <= 8, and the n RVEs
+ * must fit the array (1.69 MB per RVE at N = 32, i.e. 39 RVEs; 0.29 MB at
+ * N = 16, 230 RVEs); larger requests return FE2_ERR_BUDGET without running anything.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; until one call on the
+ * device has passed it, a call also waits for its stream and reads the set-up
  * descriptors back to check them (FE2_ERR_CUDA if they are not as written), so
  * make the first call on each device before any stream capture.  Every call
- * reuses the same array and leaves the previous call's data in it: calls that overlap on the GPU (other streams, other host
- * threads) race and corrupt each other -- serialise them.
+ * reuses the same array and leaves the previous call's data in it: calls that
+ * overlap on the GPU (other streams, other host threads) race and corrupt each
+ * other -- serialise them.
  */
 #define FE2_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint8_t* phase, const double* mat,

@@ -84,6 +84,7 @@ struct fe2_ctx {
     // macro problem
     bool macro_ready = false;
     MacroDev macro{};
+    std::vector<double> macro_X;    // reference nodal positions [nnode][d] (host copy)
     std::vector<void*> macro_bufs;  // device buffers owned by the macro problem
     int* d_macro_status = nullptr;
 };
@@ -976,6 +977,7 @@ fe2_status fe2_macro_setup(fe2_ctx* ctx, int nnode, const double* X, int nelem, 
     std::vector<int> cn(conn, conn + (size_t)nen * nelem);
     for (int v : cn)
         if (v < 0 || v >= nnode) return fail(ctx, FE2_ERR_ARG, "connectivity references node %d", v);
+    ctx->macro_X.assign(X, X + (size_t)d * nnode);
     // free DOFs in natural order; band width from the element couplings
     std::vector<int> d2f((size_t)d * nnode, -1);
     int nfree = 0;
@@ -1114,6 +1116,31 @@ fe2_status fe2_macro_set_load(fe2_ctx* ctx, const double* fext_host) {
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(const_cast<double*>(ctx->macro.fext), f.data(), sizeof(double) * nd, cudaMemcpyHostToDevice));
     return FE2_OK;
+}
+
+fe2_status fe2_macro_set_edge_load(fe2_ctx* ctx, int n, const int* nodes, const double* T, double scale) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready) return fail(ctx, FE2_ERR_ARG, "no macro problem");
+    if (ctx->macro.d != 2) return fail(ctx, FE2_ERR_ARG, "edge loads are 2D (Q4 macro meshes)");
+    if (n < 2 || !nodes || !T) return fail(ctx, FE2_ERR_ARG, "an edge load needs >= 2 nodes and a traction");
+    const int nnode = ctx->macro.nnode;
+    for (int k = 0; k < n; ++k)
+        if (nodes[k] < 0 || nodes[k] >= nnode) return fail(ctx, FE2_ERR_ARG, "edge node %d out of range", nodes[k]);
+    if (!std::isfinite(T[0]) || !std::isfinite(T[1]) || !std::isfinite(scale))
+        return fail(ctx, FE2_ERR_NAN, "traction or scale not finite");
+    // Neumann term of Eq. (weakMech) for a constant traction on straight
+    // bilinear edges: each segment of length l gives T l / 2 to both end nodes
+    std::vector<double> f((size_t)2 * nnode, 0.0);
+    const std::vector<double>& X = ctx->macro_X;
+    for (int k = 0; k + 1 < n; ++k) {
+        const int a = nodes[k], b = nodes[k + 1];
+        const double l = std::hypot(X[2 * b] - X[2 * a], X[2 * b + 1] - X[2 * a + 1]);
+        for (int c = 0; c < 2; ++c) {
+            f[2 * a + c] += 0.5 * l * T[c] * scale;
+            f[2 * b + c] += 0.5 * l * T[c] * scale;
+        }
+    }
+    return fe2_macro_set_load(ctx, f.data());
 }
 
 fe2_status fe2_macro_get_positions(fe2_ctx* ctx, double* q_host) {

@@ -13,10 +13,15 @@
 //
 // It runs the same kernels as fe2_rve_solve on the mixed path (general
 // assembly kernel for both material models, FP32 band factor, FP64 residual,
-// residual-corrected Schur complement, no refinement sweeps).  The first call
-// on a device reads back what the set-up kernel wrote and checks every address
-// and index the solve kernels take from it before launching them; failures
-// leave a reason for fe2_noalloc_last_error.
+// residual-corrected Schur complement, no refinement sweeps).  Until one call
+// on a device has passed it, every call reads back what the set-up kernel
+// wrote and checks every address and index the solve kernels take from it
+// before launching them; failures leave a reason for fe2_noalloc_last_error.
+// The inputs live on the device, so a small kernel validates them there: an
+// RVE with a phase index >= nphase or an unknown material model gets
+// rve_status FE2_ERR_ARG, and its descriptor is pointed at a single-phase
+// linear material in the scratch array so that no kernel reads outside the
+// caller's arrays; its outputs are then meaningless.
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -32,6 +37,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[FE2_NOALLOC_SCR
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {nullptr};   // device address of the array, per device
+bool g_verified[kMaxDevices] = {false};          // a call on the device passed the set-up read-back
 char g_err[256] = "";                            // reason of the last failed call
 
 fe2_status fail_msg(fe2_status st, const char* fmt, ...) {
@@ -46,7 +52,8 @@ size_t a256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NoallocLayout {
     int N, nn, nm, kd, nmp, nr;
-    size_t off_desc, off_ids, off_tol, off_nbr, off_rve, rve_stride, off_ws, ws_stride, offY, offR, offD, total;
+    size_t off_desc, off_ids, off_tol, off_nbr, off_safe, off_rve, rve_stride, off_ws, ws_stride, offY, offR, offD,
+        total;
     size_t o_st, o_rhs, o_X, o_mm;
 };
 
@@ -69,6 +76,8 @@ NoallocLayout layout_for(int N, int n) {
     o += 256;
     L.off_nbr = o;
     o += a256(sizeof(int) * 9 * (size_t)L.nn);
+    L.off_safe = o;  // stand-in inputs of a rejected RVE: one linear material, phase 0 everywhere
+    o += a256(4 * sizeof(double) + (size_t)L.nn);
     // per-RVE reduced operators and solutions
     L.o_st = 0;
     size_t r = a256(36 * (size_t)L.nn * 8);
@@ -135,17 +144,46 @@ __global__ void k_noalloc_setup(unsigned char* base, NoallocLayout L, int n, int
         ids[t] = t;
     }
     if (t == 0) {
+        double* sm = (double*)(base + L.off_safe);
+        sm[0] = FE2_MODEL_LINEAR, sm[1] = 1.0, sm[2] = 0.3, sm[3] = 0.0;
         *(double*)(base + L.off_tol) = tol;
         // the kernel's view of the layout and of the descriptor size, for the host's first-call check
         int* v = (int*)(base + L.off_tol + 16);
         v[0] = L.N, v[1] = L.nn, v[2] = L.nm, v[3] = L.kd, v[4] = L.nmp, v[5] = L.nr;
         v[6] = (int)sizeof(RveDev), v[7] = (int)sizeof(NoallocLayout);
     }
+    uint8_t* sp = base + L.off_safe + 4 * sizeof(double);
+    for (int k = t; k < L.nn; k += gridDim.x * blockDim.x) sp[k] = 0;
     for (int k = t; k < L.nn * 9; k += gridDim.x * blockDim.x) {
         const int q = k / 9, off = k - 9 * q;
         const int i = unfold_pos(q % N, N), j = unfold_pos(q / N, N);
         const int dx = off % 3 - 1, dy = off / 3 - 1;
         nbr[k] = fold_pos((i + dx + N) % N, N) + N * fold_pos((j + dy + N) % N, N);
+    }
+}
+
+// One CTA per RVE: every phase byte below nphase, every material model known
+// (its parameters finite).  A rejected RVE keeps FE2_ERR_ARG in rve_status
+// (the later kernels only overwrite FE2_OK) and reads the stand-in inputs.
+__global__ void k_noalloc_validate(unsigned char* base, NoallocLayout L, int nphase, const uint8_t* __restrict__ phase,
+                                   const double* __restrict__ mat, int* __restrict__ status) {
+    const int t = blockIdx.x;
+    int bad = 0;
+    const uint8_t* ph = phase + (size_t)t * L.nn;
+    for (int k = threadIdx.x; k < L.nn; k += blockDim.x) bad |= ph[k] >= nphase;
+    if (threadIdx.x < nphase) {
+        const double* m = mat + ((size_t)t * nphase + threadIdx.x) * 4;
+        const double model = m[0];
+        bad |= !(model == FE2_MODEL_LINEAR || model == FE2_MODEL_NEOHOOKE || model == FE2_MODEL_MOONEY_RIVLIN);
+        bad |= !(isfinite(m[1]) && isfinite(m[2]) && isfinite(m[3]));
+    }
+    bad = __syncthreads_or(bad);
+    if (bad && threadIdx.x == 0) {
+        RveDev* r = (RveDev*)(base + L.off_desc) + t;
+        r->mat = (const double*)(base + L.off_safe);
+        r->phase = base + L.off_safe + 4 * sizeof(double);
+        r->nphase = 1;
+        status[t] = FE2_ERR_ARG;
     }
 }
 
@@ -222,13 +260,11 @@ extern "C" fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint
         return fail_msg(FE2_ERR_ARG, "N=%d: factor window exceeds shared memory", N);
     // one-time set-up per device (with that device current): the device address
     // of the scratch array; host code must not use the symbol itself
-    bool first = false;
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return fail_msg(FE2_ERR_CUDA, "scratch address: %s", cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
-        first = true;
     }
     unsigned char* base = (unsigned char*)g_scratch_addr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
@@ -237,11 +273,13 @@ extern "C" fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint
     k_noalloc_setup<<<setup_blocks, setup_threads, 0, s>>>(base, L, n, nphase, phase, mat, 1e-10);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return fail_msg(FE2_ERR_CUDA, "set-up launch: %s", cudaGetErrorString(le));
-    // first call on this device: read the descriptors, ids and neighbour table back
-    // and confirm every address and index the solve kernels derive from them
-    if (first) {
+    // until a call on this device has passed it: read the descriptors, ids and
+    // neighbour table back and confirm every address and index the solve kernels
+    // derive from them (a failed check is repeated by the next call)
+    if (!g_verified[dev]) {
         const fe2_status st = check_setup(base, L, n, nphase, phase, mat, s);
         if (st != FE2_OK) return st;
+        g_verified[dev] = true;
     }
     const RveDev* tab = (const RveDev*)(base + L.off_desc);
     const int* ids = (const int*)(base + L.off_ids);
@@ -251,6 +289,8 @@ extern "C" fe2_status fe2_rve_solve_noalloc(int N, int n, int nphase, const uint
 #define NOALLOC_STEP(what, call) \
     if ((e = (call)) != cudaSuccess) return fail_msg(FE2_ERR_CUDA, "%s launch: %s", what, cudaGetErrorString(e))
     NOALLOC_STEP("check", launch_check_fbar(Fbar, n, 2, rve_status, s));
+    k_noalloc_validate<<<n, 128, 0, s>>>(base, L, nphase, phase, mat, rve_status);
+    NOALLOC_STEP("input validation", cudaGetLastError());
     NOALLOC_STEP("assembly", launch_assemble_fused(tab, ids, n, Fbar, 2, N, 0, s));
     NOALLOC_STEP("factor", launch_factor<float>(tab, ids, n, ws, rve_status, L.kd, L.nr, s));
     NOALLOC_STEP("backward solve", launch_backward<float>(tab, ids, n, ws, 0, L.kd, L.nr, L.nmp, rve_status, s));

@@ -51,19 +51,6 @@ def macro_mesh3(nx, ny, nz, Lx=1.0, Ly=1.0, Lz=1.0):
     return X, conn, fixed
 
 
-def edge_load(X, edge_nodes, T):
-    """Nodal forces of a constant surface load T on a boundary polyline of
-    bilinear-element edges (Neumann term of Eq. (weakMech)): T L/2 per end
-    node of every segment of length L."""
-    X = np.asarray(X, dtype=np.float64)
-    f = np.zeros_like(X)
-    for a, b in zip(edge_nodes[:-1], edge_nodes[1:]):
-        L = float(np.hypot(*(X[b] - X[a])))
-        f[a] += 0.5 * L * np.asarray(T, dtype=np.float64)
-        f[b] += 0.5 * L * np.asarray(T, dtype=np.float64)
-    return f
-
-
 @dataclass
 class NewtonLog:
     iters: list = field(default_factory=list)      # Newton iterations per load step
@@ -118,9 +105,11 @@ class MonolithicFE2:
                     sigma_eff=sig.cpu().numpy().copy(), Cbar=Cb.cpu().numpy().copy(),
                     status=st.cpu().numpy().copy(), err=err.cpu().numpy().copy())
 
-    def set_load(self, fext):
-        """Nodal external forces of the current load step (Eq. (weakMech))."""
-        self.ctx.macro_set_load(fext)
+    def set_traction(self, nodes, T, scale):
+        """Surface load of the current load step (Neumann term of Eq. (weakMech)):
+        the traction T on the boundary polyline `nodes`, times `scale`; the
+        library forms the nodal forces."""
+        self.ctx.macro_set_edge_load(nodes, T, scale)
 
     def load_step(self, Fk, step, tol_macro=1e-9, tol_micro=1e-9, maxit=25, log=None, F_prev=None):
         """One load step.  The previous converged state is the start value
@@ -226,11 +215,11 @@ class MonolithicFE2:
             log.failed = True
         raise RuntimeError("macro Newton did not converge")
 
-    def run(self, F_final, n_steps, predictor=False, scheme="monolithic", log=None, fext=None, **kw):
+    def run(self, F_final, n_steps, predictor=False, scheme="monolithic", log=None, traction=None, **kw):
         """Load-stepped solve; ``scheme`` is "monolithic" (Section 4.2) or
         "staggered" (Section 4.1).  Step k applies the Dirichlet data of
-        F_k = I + k/n (F_final - I) and, with ``fext`` (nodal forces [nnode][2]
-        of a surface load), the load k/n fext (Section 5.2: T_k = k T / n_l).
+        F_k = I + k/n (F_final - I) and, with ``traction`` = (boundary nodes,
+        T), the surface load k/n T on that edge (Section 5.2: T_k = k T / n_l).
         A failing step raises; ``log`` (if given) keeps what was recorded up
         to the failure."""
         log = NewtonLog() if log is None else log
@@ -240,8 +229,8 @@ class MonolithicFE2:
         F_prev = I
         for k in range(1, n_steps + 1):
             Fk = I + (k / n_steps) * (F_final - I)
-            if fext is not None:
-                self.set_load((k / n_steps) * np.asarray(fext, dtype=np.float64))
+            if traction is not None:
+                self.set_traction(traction[0], traction[1], k / n_steps)
             step_fn(Fk, k, log=log, F_prev=F_prev if predictor else None, **kw)
             F_prev = Fk
         return log

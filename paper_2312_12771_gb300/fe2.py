@@ -66,6 +66,7 @@ _SIGS = {
     "fe2_macro_set_positions": (_I, [_P, _DP, C.POINTER(C.c_uint8)]),
     "fe2_macro_get_positions": (_I, [_P, _DP]),
     "fe2_macro_set_load": (_I, [_P, _DP]),
+    "fe2_macro_set_edge_load": (_I, [_P, _I, _IP, _DP, C.c_double]),
     "fe2_rve_set_quad_weights": (_I, [_P, _I, _IP, _DP]),
     "fe2_macro_gradients": (_I, [_P, _P, _P]),
     "fe2_macro_residual": (_I, [_P, _P, _P]),
@@ -147,12 +148,30 @@ def rve_solve_noalloc(N, phase, mat, Fbar, out, stream=None):
     intermediate data in the library's fixed device scratch array (no device
     allocation by the library).  phase [n, N*N] uint8, mat [n, nphase, 4] f64,
     Fbar [n, 2, 2] f64 and the outputs out = (sigma [n,4], Cbar [n,4,4],
-    status [n] int32, err [n] f64) are caller-owned CUDA tensors."""
+    status [n] int32, err [n] f64 or None) are caller-owned CUDA tensors on the
+    current device; a wrong device, dtype, shape or layout raises ValueError
+    before the library is called."""
     import torch
+    if Fbar.dim() != 3 or tuple(Fbar.shape[1:]) != (2, 2):
+        raise ValueError(f"Fbar must be [n, 2, 2], got {tuple(Fbar.shape)}")
     n = Fbar.shape[0]
+    if mat.dim() != 3 or mat.shape[0] != n or mat.shape[2] != 4:
+        raise ValueError(f"mat must be [n, nphase, 4], got {tuple(mat.shape)}")
     nphase = mat.shape[1]
-    s = stream if stream is not None else torch.cuda.current_stream()
     sig, Cb, st, err = out
+    dev = torch.device("cuda", torch.cuda.current_device())
+    want = [("phase", phase, torch.uint8, (n, N * N)), ("mat", mat, torch.float64, (n, nphase, 4)),
+            ("Fbar", Fbar, torch.float64, (n, 2, 2)), ("sigma", sig, torch.float64, (n, 4)),
+            ("Cbar", Cb, torch.float64, (n, 4, 4)), ("status", st, torch.int32, (n,))]
+    if err is not None:
+        want.append(("err", err, torch.float64, (n,)))
+    for name, t, dt, shape in want:
+        if not isinstance(t, torch.Tensor) or t.device != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device {dev}")
+        if t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor of shape {shape}, got {t.dtype} "
+                             f"{tuple(t.shape)}{'' if t.is_contiguous() else ' (not contiguous)'}")
+    s = stream if stream is not None else torch.cuda.current_stream()
     code = load().fe2_rve_solve_noalloc(int(N), int(n), int(nphase), _ptr(phase), _ptr(mat), _ptr(Fbar),
                                         _ptr(sig), _ptr(Cb), _ptr(st), _ptr(err), C.c_void_p(s.cuda_stream))
     if code != FE2_OK:
@@ -297,6 +316,14 @@ class Fe2Context:
             return
         f = np.ascontiguousarray(np.asarray(fext, dtype=np.float64).reshape(self.macro_nnode, self.dim))
         self._check(self.lib.fe2_macro_set_load(self.h, f.ctypes.data_as(_DP)), "fe2_macro_set_load")
+
+    def macro_set_edge_load(self, nodes, T, scale=1.0):
+        """Surface load of a constant traction T on the boundary polyline `nodes`
+        (consistent nodal forces computed by the library), times `scale`."""
+        a, p = _ids(nodes)
+        t = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(2))
+        self._check(self.lib.fe2_macro_set_edge_load(self.h, len(a), p, t.ctypes.data_as(_DP), float(scale)),
+                    "fe2_macro_set_edge_load")
 
     def macro_gradients(self, Fbar, eta=None):
         """Fbar_b of every macro Gauss point; eta (optional) receives the weights."""

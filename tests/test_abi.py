@@ -58,3 +58,27 @@ def _load_fresh(path):
         return fe2.load(path)
     finally:
         fe2._lib = saved
+
+
+def test_noalloc_argument_errors_return_before_any_device_work(lib):
+    """fe2_rve_solve_noalloc refuses bad sizes, NULL pointers and requests
+    beyond its fixed scratch array before it touches the device (so this runs
+    without a GPU), each with a reason in fe2_noalloc_last_error."""
+    from paper_2312_12771_gb300 import fe2
+    f = fe2.load()
+    P = ctypes.c_void_p
+    dummy = P(256)                      # never dereferenced: every case returns first
+
+    def call(N, n, nphase, ptr=dummy):
+        return f.fe2_rve_solve_noalloc(N, n, nphase, ptr, ptr, ptr, ptr, ptr, ptr, None, None)
+
+    cases = [(call(2, 4, 2), fe2.FE2_ERR_ARG),          # N < 3
+             (call(8, 0, 2), fe2.FE2_ERR_ARG),          # no RVEs
+             (call(8, 4, 9), fe2.FE2_ERR_ARG),          # nphase > 8
+             (call(8, 4, 0), fe2.FE2_ERR_ARG),          # nphase < 1
+             (call(8, 4, 2, P(0)), fe2.FE2_ERR_ARG),    # NULL inputs / outputs
+             (call(32, 40, 2), fe2.FE2_ERR_BUDGET),     # 40 RVEs of 32^2 exceed 64 MiB (39 fit)
+             (call(16, 231, 2), fe2.FE2_ERR_BUDGET)]    # 231 RVEs of 16^2 too (230 fit)
+    for got, want in cases:
+        assert got == want
+        assert f.fe2_noalloc_last_error().decode() != ""

@@ -714,7 +714,7 @@ def test_cook_membrane_matches_oracle(torch, scheme):
     clamped left edge, traction (-5, 10) on the right edge in n_l = 2 load
     steps.  Newton iteration counts, tip position and converged Pbar, Cbar
     equal the oracle's (FP64 path)."""
-    from paper_2312_12771_gb300.driver import MonolithicFE2, edge_load
+    from paper_2312_12771_gb300.driver import MonolithicFE2
     X, conn, left, right = W.cook_mesh(2, 2)
     fixed = np.zeros(2 * len(X), np.uint8)
     for n in left:
@@ -722,9 +722,8 @@ def test_cook_membrane_matches_oracle(torch, scheme):
     b = W.cook_batch(4 * len(conn), 6)
     ctx = ctx_for(torch, "fp64")
     fe = MonolithicFE2(ctx, X, conn, fixed, b)
-    fext = edge_load(X, right, W.MEMBRANE_TRACTION)
     kw = dict(tol_macro=1e-9, tol_micro=1e-11) if scheme == "staggered" else dict(tol_macro=1e-9, tol_micro=1e-9)
-    log = fe.run(np.eye(2), 2, scheme=scheme, fext=fext, **kw)
+    log = fe.run(np.eye(2), 2, scheme=scheme, traction=(right, W.MEMBRANE_TRACTION), **kw)
     st = fe.state()
     q = fe.ctx.macro_get_positions()
     rves = [dict(N=6, phase=b.phase[k], mat=b.mat[k]) for k in range(b.nrve)]

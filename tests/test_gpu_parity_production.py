@@ -1,0 +1,197 @@
+"""Parity with the FP64 oracle at the mesh sizes the nonlinear workloads run.
+
+The general (Neo-Hooke / Mooney-Rivlin) assembly integrates strips of
+R = floor(256 / N) element rows through a ring of R + 1 shared-memory slots;
+for N > 16 a mesh takes several strips and the ring wraps (N = 17: 2 strips;
+24: 3, the last one ragged; 30 and 32: 4; 48: 10, the last one ragged).
+These tests drive that path at the sizes of the finite-strain inclusion
+problem (N = 32), of the serving stream (N in {16, 24, 32, 48}) and of the
+membrane RVEs of Section 5.2 (N = 30), with a nonzero fluctuation w~ and a
+non-symmetric Fbar, and compare sigma_eff and Cbar per RVE with the oracle
+(Section 4.2, Eq. (solution2)): relative error <= 1e-10 on the FP64 path and
+<= 1e-8 on the mixed path; reduced operators entry by entry to 1e-13.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+from oracle import fe2_oracle as O
+from paper_2312_12771_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-8}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_12771_gb300 import build
+    build.build()
+    return t
+
+
+def rel_sigma(sig, ref, F, d=2):
+    floor = np.linalg.norm(ref["Cbar"]) * np.linalg.norm(np.asarray(F) - np.eye(d))
+    return O.rel_err(sig, ref["sigma_eff"], floor)
+
+
+@functools.lru_cache(maxsize=None)
+def nh_case(N, n=3):
+    """n NH inclusion RVEs of N x N at a non-symmetric finite Fbar, each with
+    a seeded fluctuation w~ of amplitude 0.03 / N per DOF (so grad w~ stays
+    O(0.05) at every N), and the oracle's solution of each."""
+    b = W.inclusion_batch(n, N, stretch=1.1, seed=W.GLOBAL_SEED + 17 * N)
+    b.Fbar = W.perturbed_F(b, 100 + N, 0.03)
+    rng = np.random.default_rng(1000 + N)
+    ws = [0.03 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
+    refs = [O.rve_solve(N, 2, b.phase[k], b.mat[k], b.Fbar[k], ws[k]) for k in range(n)]
+    return b, ws, refs
+
+
+def solve_with_w(torch, precision, b, ws, **kw):
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    ctx = Fe2Context(dim=2, precision=precision, **kw)
+    ids = ctx.register_batch(b)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    out = sig.cpu().numpy(), Cb.cpu().numpy(), st.cpu().numpy()
+    ctx.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [17, 24, 32, 48])
+def test_neohooke_multistrip_assembly_parity(torch, precision, N):
+    """NH inclusion RVEs (1-6 random inclusions, mu_i/mu_m = 20, kappa = 10 mu)
+    with w~ != 0 and Fbar non-symmetric, through the multi-strip assembly."""
+    b, ws, refs = nh_case(N)
+    sig, Cb, st = solve_with_w(torch, precision, b, ws)
+    for k in range(b.nrve):
+        assert st[k] == 0, (k, st[k])
+        eC = O.rel_err(Cb[k], refs[k]["Cbar"])
+        eS = rel_sigma(sig[k], refs[k], b.Fbar[k])
+        assert eC <= TOL[precision], f"N={N} rve {k}: Cbar rel err {eC:.3e}"
+        assert eS <= TOL[precision], f"N={N} rve {k}: sigma rel err {eS:.3e}"
+
+
+@pytest.mark.parametrize("N", [24, 30])
+def test_reduced_operator_entrywise_multistrip(torch, N):
+    """K_mm, r_m, K_mM, K_MM and Pint of the multi-strip assembly, fused and
+    split (assemble + reduce) paths, equal the oracle's T^T K T etc."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    b, ws, refs = nh_case(N, 2) if N != 30 else (None, None, None)
+    if N == 30:      # membrane RVEs: Mooney-Rivlin cross, Section 5.2
+        b = W.cook_batch(2, N)
+        rng = np.random.default_rng(31)
+        b.Fbar = np.eye(2)[None] + 0.1 * rng.standard_normal((2, 2, 2))
+        ws = [0.02 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(2)]
+        refs = [O.rve_solve(N, 2, b.phase[k], b.mat[k], b.Fbar[k], ws[k]) for k in range(2)]
+    ctx = Fe2Context(dim=2, precision="fp64")
+    ids = ctx.register_batch(b)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    F = torch.tensor(b.Fbar, device="cuda")
+    for path in ("fused", "split"):
+        if path == "fused":
+            ctx.rve_solve(ids, F)
+        else:
+            ctx.micro_assemble(ids, F)
+            ctx.nullspace_reduce(ids)
+        torch.cuda.synchronize()
+        for k, i in enumerate(ids):
+            ref = refs[k]
+            scale = np.abs(ref["K_mm"]).max()
+            K = ctx.export(i, 0, N)
+            assert np.abs(K - ref["K_mm"]).max() <= 1e-13 * scale, (path, N)
+            r = ctx.export(i, 1, N)
+            assert np.abs(r - ref["r_m"]).max() <= 1e-13 * max(1.0, np.abs(ref["r_m"]).max()) * scale, (path, N)
+            KmM = ctx.export(i, 2, N)
+            assert np.abs(KmM - ref["K_mM"]).max() <= 1e-13 * np.abs(ref["K_mM"]).max(), (path, N)
+            mm = ctx.export(i, 4, N)
+            assert np.abs(mm[:16] - ref["K_MM"].ravel()).max() <= 1e-13 * np.abs(ref["K_MM"]).max(), (path, N)
+            assert np.abs(mm[16:] - ref["Pint"]).max() <= 1e-13 * max(1.0, np.abs(ref["Pint"]).max()), (path, N)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_mooney_rivlin_cross_N30_parity(torch, precision):
+    """The Section 5.2 membrane RVE at its printed resolution (30 x 30, the
+    cross of the two Mooney-Rivlin materials) at finite non-symmetric Fbar
+    and with a fluctuation w~ != 0."""
+    N, n = 30, 3
+    b = W.cook_batch(n, N)
+    rng = np.random.default_rng(77)
+    b.Fbar = np.eye(2)[None] + 0.1 * rng.standard_normal((n, 2, 2))
+    ws = [0.02 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
+    refs = [O.rve_solve(N, 2, b.phase[k], b.mat[k], b.Fbar[k], ws[k]) for k in range(n)]
+    sig, Cb, st = solve_with_w(torch, precision, b, ws)
+    for k in range(n):
+        assert st[k] == 0, (k, st[k])
+        assert O.rel_err(Cb[k], refs[k]["Cbar"]) <= TOL[precision]
+        assert rel_sigma(sig[k], refs[k], b.Fbar[k]) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_element_rve_N32_parity(torch, precision):
+    """Piecewise-constant macro basis (Section 3, Eqs. (constSolution1),
+    (constSolution2)) on RVEs of 32 x 32 (the resolution of the basis
+    comparison): four macro Gauss points with different Fbar and non-uniform
+    weights, w~ != 0; the 16 x 16 coupled tangent and the four stresses."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    n, N = 3, 32
+    b = W.inclusion_batch(n, N, stretch=1.0, seed=W.GLOBAL_SEED + 5)
+    rng = np.random.default_rng(21)
+    F = np.eye(2)[None, None] + 0.05 * rng.standard_normal((n, 4, 2, 2))
+    wq = rng.uniform(0.5, 1.5, (n, 4))
+    wq /= wq.sum(axis=1, keepdims=True)
+    ws = [0.02 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
+    ctx = Fe2Context(dim=2, precision=precision, basis="const")
+    ids = ctx.register_batch(b)
+    ctx.rve_set_quad_weights(ids, wq)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(F, device="cuda"))
+    torch.cuda.synchronize()
+    assert (st.cpu().numpy() == 0).all()
+    sig = sig.cpu().numpy().reshape(n, 4, 4)
+    Cb = Cb.cpu().numpy()
+    for k in range(n):
+        ref = O.rve_solve_elem(N, 2, b.phase[k], b.mat[k], list(F[k]), wq[k], ws[k])
+        assert O.rel_err(Cb[k], ref["Cbar"]) <= TOL[precision]
+        floor = np.linalg.norm(ref["Cbar"]) * np.linalg.norm(F[k] - np.eye(2)[None])
+        assert O.rel_err(sig[k], ref["sigma_eff"], floor) <= TOL[precision]
+    ctx.close()
+
+
+def test_served_stream_matches_oracle(torch):
+    """A served stream of NH inclusion RVEs of 16, 24, 32 and 48 squared,
+    Poisson arrivals, overlapping batches on two lanes: every result equals
+    the oracle's within the mixed-path tolerance."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    from paper_2312_12771_gb300.serve import Server, simulate
+    n = 16
+    sizes = np.array([16, 24, 32, 48] * (n // 4), dtype=np.int32)
+    b = W.inclusion_batch(n, sizes, stretch=1.05, seed=W.GLOBAL_SEED + 3)
+    b.Fbar = W.perturbed_F(b, 41, 0.02)
+    ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+    ids = np.asarray(ctx.register_batch(b))
+    srv = Server(ctx, max_batch=4, lanes=2)
+    res, p50, p99, thr = simulate(srv, ids, b.Fbar, W.poisson_arrivals(9, n, rate=500.0))
+    srv.close()
+    assert len(res["tickets"]) == n and (res["status"] == 0).all()
+    # tickets are numbered in submission order, and requests are submitted in
+    # the stable order of their arrival times
+    order = np.argsort(res["tickets"])
+    sub = np.argsort(W.poisson_arrivals(9, n, rate=500.0), kind="stable")
+    for j, k in enumerate(order):
+        r = int(sub[j])
+        ref = O.rve_solve(int(b.N[r]), 2, b.phase[r], b.mat[r], b.Fbar[r])
+        assert O.rel_err(res["Cbar"][k], ref["Cbar"]) <= TOL["mixed"], (r, int(b.N[r]))
+        assert rel_sigma(res["sigma"][k], ref, b.Fbar[r]) <= TOL["mixed"], (r, int(b.N[r]))
+    ctx.close()

@@ -28,11 +28,10 @@ def _worker(rank, world, port, out):
     # each rank builds its own shard of independent RVEs (different seeds)
     b = W.fiber_batch(8, 4, seed=W.GLOBAL_SEED + rank)
     t = float(10 + 5 * rank)                       # a per-rank elapsed time
-    tmax = torch.tensor([t], dtype=torch.float64)
-    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)    # the bench's max-over-ranks timing
+    tmax = bench.max_over_ranks(t, True)           # the bench's max-over-ranks timing
     n = torch.tensor([b.nrve], dtype=torch.int64)
     dist.all_reduce(n)                             # total units processed
-    out[rank] = (float(tmax.item()), int(n.item()), float(b.mat[:, 0, 1].sum()))
+    out[rank] = (float(tmax), int(n.item()), float(b.mat[:, 0, 1].sum()))
     dist.barrier()
     dist.destroy_process_group()
 
