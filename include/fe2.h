@@ -242,8 +242,8 @@ fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double
 /*
  * Test/diagnostic export of one RVE in the natural periodic numbering
  * (node p = i + N j (+N^2 k), reduced DOF d*(p-1)+c):  what = 0: dense K_mm
- * [nm][nm]; 1: r_m [nm]; 2: K_mM [nm][d*d]; 3: w~ [nm]; 4: K_MM [d^2][d^2]
- * then Pint [d^2].  host_out [host] must hold the stated doubles.
+ * [nm][nm] (2D only); 1: r_m [nm]; 2: K_mM [nm][d*d]; 3: w~ [nm]; 4: K_MM
+ * [d^2][d^2] then Pint [d^2].  host_out [host] must hold the stated doubles.
  * Synchronises the stream.
  */
 fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* host_out);

@@ -897,6 +897,14 @@ fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double*
     return FE2_OK;
 }
 
+// folded index of natural node p = i + N j (+ N^2 k) of a 2D or 3D RVE
+static int fold_node(int p, int N, int d) {
+    const int i = p % N, j = (p / N) % N;
+    int q = fold_pos(i, N) + N * fold_pos(j, N);
+    if (d == 3) q += N * N * fold_pos(p / (N * N), N);
+    return q;
+}
+
 fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w) {
     if (!ctx) return FE2_ERR_ARG;
     if (rve_id < 0 || rve_id >= (int)ctx->host.size() || !ctx->host[rve_id].active || !host_w)
@@ -905,8 +913,7 @@ fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w) {
     const int N = r.N, d = r.d;
     std::vector<double> wf(r.nm);
     for (int p = 1; p < r.nn; ++p) {
-        const int i = p % N, j = p / N;
-        const int q = fold_pos(i, N) + N * fold_pos(j, N);
+        const int q = fold_node(p, N, d);
         for (int c = 0; c < d; ++c) wf[d * (q - 1) + c] = host_w[d * (p - 1) + c];
     }
     CK(cudaStreamSynchronize(ctx->stream));
@@ -922,9 +929,9 @@ fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* out) {
     CK(cudaStreamSynchronize(ctx->stream));
     const RveDev& r = ctx->mirror[rve_id];
     const int N = r.N, d = r.d, nm = r.nm, nn = r.nn, dd = d * d;
-    if (d != 2) return fail(ctx, FE2_ERR_ARG, "export supports 2D only");
+    if (d != 2 && what == 0) return fail(ctx, FE2_ERR_ARG, "the dense K_mm export is 2D only");
     std::vector<int> q2p(nn);
-    for (int p = 0; p < nn; ++p) q2p[fold_pos(p % N, N) + N * fold_pos(p / N, N)] = p;
+    for (int p = 0; p < nn; ++p) q2p[fold_node(p, N, d)] = p;
     auto nat = [&](int fdof) { return d * (q2p[fdof / d + 1] - 1) + fdof % d; };
     if (what == 0) {
         std::vector<double> st((size_t)9 * 4 * nn);

@@ -42,12 +42,13 @@ def rel_sigma(sig, ref, F, d=2):
 @functools.lru_cache(maxsize=None)
 def nh_case(N, n=3):
     """n NH inclusion RVEs of N x N at a non-symmetric finite Fbar, each with
-    a seeded fluctuation w~ of amplitude 0.03 / N per DOF (so grad w~ stays
-    O(0.05) at every N), and the oracle's solution of each."""
+    a seeded fluctuation w~ of amplitude 0.01 / N per DOF (so grad w~ stays
+    O(0.02) at every N and K_mm positive definite), and the oracle's solution
+    of each."""
     b = W.inclusion_batch(n, N, stretch=1.1, seed=W.GLOBAL_SEED + 17 * N)
     b.Fbar = W.perturbed_F(b, 100 + N, 0.03)
     rng = np.random.default_rng(1000 + N)
-    ws = [0.03 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
+    ws = [0.01 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
     refs = [O.rve_solve(N, 2, b.phase[k], b.mat[k], b.Fbar[k], ws[k]) for k in range(n)]
     return b, ws, refs
 
@@ -141,16 +142,19 @@ def test_mooney_rivlin_cross_N30_parity(torch, precision):
 def test_element_rve_N32_parity(torch, precision):
     """Piecewise-constant macro basis (Section 3, Eqs. (constSolution1),
     (constSolution2)) on RVEs of 32 x 32 (the resolution of the basis
-    comparison): four macro Gauss points with different Fbar and non-uniform
-    weights, w~ != 0; the 16 x 16 coupled tangent and the four stresses."""
+    comparison): four macro Gauss points with different Fbar (stretch 1.05
+    plus a seeded perturbation; under compression these high-contrast RVEs
+    can have an indefinite micro Hessian, which the oracle and the GPU both
+    report) and non-uniform weights, w~ != 0; the 16 x 16 coupled tangent and
+    the four stresses."""
     from paper_2312_12771_gb300.fe2 import Fe2Context
     n, N = 3, 32
     b = W.inclusion_batch(n, N, stretch=1.0, seed=W.GLOBAL_SEED + 5)
     rng = np.random.default_rng(21)
-    F = np.eye(2)[None, None] + 0.05 * rng.standard_normal((n, 4, 2, 2))
+    F = np.diag([1.05, 1.0])[None, None] + 0.02 * rng.standard_normal((n, 4, 2, 2))
     wq = rng.uniform(0.5, 1.5, (n, 4))
     wq /= wq.sum(axis=1, keepdims=True)
-    ws = [0.02 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
+    ws = [0.01 / N * rng.standard_normal(2 * (N * N - 1)) for _ in range(n)]
     ctx = Fe2Context(dim=2, precision=precision, basis="const")
     ids = ctx.register_batch(b)
     ctx.rve_set_quad_weights(ids, wq)
