@@ -48,7 +48,8 @@ FACTOR_TRAFFIC_PER_RVE = {"sha1": "48f254217286", "bytes": (113871104 + 28824780
 # launches whose work depends on how many RVEs the error estimate flags for an
 # FP64-residual refinement sweep; their algorithmic work per launch is not known
 # to the bench, so no roofline is reported for them
-DATA_DEPENDENT = ("band_refine_fp32", "residual_fp64_refine", "schur_refine")
+DATA_DEPENDENT = ("band_refine_fp32", "residual_fp64_refine", "schur_refine", "band_correct_fp32",
+                  "schur_second_order")
 
 
 def sm_count():
@@ -125,12 +126,16 @@ def work_per_rve(N, d=2):
         # rows tabulated per phase combination: the kernel streams the stencil and [K_mM | r_m] out
         "assemble_reduce_linear": {"hbm_bytes": stencil_bytes + nn},
         "band_factor_fp32": {"flops": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
+        "band_factor_fp32_pipelined": {"flops": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
         "band_factor_tc": {"flops_tc": chol + nr * tri, "bytes": stencil_bytes + L_bytes + 4 * nr * nm},
         "band_backward_fp32": {"flops": nr * tri, "bytes": L_bytes + 4 * nr * nm + 8 * nr * nm},
         "band_refine_fp32": {"flops": 2 * nr * tri, "bytes": 2 * L_bytes + 8 * 3 * nr * nm},
+        # the correction dx = (L L^T)^-1 R of every RVE (second-order corrected Schur complement)
+        "band_correct_fp32": {"flops": 2 * nr * tri, "bytes": 2 * L_bytes + 8 * nr * nm + 4 * nr * nm},
         "residual_fp64": {"flops64": 2 * nr * nnz, "bytes": 9 * d * d * nn * 8 + 3 * nr * nm * 8},
         "schur": {"flops64": 2 * 2 * d * d * nr * nm, "bytes": 3 * nr * nm * 8},
         "band_factor_fp64": {"flops64": chol + nr * tri, "bytes": stencil_bytes + 2 * L_bytes + 8 * nr * nm},
+        "band_factor_fp64_pipelined": {"flops64": chol + nr * tri, "bytes": stencil_bytes + 2 * L_bytes + 8 * nr * nm},
         "band_backward_fp64": {"flops64": nr * tri, "bytes": 2 * L_bytes + 8 * 2 * nr * nm},
     }
 
@@ -328,11 +333,12 @@ def run_gpu(args, rank, world, dist):
 
     results = {}
     F = torch.tensor(batch.Fbar, device=dev)
-    legs = ("mixed", "tensor_core", "fp64") if not args.no_tc else ("mixed", "fp64")
+    legs = ("mixed", "tensor_core", "pipelined", "fp64") if not args.no_tc else ("mixed", "pipelined", "fp64")
     for prec in legs:
-        # "tensor_core": the mixed path with the tcgen05 (3xTF32) band factor
+        # "tensor_core": the mixed path with the tcgen05 (3xTF32) band factor; "pipelined":
+        # the mixed path with the pipelined-chain CUDA-core factor
         ctx = Fe2Context(dim=2, precision="fp64" if prec == "fp64" else "mixed", max_refine=args.refine,
-                         factor="tensor_core" if prec == "tensor_core" else "auto")
+                         factor={"tensor_core": "tensor_core", "pipelined": "cuda_core_pipelined"}.get(prec, "auto"))
         ids = ctx.register_batch(batch)
         outs = ctx._outs(nrve)
         steps = args.steps if prec == "mixed" else max(2, min(args.steps, 3))
@@ -397,7 +403,7 @@ def run_serving(args, dev):
     sizes = W.serving_sizes(W.GLOBAL_SEED, nmax)
     batch = W.inclusion_batch(nmax, sizes, stretch=1.05)
     Fb = W.perturbed_F(batch, 5, 0.01)
-    ctx = Fe2Context(dim=2, precision="mixed", max_refine=1, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30))
+    ctx = Fe2Context(dim=2, precision="mixed", max_refine=2, hbm_budget_bytes=int(args.serve_budget_gb * 2 ** 30))
     ids = np.asarray(ctx.register_batch(batch))
     summary_n = 8192 if 8192 in nreqs else nreqs[0]
     # burst capacity with each lane's launch sequence issued kernel by kernel
@@ -486,7 +492,7 @@ def run_hex8(args):
     from paper_2312_12771_gb300.fe2 import Fe2Context
     b = W.sphere_batch(args.hex8_rves, 8, gamma=0.02)
     b.Fbar = W.perturbed_F(b, 9, 1e-3)
-    ctx = Fe2Context(dim=3, precision="mixed", max_refine=1)
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=2)
     ids = ctx.register_batch(b)
     F = torch.tensor(b.Fbar, device="cuda")
     outs = ctx._outs(b.nrve)
@@ -541,7 +547,7 @@ def run_config5(args):
     nx = args.c5_macro
     X, conn, fixed = macro_mesh3(nx, nx, nx)
     b = W.sphere_batch(8 * nx ** 3, 8)
-    ctx = Fe2Context(dim=3, precision="mixed", max_refine=1)
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=2)
     fe = MonolithicFE2(ctx, X, conn, fixed, b)
     # warm-up outside the timed region: one RVE solve at the reference state
     ctx.macro_gradients(fe.Fbar)
@@ -581,7 +587,7 @@ def run_nh_newton(args):
     nx = args.nh_macro
     X, conn, fixed = macro_mesh(nx, nx)
     b = W.inclusion_batch(4 * nx * nx, 32, stretch=1.0)
-    ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+    ctx = Fe2Context(dim=2, precision="mixed", max_refine=2)
     fe = MonolithicFE2(ctx, X, conn, fixed, b)
     # warm-up outside the timed region: one RVE solve at the reference state
     # (workspace allocation, first launches)
@@ -619,7 +625,7 @@ def run_schemes(args):
            "runs": []}
     for n_l in [int(x) for x in args.scheme_steps.split(",") if x]:
         for scheme in ("monolithic", "staggered"):
-            ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+            ctx = Fe2Context(dim=2, precision="mixed", max_refine=2)
             fe = MonolithicFE2(ctx, X, conn, fixed, b)
             log = NewtonLog()
             torch.cuda.synchronize()
@@ -661,7 +667,7 @@ def run_basis(args):
     bd = be.subset(np.repeat(np.arange(nx * nx), 4))
     for basis, b in (("dirac", bd), ("const", be)):
         nrve = b.nrve
-        ctx = Fe2Context(dim=2, precision="mixed", max_refine=1, basis=basis)
+        ctx = Fe2Context(dim=2, precision="mixed", max_refine=2, basis=basis)
         fe = MonolithicFE2(ctx, X, conn, fixed, b)
         log = NewtonLog()
         # warm-up outside the timed region: one RVE solve at the reference state
@@ -721,7 +727,7 @@ def run_cook(args):
            "runs": []}
     for n_l in [int(x) for x in args.cook_steps.split(",") if x]:
         for scheme in ("monolithic", "staggered"):
-            ctx = Fe2Context(dim=2, precision="mixed", max_refine=1)
+            ctx = Fe2Context(dim=2, precision="mixed", max_refine=2)
             fe = MonolithicFE2(ctx, X, conn, fixed, b)
             log = NewtonLog()
             torch.cuda.synchronize()
@@ -773,7 +779,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rves", type=int, default=N_RVE)
     ap.add_argument("--N", type=int, default=N_MESH)
-    ap.add_argument("--refine", type=int, default=1)
+    ap.add_argument("--refine", type=int, default=2)
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -901,6 +907,21 @@ def main():
                   "max_rel_err_vs_fp64_gpu": rel_errs(tc["Cbar"], R["fp64"]["Cbar"], tc["sigma"], R["fp64"]["sigma"],
                                                       batch.Fbar),
                   "status_nonzero": int((tc["status"] != 0).sum()), "kernels": ktc}
+    panel_leg = None
+    if "pipelined" in R:
+        pl = R["pipelined"]
+        ms_pl = max_over_ranks(pl["ms"], dist)
+        kpl = {}
+        for name, (tms, cnt) in pl["prof"].items():
+            avg = tms / max(cnt, 1)
+            kpl[name] = {"avg_ms": round(avg, 4), "roofline": roofline_for(name, avg, args.rves, pk, args.N)}
+        panel_leg = {"value": round(total * pl["steps"] / (ms_pl * 1e-3), 1), "unit": UNIT,
+                     "ms_per_step": round(ms_pl / pl["steps"], 4), "steps": pl["steps"],
+                     "factor_kernel": "band_factor_fp32_pipelined (diagonal block published per column, "
+                                      "panel rows pipelined behind it, update blocks from a shared counter)",
+                     "max_rel_err_vs_fp64_gpu": rel_errs(pl["Cbar"], R["fp64"]["Cbar"], pl["sigma"],
+                                                         R["fp64"]["sigma"], batch.Fbar),
+                     "status_nonzero": int((pl["status"] != 0).sum()), "kernels": kpl}
     kern64 = {}
     for name, (tms, cnt) in R["fp64"]["prof"].items():
         avg = tms / max(cnt, 1)
@@ -913,7 +934,7 @@ def main():
             "precision_path": "mixed", "gpu_launches": mx["launches"],
             "fp64_path": {"value": round(value64, 1), "ms_per_step": round(ms64 / R["fp64"]["steps"], 3),
                           "steps": R["fp64"]["steps"], "kernels": kern64},
-            "tensor_core_path": tc_leg,
+            "tensor_core_path": tc_leg, "pipelined_factor_path": panel_leg,
             "speedup_mixed_vs_fp64": round(value / value64, 2),
             "max_rel_err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
             "status_nonzero": int((mx["status"] != 0).sum()),

@@ -63,15 +63,23 @@ typedef enum {
 enum { FE2_ELEM_Q4 = 0, FE2_ELEM_HEX8 = 1 };
 enum { FE2_PREC_FP64 = 0, FE2_PREC_MIXED = 1 };
 enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1, FE2_MODEL_MOONEY_RIVLIN = 2 };
-/* FP32 band factor of the mixed path (Section 4: K_mm factorised once per
- * RVE and Newton iteration).  FE2_FACTOR_CUDA_CORE: shared-memory band
- * Cholesky on the FP32 pipes, two RVEs per SM.  FE2_FACTOR_TENSOR_CORE: the
- * dense trailing updates as tcgen05 MMAs (3xTF32, fp32 accumulation in tensor
- * memory), one RVE per SM, for 2D bands with 32 + kd + d*d+1 <= 192 whose
- * shared memory fits; other bands take the CUDA-core kernel.  FE2_FACTOR_AUTO
- * is the library's choice, currently the CUDA-core kernel (measured faster on
- * GB300 for these bands: the panel chain, not the update, bounds both). */
-enum { FE2_FACTOR_AUTO = 0, FE2_FACTOR_CUDA_CORE = 1, FE2_FACTOR_TENSOR_CORE = 2 };
+/* Band factor (Section 4: K_mm factorised once per RVE and Newton iteration).
+ * FE2_FACTOR_CUDA_CORE: shared-memory band Cholesky on the CUDA cores, two
+ * RVEs per SM, panel phases (diagonal block, panel rows, trailing update)
+ * separated by block barriers with a one-panel look-ahead (FP32 on the mixed
+ * path, FP64 on the FP64 path).  FE2_FACTOR_CUDA_CORE_PIPELINED: the same
+ * factorisation with the panel chain pipelined: warp 0 factors each 32 x 32
+ * diagonal block and publishes it column by column (one mbarrier per column)
+ * to the threads that solve the panel rows below it, while the other warps
+ * take the previous panel's trailing update blocks from a shared counter
+ * (2D bands with 32 + kd + d*d+1 <= 224; measured slower on GB300, kept as an
+ * option).  FE2_FACTOR_TENSOR_CORE (mixed path): the dense trailing updates as
+ * tcgen05 MMAs (3xTF32, fp32 accumulation in tensor memory), one RVE per SM,
+ * for 2D bands with 32 + kd + d*d+1 <= 192 whose shared memory fits; other
+ * bands take the CUDA-core kernel.  FE2_FACTOR_AUTO is the library's choice,
+ * currently FE2_FACTOR_CUDA_CORE (measured fastest on GB300 for these bands).
+ * 3D (Hex8) bands always take the wide-band kernel. */
+enum { FE2_FACTOR_AUTO = 0, FE2_FACTOR_CUDA_CORE = 1, FE2_FACTOR_TENSOR_CORE = 2, FE2_FACTOR_CUDA_CORE_PIPELINED = 3 };
 /* Macro interpolation of the fluctuation w~ (Section 3).  FE2_BASIS_DIRAC: Dirac
  * pulses at the macro Gauss points, one RVE per Gauss point (Eqs.
  * (fluctVaria_dirac), (fluctSolution)).  FE2_BASIS_CONST: piecewise constant
@@ -90,10 +98,22 @@ typedef struct {
     size_t hbm_budget_bytes; /* device bytes the context may hold; 0 = no limit   */
     void* cuda_stream;       /* cudaStream_t the work is queued on; NULL = default */
     double refine_tol;       /* mixed path: accepted relative error estimate      */
-    int max_refine;          /* mixed path: FP64-residual refinement sweeps (>=0) */
-    int factor_kernel;       /* FE2_FACTOR_AUTO, _CUDA_CORE or _TENSOR_CORE       */
+    int max_refine;          /* mixed path: correction sweeps (>= 0), see below   */
+    int factor_kernel;       /* FE2_FACTOR_AUTO, _CUDA_CORE, _TENSOR_CORE, _PIPELINED */
     int macro_basis;         /* FE2_BASIS_DIRAC or FE2_BASIS_CONST                */
 } fe2_config;
+
+/* Mixed-path accuracy (Section 4.2 with an FP32 factor): sigma_eff and Cbar
+ * come from the Schur complement corrected with the FP64 residual R of the
+ * FP32 solve, whose error is second order in the solve error.  With
+ * max_refine >= 1 every RVE whose first-order estimate exceeds 1e-4 refine_tol
+ * also gets dX = (L L^T)^-1 R from the FP32 factor and the second-order
+ * correction (the remaining error is the FP32 solve's relative error times the
+ * second-order term); each further sweep (up to max_refine in all) refines the
+ * RVEs whose estimate still exceeds refine_tol (X += dX, new FP64 residual).
+ * An RVE still above refine_tol after the last sweep gets FE2_ERR_NO_CONV.
+ * With max_refine = 0 only the first-order correction runs (its estimate can
+ * understate the error of high-contrast RVEs several hundredfold). */
 
 /* Create a context on the current CUDA device.  Allocates nothing large. */
 fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out);

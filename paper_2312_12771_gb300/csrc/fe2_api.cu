@@ -65,7 +65,8 @@ struct fe2_ctx {
     size_t status_tmp_n = 0;
     int* d_redo = nullptr;          // per-slot "refine again" flags of the mixed path
     size_t redo_n = 0;
-    double* d_tol = nullptr;        // device copy of cfg.refine_tol
+    double* d_tol = nullptr;        // device copy of cfg.refine_tol, then the screening threshold
+                                    // of the second-order correction (refine_tol * kScreen)
     // id-list cache
     std::vector<IdList> idcache;
     unsigned long long tick = 0;
@@ -88,6 +89,12 @@ struct fe2_ctx {
     std::vector<void*> macro_bufs;  // device buffers owned by the macro problem
     int* d_macro_status = nullptr;
 };
+
+// The first-order estimate of the residual-corrected Schur complement can
+// understate its error by a factor of several hundred on high-contrast RVEs
+// (measured on GB300: 400 at N = 48); every RVE whose first-order estimate
+// exceeds refine_tol * kScreen therefore gets the second-order correction.
+constexpr double kScreen = 1e-4;
 
 static fe2_status fail(fe2_ctx* c, fe2_status s, const char* fmt, ...) {
     char buf[512];
@@ -206,6 +213,12 @@ static bool use_smem_factor(int kd, int nr, bool fp64, int max_smem, int d) {
 static bool use_tc_factor(const fe2_ctx* ctx, int maxkd, int maxnr) {
     return ctx->cfg.factor_kernel == FE2_FACTOR_TENSOR_CORE &&
            factor_tc_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem);
+}
+
+// The pipelined band factor when the context asks for it and the band fits it.
+static bool use_la_factor(const fe2_ctx* ctx, int maxkd, int maxnr, bool fp64) {
+    return ctx->cfg.factor_kernel == FE2_FACTOR_CUDA_CORE_PIPELINED && ctx->cfg.dim == 2 &&
+           factor_la_eligible(maxkd, maxnr, fp64, ctx->max_smem);
 }
 
 static WsLayout ws_layout(int maxkd, int maxnr, int maxnm, int maxnmp, bool fp64, int max_smem, int d) {
@@ -450,6 +463,8 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
         if (fp64) {
             if (l.gw)
                 TIMED("band_factor_fp64_gw", launch_factor_gw<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            else if (use_la_factor(ctx, b.maxkd, b.maxnr, true))
+                TIMED("band_factor_fp64_pipelined", launch_factor_la<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else
                 TIMED("band_factor_fp64", launch_factor<double>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp64",
@@ -471,14 +486,32 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
                 TIMED("band_factor_fp32_gw", launch_factor_gw<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else if (use_tc_factor(ctx, b.maxkd, b.maxnr))
                 TIMED("band_factor_tc", launch_factor_tc(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+            else if (use_la_factor(ctx, b.maxkd, b.maxnr, false))
+                TIMED("band_factor_fp32_pipelined", launch_factor_la<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else
                 TIMED("band_factor_fp32", launch_factor<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             TIMED("band_backward_fp32",
                   launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
             TIMED("residual_fp64", residual(di, m, nullptr));
-            TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->cfg.max_refine > 0 ? 0 : 3));
-            for (int it = 0; it < ctx->cfg.max_refine; ++it) {
+            // Dirac-basis RVEs: every RVE whose first-order estimate exceeds
+            // refine_tol * kScreen gets the correction dx from the FP32 factor and
+            // the second-order corrected Schur complement; further sweeps, and every
+            // sweep of element RVEs, go to the RVEs whose estimate exceeds refine_tol
+            int it0 = 0;
+            if (!elem && ctx->cfg.max_refine > 0) {
+                TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol + 1, redo, 0));
+                TIMED("band_correct_fp32", launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr,
+                                                                       b.maxnmp, stp, redo, ctx->stream, 1));
+                TIMED("schur_second_order", schur(di, m, 2, sg, cb, stp, er, ctx->d_tol, redo,
+                                                  ctx->cfg.max_refine > 1 ? 1 : 2));
+                it0 = 1;
+            } else {
+                TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->cfg.max_refine > 0 ? 0 : 3));
+            }
+            for (int it = it0; it < ctx->cfg.max_refine; ++it) {
                 const bool last = it + 1 == ctx->cfg.max_refine;
+                // after the second-order pass X has advanced: its residual first
+                if (it0) TIMED("residual_fp64_refine", residual(di, m, ctx->d_redo));
                 TIMED("band_refine_fp32", launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr, b.maxnmp,
                                                                       stp, ctx->d_redo, ctx->stream));
                 TIMED("residual_fp64_refine", residual(di, m, ctx->d_redo));
@@ -510,7 +543,7 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     if ((cfg->dim == 2) != (cfg->elem == FE2_ELEM_Q4)) return FE2_ERR_ARG;
     if (cfg->precision != FE2_PREC_FP64 && cfg->precision != FE2_PREC_MIXED) return FE2_ERR_ARG;
     if (cfg->max_refine < 0 || cfg->max_refine > 16) return FE2_ERR_ARG;
-    if (cfg->factor_kernel < FE2_FACTOR_AUTO || cfg->factor_kernel > FE2_FACTOR_TENSOR_CORE) return FE2_ERR_ARG;
+    if (cfg->factor_kernel < FE2_FACTOR_AUTO || cfg->factor_kernel > FE2_FACTOR_CUDA_CORE_PIPELINED) return FE2_ERR_ARG;
     if (cfg->macro_basis != FE2_BASIS_DIRAC && cfg->macro_basis != FE2_BASIS_CONST) return FE2_ERR_ARG;
     if (cfg->macro_basis == FE2_BASIS_CONST && cfg->dim != 2) return FE2_ERR_ARG;
     ctx = new fe2_ctx();
@@ -520,8 +553,9 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tol, sizeof(double));
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tol, &ctx->cfg.refine_tol, sizeof(double), cudaMemcpyHostToDevice);
+    const double tols[2] = {ctx->cfg.refine_tol, ctx->cfg.refine_tol * kScreen};
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tol, sizeof(tols));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tol, tols, sizeof(tols), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         delete ctx;
         return FE2_ERR_CUDA;
@@ -1361,7 +1395,7 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
         ++srv->graph_replays;
     }
     CK(cudaGraphLaunch(it->second, s));
-    ctx->launches += fp64 ? 5 : 6 + 3 * ctx->cfg.max_refine;
+    ctx->launches += fp64 ? 5 : 6 + (ctx->cfg.max_refine > 0 ? 2 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
     CK(cudaEventRecord(L.ev, s));
     L.busy = true;
     return FE2_OK;
@@ -1383,6 +1417,8 @@ static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo&
     if (fp64) {
         if (l.gw)
             CK(launch_factor_gw<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        else if (use_la_factor(ctx, b.maxkd, b.maxnr, true))
+            CK(launch_factor_la<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else
             CK(launch_factor<double>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<double>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
@@ -1393,20 +1429,31 @@ static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo&
             CK(launch_factor_gw<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else if (tc)
             CK(launch_factor_tc(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+        else if (use_la_factor(ctx, b.maxkd, b.maxnr, false))
+            CK(launch_factor_la<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else
             CK(launch_factor<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         CK(launch_backward<float>(ctx->d_tab, L.d_ids, n, ws, 0, b.maxkd, b.maxnr, b.maxnmp, L.d_st, s));
         CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, nullptr, s));
         int* redo = ctx->cfg.max_refine > 0 ? L.d_redo : nullptr;
-        CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s,
-                        ctx->cfg.max_refine > 0 ? 0 : 3));
-        for (int it = 0; it < ctx->cfg.max_refine; ++it) {
+        int it0 = 0;
+        if (ctx->cfg.max_refine > 0) {  // screened second-order pass, as in fe2_condense
+            CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol + 1, redo, s, 0));
+            CK(launch_solve_correct<float>(ctx->d_tab, L.d_ids, n, ws, b.maxkd, b.maxnr, b.maxnmp, L.d_st, redo, s, 1));
+            CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 2, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s,
+                            ctx->cfg.max_refine > 1 ? 1 : 2));
+            it0 = 1;
+        } else {
+            CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s, 3));
+        }
+        for (int it = it0; it < ctx->cfg.max_refine; ++it) {
+            CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, L.d_redo, s));
             CK(launch_solve_correct<float>(ctx->d_tab, L.d_ids, n, ws, b.maxkd, b.maxnr, b.maxnmp, L.d_st, L.d_redo, s));
             CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, L.d_redo, s));
             CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, L.d_redo, s,
                             it + 1 == ctx->cfg.max_refine ? 2 : 1));
         }
-        if (record) ctx->launches += 6 + 3 * ctx->cfg.max_refine;
+        if (record) ctx->launches += 6 + (ctx->cfg.max_refine > 0 ? 2 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
     }
     CK(cudaMemcpyAsync(L.h_sig, L.d_sig, sizeof(double) * dd * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(L.h_C, L.d_C, sizeof(double) * dd * dd * n, cudaMemcpyDeviceToHost, s));

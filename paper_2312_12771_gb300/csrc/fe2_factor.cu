@@ -440,6 +440,441 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
 }
 
+// ------------------------------------------------------------ look-ahead factor
+// k_band_factor_la: the band Cholesky of k_band_factor with the panel chain
+// pipelined and the trailing updates taken off it.  Per panel p (columns
+// [j0, j0 + NB)), with U(p) = the rank-NB update of panel p split into U0(p)
+// (the next panel's NB columns) and U1(p) (the columns after them):
+//   B0  all warps apply U0(p-1) to the NB x NB diagonal block of panel p;
+//   B1  warp 0 factors the diagonal block column by column and publishes each
+//       column of L11 (and its reciprocal pivot) behind one mbarrier per
+//       column; the threads owning the panel rows below (L21 and the d^2+1
+//       right-hand-side rows, one row per thread, in registers) consume each
+//       column as soon as it is published, and apply U0(p-1) to their own row
+//       one column ahead of its use (a dot product with the previous panel's
+//       rows), so the panel rows finish a few steps after the diagonal block;
+//       the warps without a panel row fill the entering window columns from
+//       the staged stencil and stage the next ones; then every warp takes
+//       32 x 32 blocks of U1(p-1) from a shared counter until none is left;
+//       finished columns of L, y and the reciprocal diagonal go straight from
+//       registers to HBM;
+//   B2  the panel rows are read back (each thread its own, from HBM/L2) into
+//       the transposed panel Pn used by U0(p) and U1(p).
+// The window ring holds S = kd columns: panel p's columns leave it (into
+// registers) at the start of B1, and their slots receive the columns that
+// U1(p) touches first.
+constexpr int LA_D0T = NB + 4;  // row stride of the transposed diagonal part of Pn (16-byte rows)
+
+template <typename T>
+struct LaLayout {
+    int kd, S, LDW, KR, KP, nr, nblk1, rows, free_warp0;
+    size_t offBw, offPn, offL11, offDinv, offD0T, offBar, offBlk, offStg, offBstg, total;
+    __host__ __device__ void init(int kd_, int nr_) {
+        kd = kd_;
+        nr = nr_;
+        S = kd;
+        LDW = (kd + 2) & ~1;
+        KR = kd + nr;
+        KP = (KR + 31) & ~31;
+        rows = NB + KR;                 // threads that own a panel row
+        free_warp0 = (rows + 31) / 32;  // first warp without one
+        const int RB = KP / 32, CB = (kd + 31) / 32;
+        nblk1 = 0;
+        for (int K = 1; K < CB; ++K) nblk1 += RB - K;
+        size_t o = (size_t)S * LDW * sizeof(T);
+        offBw = o;
+        o += (size_t)nr * S * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offPn = o;
+        o += (size_t)NB * KP * sizeof(T);
+        offL11 = o;
+        o += (size_t)NB * NB * sizeof(T);
+        offDinv = o;
+        o += NB * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offD0T = o;
+        o += (size_t)NB * LA_D0T * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offBar = o;
+        o += (size_t)(NB + 1) * 8;
+        offBlk = o;
+        o += (size_t)(nblk1 + 1) * 4;
+        o = (o + 15) & ~(size_t)15;
+        offStg = o;
+        o += (size_t)STG_COMPS * STG_NODES * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offBstg = o;
+        o += (size_t)nr * NB * sizeof(T);
+        total = (o + 15) & ~(size_t)15;
+    }
+};
+
+// Warp 0: column K of the register-resident Cholesky of the diagonal block
+// (lane = row), as in chol_block_steps, with every scaled column written to
+// its own slot L11[K][.] and published to the panel-row threads by the
+// column's mbarrier (each lane arrives after its own store; lane 0 stores the
+// reciprocal pivot first).
+template <typename T, int K>
+__device__ __forceinline__ void la_producer_steps(T (&a)[NB], int lane, T* __restrict__ L11, T* __restrict__ dinv,
+                                                  uint64_t* bars, int& bad) {
+    if constexpr (K < NB) {
+        T piv = __shfl_sync(0xffffffffu, a[K], K);
+        const bool badk = !(piv > T(0));
+        if (badk) piv = T(1);
+        const T dk = rsqrt(piv);
+        if (lane == K)
+            a[K] = piv * dk;
+        else if (lane > K)
+            a[K] *= dk;
+        bad |= badk;
+        T* col = L11 + K * NB;
+        col[lane] = a[K];
+        if (lane == 0) dinv[K] = dk;
+        mbar_arrive(bars + K);
+        if constexpr (K + 1 < NB) {
+            __syncwarp();
+#pragma unroll
+            for (int g = (K + 1) / 4; g < NB / 4; ++g) {
+                T lc[4];
+                Vec4<T>::load(col + 4 * g, lc);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = 4 * g + u;
+                    if (c >= K + 1 && lane >= c) a[c] -= a[K] * lc[u];
+                }
+            }
+        }
+        la_producer_steps<T, K + 1>(a, lane, L11, dinv, bars, bad);
+    }
+}
+
+// A panel-row thread: step K of the solve of its row v against L11 (L21 and
+// forward elimination y = L^-1 b alike).  With a previous panel (`prev`), the
+// row first receives U0(p-1) in column K: v[K] -= sum_k pr[k] L_prev(j0 + K, k),
+// with pr its own row of the previous panel and D0T[K][.] the previous panel's
+// row j0 + K.
+template <typename T, int K>
+__device__ __forceinline__ void la_consumer_steps(T (&v)[NB], const T (&pr)[NB], const T* __restrict__ D0T,
+                                                  const T* __restrict__ L11, const T* __restrict__ dinv,
+                                                  uint64_t* bars, uint32_t par, bool prev, int& to) {
+    if constexpr (K < NB) {
+        if (prev) {
+            const T* d = D0T + K * LA_D0T;
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+            for (int g = 0; g < NB / 4; ++g) {
+                T q[4];
+                Vec4<T>::load(d + 4 * g, q);
+                s0 += pr[4 * g] * q[0];
+                s1 += pr[4 * g + 1] * q[1];
+                s2 += pr[4 * g + 2] * q[2];
+                s3 += pr[4 * g + 3] * q[3];
+            }
+            v[K] -= (s0 + s1) + (s2 + s3);
+        }
+        if (!to && !mbar_wait_bounded(bars + K, par)) to = 1;
+        v[K] *= dinv[K];
+        const T* Lc = L11 + K * NB;
+#pragma unroll
+        for (int g = (K + 1) / 4; g < NB / 4; ++g) {
+            T lc[4];
+            Vec4<T>::load(Lc + 4 * g, lc);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c = 4 * g + u;
+                if (c >= K + 1) v[c] -= v[K] * lc[u];
+            }
+        }
+        la_consumer_steps<T, K + 1>(v, pr, D0T, L11, dinv, bars, par, prev, to);
+    }
+}
+
+// Block b of U1(p-1) (update_block with the window addressed from `base`, the
+// ring slot of column j0: column j0 + t2 sits in slot base + t2 (mod S)).
+// The operands are the previous panel's rows in Pn; row t1 < kd of Pn is
+// matrix row j0 + t1, rows kd .. KR-1 are the right-hand-side rows.
+template <typename T>
+__device__ __forceinline__ void update_block_la(unsigned bv, const T* __restrict__ Pn, T* __restrict__ W,
+                                                T* __restrict__ Bw, int base, int S, int LDW, int KP, int kd, int KR,
+                                                int lane) {
+    const int rg = lane >> 3, cg = lane & 7;
+    const int I = bv & 0xffff, K = bv >> 16;
+    const int r0 = 32 * I + 8 * rg, q0 = 32 * K + cg;
+    T acc[8][4];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+    for (int c = 0; c < NB; ++c) {
+        const T* pc = Pn + c * KP;
+        T a[8], bb[4];
+        Vec4<T>::load(pc + r0, a);
+        Vec4<T>::load(pc + r0 + 4, a + 4);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + 8 * w];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
+    }
+    if (I > K && r0 + 8 <= kd && q0 + 24 < kd) {
+        T old[4][8];
+        int cb[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int t2 = q0 + 8 * w;
+            cb[w] = wrapS(base + t2, S) * LDW + r0 - t2;
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) old[w][u] = W[cb[w] + u];
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) W[cb[w] + u] = old[w][u] - acc[u][w];
+        return;
+    }
+    const int boff = (int)(Bw - W);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int t2 = q0 + 8 * w;
+        const int slot = wrapS(base + t2, S);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t1 = r0 + u;
+            const int ix = t1 < kd ? slot * LDW + (t1 - t2) : boff + (t1 - kd) * S + slot;
+            if (t2 < kd && t1 >= t2 && t1 < KR) W[ix] -= acc[u][w];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_band_factor_la(const RveDev* __restrict__ tab, const int* __restrict__ ids, Workspace ws,
+                     int* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const RveDev r = tab[ids[blockIdx.x]];
+    LaLayout<T> lay;
+    lay.init(r.kd, r.nr);
+    const int kd = lay.kd, S = lay.S, LDW = lay.LDW, KR = lay.KR, KP = lay.KP, nr = lay.nr;
+    const int nmp = r.nm_pad, nm = r.nm, nn = r.nn, LDL = kd + 1;
+    const int rows = lay.rows, fw0 = lay.free_warp0;
+    T* W = (T*)smem;
+    T* Bw = (T*)(smem + lay.offBw);
+    T* Pn = (T*)(smem + lay.offPn);
+    T* L11 = (T*)(smem + lay.offL11);
+    T* dinv = (T*)(smem + lay.offDinv);
+    T* D0T = (T*)(smem + lay.offD0T);
+    uint64_t* bars = (uint64_t*)(smem + lay.offBar);  // [0, NB): columns of L11; [NB]: panel rows loaded
+    unsigned* blk = (unsigned*)(smem + lay.offBlk);   // U1 block list, then the block counter
+    unsigned* s_next = blk + lay.nblk1;
+    T* Stg = (T*)(smem + lay.offStg);
+    T* Bstg = (T*)(smem + lay.offBstg);
+    __shared__ int s_bad, s_to;
+    T* Lg = (T*)(ws.base + blockIdx.x * ws.stride);
+    T* Yg = (T*)(ws.base + blockIdx.x * ws.stride + ws.offY);
+    T* Dg = (T*)(ws.base + blockIdx.x * ws.stride + ws.offD);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nfill = FACT_THREADS - 32 * fw0;  // threads of the warps without a panel row (>= 32)
+    const double* __restrict__ sten = r.stencil;
+    const int* __restrict__ nbr = r.nbr;
+
+    // ---- init: block list, barriers, zero buffers, first kd columns from HBM
+    if (tid == 0) {
+        s_bad = 0;
+        s_to = 0;
+        const int RB = KP / 32, CB = (kd + 31) / 32;
+        int x = 0;
+        for (int K = 1; K < CB; ++K)
+            for (int I = K; I < RB; ++I) blk[x++] = (unsigned)I | ((unsigned)K << 16);
+        *s_next = 0;
+        for (int k = 0; k < NB; ++k) mbar_init(bars + k, 32);
+        mbar_init(bars + NB, rows);
+        mbar_fence_init();
+    }
+    for (int k = tid; k < NB * KP; k += blockDim.x) Pn[k] = T(0);
+    for (int k = tid; k < S * LDW; k += blockDim.x) W[k] = T(0);
+    for (int k = tid; k < nr * S; k += blockDim.x) {
+        const int rr = k / S, c = k - rr * S;
+        Bw[k] = (c < nm) ? (T)r.rhs[(size_t)rr * nm + c] : T(0);
+    }
+    prefetch_columns<T>(Stg, Bstg, sten, r.rhs, kd, nm, nn, nr, tid, blockDim.x);
+    __syncthreads();
+    for (int c = tid; c < min(kd, nmp); c += blockDim.x) {
+        T* Wc = W + (size_t)c * LDW;
+        if (c < nm) {
+            const int q = c / 2 + 1, cc = c & 1;
+            for (int off = 0; off < 9; ++off) {
+                const int qn = nbr[q * 9 + off];
+                if (qn == 0) continue;
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int row = 2 * (qn - 1) + c2;
+                    if (row >= c) Wc[row - c] = (T)sten[(size_t)((off * 2 + cc) * 2 + c2) * nn + q];
+                }
+            }
+        } else {
+            Wc[0] = T(1);  // padding columns: identity
+        }
+    }
+    __syncthreads();
+
+    int base = 0;  // ring slot of column j0
+    for (int j0 = 0; j0 < nmp; j0 += NB) {
+        const bool prev = j0 > 0;
+        const uint32_t par = (uint32_t)((j0 / NB) & 1);
+        // ---- B0: U0(p-1) on the diagonal block (lower triangle) of panel p
+        if (prev) {
+            for (int e = tid; e < NB * NB; e += blockDim.x) {
+                const int t1 = e >> 5, t2 = e & 31;
+                if (t2 > t1) continue;
+                const T* x1 = D0T + t1 * LA_D0T;
+                const T* x2 = D0T + t2 * LA_D0T;
+                T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+#pragma unroll
+                for (int g = 0; g < NB / 4; ++g) {
+                    T p1[4], p2[4];
+                    Vec4<T>::load(x1 + 4 * g, p1);
+                    Vec4<T>::load(x2 + 4 * g, p2);
+                    s0 += p1[0] * p2[0];
+                    s1 += p1[1] * p2[1];
+                    s2 += p1[2] * p2[2];
+                    s3 += p1[3] * p2[3];
+                }
+                W[(size_t)wrapS(base + t2, S) * LDW + (t1 - t2)] -= (s0 + s1) + (s2 + s3);
+            }
+            __syncthreads();
+        }
+        // ---- B1
+        if (warp == 0) {
+            T a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                a[c] = (c <= lane) ? W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] : T(0);
+            mbar_arrive(bars + NB);
+            int badb = 0;
+            la_producer_steps<T, 0>(a, lane, L11, dinv, bars, badb);
+            if (badb) s_bad = 1;
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c <= lane) Lg[(size_t)(j0 + c) * LDL + (lane - c)] = a[c];
+            Dg[j0 + lane] = dinv[lane];
+        } else if (tid < rows) {
+            T v[NB], pr[NB];
+            const bool mrow = tid < NB + kd;  // a row of L21 (else a right-hand-side row)
+            const int rr = tid - NB - kd;
+            if (mrow) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = tid - c;
+                    v[c] = (off <= kd) ? W[(size_t)wrapS(base + c, S) * LDW + off] : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) v[c] = Bw[rr * S + wrapS(base + c, S)];
+            }
+            // this row in the previous panel: Pn row tid (rows beyond kd - 1 lie outside its band)
+            const int pi = mrow ? (tid < kd ? tid : -1) : kd + rr;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) pr[k] = (prev && pi >= 0) ? Pn[k * KP + pi] : T(0);
+            mbar_arrive(bars + NB);
+            int to = s_to;
+            la_consumer_steps<T, 0>(v, pr, D0T, L11, dinv, bars, par, prev, to);
+            if (to) s_to = 1;
+            if (mrow) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = tid - c;
+                    if (off <= kd) Lg[(size_t)(j0 + c) * LDL + off] = v[c];
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) Yg[(size_t)rr * nmp + j0 + c] = v[c];
+            }
+        } else if (warp >= fw0) {
+            // entering columns j0 + kd + x (slot base + x, freed by panel p's rows) from the staged stencil
+            const int t0 = tid - 32 * fw0;
+            if (!s_to && !mbar_wait_bounded(bars + NB, par)) s_to = 1;
+            const int c0 = j0 + kd;
+            for (int c = warp - fw0; c < NB; c += nfill / 32) {
+                T* Wc = W + (size_t)wrapS(base + c, S) * LDW;
+                for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
+            }
+            bar_sync_named(1, nfill);
+            const int qa = c0 / 2 + 1;
+            for (int p = t0; p < NB * 9; p += nfill) {
+                const int x = p / 9, off = p - 9 * x, cn = c0 + x;
+                T* Wc = W + (size_t)wrapS(base + x, S) * LDW;
+                if (cn < nm) {
+                    const int q = cn / 2 + 1, cc = cn & 1;
+                    const int qn = nbr[q * 9 + off];
+                    if (qn != 0) {
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int row = 2 * (qn - 1) + c2;
+                            if (row >= cn) Wc[row - cn] = Stg[((off * 2 + cc) * 2 + c2) * STG_NODES + (q - qa)];
+                        }
+                    }
+                } else if (cn < nmp && off == 0) {
+                    Wc[0] = T(1);
+                }
+            }
+            for (int p = t0; p < nr * NB; p += nfill) {
+                const int q = p / NB, x = p - q * NB;
+                Bw[q * S + wrapS(base + x, S)] = (c0 + x < nm) ? Bstg[p] : T(0);
+            }
+            bar_sync_named(1, nfill);  // the staged columns are consumed: stage the next ones
+            prefetch_columns<T>(Stg, Bstg, sten, r.rhs, c0 + NB, nm, nn, nr, t0, nfill);
+        }
+        __syncwarp();
+        // U1(p-1), block by block from the shared counter, by every warp
+        if (prev) {
+            for (;;) {
+                unsigned b = 0;
+                if (lane == 0) b = atomicAdd(s_next, 1u);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (b >= (unsigned)lay.nblk1) break;
+                update_block_la<T>(blk[b], Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
+            }
+        }
+        // ---- B2: panel p's rows (read back by their own threads) into Pn and D0T
+        T w2[NB];
+        if (tid >= NB && tid < rows) {
+            if (tid < NB + kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = tid - c;
+                    w2[c] = (off <= kd) ? Lg[(size_t)(j0 + c) * LDL + off] : T(0);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) w2[c] = Yg[(size_t)(tid - NB - kd) * nmp + j0 + c];
+            }
+        }
+        __syncthreads();
+        if (tid >= NB && tid < rows) {
+            const int t = tid - NB;
+#pragma unroll
+            for (int c = 0; c < NB; ++c) Pn[c * KP + t] = w2[c];
+            if (t < NB) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) D0T[t * LA_D0T + c] = w2[c];
+            }
+        }
+        if (tid == 0) *s_next = 0;
+        __syncthreads();
+        base = wrapS(base + NB, S);
+    }
+    if (tid == 0) {
+        if (s_to)
+            status[blockIdx.x] = FE2_ERR_TIMEOUT;
+        else if (s_bad && status[blockIdx.x] == FE2_OK)
+            status[blockIdx.x] = FE2_ERR_NOT_PD;
+    }
+}
+
 // ------------------------------------------------------------------ solves
 // L is read block by block (NB columns = NB*(kd+1) contiguous elements) with
 // double-buffered 1D TMA bulk copies.
@@ -549,7 +984,8 @@ __device__ __forceinline__ void panel_dots(const T* __restrict__ Lb, const T* __
 
 template <typename T, bool WIDE>
 __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout<T>& lay, LStream<T>& ls, int& k0,
-                              T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to) {
+                              T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to,
+                              T* __restrict__ dxout = nullptr) {
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __shared__ T tv[MAX_NR][NB];
@@ -609,7 +1045,9 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
             xr[rr * 2 * S + idx] = xc;
             xr[rr * 2 * S + idx + S] = xc;
             const int row = j0 + lane;
-            if (row < nm) {
+            if (dxout) {
+                dxout[(size_t)rr * nmp + row] = xc;  // the correction itself, X untouched
+            } else if (row < nm) {
                 double* Xp = r.X + (size_t)rr * nm + row;
                 *Xp = accumulate ? (*Xp + (double)xc) : (double)xc;
             }
@@ -641,12 +1079,13 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
         status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
-// Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx.
+// Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx (or dx
+// written to the slot's y region, to_y).
 template <typename T, bool WIDE>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDev* __restrict__ tab,
                                                                      const int* __restrict__ ids, Workspace ws,
                                                                      int* __restrict__ status,
-                                                                     const int* __restrict__ active) {
+                                                                     const int* __restrict__ active, int to_y) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_to;
     if (active && !active[blockIdx.x]) return;
@@ -712,7 +1151,10 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
         jb = wrapS(jb + NB, S);
     }
     int k0 = nblk;
-    if (!backward_pass<T, WIDE>(r, lay, ls, k0, bw, ys, 1, &s_to) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
+    // to_y: dx goes to the slot's y region in global memory (free once y sits in shared
+    // memory) for the second-order corrected Schur complement; else X += dx
+    T* dxg = to_y ? (T*)(ws.base + blockIdx.x * ws.stride + ws.offY) : nullptr;
+    if (!backward_pass<T, WIDE>(r, lay, ls, k0, bw, ys, 1, &s_to, dxg) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
 // FP64 residual R = [K_mM | r_m] - K_mm X from the node-row stencil.
@@ -769,6 +1211,33 @@ cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws
     return cudaGetLastError();
 }
 
+bool factor_la_eligible(int kd, int nr, bool fp64, int max_smem) {
+    if (kd < NB) return false;
+    size_t total;
+    int rows;
+    if (fp64) {
+        LaLayout<double> l;
+        l.init(kd, nr);
+        total = l.total, rows = l.rows;
+    } else {
+        LaLayout<float> l;
+        l.init(kd, nr);
+        total = l.total, rows = l.rows;
+    }
+    return rows <= FACT_THREADS - 32 && (int)total <= max_smem;
+}
+
+template <typename T>
+cudaError_t launch_factor_la(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                             int maxnr, cudaStream_t s) {
+    LaLayout<T> lay;
+    lay.init(maxkd, maxnr);
+    cudaError_t e = set_smem(k_band_factor_la<T>, lay.total);
+    if (e != cudaSuccess) return e;
+    k_band_factor_la<T><<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate, int maxkd,
                             int maxnr, int maxnm_pad, int* status, cudaStream_t s) {
@@ -783,13 +1252,13 @@ cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace 
 
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd, int maxnr,
-                                 int maxnm_pad, int* status, const int* active, cudaStream_t s) {
+                                 int maxnm_pad, int* status, const int* active, cudaStream_t s, int to_y) {
     SolveLayout<T> lay;
     lay.init(maxkd, maxnr, maxnm_pad, true);
     auto kern = maxkd > BW_WIDE ? k_band_solve_correct<T, true> : k_band_solve_correct<T, false>;
     cudaError_t e = set_smem(kern, lay.total);
     if (e != cudaSuccess) return e;
-    kern<<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status, active);
+    kern<<<n, FACT_THREADS, lay.total, s>>>(tab, ids, ws, status, active, to_y);
     return cudaGetLastError();
 }
 
@@ -823,14 +1292,16 @@ size_t factor_smem_bytes(int kd, int nr, bool fp64) {
 }
 
 template cudaError_t launch_factor<float>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
+template cudaError_t launch_factor_la<float>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
+template cudaError_t launch_factor_la<double>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
 template cudaError_t launch_factor<double>(const RveDev*, const int*, int, Workspace, int*, int, int, cudaStream_t);
 template cudaError_t launch_backward<float>(const RveDev*, const int*, int, Workspace, int, int, int, int, int*,
                                             cudaStream_t);
 template cudaError_t launch_backward<double>(const RveDev*, const int*, int, Workspace, int, int, int, int, int*,
                                              cudaStream_t);
 template cudaError_t launch_solve_correct<float>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
-                                                 const int*, cudaStream_t);
+                                                 const int*, cudaStream_t, int);
 template cudaError_t launch_solve_correct<double>(const RveDev*, const int*, int, Workspace, int, int, int, int*,
-                                                  const int*, cudaStream_t);
+                                                  const int*, cudaStream_t, int);
 
 }  // namespace fe2

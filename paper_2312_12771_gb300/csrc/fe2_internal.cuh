@@ -71,6 +71,11 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
 template <typename T>
 cudaError_t launch_factor(const RveDev* tab, const int* ids, int n, Workspace ws, int* status,
                           int maxkd, int maxnr, cudaStream_t s);
+// look-ahead band factor (pipelined panel chain, U1 blocks off the chain)
+bool factor_la_eligible(int kd, int nr, bool fp64, int max_smem);
+template <typename T>
+cudaError_t launch_factor_la(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                             int maxnr, cudaStream_t s);
 // tensor-core FP32 band factor (2D): eligibility, shared memory, launch
 bool factor_tc_eligible(int kd, int nr, int d, int max_smem);
 size_t factor_tc_smem_bytes(int kd, int nr);
@@ -81,12 +86,17 @@ cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace 
                             int maxkd, int maxnr, int maxnm_pad, int* status, cudaStream_t s);
 template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd,
-                                 int maxnr, int maxnm_pad, int* status, const int* active, cudaStream_t s);
-// `active` (may be null): only slots with active[slot] != 0 do work
+                                 int maxnr, int maxnm_pad, int* status, const int* active, cudaStream_t s,
+                                 int to_y = 0);
+// `active` (may be null): only slots with active[slot] != 0 do work; to_y: the
+// correction dx is written (FP32) to the slot's y region instead of added to X
 cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace ws, int maxnn,
                             const int* active, cudaStream_t s);
 // Schur complement; with `redo` != null, redo[i] = 1 marks RVEs whose error
 // estimate exceeds *tol (device scalar) for another refinement sweep.
+// corrected: 0 = plain (FP64 path), 1 = first-order residual correction,
+// 2 = second-order correction with the FP32 correction dx in the y region
+// (X is advanced to X + dx); 2 is available for 2D and 3D Dirac-basis RVEs.
 cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected,
                          double* sigma, double* Cbar, int* status, double* err, const double* tol,
                          int* redo, cudaStream_t s, int refine_sweep = 0);

@@ -306,17 +306,33 @@ __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, 
                                                 double* __restrict__ err, const double* __restrict__ tol,
                                                 int* __restrict__ redo, int only_flagged, int final_sweep) {
     __shared__ double red[256];
-    __shared__ double tot[180];
+    __shared__ double tot[183];
     if (only_flagged && !redo[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
-    const int nm = r.nm;
+    const int nm = r.nm, nmp = r.nm_pad;
     const double* R = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
-    for (int v = 0; v < (corrected ? 180 : 90); ++v) {
+    // corrected = 2: the FP32 correction dx of every column in the slot's y region;
+    // the correction term uses X' = X + dx (as in the 2D kernel), X' is stored
+    const float* dX = (const float*)(ws.base + blockIdx.x * ws.stride + ws.offY);
+    const int nv = corrected == 2 ? 183 : (corrected ? 180 : 90);
+    for (int v = 0; v < nv; ++v) {
         const int which = v / 90, a = (v % 90) / 10, b = v % 10;
         double acc = 0.0;
-        for (int m = threadIdx.x; m < nm; m += blockDim.x)
-            acc += which == 0 ? r.rhs[(size_t)a * nm + m] * r.X[(size_t)b * nm + m]
-                              : r.X[(size_t)a * nm + m] * R[(size_t)b * nm + m];
+        for (int m = threadIdx.x; m < nm; m += blockDim.x) {
+            if (v >= 180) {
+                for (int c = 0; c < 9; ++c) {
+                    const double dx = (double)dX[(size_t)c * nmp + m];
+                    const double x = r.X[(size_t)c * nm + m];
+                    acc += v == 180 ? dx * R[(size_t)c * nm + m] : (v == 181 ? dx * dx : x * x);
+                }
+            } else if (which == 0) {
+                acc += r.rhs[(size_t)a * nm + m] * r.X[(size_t)b * nm + m];
+            } else {
+                double xa = r.X[(size_t)a * nm + m];
+                if (corrected == 2) xa += (double)dX[(size_t)a * nmp + m];
+                acc += xa * R[(size_t)b * nm + m];
+            }
+        }
         red[threadIdx.x] = acc;
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -326,6 +342,11 @@ __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, 
         if (threadIdx.x == 0) tot[v] = red[0];
         __syncthreads();
     }
+    if (corrected == 2)
+        for (int k = threadIdx.x; k < 10 * nm; k += blockDim.x) {
+            const int c = k / nm, m = k - c * nm;
+            r.X[k] += (double)dX[(size_t)c * nmp + m];
+        }
     if (threadIdx.x == 0) {
         double cn = 0.0, corr = 0.0;
         int bad = 0;
@@ -345,7 +366,9 @@ __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, 
             bad |= !isfinite(sg);
             sigma[(size_t)blockIdx.x * 9 + a] = sg;
         }
-        const double e = corrected ? corr / fmax(cn, 1e-300) : 0.0;
+        double e = 0.0;
+        if (corrected == 1) e = corr / fmax(cn, 1e-300);
+        if (corrected == 2) e = fabs(tot[180]) / sqrt(fmax(cn, 1e-300)) * sqrt(tot[181] / fmax(tot[182], 1e-300));
         if (err) err[blockIdx.x] = e;
         if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
         const bool over = corrected && !(e <= *tol);

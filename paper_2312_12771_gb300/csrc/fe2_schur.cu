@@ -39,23 +39,31 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*
 }
 
 // One CTA per RVE (2D: d^2 = 4, nr = 5).  G1 = rhs^T X (4 x 5), G2 = X_M^T R (4 x 5).
+// corrected = 2 (second order): dx = (L L^T)^-1 R from the FP32 factor sits in
+// the slot's y region; with X' = X + dx,
+//   Cbar = K_MM - K_Mm X - X'_M^T R_M,  sigma = Pint - K_Mm x_r - X'_M^T r_x,
+// which is the exact Schur complement up to (dx - K_mm^-1 R)^T R, a term of
+// the order of the FP32 solve's relative error times the second-order term
+// dx^T R; X' is stored.  The estimate |tr(dx_M^T R_M)| / ||Cbar|| *
+// ||dx_M|| / ||X_M|| is that product.
 __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
                                                 Workspace ws, int corrected, double* __restrict__ sigma,
                                                 double* __restrict__ Cbar, int* __restrict__ status,
                                                 double* __restrict__ err, const double* __restrict__ tol,
                                                 int* __restrict__ redo, int only_flagged, int final_sweep) {
-    __shared__ double red[40 * 33];
+    __shared__ double red[43 * 33];
     if (only_flagged && !redo[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
-    const int nm = r.nm;
+    const int nm = r.nm, nmp = r.nm_pad;
     const double* __restrict__ R = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
+    const float* __restrict__ dX = (const float*)(ws.base + blockIdx.x * ws.stride + ws.offY);
     const double* __restrict__ B = r.rhs;
-    const double* __restrict__ X = r.X;
-    double acc[40];
+    double* __restrict__ X = r.X;
+    double acc[43];
 #pragma unroll
-    for (int k = 0; k < 40; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 43; ++k) acc[k] = 0.0;
     for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-        double b[4], x[5], rr[5];
+        double b[4], x[5], xn[5], rr[5];
 #pragma unroll
         for (int a = 0; a < 4; ++a) b[a] = B[(size_t)a * nm + m];
 #pragma unroll
@@ -67,15 +75,31 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
 #pragma unroll
             for (int c = 0; c < 5; ++c) rr[c] = 0.0;
         }
+        if (corrected == 2) {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const double dx = (double)dX[(size_t)c * nmp + m];
+                xn[c] = x[c] + dx;
+                if (c < 4) {
+                    acc[40] += dx * rr[c];
+                    acc[41] += dx * dx;
+                    acc[42] += x[c] * x[c];
+                }
+                X[(size_t)c * nm + m] = xn[c];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 5; ++c) xn[c] = x[c];
+        }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 acc[a * 5 + c] += b[a] * x[c];
-                acc[20 + a * 5 + c] += x[a] * rr[c];
+                acc[20 + a * 5 + c] += xn[a] * rr[c];
             }
     }
-    cta_sum<40>(acc, red);
+    cta_sum<43>(acc, red);
     if (threadIdx.x == 0) {
         double cn = 0.0, corr = 0.0;
         int bad = 0;
@@ -95,8 +119,12 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
             bad |= !isfinite(sg);
             sigma[(size_t)blockIdx.x * 4 + a] = sg;
         }
-        // (first-order term)^2 / |Cbar|^2 estimates the error left after the correction
-        const double e = corrected ? corr / fmax(cn, 1e-300) : 0.0;
+        // first order: (first-order term)^2 / |Cbar|^2; second order: the size of the
+        // second-order term times the relative size of the FP32 correction
+        double e = 0.0;
+        if (corrected == 1) e = corr / fmax(cn, 1e-300);
+        if (corrected == 2)
+            e = fabs(acc[40]) / sqrt(fmax(cn, 1e-300)) * sqrt(acc[41] / fmax(acc[42], 1e-300));
         if (err) err[blockIdx.x] = e;
         if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
         const bool over = corrected && !(e <= *tol);

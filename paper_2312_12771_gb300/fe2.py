@@ -22,8 +22,9 @@ FE2_OK, FE2_ERR_ARG, FE2_ERR_CUDA, FE2_ERR_BUDGET = 0, 1, 2, 3
 FE2_ERR_NOT_PD, FE2_ERR_NAN, FE2_ERR_NO_CONV, FE2_ERR_TIMEOUT = 4, 5, 6, 7
 FE2_ELEM_Q4, FE2_ELEM_HEX8 = 0, 1
 FE2_PREC_FP64, FE2_PREC_MIXED = 0, 1
-FE2_FACTOR_AUTO, FE2_FACTOR_CUDA_CORE, FE2_FACTOR_TENSOR_CORE = 0, 1, 2
-FACTOR_KERNELS = {"auto": FE2_FACTOR_AUTO, "cuda_core": FE2_FACTOR_CUDA_CORE, "tensor_core": FE2_FACTOR_TENSOR_CORE}
+FE2_FACTOR_AUTO, FE2_FACTOR_CUDA_CORE, FE2_FACTOR_TENSOR_CORE, FE2_FACTOR_CUDA_CORE_PIPELINED = 0, 1, 2, 3
+FACTOR_KERNELS = {"auto": FE2_FACTOR_AUTO, "cuda_core": FE2_FACTOR_CUDA_CORE, "tensor_core": FE2_FACTOR_TENSOR_CORE,
+                  "cuda_core_pipelined": FE2_FACTOR_CUDA_CORE_PIPELINED}
 FE2_BASIS_DIRAC, FE2_BASIS_CONST = 0, 1
 MACRO_BASES = {"dirac": FE2_BASIS_DIRAC, "const": FE2_BASIS_CONST}
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_BUDGET", 4: "NOT_PD", 5: "NAN",
@@ -183,7 +184,7 @@ def rve_solve_noalloc(N, phase, mat, Fbar, out, stream=None):
 class Fe2Context:
     """A libfe2 context on the current CUDA device and stream."""
 
-    def __init__(self, dim=2, precision="mixed", hbm_budget_bytes=0, refine_tol=1e-10, max_refine=1,
+    def __init__(self, dim=2, precision="mixed", hbm_budget_bytes=0, refine_tol=1e-10, max_refine=2,
                  stream=None, factor="auto", basis="dirac"):
         import torch
         if not torch.cuda.is_available():
