@@ -48,8 +48,7 @@ FACTOR_TRAFFIC_PER_RVE = {"sha1": "48f254217286", "bytes": (113871104 + 28824780
 # launches whose work depends on how many RVEs the error estimate flags for an
 # FP64-residual refinement sweep; their algorithmic work per launch is not known
 # to the bench, so no roofline is reported for them
-DATA_DEPENDENT = ("band_refine_fp32", "residual_fp64_refine", "schur_refine", "band_correct_fp32",
-                  "schur_second_order")
+DATA_DEPENDENT = ("band_refine_fp32", "residual_fp64_refine", "schur_refine")
 
 
 def sm_count():

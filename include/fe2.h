@@ -106,14 +106,17 @@ typedef struct {
 /* Mixed-path accuracy (Section 4.2 with an FP32 factor): sigma_eff and Cbar
  * come from the Schur complement corrected with the FP64 residual R of the
  * FP32 solve, whose error is second order in the solve error.  With
- * max_refine >= 1 every RVE whose first-order estimate exceeds 1e-4 refine_tol
- * also gets dX = (L L^T)^-1 R from the FP32 factor and the second-order
- * correction (the remaining error is the FP32 solve's relative error times the
- * second-order term); each further sweep (up to max_refine in all) refines the
- * RVEs whose estimate still exceeds refine_tol (X += dX, new FP64 residual).
- * An RVE still above refine_tol after the last sweep gets FE2_ERR_NO_CONV.
- * With max_refine = 0 only the first-order correction runs (its estimate can
- * understate the error of high-contrast RVEs several hundredfold). */
+ * max_refine >= 1 every RVE (Dirac basis) also gets one refinement step,
+ * dX = (L L^T)^-1 R from the FP32 factor, and the second-order correction
+ * Cbar = K_MM - K_Mm X - (X + dX)_M^T R_M (sigma_eff alike, X advanced to
+ * X + dX): the remaining error is the FP32 solve's relative error times the
+ * second-order term.  Each further sweep (up to max_refine in all) refines the
+ * RVEs whose estimate still exceeds refine_tol (X += dX, new FP64 residual);
+ * element RVEs take every sweep this way.  An RVE still above refine_tol after
+ * the last sweep gets FE2_ERR_NO_CONV.  With max_refine = 0 only the
+ * first-order correction runs; its error estimate can understate the error of
+ * high-contrast RVEs by four orders of magnitude (measured on Neo-Hooke
+ * inclusion RVEs of 32^2 and 48^2: errors up to 1e-7). */
 
 /* Create a context on the current CUDA device.  Allocates nothing large. */
 fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out);

@@ -65,8 +65,7 @@ struct fe2_ctx {
     size_t status_tmp_n = 0;
     int* d_redo = nullptr;          // per-slot "refine again" flags of the mixed path
     size_t redo_n = 0;
-    double* d_tol = nullptr;        // device copy of cfg.refine_tol, then the screening threshold
-                                    // of the second-order correction (refine_tol * kScreen)
+    double* d_tol = nullptr;        // device copy of cfg.refine_tol
     // id-list cache
     std::vector<IdList> idcache;
     unsigned long long tick = 0;
@@ -89,12 +88,6 @@ struct fe2_ctx {
     std::vector<void*> macro_bufs;  // device buffers owned by the macro problem
     int* d_macro_status = nullptr;
 };
-
-// The first-order estimate of the residual-corrected Schur complement can
-// understate its error by a factor of several hundred on high-contrast RVEs
-// (measured on GB300: 400 at N = 48); every RVE whose first-order estimate
-// exceeds refine_tol * kScreen therefore gets the second-order correction.
-constexpr double kScreen = 1e-4;
 
 static fe2_status fail(fe2_ctx* c, fe2_status s, const char* fmt, ...) {
     char buf[512];
@@ -493,17 +486,14 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
             TIMED("band_backward_fp32",
                   launch_backward<float>(ctx->d_tab, di, m, ws, 0, b.maxkd, b.maxnr, b.maxnmp, stp, ctx->stream));
             TIMED("residual_fp64", residual(di, m, nullptr));
-            // Dirac-basis RVEs: every RVE whose first-order estimate exceeds
-            // refine_tol * kScreen gets the correction dx from the FP32 factor and
-            // the second-order corrected Schur complement; further sweeps, and every
+            // Dirac-basis RVEs: every RVE gets the correction dx from the FP32 factor
+            // and the second-order corrected Schur complement; further sweeps, and every
             // sweep of element RVEs, go to the RVEs whose estimate exceeds refine_tol
             int it0 = 0;
             if (!elem && ctx->cfg.max_refine > 0) {
-                TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol + 1, redo, 0));
                 TIMED("band_correct_fp32", launch_solve_correct<float>(ctx->d_tab, di, m, ws, b.maxkd, b.maxnr,
-                                                                       b.maxnmp, stp, redo, ctx->stream, 1));
-                TIMED("schur_second_order", schur(di, m, 2, sg, cb, stp, er, ctx->d_tol, redo,
-                                                  ctx->cfg.max_refine > 1 ? 1 : 2));
+                                                                       b.maxnmp, stp, nullptr, ctx->stream, 1));
+                TIMED("schur", schur(di, m, 2, sg, cb, stp, er, ctx->d_tol, redo, ctx->cfg.max_refine > 1 ? 0 : 3));
                 it0 = 1;
             } else {
                 TIMED("schur", schur(di, m, 1, sg, cb, stp, er, ctx->d_tol, redo, ctx->cfg.max_refine > 0 ? 0 : 3));
@@ -553,9 +543,8 @@ fe2_status fe2_create(const fe2_config* cfg, fe2_ctx** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const double tols[2] = {ctx->cfg.refine_tol, ctx->cfg.refine_tol * kScreen};
-    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tol, sizeof(tols));
-    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tol, tols, sizeof(tols), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_tol, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(ctx->d_tol, &ctx->cfg.refine_tol, sizeof(double), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         delete ctx;
         return FE2_ERR_CUDA;
@@ -1395,7 +1384,7 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
         ++srv->graph_replays;
     }
     CK(cudaGraphLaunch(it->second, s));
-    ctx->launches += fp64 ? 5 : 6 + (ctx->cfg.max_refine > 0 ? 2 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
+    ctx->launches += fp64 ? 5 : 6 + (ctx->cfg.max_refine > 0 ? 1 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
     CK(cudaEventRecord(L.ev, s));
     L.busy = true;
     return FE2_OK;
@@ -1437,11 +1426,11 @@ static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo&
         CK(launch_residual(ctx->d_tab, L.d_ids, n, ws, b.maxnn, nullptr, s));
         int* redo = ctx->cfg.max_refine > 0 ? L.d_redo : nullptr;
         int it0 = 0;
-        if (ctx->cfg.max_refine > 0) {  // screened second-order pass, as in fe2_condense
-            CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol + 1, redo, s, 0));
-            CK(launch_solve_correct<float>(ctx->d_tab, L.d_ids, n, ws, b.maxkd, b.maxnr, b.maxnmp, L.d_st, redo, s, 1));
+        if (ctx->cfg.max_refine > 0) {  // second-order pass over every RVE, as in fe2_condense
+            CK(launch_solve_correct<float>(ctx->d_tab, L.d_ids, n, ws, b.maxkd, b.maxnr, b.maxnmp, L.d_st, nullptr, s,
+                                           1));
             CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 2, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s,
-                            ctx->cfg.max_refine > 1 ? 1 : 2));
+                            ctx->cfg.max_refine > 1 ? 0 : 3));
             it0 = 1;
         } else {
             CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, redo, s, 3));
@@ -1453,7 +1442,7 @@ static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo&
             CK(launch_schur(ctx->d_tab, L.d_ids, n, ws, 1, L.d_sig, L.d_C, L.d_st, L.d_err, ctx->d_tol, L.d_redo, s,
                             it + 1 == ctx->cfg.max_refine ? 2 : 1));
         }
-        if (record) ctx->launches += 6 + (ctx->cfg.max_refine > 0 ? 2 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
+        if (record) ctx->launches += 6 + (ctx->cfg.max_refine > 0 ? 1 : 0) + 4 * std::max(0, ctx->cfg.max_refine - 1);
     }
     CK(cudaMemcpyAsync(L.h_sig, L.d_sig, sizeof(double) * dd * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(L.h_C, L.d_C, sizeof(double) * dd * dd * n, cudaMemcpyDeviceToHost, s));

@@ -1079,6 +1079,31 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
         status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
+constexpr int YT_LD = MAX_NR + 3;  // row stride of the per-block y copy (20: 16-byte rows in FP32)
+
+// Forward solve, rows below the current block: bw(i) -= sum_c L(i, c) y_c for the
+// NRT (>= nr) right-hand sides, one thread per row, every L entry read once.
+template <typename T, int NRT>
+__device__ __forceinline__ void fwd_rows_below(const T* __restrict__ Lb, const T* __restrict__ yt, T* __restrict__ bw,
+                                               int kd, int LDL, int S, int jb, int nr) {
+    for (int t = threadIdx.x; t < kd; t += blockDim.x) {
+        T s[NRT];
+#pragma unroll
+        for (int rr = 0; rr < NRT; ++rr) s[rr] = T(0);
+        for (int c = max(0, NB + t - kd); c < NB; ++c) {
+            const T l = Lb[c * LDL + (NB + t - c)];
+            const T* yc = yt + c * YT_LD;
+#pragma unroll
+            for (int rr = 0; rr < NRT; ++rr) s[rr] += l * yc[rr];
+        }
+        int idx = jb + NB + t;
+        idx = idx >= 2 * S ? idx - 2 * S : (idx >= S ? idx - S : idx);
+#pragma unroll
+        for (int rr = 0; rr < NRT; ++rr)
+            if (rr < nr) bw[rr * S + idx] -= s[rr];
+    }
+}
+
 // Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx (or dx
 // written to the slot's y region, to_y).
 template <typename T, bool WIDE>
@@ -1099,12 +1124,14 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
             (const T*)(ws.base + blockIdx.x * ws.stride + ws.offD));
     T* bw = (T*)(smem + lay.offX);   // ring [nr][S] of pending right-hand-side rows
     T* ys = (T*)(smem + lay.offY);
+    __shared__ __align__(16) T yt[NB * YT_LD];  // y of the current block, [column][right-hand side]
     const double* Rg = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = tid; k < nr * S; k += blockDim.x) {
         const int rr = k / S, row = k - rr * S;
         bw[k] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
     }
+    for (int k = tid; k < NB * YT_LD; k += blockDim.x) yt[k] = T(0);
     const int nblk = nmp / NB;
     ls.issue(0, 0);
     __syncthreads();
@@ -1130,18 +1157,17 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
                 if (lane > c && lane - c <= kd) bv -= Lb[c * LDL + (lane - c)] * yv;
             }
             ys[(size_t)rr * nmp + j0 + lane] = yc;
+            yt[lane * YT_LD + rr] = yc;
         }
         __syncthreads();
-        // rows below the block: b_i -= sum_c L(i, c) y_c ; refill the freed ring rows
-        for (int k = tid; k < nr * kd; k += blockDim.x) {
-            const int rr = k / kd, t = k - rr * kd;
-            const T* yb = ys + (size_t)rr * nmp + j0;
-            T s = T(0);
-            for (int c = max(0, NB + t - kd); c < NB; ++c) s += Lb[c * LDL + (NB + t - c)] * yb[c];
-            int idx = jb + NB + t;
-            idx = idx >= 2 * S ? idx - 2 * S : (idx >= S ? idx - S : idx);
-            bw[rr * S + idx] -= s;
-        }
+        // rows below the block: b_i -= sum_c L(i, c) y_c, one thread per row i for every
+        // right-hand side (each L entry loaded once); refill the freed ring rows
+        if (nr <= 5)
+            fwd_rows_below<T, 5>(Lb, yt, bw, kd, LDL, S, jb, nr);
+        else if (nr <= 10)
+            fwd_rows_below<T, 10>(Lb, yt, bw, kd, LDL, S, jb, nr);
+        else
+            fwd_rows_below<T, MAX_NR>(Lb, yt, bw, kd, LDL, S, jb, nr);
         for (int k = tid; k < nr * NB; k += blockDim.x) {
             const int rr = k / NB, c = k - rr * NB;
             const int row = j0 + S + c;
@@ -1273,11 +1299,11 @@ size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64) {
     if (fp64) {
         SolveLayout<double> l;
         l.init(kd, nr, nmp, true);
-        return l.total + MAX_NR * NB * sizeof(double);
+        return l.total + (MAX_NR + YT_LD) * NB * sizeof(double);
     }
     SolveLayout<float> l;
     l.init(kd, nr, nmp, true);
-    return l.total + MAX_NR * NB * sizeof(float);
+    return l.total + (MAX_NR + YT_LD) * NB * sizeof(float);
 }
 
 size_t factor_smem_bytes(int kd, int nr, bool fp64) {

@@ -46,12 +46,14 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*
 // the order of the FP32 solve's relative error times the second-order term
 // dx^T R; X' is stored.  The estimate |tr(dx_M^T R_M)| / ||Cbar|| *
 // ||dx_M|| / ||X_M|| is that product.
+template <int SECOND>
 __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
                                                 Workspace ws, int corrected, double* __restrict__ sigma,
                                                 double* __restrict__ Cbar, int* __restrict__ status,
                                                 double* __restrict__ err, const double* __restrict__ tol,
                                                 int* __restrict__ redo, int only_flagged, int final_sweep) {
-    __shared__ double red[43 * 33];
+    constexpr int NA = SECOND ? 43 : 40;
+    __shared__ double red[NA * 33];
     if (only_flagged && !redo[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
     const int nm = r.nm, nmp = r.nm_pad;
@@ -59,9 +61,9 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
     const float* __restrict__ dX = (const float*)(ws.base + blockIdx.x * ws.stride + ws.offY);
     const double* __restrict__ B = r.rhs;
     double* __restrict__ X = r.X;
-    double acc[43];
+    double acc[NA];
 #pragma unroll
-    for (int k = 0; k < 43; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
     for (int m = threadIdx.x; m < nm; m += blockDim.x) {
         double b[4], x[5], xn[5], rr[5];
 #pragma unroll
@@ -75,15 +77,15 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
 #pragma unroll
             for (int c = 0; c < 5; ++c) rr[c] = 0.0;
         }
-        if (corrected == 2) {
+        if constexpr (SECOND) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 const double dx = (double)dX[(size_t)c * nmp + m];
                 xn[c] = x[c] + dx;
                 if (c < 4) {
-                    acc[40] += dx * rr[c];
-                    acc[41] += dx * dx;
-                    acc[42] += x[c] * x[c];
+                    acc[NA - 3] += dx * rr[c];
+                    acc[NA - 2] += dx * dx;
+                    acc[NA - 1] += x[c] * x[c];
                 }
                 X[(size_t)c * nm + m] = xn[c];
             }
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
                 acc[20 + a * 5 + c] += xn[a] * rr[c];
             }
     }
-    cta_sum<43>(acc, red);
+    cta_sum<NA>(acc, red);
     if (threadIdx.x == 0) {
         double cn = 0.0, corr = 0.0;
         int bad = 0;
@@ -123,8 +125,8 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
         // second-order term times the relative size of the FP32 correction
         double e = 0.0;
         if (corrected == 1) e = corr / fmax(cn, 1e-300);
-        if (corrected == 2)
-            e = fabs(acc[40]) / sqrt(fmax(cn, 1e-300)) * sqrt(acc[41] / fmax(acc[42], 1e-300));
+        if constexpr (SECOND)
+            e = fabs(acc[NA - 3]) / sqrt(fmax(cn, 1e-300)) * sqrt(acc[NA - 2] / fmax(acc[NA - 1], 1e-300));
         if (err) err[blockIdx.x] = e;
         if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
         const bool over = corrected && !(e <= *tol);
@@ -155,8 +157,9 @@ cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws,
     // refine_sweep: 0 = first pass over all RVEs; 1 = flagged RVEs only (after a
     // refinement sweep); 2 = flagged only, last allowed sweep; 3 = all RVEs, no
     // sweep allowed.  On the last pass an estimate above *tol sets FE2_ERR_NO_CONV.
-    k_schur2<<<n, 256, 0, s>>>(tab, ids, ws, corrected, sigma, Cbar, status, err, tol, redo,
-                               refine_sweep == 1 || refine_sweep == 2, refine_sweep >= 2);
+    auto kern = corrected == 2 ? k_schur2<1> : k_schur2<0>;
+    kern<<<n, 256, 0, s>>>(tab, ids, ws, corrected, sigma, Cbar, status, err, tol, redo,
+                           refine_sweep == 1 || refine_sweep == 2, refine_sweep >= 2);
     return cudaGetLastError();
 }
 
