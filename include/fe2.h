@@ -255,6 +255,32 @@ fe2_status fe2_macro_residual(fe2_ctx* ctx, const double* stress, double* rnorm)
  * FE2_ERR_NOT_PD if the macro tangent had a non-positive pivot. */
 fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* dFbar, double* rnorm,
                            int* status);
+/*
+ * The same macro update in steps, for a macro Newton whose RVEs are spread
+ * over several processes (one GPU each; paper Section 4.1: L is block diagonal
+ * over the macro Gauss points, so only the macro system couples them).  Each
+ * process assembles the contributions of its own Gauss points (the rows of
+ * sigma / Cbar of the others set to zero), the processes sum K and R (e.g. one
+ * NCCL all-reduce of each buffer), and every process solves the same reduced
+ * system, so all keep the same nodal positions.
+ *
+ * fe2_macro_system_size [host out]: free DOFs nfree and half bandwidth kd.
+ * fe2_macro_assemble: K [device] double[nfree][kd+1] (lower band, column-
+ *   major, caller-owned; overwritten) and R [device] double[nfree] from sigma
+ *   [device] double[2^d nelem][d][d] and Cbar (layout as fe2_macro_solve);
+ *   Cbar = NULL assembles R only (K untouched, may be NULL).  R includes the
+ *   current external load (-fext), so exactly one process should hold a load.
+ * fe2_macro_norm: rnorm [device] double[1] = ||R||_2 of a (summed) R.
+ * fe2_macro_solve_assembled: rnorm = ||R||, factorise K in place (blocked FP64
+ *   band Cholesky, K becomes its factor, R the solution), dq = -K^-1 R,
+ *   q += dq, dFbar [device] double[2^d nelem][d][d] = B_b dq, status as in
+ *   fe2_macro_solve.  fe2_macro_assemble + fe2_macro_solve_assembled on one
+ *   process equals fe2_macro_solve bit for bit.
+ */
+fe2_status fe2_macro_system_size(const fe2_ctx* ctx, int* nfree, int* kd);
+fe2_status fe2_macro_assemble(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* K, double* R);
+fe2_status fe2_macro_norm(fe2_ctx* ctx, const double* R, double* rnorm);
+fe2_status fe2_macro_solve_assembled(fe2_ctx* ctx, double* K, double* R, double* dFbar, double* rnorm, int* status);
 /* Volume-averaged stress Pbar = Pint / |Omega| (Section 2.2, Eq. (averageStress))
  * of each RVE at its last assembly: Pbar [device] double[n][d*d]. */
 fe2_status fe2_rve_average_stress(fe2_ctx* ctx, int n, const int* rve_ids, double* Pbar);

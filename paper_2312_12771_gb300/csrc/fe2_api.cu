@@ -1212,6 +1212,50 @@ fe2_status fe2_macro_solve(fe2_ctx* ctx, const double* sigma, const double* Cbar
     return FE2_OK;
 }
 
+fe2_status fe2_macro_system_size(const fe2_ctx* ctx, int* nfree, int* kd) {
+    if (!ctx || !ctx->macro_ready || !nfree || !kd) return FE2_ERR_ARG;
+    *nfree = ctx->macro.nfree;
+    *kd = ctx->macro.kd;
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_assemble(fe2_ctx* ctx, const double* sigma, const double* Cbar, double* K, double* R) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !sigma || !R || (Cbar && !K))
+        return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    MacroDev M = ctx->macro;
+    M.K = K;
+    M.R = R;
+    TIMED("macro_assemble", launch_macro_assemble_only(M, sigma, Cbar, nq_of(ctx) > 1, ctx->stream));
+    ctx->launches += 1;
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_norm(fe2_ctx* ctx, const double* R, double* rnorm) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !R || !rnorm) return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    MacroDev M = ctx->macro;
+    M.R = const_cast<double*>(R);
+    TIMED("macro_norm", launch_macro_norm(M, rnorm, ctx->stream));
+    ctx->launches += 1;
+    return FE2_OK;
+}
+
+fe2_status fe2_macro_solve_assembled(fe2_ctx* ctx, double* K, double* R, double* dFbar, double* rnorm,
+                                     int* status) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!ctx->macro_ready || !K || !R || !dFbar || !rnorm)
+        return fail(ctx, FE2_ERR_ARG, "no macro problem / NULL pointer");
+    MacroDev M = ctx->macro;
+    M.K = K;
+    M.R = R;
+    int nl = 0;
+    TIMED("macro_solve", launch_macro_factor_apply(M, dFbar, rnorm, status ? status : ctx->d_macro_status,
+                                                   ctx->stream, &nl));
+    ctx->launches += nl;
+    return FE2_OK;
+}
+
 fe2_status fe2_rve_average_stress(fe2_ctx* ctx, int n, const int* rve_ids, double* Pbar) {
     if (!ctx) return FE2_ERR_ARG;
     if (!Pbar) return fail(ctx, FE2_ERR_ARG, "Pbar is NULL");

@@ -141,6 +141,12 @@ cudaError_t launch_macro_residual(const MacroDev& M, const double* stress, doubl
 cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
                                double* rnorm, int* status, cudaStream_t s, int* launches);
 cudaError_t launch_rve_avg_stress(const RveDev* tab, const int* ids, int n, double* Pbar, cudaStream_t s);
+// the macro update in steps, on the K and R the MacroDev points to (sharded macro Newton)
+cudaError_t launch_macro_assemble_only(const MacroDev& M, const double* stress, const double* Cbar, int elem,
+                                       cudaStream_t s);
+cudaError_t launch_macro_norm(const MacroDev& M, double* rnorm, cudaStream_t s);
+cudaError_t launch_macro_factor_apply(const MacroDev& M, double* dFbar, double* rnorm, int* status, cudaStream_t s,
+                                      int* launches);
 
 // element RVEs (piecewise-constant macro basis, 2D, nq = 4, nr = 17)
 cudaError_t launch_check_fbar_dd(const double* Fbar, int n, int dd, int* status, cudaStream_t s);

@@ -433,6 +433,35 @@ cudaError_t launch_macro_solve(const MacroDev& M, const double* stress, const do
     return cudaGetLastError();
 }
 
+// The steps of launch_macro_solve on caller-owned K and R (the MacroDev's K and R
+// pointers replaced): assemble (K only when Cbar is given) ...
+cudaError_t launch_macro_assemble_only(const MacroDev& M, const double* stress, const double* Cbar, int elem,
+                                       cudaStream_t s) {
+    if (Cbar) {
+        cudaError_t e = cudaMemsetAsync(M.K, 0, sizeof(double) * (size_t)M.nfree * (M.kd + 1), s);
+        if (e != cudaSuccess) return e;
+    }
+    if (elem && Cbar)
+        k_macro_assemble_elem<<<(2 * M.nnode + 127) / 128, 128, 0, s>>>(M, stress, Cbar);
+    else
+        macro_assemble(M, stress, Cbar, Cbar ? 1 : 0, s);
+    return cudaGetLastError();
+}
+
+// ... the norm of R ...
+cudaError_t launch_macro_norm(const MacroDev& M, double* rnorm, cudaStream_t s) {
+    k_macro_norm<<<1, 1024, 0, s>>>(M, rnorm);
+    return cudaGetLastError();
+}
+
+// ... and the factorisation, solve and update (K is overwritten by its factor).
+cudaError_t launch_macro_factor_apply(const MacroDev& M, double* dFbar, double* rnorm, int* status, cudaStream_t s,
+                                      int* launches) {
+    k_macro_norm<<<1, 1024, 0, s>>>(M, rnorm);
+    *launches = 1 + macro_factor_solve_apply(M, dFbar, status, s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_macro_solve_elem(const MacroDev& M, const double* stress, const double* Cbar, double* dFbar,
                                     double* rnorm, int* status, cudaStream_t s, int* launches) {
     cudaError_t e = cudaMemsetAsync(M.K, 0, sizeof(double) * (size_t)M.nfree * (M.kd + 1), s);

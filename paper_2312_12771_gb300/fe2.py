@@ -72,6 +72,10 @@ _SIGS = {
     "fe2_macro_gradients": (_I, [_P, _P, _P]),
     "fe2_macro_residual": (_I, [_P, _P, _P]),
     "fe2_macro_solve": (_I, [_P, _P, _P, _P, _P, _P]),
+    "fe2_macro_system_size": (_I, [_P, _IP, _IP]),
+    "fe2_macro_assemble": (_I, [_P, _P, _P, _P, _P]),
+    "fe2_macro_norm": (_I, [_P, _P, _P]),
+    "fe2_macro_solve_assembled": (_I, [_P, _P, _P, _P, _P, _P]),
     "fe2_rve_average_stress": (_I, [_P, _I, _IP, _P]),
     "fe2_rve_residual_norm": (_I, [_P, _I, _IP, _P]),
     "fe2_rve_export": (_I, [_P, _I, _I, _DP]),
@@ -337,6 +341,24 @@ class Fe2Context:
     def macro_solve(self, sigma, Cbar, dFbar, rnorm, status=None):
         self._check(self.lib.fe2_macro_solve(self.h, _ptr(sigma), _ptr(Cbar), _ptr(dFbar), _ptr(rnorm),
                                              _ptr(status)), "fe2_macro_solve")
+
+    def macro_system_size(self):
+        """(free macro DOFs, half bandwidth) of the assembled macro system."""
+        nf, kd = C.c_int(0), C.c_int(0)
+        self._check(self.lib.fe2_macro_system_size(self.h, C.byref(nf), C.byref(kd)), "fe2_macro_system_size")
+        return nf.value, kd.value
+
+    def macro_assemble(self, sigma, Cbar, K, R):
+        """Assemble K (None with Cbar None: R only) and R into caller-owned buffers."""
+        self._check(self.lib.fe2_macro_assemble(self.h, _ptr(sigma), _ptr(Cbar), _ptr(K), _ptr(R)),
+                    "fe2_macro_assemble")
+
+    def macro_norm(self, R, rnorm):
+        self._check(self.lib.fe2_macro_norm(self.h, _ptr(R), _ptr(rnorm)), "fe2_macro_norm")
+
+    def macro_solve_assembled(self, K, R, dFbar, rnorm, status=None):
+        self._check(self.lib.fe2_macro_solve_assembled(self.h, _ptr(K), _ptr(R), _ptr(dFbar), _ptr(rnorm),
+                                                       _ptr(status)), "fe2_macro_solve_assembled")
 
     def rve_average_stress(self, ids, Pbar):
         a, p = _ids(ids)
