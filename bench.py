@@ -516,6 +516,28 @@ def run_hex8(args):
     out["vs_oracle"] = oracle_errors(getattr(args, "pool", None),
                                      [(8, b.phase[k], b.mat[k], b.Fbar[k], 3, None) for k in idx],
                                      outs[0][idx].cpu().numpy(), outs[1][idx].cpu().numpy())
+    mixed = [t.cpu().numpy().copy() for t in outs]
+    ctx.close()
+    # the FP64 path on the same RVEs (wide-band FP64 factor, L streamed one block at a time)
+    ctx = Fe2Context(dim=3, precision="fp64")
+    ids = ctx.register_batch(b)
+    outs = ctx._outs(b.nrve)
+    ctx.rve_solve(ids, F, out=outs)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    e0.record(ctx.stream)
+    for _ in range(2):
+        ctx.rve_solve(ids, F, out=outs)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / 2
+    prof = ctx.profile_read()
+    out["fp64_path"] = {"solves_per_s": round(b.nrve / (ms64 * 1e-3), 1), "ms_per_step": round(ms64, 3),
+                        "status_nonzero": int((outs[2] != 0).sum().item()),
+                        "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof.items()}}
+    out["speedup_mixed_vs_fp64"] = round(ms64 / ms, 2)
+    out["max_rel_err_mixed_vs_fp64_gpu"] = rel_errs(mixed[1], outs[1].cpu().numpy(), mixed[0],
+                                                    outs[0].cpu().numpy(), b.Fbar, 3)
     ctx.close()
     return out
 

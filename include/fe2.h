@@ -140,8 +140,8 @@ size_t fe2_rve_bytes(const fe2_ctx* ctx, int N);
  * registering nothing, if the context's HBM budget would be exceeded, and
  * FE2_ERR_ARG, registering nothing, for N outside [3, 256], an unknown material
  * model (Mooney-Rivlin is 2D only), a phase index >= nphase, or a band too wide
- * for the context's precision (the FP64 path takes half bandwidths whose factor
- * fits in shared memory, which excludes Hex8 RVEs of 8^3; the mixed path takes them).
+ * for the solve kernels' shared memory (both paths take every 2D mesh up to
+ * N = 62 and Hex8 RVEs up to 8^3).
  */
 fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase,
                             int nphase, const double* mat, int* rve_ids_out);

@@ -879,8 +879,15 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1)
 // L is read block by block (NB columns = NB*(kd+1) contiguous elements) with
 // double-buffered 1D TMA bulk copies.
 template <typename T>
+constexpr int YT_LD = MAX_NR + 3;  // row stride of the per-block y copy (20: 16-byte rows in FP32)
+constexpr size_t SOLVE_SMEM_CAP = 220 * 1024;  // dynamic + static shared memory of a solve kernel
+
+// L blocks are double-buffered unless two blocks and the rest do not fit
+// SOLVE_SMEM_CAP (FP64 Hex8 bands: 113 KB per block); then one buffer is
+// reloaded after each block (nbuf = 1).
+template <typename T>
 struct SolveLayout {
-    int kd, S, LDL, nr, nmp;
+    int kd, S, LDL, nr, nmp, nbuf;
     size_t blk, offL1, offX, offY, offBar, total;
     __host__ __device__ void init(int kd_, int nr_, int nmp_, bool ysm) {
         kd = kd_;
@@ -889,8 +896,11 @@ struct SolveLayout {
         S = kd + NB;
         LDL = kd + 1;
         blk = ((size_t)NB * LDL * sizeof(T) + NB * sizeof(T) + 127) & ~(size_t)127;
+        const size_t rest = (((size_t)nr * 2 * S * sizeof(T) + 15) & ~(size_t)15) +
+                            (ysm ? (size_t)nr * nmp * sizeof(T) : 0) + 32 + (size_t)(MAX_NR + YT_LD) * NB * sizeof(T);
+        nbuf = 2 * blk + rest <= SOLVE_SMEM_CAP ? 2 : 1;
         offL1 = blk;
-        size_t o = 2 * blk;
+        size_t o = nbuf * blk;
         offX = o;                                   // x ring [nr][2S] (mirrored) or rhs ring [nr][S]
         o += (size_t)nr * 2 * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
@@ -913,8 +923,9 @@ struct LStream {
     const T* Dg;
     uint32_t bytes;
     int LDL, stride;   // stride: elements between the two buffers
-    // buffer k & 1 holds NB columns of L followed by their NB reciprocal diagonals
-    __device__ __forceinline__ const T* buf(int k) const { return buf0 + (k & 1) * stride; }
+    int nbuf;          // 2: double-buffered; 1: one buffer, the next block issued after use
+    // buffer k & 1 (or 0) holds NB columns of L followed by their NB reciprocal diagonals
+    __device__ __forceinline__ const T* buf(int k) const { return buf0 + (nbuf == 2 ? (k & 1) : 0) * stride; }
     __device__ __forceinline__ const T* dinv(int k) const { return buf(k) + NB * LDL; }
     __device__ __forceinline__ void init(unsigned char* smem, const SolveLayout<T>& lay, const T* L, const T* D) {
         buf0 = (T*)smem;
@@ -923,6 +934,7 @@ struct LStream {
         Lg = L;
         Dg = D;
         LDL = lay.LDL;
+        nbuf = lay.nbuf;
         bytes = (uint32_t)(NB * LDL * sizeof(T));
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
@@ -934,14 +946,17 @@ struct LStream {
     __device__ __forceinline__ void issue(int k, int j0) {
         if (threadIdx.x == 0) {
             const uint32_t db = (uint32_t)(NB * sizeof(T));
-            T* dst = buf0 + (k & 1) * stride;
-            uint64_t* b = bar + (k & 1);
+            T* dst = buf0 + (nbuf == 2 ? (k & 1) : 0) * stride;
+            uint64_t* b = bar + (nbuf == 2 ? (k & 1) : 0);
             mbar_arrive_expect_tx(b, bytes + db);
             bulk_g2s(dst, Lg + (size_t)j0 * LDL, bytes, b);
             bulk_g2s(dst + NB * LDL, Dg + j0, db, b);
         }
     }
-    __device__ __forceinline__ bool wait(int k) { return mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1)); }
+    __device__ __forceinline__ bool wait(int k) {
+        return nbuf == 2 ? mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1))
+                         : mbar_wait_bounded(bar, (uint32_t)(k & 1));
+    }
 };
 
 // Backward substitution x = L^-T y over the band, blocks from the bottom.
@@ -997,7 +1012,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
     for (int b = nblk - 1; b >= 0; --b) {
         const int k = k0 + (nblk - 1 - b);
         const int j0 = b * NB;
-        if (b > 0) ls.issue(k + 1, j0 - NB);
+        if (b > 0 && ls.nbuf == 2) ls.issue(k + 1, j0 - NB);
         if (!ls.wait(k)) *s_to = 1;
         __syncthreads();
         if (*s_to) return false;
@@ -1053,6 +1068,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
             }
         }
         __syncthreads();
+        if (b > 0 && ls.nbuf == 1) ls.issue(k + 1, j0 - NB);  // the buffer is free again
         jb = jb - NB < 0 ? jb - NB + S : jb - NB;
     }
     k0 += nblk;
@@ -1078,8 +1094,6 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
     if (!backward_pass<T, WIDE>(r, lay, ls, k0, xr, Yg, accumulate, &s_to) && threadIdx.x == 0)
         status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
-
-constexpr int YT_LD = MAX_NR + 3;  // row stride of the per-block y copy (20: 16-byte rows in FP32)
 
 // Forward solve, rows below the current block: bw(i) -= sum_c L(i, c) y_c for the
 // NRT (>= nr) right-hand sides, one thread per row, every L entry read once.
@@ -1138,7 +1152,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
     int jb = 0;
     for (int b = 0; b < nblk; ++b) {
         const int j0 = b * NB;
-        if (b + 1 < nblk) ls.issue(b + 1, j0 + NB);
+        if (b + 1 < nblk && ls.nbuf == 2) ls.issue(b + 1, j0 + NB);
         if (!ls.wait(b)) s_to = 1;
         __syncthreads();
         if (s_to) {
@@ -1174,6 +1188,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
             bw[rr * S + wrapS(jb + c, S)] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
         }
         __syncthreads();
+        if (b + 1 < nblk && ls.nbuf == 1) ls.issue(b + 1, j0 + NB);  // the buffer is free again
         jb = wrapS(jb + NB, S);
     }
     int k0 = nblk;

@@ -280,3 +280,32 @@ def test_mixed_path_within_1e8_on_high_contrast_serving_rves(torch):
         assert O.rel_err(C32[k], ref["Cbar"]) <= TOL["mixed"]
         assert rel_sigma(s32[k], ref, b.Fbar[k]) <= TOL["mixed"]
         assert O.rel_err(C64[k], ref["Cbar"]) <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_hex8_8cubed_both_paths(torch, precision):
+    """The Hex8 RVE of 8^3 (n_m = 1533, half bandwidth 440): the FP64 path
+    (wide-band FP64 factor, L streamed one block at a time through shared
+    memory) and the mixed path, against the oracle, at a sheared Fbar with a
+    fluctuation w~ != 0."""
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    N, n = 8, 3
+    b = W.sphere_batch(n, N, gamma=0.04)
+    b.Fbar = W.perturbed_F(b, 88, 0.01)
+    rng = np.random.default_rng(89)
+    ws = [0.005 / N * rng.standard_normal(3 * (N ** 3 - 1)) for _ in range(n)]
+    ctx = Fe2Context(dim=3, precision=precision)
+    ids = ctx.register_batch(b)
+    for k, i in enumerate(ids):
+        ctx.set_w(i, ws[k])
+    sig, Cb, st, err = ctx.rve_solve(ids, torch.tensor(b.Fbar, device="cuda"))
+    torch.cuda.synchronize()
+    sig, Cb, st = sig.cpu().numpy(), Cb.cpu().numpy(), st.cpu().numpy()
+    for k in range(n):
+        assert st[k] == 0, (k, st[k])
+        ref = O.rve_solve(N, 3, b.phase[k], b.mat[k], b.Fbar[k], ws[k])
+        assert O.rel_err(Cb[k], ref["Cbar"]) <= TOL[precision]
+        assert rel_sigma(sig[k], ref, b.Fbar[k], d=3) <= TOL[precision]
+        w = ctx.export(ids[k], 3, N)
+        assert np.abs(w - ws[k]).max() <= 1e-15       # w~ round trip in 3D
+    ctx.close()
