@@ -878,7 +878,6 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1)
 // ------------------------------------------------------------------ solves
 // L is read block by block (NB columns = NB*(kd+1) contiguous elements) with
 // double-buffered 1D TMA bulk copies.
-template <typename T>
 constexpr int YT_LD = MAX_NR + 3;  // row stride of the per-block y copy (20: 16-byte rows in FP32)
 constexpr size_t SOLVE_SMEM_CAP = 220 * 1024;  // dynamic + static shared memory of a solve kernel
 
