@@ -149,6 +149,30 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
 fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids);
 
 /*
+ * RVEs whose device state comes and goes within the HBM budget (no counterpart
+ * in the paper; the serving loop's admission, config 4).  fe2_rve_define takes
+ * the arguments of fe2_rve_register (Dirac basis) but allocates nothing: the
+ * definition (mesh size, phases, materials) stays on the host, w~ starts at
+ * zero.  A defined RVE is resident while its persistent state occupies a
+ * device slot; slots have one size (the persistent bytes of the largest RVE of
+ * the first fe2_rve_define call; a later call with a larger RVE returns
+ * FE2_ERR_ARG), come from slabs of up to 16 slots allocated within the budget,
+ * and are recycled, not freed.  fe2_rve_admit makes RVEs resident, evicting
+ * other defined RVEs by least recent use when no slot is free and no slab fits
+ * (FE2_ERR_BUDGET if still none; synchronises).  fe2_rve_evict copies w~ of
+ * idle RVEs to the host and frees their slots (synchronises).  Every other
+ * call on a defined RVE that is not resident returns FE2_ERR_ARG, except
+ * fe2_rve_set_w (kept on the host until admission) and fe2_rve_release.
+ * fe2_rve_resident: 1 resident, 0 not, -1 unknown id.  The server admits
+ * defined RVEs by itself (fe2_server_*).
+ */
+fe2_status fe2_rve_define(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase, int nphase,
+                          const double* mat, int* rve_ids_out);
+fe2_status fe2_rve_admit(fe2_ctx* ctx, int n, const int* rve_ids);
+fe2_status fe2_rve_evict(fe2_ctx* ctx, int n, const int* rve_ids);
+int fe2_rve_resident(const fe2_ctx* ctx, int rve_id);
+
+/*
  * S1 + S2 (Section 2.2 Eqs. (microdefo), (microGrad); Section 3 Eqs. (linSys3),
  * (linSys4)): at F~ = Fbar + grad w~ evaluate P~ and A = dP~/dF~ at every
  * micro Gauss point and integrate, per element, the rows of the element
@@ -343,8 +367,12 @@ const char* fe2_noalloc_last_error(void);
 /*
  * Serving: continuous batching of RVE solve requests (S1 - S6 per request) as
  * macro Newton iterations emit them.  RVE state stays resident in the context
- * between requests; admission of new RVEs is by the context's HBM budget
- * (fe2_rve_register).  The server runs `nlanes` execution lanes, each with its
+ * between requests.  Requests may name defined RVEs that are not resident
+ * (fe2_rve_define): a batch admits them as device memory allows within the
+ * context's HBM budget (the lanes' buffers and workspaces count against it),
+ * evicting idle defined RVEs (not in flight, least recently served first,
+ * w~ kept on the host); a request that cannot be admitted stays queued until
+ * memory frees up.  The server runs `nlanes` execution lanes, each with its
  * own CUDA stream, factorisation workspace, pinned staging and completion
  * event: a batch formed while another runs is launched at once and overlaps it
  * on the device.  A batch takes up to max_batch queued requests of one mesh
@@ -365,6 +393,12 @@ const char* fe2_noalloc_last_error(void);
  *   batches of that shape; on by default, enable = 0 launches every kernel
  *   from the host instead.  The results are the same either way.
  * fe2_server_graph_stats: captures and replays so far ([host], may be NULL).
+ * fe2_server_bucket: with graphs on, round each batch down to a power of two
+ *   (the rest stay at the head of the queue) so that captured graphs are
+ *   replayed (default on).
+ * fe2_server_memory_stats: defined RVEs admitted and evicted so far, requests
+ *   passed over for lack of memory, device bytes held against the budget
+ *   ([host], may be NULL).
  */
 typedef struct fe2_server fe2_server;
 fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server** out);
@@ -376,6 +410,9 @@ int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma,
 int fe2_server_pending(const fe2_server* srv);
 fe2_status fe2_server_use_graphs(fe2_server* srv, int enable);
 fe2_status fe2_server_graph_stats(const fe2_server* srv, long long* captures, long long* replays);
+fe2_status fe2_server_bucket(fe2_server* srv, int enable);
+fe2_status fe2_server_memory_stats(const fe2_server* srv, long long* admitted, long long* evicted,
+                                   long long* deferred, size_t* device_bytes);
 
 /*
  * Self-test of the bounded device waits used by the TMA streams of the solve

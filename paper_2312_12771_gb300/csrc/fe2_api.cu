@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -24,6 +25,14 @@ struct HostRve {
     bool all_linear = true;
     int chunk = -1;       // allocation chunk
     std::vector<double> mat;
+    // RVEs defined by fe2_rve_define hold device state only while resident (in a slot)
+    bool deferred = false;
+    bool resident = true;
+    char* slot = nullptr;
+    std::vector<uint8_t> phase;  // host definition
+    std::vector<double> w;       // w~ (folded order) while not resident
+    bool w_zero = true;
+    unsigned long long last_use = 0;
 };
 
 struct Chunk {
@@ -86,6 +95,13 @@ struct fe2_ctx {
     MacroDev macro{};
     std::vector<double> macro_X;    // reference nodal positions [nnode][d] (host copy)
     std::vector<void*> macro_bufs;  // device buffers owned by the macro problem
+    // slots of the RVEs defined by fe2_rve_define (uniform size, allocated in slabs)
+    size_t slot_bytes = 0;
+    std::vector<void*> slabs;
+    std::vector<char*> free_slots;
+    size_t extra_bytes = 0;         // device bytes counted against the budget by a server (lanes)
+    std::set<std::pair<unsigned long long, int>> lru;  // resident defined RVEs by last use
+    long long n_admitted = 0, n_evicted = 0;
     int* d_macro_status = nullptr;
 };
 
@@ -187,6 +203,27 @@ static size_t persistent_bytes_of(int N, int d, int nphase, int nq = 1) {
     return b;
 }
 
+// Device pointers of one RVE's persistent state inside `base` (the layout that
+// persistent_bytes_of counts); r.d, nn, nm, nr and nphase must be set.
+static void place_rve(RveDev& r, char* base, int nst, int nq) {
+    const int d = r.d, nn = r.nn, nm = r.nm, nr = r.nr;
+    size_t o = 0;
+    r.phase = (const uint8_t*)(base + o);
+    o += align256(nn);
+    r.mat = (const double*)(base + o);
+    o += align256((size_t)r.nphase * 4 * 8);
+    r.w = (double*)(base + o);
+    o += align256((size_t)nm * 8);
+    r.stencil = (double*)(base + o);
+    o += align256((size_t)nst * nn * 8);
+    r.rhs = (double*)(base + o);
+    o += align256((size_t)nr * nm * 8);
+    r.X = (double*)(base + o);
+    o += align256((size_t)nr * nm * 8);
+    r.KMM = (double*)(base + o);  // [nq][d^4], then Pint [nq][d^2]
+    r.Pint = r.KMM + d * d * d * d * nq;
+}
+
 // macro Gauss points per RVE: 1 (Dirac basis) or 4 (element RVE, piecewise-constant basis)
 static int nq_of(const fe2_ctx* ctx) { return ctx->cfg.macro_basis == FE2_BASIS_CONST ? MAX_NQ : 1; }
 
@@ -256,7 +293,10 @@ static fe2_status ensure_ws(fe2_ctx* ctx, size_t bytes, size_t limit = (size_t)-
     return FE2_OK;
 }
 
-static size_t used_bytes(const fe2_ctx* c) { return c->persistent_bytes + c->ws_bytes + c->elem_bytes; }
+// device bytes held against the HBM budget (a server's lane buffers included)
+static size_t used_bytes(const fe2_ctx* c) {
+    return c->persistent_bytes + c->ws_bytes + c->elem_bytes + c->extra_bytes;
+}
 
 // ------------------------------------------------------------------ id lists
 static fe2_status get_ids(fe2_ctx* ctx, int n, const int* ids, const int** dev) {
@@ -265,6 +305,8 @@ static fe2_status get_ids(fe2_ctx* ctx, int n, const int* ids, const int** dev) 
         const int id = ids[k];
         if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
             return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        if (!ctx->host[id].resident)
+            return fail(ctx, FE2_ERR_ARG, "rve %d is not resident (fe2_rve_admit it first)", id);
     }
     ++ctx->tick;
     for (auto& e : ctx->idcache) {
@@ -558,6 +600,7 @@ void fe2_destroy(fe2_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     for (auto& c : ctx->chunks)
         if (c.dev) cudaFree(c.dev);
+    for (void* p : ctx->slabs) cudaFree(p);
     for (auto& e : ctx->idcache) {
         cudaFree(e.dev);
         cudaFreeHost(e.pinned);
@@ -627,6 +670,36 @@ size_t fe2_rve_bytes(const fe2_ctx* ctx, int N) {
     return persistent_bytes_of(N, d, 2, nq) + l.stride;
 }
 
+// ids for nrve new RVEs (released ids first); the device descriptor table grows
+// to hold them
+static fe2_status new_ids(fe2_ctx* ctx, int nrve, std::vector<int>& ids) {
+    ids.assign(nrve, -1);
+    for (int k = 0; k < nrve; ++k) {
+        if (!ctx->free_ids.empty()) {
+            ids[k] = ctx->free_ids.back();
+            ctx->free_ids.pop_back();
+        } else {
+            ids[k] = (int)ctx->host.size();
+            ctx->host.emplace_back();
+            ctx->mirror.emplace_back();
+        }
+    }
+    const int need_cap = (int)ctx->host.size();
+    if (need_cap > ctx->tab_cap) {
+        int cap = std::max(need_cap, std::max(64, ctx->tab_cap * 2));
+        RveDev* nt = nullptr;
+        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMalloc(&nt, sizeof(RveDev) * cap));
+        if (ctx->d_tab) {
+            CK(cudaMemcpy(nt, ctx->d_tab, sizeof(RveDev) * ctx->tab_cap, cudaMemcpyDeviceToDevice));
+            CK(cudaFree(ctx->d_tab));
+        }
+        ctx->d_tab = nt;
+        ctx->tab_cap = cap;
+    }
+    return FE2_OK;
+}
+
 fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase, int nphase,
                             const double* mat, int* rve_ids_out) {
     if (!ctx) return FE2_ERR_ARG;
@@ -681,30 +754,10 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
             if (st != FE2_OK) return st;
         }
     }
-    // ids
-    std::vector<int> ids(nrve);
-    for (int k = 0; k < nrve; ++k) {
-        if (!ctx->free_ids.empty()) {
-            ids[k] = ctx->free_ids.back();
-            ctx->free_ids.pop_back();
-        } else {
-            ids[k] = (int)ctx->host.size();
-            ctx->host.emplace_back();
-            ctx->mirror.emplace_back();
-        }
-    }
-    const int need_cap = (int)ctx->host.size();
-    if (need_cap > ctx->tab_cap) {
-        int cap = std::max(need_cap, std::max(64, ctx->tab_cap * 2));
-        RveDev* nt = nullptr;
-        CK(cudaStreamSynchronize(ctx->stream));
-        CK(cudaMalloc(&nt, sizeof(RveDev) * cap));
-        if (ctx->d_tab) {
-            CK(cudaMemcpy(nt, ctx->d_tab, sizeof(RveDev) * ctx->tab_cap, cudaMemcpyDeviceToDevice));
-            CK(cudaFree(ctx->d_tab));
-        }
-        ctx->d_tab = nt;
-        ctx->tab_cap = cap;
+    std::vector<int> ids;
+    {
+        fe2_status st = new_ids(ctx, nrve, ids);
+        if (st != FE2_OK) return st;
     }
     Chunk ch;
     CK(cudaMalloc(&ch.dev, total));
@@ -741,23 +794,9 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         r.nphase = nphase;
         r.nm_pad = (nm + NB - 1) / NB * NB;
         r.nr = nr;
-        size_t o = 0;
-        r.phase = (const uint8_t*)(base + o);
-        std::memcpy(hb + o, phase + phase_off, nn);
-        o += align256(nn);
-        r.mat = (const double*)(base + o);
-        std::memcpy(hb + o, mat + (size_t)k * nphase * 4, (size_t)nphase * 4 * 8);
-        o += align256((size_t)nphase * 4 * 8);
-        r.w = (double*)(base + o);
-        o += align256((size_t)nm * 8);
-        r.stencil = (double*)(base + o);
-        o += align256((size_t)nst * nn * 8);
-        r.rhs = (double*)(base + o);
-        o += align256((size_t)nr * nm * 8);
-        r.X = (double*)(base + o);
-        o += align256((size_t)nr * nm * 8);
-        r.KMM = (double*)(base + o);                 // [nq][d^4], then Pint [nq][d^2]
-        r.Pint = r.KMM + d * d * d * d * nq;
+        place_rve(r, base, nst, nq);
+        std::memcpy(hb + ((const char*)r.phase - base), phase + phase_off, nn);
+        std::memcpy(hb + ((const char*)r.mat - base), mat + (size_t)k * nphase * 4, (size_t)nphase * 4 * 8);
         r.nq = nq;
         for (int g = 0; g < MAX_NQ; ++g) r.wq[g] = g < nq ? 1.0 / nq : 0.0;
         r.elem = nullptr;
@@ -768,6 +807,7 @@ fe2_status fe2_rve_register(fe2_ctx* ctx, int nrve, const int* N, const uint8_t*
         const int id = ids[k];
         ctx->mirror[id] = r;
         HostRve& h = ctx->host[id];
+        h = HostRve();
         h.active = true;
         h.chunk = chunk_id;
         h.mat.assign(mat + (size_t)k * nphase * 4, mat + (size_t)(k + 1) * nphase * 4);
@@ -801,6 +841,13 @@ fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids) {
         HostRve& h = ctx->host[id];
         if (!h.active) continue;
         h.active = false;
+        if (h.deferred) {  // its slot (if any) goes back to the pool
+            if (h.resident && h.slot) ctx->free_slots.push_back(h.slot);
+            ctx->lru.erase({h.last_use, id});
+            h = HostRve();
+            ctx->free_ids.push_back(id);
+            continue;
+        }
         const RveDev& r = ctx->mirror[id];
         ctx->persistent_bytes -= persistent_bytes_of(r.N, r.d, r.nphase, r.nq > 0 ? r.nq : 1);
         Chunk& c = ctx->chunks[h.chunk];
@@ -812,6 +859,211 @@ fe2_status fe2_rve_release(fe2_ctx* ctx, int n, const int* rve_ids) {
         ctx->free_ids.push_back(id);
     }
     return FE2_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ defined RVEs
+// RVEs defined by fe2_rve_define keep their definition (mesh size, phases,
+// materials) and, while not resident, their fluctuation w~ on the host; their
+// device state lives in uniform slots (the largest defined RVE's persistent
+// bytes), carved from slabs allocated within the HBM budget and recycled, not
+// freed, when an RVE is evicted.
+
+static void touch(fe2_ctx* ctx, int id) {
+    HostRve& h = ctx->host[id];
+    ctx->lru.erase({h.last_use, id});
+    h.last_use = ++ctx->tick;
+    ctx->lru.insert({h.last_use, id});
+}
+
+// Move w~ of an idle resident defined RVE to the host and give back its slot.
+static fe2_status evict_one(fe2_ctx* ctx, int id) {
+    HostRve& h = ctx->host[id];
+    if (!h.deferred || !h.resident) return FE2_OK;
+    RveDev& r = ctx->mirror[id];
+    CK(cudaStreamSynchronize(ctx->stream));
+    h.w_zero = r.zero_w != 0;
+    if (!h.w_zero) {
+        h.w.resize(r.nm);
+        CK(cudaMemcpy(h.w.data(), r.w, sizeof(double) * r.nm, cudaMemcpyDeviceToHost));
+    }
+    ctx->free_slots.push_back(h.slot);
+    ctx->lru.erase({h.last_use, id});
+    h.slot = nullptr;
+    h.resident = false;
+    ++ctx->n_evicted;
+    return FE2_OK;
+}
+
+// Make a defined RVE resident, its state copied in on stream s.  *ok = false
+// (nothing changed) when no slot is free, no slab fits the budget and no
+// evictable RVE is left; `busy(id)` marks RVEs that must not be evicted.
+template <typename Busy>
+static fe2_status admit_one(fe2_ctx* ctx, int id, cudaStream_t s, bool* ok, Busy busy) {
+    HostRve& h = ctx->host[id];
+    *ok = true;
+    if (h.resident) {
+        if (h.deferred) touch(ctx, id);
+        return FE2_OK;
+    }
+    if (ctx->free_slots.empty()) {
+        const size_t budget = ctx->cfg.hbm_budget_bytes;
+        int per = 16;
+        if (budget) {
+            const size_t used = used_bytes(ctx);
+            const size_t room = budget > used ? budget - used : 0;
+            per = std::min<size_t>(per, room / ctx->slot_bytes);
+        }
+        if (per >= 1) {
+            void* p = nullptr;
+            CK(cudaMalloc(&p, ctx->slot_bytes * per));
+            ctx->slabs.push_back(p);
+            ctx->persistent_bytes += ctx->slot_bytes * per;
+            for (int k = 0; k < per; ++k) ctx->free_slots.push_back((char*)p + ctx->slot_bytes * k);
+        } else {
+            for (auto it = ctx->lru.begin(); it != ctx->lru.end(); ++it)
+                if (it->second != id && !busy(it->second)) {
+                    fe2_status st = evict_one(ctx, it->second);
+                    if (st != FE2_OK) return st;
+                    break;
+                }
+        }
+        if (ctx->free_slots.empty()) {
+            *ok = false;
+            return FE2_OK;
+        }
+    }
+    char* slot = ctx->free_slots.back();
+    ctx->free_slots.pop_back();
+    RveDev& r = ctx->mirror[id];
+    const int nst = (r.d == 2 ? 9 : 27) * r.d * r.d;
+    place_rve(r, slot, nst, 1);
+    r.zero_w = h.w_zero ? 1 : 0;
+    CK(cudaMemcpyAsync((void*)r.phase, h.phase.data(), h.phase.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void*)r.mat, h.mat.data(), sizeof(double) * h.mat.size(), cudaMemcpyHostToDevice, s));
+    if (h.w_zero)
+        CK(cudaMemsetAsync(r.w, 0, sizeof(double) * r.nm, s));
+    else
+        CK(cudaMemcpyAsync(r.w, h.w.data(), sizeof(double) * r.nm, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->d_tab + id, &r, sizeof(RveDev), cudaMemcpyHostToDevice, s));
+    h.slot = slot;
+    h.resident = true;
+    touch(ctx, id);
+    ++ctx->n_admitted;
+    return FE2_OK;
+}
+
+extern "C" {
+
+fe2_status fe2_rve_define(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* phase, int nphase,
+                          const double* mat, int* rve_ids_out) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (nrve <= 0 || !N || !phase || !mat || !rve_ids_out) return fail(ctx, FE2_ERR_ARG, "bad define arguments");
+    if (nphase < 1 || nphase > MAX_PHASES) return fail(ctx, FE2_ERR_ARG, "nphase must be in [1, %d]", MAX_PHASES);
+    if (nq_of(ctx) > 1) return fail(ctx, FE2_ERR_ARG, "defined RVEs take the Dirac basis");
+    const int d = ctx->cfg.dim;
+    const bool fp64 = ctx->cfg.precision == FE2_PREC_FP64;
+    size_t need = 0, phase_off = 0;
+    for (int k = 0; k < nrve; ++k) {
+        if (N[k] < 3 || N[k] > 256) return fail(ctx, FE2_ERR_ARG, "mesh size N=%d out of range (N >= 3)", N[k]);
+        const int kd = compute_kd(ctx, N[k], d), nr = d * d + 1;
+        const int nmk = d * (nodes_of(N[k], d) - 1), nmpk = (nmk + NB - 1) / NB * NB;
+        if ((!use_smem_factor(kd, nr, fp64, ctx->max_smem, d) && (int)factor_gw_smem_bytes(kd, nr, fp64) > ctx->max_smem) ||
+            (int)solve_smem_bytes(kd, nr, fp64 ? 0 : nmpk, fp64) > ctx->max_smem)
+            return fail(ctx, FE2_ERR_ARG, "N=%d: band of half width %d is too wide", N[k], kd);
+        for (int p = 0; p < nphase; ++p) {
+            const int model = (int)mat[((size_t)k * nphase + p) * 4];
+            if (model != FE2_MODEL_LINEAR && model != FE2_MODEL_NEOHOOKE && model != FE2_MODEL_MOONEY_RIVLIN)
+                return fail(ctx, FE2_ERR_ARG, "rve %d phase %d: unknown material model", k, p);
+            if (model == FE2_MODEL_MOONEY_RIVLIN && d != 2)
+                return fail(ctx, FE2_ERR_ARG, "rve %d phase %d: the Mooney-Rivlin model is 2D only", k, p);
+        }
+        const int nn = nodes_of(N[k], d);
+        for (int e = 0; e < nn; ++e)
+            if (phase[phase_off + e] >= nphase) return fail(ctx, FE2_ERR_ARG, "rve %d: phase index out of range", k);
+        phase_off += nn;
+        need = std::max(need, persistent_bytes_of(N[k], d, nphase, 1));
+    }
+    if (ctx->slot_bytes == 0) ctx->slot_bytes = need;
+    if (need > ctx->slot_bytes)
+        return fail(ctx, FE2_ERR_ARG, "defined RVEs need %zu B slots, the pool has %zu B (define the largest first)",
+                    need, ctx->slot_bytes);
+    std::vector<int> ids;
+    fe2_status st = new_ids(ctx, nrve, ids);
+    if (st != FE2_OK) return st;
+    phase_off = 0;
+    for (int k = 0; k < nrve; ++k) {
+        const int nn = nodes_of(N[k], d), nm = d * (nn - 1);
+        RveDev r{};
+        r.N = N[k];
+        r.d = d;
+        r.nm = nm;
+        r.kd = compute_kd(ctx, N[k], d);
+        r.nn = nn;
+        r.nphase = nphase;
+        r.nm_pad = (nm + NB - 1) / NB * NB;
+        r.nr = d * d + 1;
+        r.nq = 1;
+        r.wq[0] = 1.0;
+        r.nbr = nbr_table(ctx, N[k], d);
+        if (!r.nbr) return fail(ctx, FE2_ERR_CUDA, "neighbour table allocation failed");
+        r.zero_w = 1;
+        const int id = ids[k];
+        ctx->mirror[id] = r;
+        HostRve& h = ctx->host[id];
+        h = HostRve();
+        h.active = true;
+        h.deferred = true;
+        h.resident = false;
+        h.mat.assign(mat + (size_t)k * nphase * 4, mat + (size_t)(k + 1) * nphase * 4);
+        h.all_linear = true;
+        for (int p = 0; p < nphase; ++p) h.all_linear &= (int)h.mat[4 * p] == FE2_MODEL_LINEAR;
+        h.phase.assign(phase + phase_off, phase + phase_off + nn);
+        phase_off += nn;
+        rve_ids_out[k] = id;
+    }
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_admit(fe2_ctx* ctx, int n, const int* rve_ids) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (n < 0 || (n > 0 && !rve_ids)) return fail(ctx, FE2_ERR_ARG, "bad admit arguments");
+    std::unordered_set<int> keep;
+    for (int k = 0; k < n; ++k) {
+        const int id = rve_ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        keep.insert(id);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < n; ++k) {
+        bool ok = true;
+        fe2_status st = admit_one(ctx, rve_ids[k], ctx->stream, &ok, [&](int x) { return keep.count(x) > 0; });
+        if (st != FE2_OK) return st;
+        if (!ok) return fail(ctx, FE2_ERR_BUDGET, "no room for rve %d within the HBM budget", rve_ids[k]);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FE2_OK;
+}
+
+fe2_status fe2_rve_evict(fe2_ctx* ctx, int n, const int* rve_ids) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (n < 0 || (n > 0 && !rve_ids)) return fail(ctx, FE2_ERR_ARG, "bad evict arguments");
+    for (int k = 0; k < n; ++k) {
+        const int id = rve_ids[k];
+        if (id < 0 || id >= (int)ctx->host.size() || !ctx->host[id].active)
+            return fail(ctx, FE2_ERR_ARG, "rve id %d is not registered", id);
+        if (!ctx->host[id].deferred) return fail(ctx, FE2_ERR_ARG, "rve %d was registered, not defined", id);
+        fe2_status st = evict_one(ctx, id);
+        if (st != FE2_OK) return st;
+    }
+    return FE2_OK;
+}
+
+int fe2_rve_resident(const fe2_ctx* ctx, int rve_id) {
+    if (!ctx || rve_id < 0 || rve_id >= (int)ctx->host.size() || !ctx->host[rve_id].active) return -1;
+    return ctx->host[rve_id].resident ? 1 : 0;
 }
 
 fe2_status fe2_micro_assemble(fe2_ctx* ctx, int n, const int* rve_ids, const double* Fbar) {
@@ -939,6 +1191,12 @@ fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w) {
         const int q = fold_node(p, N, d);
         for (int c = 0; c < d; ++c) wf[d * (q - 1) + c] = host_w[d * (p - 1) + c];
     }
+    HostRve& h = ctx->host[rve_id];
+    if (!h.resident) {  // a defined RVE held on the host: its w~ is copied in when admitted
+        h.w = wf;
+        h.w_zero = false;
+        return FE2_OK;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(r.w, wf.data(), sizeof(double) * r.nm, cudaMemcpyHostToDevice));
     r.zero_w = 0;
@@ -949,6 +1207,7 @@ fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* out) {
     if (!ctx) return FE2_ERR_ARG;
     if (rve_id < 0 || rve_id >= (int)ctx->host.size() || !ctx->host[rve_id].active || !out)
         return fail(ctx, FE2_ERR_ARG, "bad rve id or NULL output");
+    if (!ctx->host[rve_id].resident) return fail(ctx, FE2_ERR_ARG, "rve %d is not resident", rve_id);
     CK(cudaStreamSynchronize(ctx->stream));
     const RveDev& r = ctx->mirror[rve_id];
     const int N = r.N, d = r.d, nm = r.nm, nn = r.nn, dd = d * d;
@@ -1365,7 +1624,17 @@ struct fe2_server {
     std::deque<ServeDone> done;
     std::unordered_set<int> inflight;
     long long next_ticket = 1;
+    bool bucket = true;                 // batch sizes rounded down to powers of two (graph reuse)
+    long long n_deferred = 0;           // requests passed over for lack of device memory
 };
+
+// device bytes of the lanes (buffers and workspaces), counted against the budget
+static size_t lanes_bytes(const fe2_server* srv) {
+    const int dd = srv->ctx->cfg.dim * srv->ctx->cfg.dim;
+    size_t b = 0;
+    for (auto& L : srv->lanes) b += L.ws_bytes + (size_t)srv->max_batch * (3 * sizeof(int) + sizeof(double) * (dd + dd + dd * dd + 1));
+    return b;
+}
 
 static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo& b, const WsLayout& l, bool tc,
                                bool record = true);
@@ -1390,6 +1659,7 @@ static fe2_status lane_launch(fe2_server* srv, Lane& L) {
         L.ws_bytes = 0;
         CK(cudaMalloc(&L.ws, l.stride * (size_t)n));
         L.ws_bytes = l.stride * (size_t)n;
+        ctx->extra_bytes = lanes_bytes(srv);
     }
     cudaStream_t s = L.s;
     const bool tc = !fp64 && !l.gw && use_tc_factor(ctx, b.maxkd, b.maxnr);
@@ -1531,12 +1801,14 @@ fe2_status fe2_server_create(fe2_ctx* ctx, int max_batch, int nlanes, fe2_server
             return fail(ctx, FE2_ERR_CUDA, "server lane allocation: %s", cudaGetErrorString(e));
         }
     }
+    ctx->extra_bytes = lanes_bytes(srv);
     *out = srv;
     return FE2_OK;
 }
 
 void fe2_server_destroy(fe2_server* srv) {
     if (!srv) return;
+    srv->ctx->extra_bytes = 0;
     for (auto& L : srv->lanes) {
         if (L.s) cudaStreamSynchronize(L.s);
         for (auto& g : L.graphs) cudaGraphExecDestroy(g.second);
@@ -1621,9 +1893,35 @@ fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes) {
                 ++it;
                 continue;
             }
+            if (!ctx->host[id].resident) {  // admission by HBM budget; idle RVEs may be evicted
+                bool ok = true;
+                fe2_status st = admit_one(ctx, id, L.s, &ok,
+                                          [&](int x) { return srv->inflight.count(x) > 0 || taken.count(x) > 0; });
+                if (st != FE2_OK) return st;
+                if (!ok) {
+                    ++srv->n_deferred;
+                    ++it;
+                    continue;
+                }
+            } else if (ctx->host[id].deferred) {
+                touch(ctx, id);
+            }
             taken.insert(id);
             L.batch.push_back(*it);
             it = srv->queue.erase(it);
+        }
+        if (srv->bucket && srv->use_graphs && L.batch.size() > 1) {
+            // a power-of-two batch size, so that lanes replay their captured graphs; the
+            // rest go back to the head of the queue in their order (their admission copies,
+            // queued on this lane's idle stream, complete first: another lane may take them)
+            size_t m = 1;
+            while (2 * m <= L.batch.size()) m *= 2;
+            if (m < L.batch.size()) CK(cudaStreamSynchronize(L.s));
+            for (size_t k = L.batch.size(); k-- > m;) {
+                taken.erase(L.batch[k].rve);
+                srv->queue.push_front(L.batch[k]);
+            }
+            L.batch.resize(m);
         }
         if (L.batch.empty()) continue;
         for (int id : taken) srv->inflight.insert(id);
@@ -1659,6 +1957,22 @@ int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma,
 fe2_status fe2_server_use_graphs(fe2_server* srv, int enable) {
     if (!srv) return FE2_ERR_ARG;
     srv->use_graphs = enable != 0;
+    return FE2_OK;
+}
+
+fe2_status fe2_server_bucket(fe2_server* srv, int enable) {
+    if (!srv) return FE2_ERR_ARG;
+    srv->bucket = enable != 0;
+    return FE2_OK;
+}
+
+fe2_status fe2_server_memory_stats(const fe2_server* srv, long long* admitted, long long* evicted,
+                                   long long* deferred, size_t* device_bytes) {
+    if (!srv) return FE2_ERR_ARG;
+    if (admitted) *admitted = srv->ctx->n_admitted;
+    if (evicted) *evicted = srv->ctx->n_evicted;
+    if (deferred) *deferred = srv->n_deferred;
+    if (device_bytes) *device_bytes = used_bytes(srv->ctx);
     return FE2_OK;
 }
 

@@ -58,6 +58,10 @@ _SIGS = {
     "fe2_rve_bytes": (C.c_size_t, [_P, _I]),
     "fe2_rve_register": (_I, [_P, _I, _IP, C.POINTER(C.c_uint8), _I, _DP, _IP]),
     "fe2_rve_release": (_I, [_P, _I, _IP]),
+    "fe2_rve_define": (_I, [_P, _I, _IP, C.POINTER(C.c_uint8), _I, _DP, _IP]),
+    "fe2_rve_admit": (_I, [_P, _I, _IP]),
+    "fe2_rve_evict": (_I, [_P, _I, _IP]),
+    "fe2_rve_resident": (_I, [_P, _I]),
     "fe2_micro_assemble": (_I, [_P, _I, _IP, _P]),
     "fe2_nullspace_reduce": (_I, [_P, _I, _IP]),
     "fe2_condense": (_I, [_P, _I, _IP, _P, _P, _P, _P]),
@@ -91,6 +95,9 @@ _SIGS = {
     "fe2_server_pending": (_I, [_P]),
     "fe2_server_use_graphs": (_I, [_P, _I]),
     "fe2_server_graph_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
+    "fe2_server_bucket": (_I, [_P, _I]),
+    "fe2_server_memory_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                     C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]),
     "fe2_selftest_wait_timeout": (_I, [_P, _P]),
     "fe2_profile": (_I, [_P, _I]),
     "fe2_profile_read": (_I, [_P, _I, C.c_char_p, _DP, C.POINTER(C.c_longlong)]),
@@ -237,6 +244,31 @@ class Fe2Context:
 
     def register_batch(self, batch):
         return self.register(batch.N, batch.phase_concat(), batch.mat)
+
+    def define(self, N, phase_concat, mat):
+        """fe2_rve_define: RVE definitions without device state (admitted on use)."""
+        N = np.ascontiguousarray(np.asarray(N, dtype=np.int32))
+        ph = np.ascontiguousarray(np.asarray(phase_concat, dtype=np.uint8))
+        mat = np.ascontiguousarray(np.asarray(mat, dtype=np.float64))
+        out = np.zeros(len(N), dtype=np.int32)
+        st = self.lib.fe2_rve_define(self.h, len(N), N.ctypes.data_as(_IP), ph.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                     mat.shape[1], mat.ctypes.data_as(_DP), out.ctypes.data_as(_IP))
+        self._check(st, "fe2_rve_define")
+        return out
+
+    def define_batch(self, batch):
+        return self.define(batch.N, batch.phase_concat(), batch.mat)
+
+    def admit(self, ids):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_admit(self.h, len(a), p), "fe2_rve_admit")
+
+    def evict(self, ids):
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_evict(self.h, len(a), p), "fe2_rve_evict")
+
+    def resident(self, rve_id):
+        return int(self.lib.fe2_rve_resident(self.h, int(rve_id)))
 
     def release(self, ids):
         a, p = _ids(ids)

@@ -18,7 +18,7 @@ from .fe2 import Fe2Error, FE2_OK, _DP, _IP, fe2_last_error
 
 
 class Server:
-    def __init__(self, ctx, max_batch=1024, lanes=2, graphs=True):
+    def __init__(self, ctx, max_batch=1024, lanes=2, graphs=True, bucket=True):
         self.ctx = ctx
         self.lib = ctx.lib
         self.h = C.c_void_p()
@@ -26,7 +26,14 @@ class Server:
         if st != FE2_OK:
             raise Fe2Error(st, f"fe2_server_create: {fe2_last_error(ctx.h)}")
         self.lib.fe2_server_use_graphs(self.h, 1 if graphs else 0)
+        self.lib.fe2_server_bucket(self.h, 1 if bucket else 0)
         self.dd = ctx.dim * ctx.dim
+
+    def memory_stats(self):
+        """(defined RVEs admitted, evicted, requests passed over for memory, device bytes held)."""
+        a, e, dfr, b = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0), C.c_size_t(0)
+        self.lib.fe2_server_memory_stats(self.h, C.byref(a), C.byref(e), C.byref(dfr), C.byref(b))
+        return a.value, e.value, dfr.value, b.value
 
     def graph_stats(self):
         """(graphs captured, graph replays) of the lanes so far."""

@@ -39,9 +39,13 @@ def test_split_macro_update_equals_fused(torch):
     for split in (False, True):
         ctx = Fe2Context(dim=2, precision="fp64")
         fe = MonolithicFE2(ctx, X, conn, fixed, b)
-        ctx.macro_set_positions(X @ np.diag([1.05, 0.98]).T, which=fixed)
+        # a smooth non-affine deformation of every node: finite, positive Jacobians
+        q = X @ np.diag([1.05, 0.98]).T + 0.01 * np.sin(3.0 * X[:, ::-1])
+        ctx.macro_set_positions(q)
         ctx.macro_gradients(fe.Fbar)
         sig, Cb, st, err = ctx.rve_solve(fe.ids, fe.Fbar)
+        torch.cuda.synchronize()
+        assert (st.cpu().numpy() == 0).all()
         dF = torch.zeros_like(fe.Fbar)
         rn = torch.zeros(1, dtype=torch.float64, device="cuda")
         if split:
@@ -56,7 +60,7 @@ def test_split_macro_update_equals_fused(torch):
         out.append((dF.cpu().numpy(), rn.cpu().numpy(), ctx.macro_get_positions()))
         ctx.close()
     for a, c in zip(out[0], out[1]):
-        assert np.array_equal(a, c)
+        assert np.isfinite(a).all() and np.array_equal(a, c)
 
 
 class ThreadComm:
