@@ -101,6 +101,7 @@ struct fe2_ctx {
     std::vector<char*> free_slots;
     size_t extra_bytes = 0;         // device bytes counted against the budget by a server (lanes)
     std::set<std::pair<unsigned long long, int>> lru;  // resident defined RVEs by last use
+    int def_maxN = 0;                                  // largest defined mesh size
     long long n_admitted = 0, n_evicted = 0;
     int* d_macro_status = nullptr;
 };
@@ -986,6 +987,7 @@ fe2_status fe2_rve_define(fe2_ctx* ctx, int nrve, const int* N, const uint8_t* p
         need = std::max(need, persistent_bytes_of(N[k], d, nphase, 1));
     }
     if (ctx->slot_bytes == 0) ctx->slot_bytes = need;
+    for (int k = 0; k < nrve; ++k) ctx->def_maxN = std::max(ctx->def_maxN, N[k]);
     if (need > ctx->slot_bytes)
         return fail(ctx, FE2_ERR_ARG, "defined RVEs need %zu B slots, the pool has %zu B (define the largest first)",
                     need, ctx->slot_bytes);
@@ -1628,11 +1630,23 @@ struct fe2_server {
     long long n_deferred = 0;           // requests passed over for lack of device memory
 };
 
-// device bytes of the lanes (buffers and workspaces), counted against the budget
+// device bytes of the lanes counted against the budget: their buffers, and their
+// workspaces at the size a full batch of the largest defined RVE needs (so that
+// admissions leave room for the workspace a lane grows to later)
 static size_t lanes_bytes(const fe2_server* srv) {
-    const int dd = srv->ctx->cfg.dim * srv->ctx->cfg.dim;
+    fe2_ctx* ctx = srv->ctx;
+    const int d = ctx->cfg.dim, dd = d * d;
+    size_t wsmax = 0;
+    if (ctx->def_maxN) {
+        const int N = ctx->def_maxN, kd = compute_kd(ctx, N, d), nm = d * (nodes_of(N, d) - 1);
+        const int nmp = (nm + NB - 1) / NB * NB;
+        wsmax = (size_t)srv->max_batch * ws_layout(kd, dd + 1, nm, nmp, ctx->cfg.precision == FE2_PREC_FP64,
+                                                   ctx->max_smem, d).stride;
+    }
     size_t b = 0;
-    for (auto& L : srv->lanes) b += L.ws_bytes + (size_t)srv->max_batch * (3 * sizeof(int) + sizeof(double) * (dd + dd + dd * dd + 1));
+    for (auto& L : srv->lanes)
+        b += std::max(L.ws_bytes, wsmax) +
+             (size_t)srv->max_batch * (3 * sizeof(int) + sizeof(double) * (dd + dd + dd * dd + 1));
     return b;
 }
 
@@ -1877,6 +1891,7 @@ fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes) {
         L.busy = false;
     }
     // launch new batches on idle lanes
+    ctx->extra_bytes = lanes_bytes(srv);
     for (auto& L : srv->lanes) {
         if (L.busy || srv->queue.empty()) continue;
         int Nsel = -1;
