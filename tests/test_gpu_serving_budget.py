@@ -119,7 +119,7 @@ def test_admit_evict_and_refusals(torch):
     torch.cuda.synchronize()
     assert torch.equal(s1[0], s2[0]) and torch.equal(s1[1], s2[1])
     ctx.close()
-    ctx = Fe2Context(dim=2, precision="mixed", hbm_budget_bytes=1 << 20)
+    ctx = Fe2Context(dim=2, precision="mixed", hbm_budget_bytes=100_000)   # less than one slot
     ids = ctx.define_batch(b.subset([1]))
     with pytest.raises(Fe2Error) as ei:
         ctx.admit(ids)
