@@ -320,6 +320,12 @@ fe2_status fe2_rve_residual_norm(fe2_ctx* ctx, int n, const int* rve_ids, double
  * Synchronises the stream.
  */
 fe2_status fe2_rve_export(fe2_ctx* ctx, int rve_id, int what, double* host_out);
+/* Copy w~ of n RVEs (folded order) to row k of buf [device] double[n][ld]
+ * (to_buf = 1) or back (to_buf = 0): a device-side snapshot of the micro
+ * states, e.g. the classical scheme's restart of every inner Newton from the
+ * last converged load step (Section 4.1; the reading of Table 2).  ld >= the
+ * largest n_m. */
+fe2_status fe2_rve_w_copy(fe2_ctx* ctx, int n, const int* rve_ids, double* buf, int ld, int to_buf);
 /* Set w~ of one RVE from the natural numbering ([host] double[nm]). */
 fe2_status fe2_rve_set_w(fe2_ctx* ctx, int rve_id, const double* host_w);
 

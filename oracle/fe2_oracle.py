@@ -366,14 +366,19 @@ def micro_equilibrate_elem(N, d, phase, mat, Fbars, wq, w=None, tol=1e-13, maxit
     raise RuntimeError("micro Newton did not converge")
 
 
-def micro_equilibrate(N, d, phase, mat, Fbar, w=None, tol=1e-13, maxit=50, L=1.0):
+def micro_equilibrate(N, d, phase, mat, Fbar, w=None, tol=1e-13, maxit=50, L=1.0, history=None):
     """Classical inner Newton on one RVE at fixed Fbar (Section 4.1) until
-    ||r_m|| < tol; returns the equilibrium fluctuation and iteration count."""
+    ||r_m|| < tol; returns the equilibrium fluctuation and iteration count.
+    ``history`` (a list, optional) receives its list of ||r_m|| values."""
     nm = d * (N ** d - 1)
     w = np.zeros(nm) if w is None else np.array(w, dtype=np.float64)
+    mine = []
+    if history is not None:
+        history.append(mine)
     for it in range(maxit):
         ints = rve_integrals(N, d, phase, mat, Fbar, w, L)
         K_mm, r_m, _ = reduce_periodic(ints)
+        mine.append(float(np.linalg.norm(r_m)))
         if np.linalg.norm(r_m) < tol:
             return w, it
         w = w - scipy.linalg.cho_solve(scipy.linalg.cho_factor(K_mm, lower=True), r_m)
@@ -635,7 +640,8 @@ def monolithic_fe2_const(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_mi
 
 
 def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-12,
-                  maxit=25, maxit_micro=50, record=None, fext=None):
+                  maxit=25, maxit_micro=50, record=None, fext=None, micro_start="predicted",
+                  micro_record=None):
     """Classical (staggered, nested) FE^2 of Section 4.1 on the same macro
     problem as ``monolithic_fe2``: in every macro Newton iteration each RVE is
     first brought to micro equilibrium r_m = 0 at its current Fbar by an inner
@@ -644,7 +650,12 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
     macro residual and stiffness (Eq. (solution1)).  After the macro update
     the micro states follow Eq. (reduction), dw~ = -L^-1 E dq = -X_M : dFbar,
     and are re-equilibrated in the next iteration.
-    ``fext`` as in monolithic_fe2.  Returns the converged per-Gauss-point
+    ``fext`` as in monolithic_fe2.  ``micro_start`` = "last_converged" starts
+    every inner Newton from the micro states of the last converged load step
+    instead (no Eq. (reduction) update): the reading of Section 5.2, Table 2,
+    whose RVE residual sequences at macro iterations 3 and 4 of load step 1
+    coincide.  ``micro_record`` (a list) receives (step, it, max_b ||r_m||)
+    before every inner update.  Returns the converged per-Gauss-point
     states, the macro iteration count of every load step, the total number of
     inner micro iterations and q."""
     X, conn, bnd = macro
@@ -657,6 +668,7 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
     for n in bnd:
         free[2 * n:2 * n + 2] = False
     iters, micro_total = [], 0
+    w_conv = [w.copy() for w in ws]
     for k in range(1, n_steps + 1):
         Fk = np.eye(2) + (k / n_steps) * (np.asarray(F_final) - np.eye(2))
         q[bnd] = X[bnd] @ Fk.T
@@ -664,12 +676,15 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
             Kg = np.zeros((2 * nnode, 2 * nnode))
             Rg = np.zeros(2 * nnode)
             sols = []
+            hist = []
             for b in range(nb):
                 e = b // 4
                 Fb = q[conn[e]].T @ grads[b]
                 r = rves[b]
+                if micro_start == "last_converged":
+                    ws[b] = w_conv[b].copy()
                 ws[b], mit = micro_equilibrate(r["N"], 2, r["phase"], r["mat"], Fb, ws[b], tol=tol_micro,
-                                               maxit=maxit_micro)
+                                               maxit=maxit_micro, history=hist)
                 micro_total += mit
                 s = rve_solve(r["N"], 2, r["phase"], r["mat"], Fb, ws[b])
                 sols.append((Fb, s))
@@ -686,14 +701,21 @@ def staggered_fe2(macro, rves, F_final, n_steps=1, tol_macro=1e-9, tol_micro=1e-
             rnorm = np.linalg.norm(Rg[free])
             if record is not None:
                 record.append((k, it, rnorm))
+            if micro_record is not None:
+                # the largest residual over the RVEs before each inner update
+                for j in range(max(len(h) for h in hist)):
+                    micro_record.append((k, it, max(h[j] for h in hist if j < len(h))))
             if rnorm < tol_macro:
                 iters.append(it)
+                w_conv = [w.copy() for w in ws]
                 break
             if not rnorm < 1e10:
                 raise RuntimeError("macro residual above 1e10: Newton diverged")
             dq = np.zeros(2 * nnode)
             dq[free] = np.linalg.solve(Kg[np.ix_(free, free)], -Rg[free])
             q = q + dq.reshape(nnode, 2)
+            if micro_start == "last_converged":
+                continue
             # Eq. (reduction): dw~ = -L^-1 E dq, i.e. -X_M : dFbar per Gauss point
             for b in range(nb):
                 e = b // 4

@@ -1174,6 +1174,20 @@ fe2_status fe2_macro_step(fe2_ctx* ctx, int n, const int* rve_ids, const double*
     return FE2_OK;
 }
 
+fe2_status fe2_rve_w_copy(fe2_ctx* ctx, int n, const int* rve_ids, double* buf, int ld, int to_buf) {
+    if (!ctx) return FE2_ERR_ARG;
+    if (!buf) return fail(ctx, FE2_ERR_ARG, "buf is NULL");
+    const int* d_ids = nullptr;
+    fe2_status st = get_ids(ctx, n, rve_ids, &d_ids);
+    if (st != FE2_OK) return st;
+    const BatchInfo b = batch_info(ctx, n, rve_ids);
+    if (ld < b.maxnm) return fail(ctx, FE2_ERR_ARG, "row length %d below the largest n_m %d", ld, b.maxnm);
+    TIMED("w_copy", launch_w_copy(ctx->d_tab, d_ids, n, buf, ld, b.maxnm, to_buf ? 1 : 0, ctx->stream));
+    if (!to_buf)
+        for (int k = 0; k < n; ++k) ctx->mirror[rve_ids[k]].zero_w = 0;
+    return FE2_OK;
+}
+
 // folded index of natural node p = i + N j (+ N^2 k) of a 2D or 3D RVE
 static int fold_node(int p, int N, int d) {
     const int i = p % N, j = (p / N) % N;

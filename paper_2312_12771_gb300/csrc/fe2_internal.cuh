@@ -103,6 +103,8 @@ cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws,
 cudaError_t launch_macro_update(const RveDev* tab, const int* ids, int n, const double* dF,
                                 int maxnm, cudaStream_t s);
 cudaError_t launch_check_fbar(const double* Fbar, int n, int d, int* status, cudaStream_t s);
+cudaError_t launch_w_copy(const RveDev* tab, const int* ids, int n, double* buf, int ld, int maxnm, int to_buf,
+                          cudaStream_t s);
 
 // 3D (Hex8) and wide-band kernels (fe2_rve3d.cu)
 cudaError_t launch_assemble_elems3(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,

@@ -149,7 +149,31 @@ __global__ void k_macro_update(RveDev* __restrict__ tab, const int* __restrict__
     if (m == 0) tab[id].zero_w = 0;
 }
 
+// w~ of RVE slot y to row y of buf (to_buf) or back (a snapshot of the micro
+// states, e.g. of the last converged load step)
+__global__ void k_w_copy(RveDev* __restrict__ tab, const int* __restrict__ ids, double* __restrict__ buf, int ld,
+                         int to_buf) {
+    const int id = ids[blockIdx.y];
+    const RveDev r = tab[id];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < r.nm) {
+        double* b = buf + (size_t)blockIdx.y * ld + m;
+        if (to_buf)
+            *b = r.zero_w ? 0.0 : r.w[m];
+        else
+            r.w[m] = *b;
+    }
+    if (!to_buf && m == 0) tab[id].zero_w = 0;
+}
+
 }  // namespace
+
+cudaError_t launch_w_copy(const RveDev* tab, const int* ids, int n, double* buf, int ld, int maxnm, int to_buf,
+                          cudaStream_t s) {
+    dim3 grid((maxnm + 255) / 256, n);
+    k_w_copy<<<grid, 256, 0, s>>>(const_cast<RveDev*>(tab), ids, buf, ld, to_buf);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_schur(const RveDev* tab, const int* ids, int n, Workspace ws, int corrected, double* sigma,
                          double* Cbar, int* status, double* err, const double* tol, int* redo, cudaStream_t s,

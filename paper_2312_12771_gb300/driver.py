@@ -58,6 +58,7 @@ class NewtonLog:
     failed: bool = False
     micro_iters: int = 0                           # staggered: inner micro Newton updates (all RVEs at once)
     rve_solve_calls: int = 0                       # batched fe2_rve_solve calls
+    micro_history: list = field(default_factory=list)  # staggered: (step, it, max ||r_m||) before each update
 
 
 class MonolithicFE2:
@@ -81,6 +82,7 @@ class MonolithicFE2:
                              f"got {batch.nrve}")
         ctx.macro_setup(self.X, conn, self.fixed)
         self.ids = ctx.register_batch(batch)
+        self.maxnm = int(max(d * (int(N) ** d - 1) for N in batch.N))
         dev = "cuda"
         f64 = torch.float64
         self.Fbar = torch.zeros((ngp, d, d), dtype=f64, device=dev)
@@ -153,28 +155,35 @@ class MonolithicFE2:
         raise RuntimeError("macro Newton did not converge")
 
     def load_step_staggered(self, Fk, step, tol_macro=1e-9, tol_micro=1e-11, maxit=25, maxit_micro=30, log=None,
-                            F_prev=None):
+                            F_prev=None, micro_start="predicted"):
         """One load step of the classical staggered scheme (Section 4.1): in
         every macro iteration all RVEs are first brought to micro equilibrium
         at their current Fbar (inner Newton w~ <- w~ - x_r, i.e. the micro
         update with dFbar = 0, until max ||r_m|| < tol_micro); Pbar and the
         condensed tangent at that equilibrium then give the macro residual and
         stiffness (Eq. (solution1)); after the macro step the micro states follow
-        Eq. (reduction), dw~ = -X_M : dFbar, before they are re-equilibrated."""
+        Eq. (reduction), dw~ = -X_M : dFbar, before they are re-equilibrated.
+        With ``micro_start`` = "last_converged" every inner Newton instead starts
+        from the micro states of the last converged load step (a device-side
+        snapshot, fe2_rve_w_copy): the reading of Section 5.2, Table 2.""" 
         ctx = self.ctx
         if F_prev is not None:
             q = ctx.macro_get_positions() + self.X @ (np.asarray(Fk) - np.asarray(F_prev)).T
             ctx.macro_set_positions(q)
         ctx.macro_set_positions(self.X @ np.asarray(Fk).T, which=self.fixed)
         sig, Cb, st, err = self.outs
+        restart = micro_start == "last_converged"
         for it in range(maxit):
             ctx.macro_gradients(self.Fbar)
+            if restart:
+                ctx.w_copy(self.ids, self.wsnap, to_buf=False)
             for mit in range(maxit_micro):
                 ctx.rve_solve(self.ids, self.Fbar, out=self.outs)
                 ctx.rve_residual_norm(self.ids, self.rnm)
                 self.t.cuda.current_stream().synchronize()
                 if log is not None:
                     log.rve_solve_calls += 1
+                    log.micro_history.append((step, it, float(self.rnm.max().item())))
                 bad = int((st != 0).sum().item())
                 if bad:
                     if log is not None:
@@ -203,14 +212,17 @@ class MonolithicFE2:
             if rmac < tol_macro:
                 if log is not None:
                     log.iters.append(it)
+                if restart:
+                    ctx.w_copy(self.ids, self.wsnap, to_buf=True)
                 return it
             if rmac > 1e10 or not np.isfinite(rmac):
                 if log is not None:
                     log.failed = True
                 raise RuntimeError(f"macro residual {rmac:.3e}: Newton diverged")
             ctx.macro_solve(sig, Cb, self.dFbar, self.rn[1:2], self.mstatus)
-            # Eq. (reduction): dw~ = -X_M : dFbar (x_r vanishes at micro equilibrium)
-            ctx.macro_step(self.ids, self.dFbar)
+            if not restart:
+                # Eq. (reduction): dw~ = -X_M : dFbar (x_r vanishes at micro equilibrium)
+                ctx.macro_step(self.ids, self.dFbar)
         if log is not None:
             log.failed = True
         raise RuntimeError("macro Newton did not converge")
@@ -224,6 +236,9 @@ class MonolithicFE2:
         to the failure."""
         log = NewtonLog() if log is None else log
         step_fn = self.load_step if scheme == "monolithic" else self.load_step_staggered
+        if kw.get("micro_start") == "last_converged":   # snapshot of the start state
+            self.wsnap = self.t.zeros((len(self.ids), self.maxnm), dtype=self.t.float64, device="cuda")
+            self.ctx.w_copy(self.ids, self.wsnap, to_buf=True)
         F_final = np.asarray(F_final, float)
         I = np.eye(self.d)
         F_prev = I

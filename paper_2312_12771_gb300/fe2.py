@@ -84,6 +84,7 @@ _SIGS = {
     "fe2_rve_residual_norm": (_I, [_P, _I, _IP, _P]),
     "fe2_rve_export": (_I, [_P, _I, _I, _DP]),
     "fe2_rve_set_w": (_I, [_P, _I, _DP]),
+    "fe2_rve_w_copy": (_I, [_P, _I, _IP, _P, _I, _I]),
     "fe2_launch_count": (C.c_longlong, [_P]),
     "fe2_rve_solve_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "fe2_noalloc_last_error": (C.c_char_p, []),
@@ -436,6 +437,12 @@ class Fe2Context:
         if what == 2:
             return out.reshape(nm, d * d)
         return out
+
+    def w_copy(self, ids, buf, to_buf):
+        """Snapshot (to_buf) or restore w~ of the RVEs through buf [n, ld] (CUDA, f64)."""
+        a, p = _ids(ids)
+        self._check(self.lib.fe2_rve_w_copy(self.h, len(a), p, _ptr(buf), int(buf.shape[1]), 1 if to_buf else 0),
+                    "fe2_rve_w_copy")
 
     def set_w(self, rve_id, w):
         w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))

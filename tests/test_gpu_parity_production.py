@@ -309,3 +309,37 @@ def test_hex8_8cubed_both_paths(torch, precision):
         w = ctx.export(ids[k], 3, N)
         assert np.abs(w - ws[k]).max() <= 1e-15       # w~ round trip in 3D
     ctx.close()
+
+
+@pytest.mark.parametrize("micro_start", ["predicted", "last_converged"])
+def test_cook_classical_scheme_restart_variants_match_oracle(torch, micro_start):
+    """Section 5.2, Cook's membrane on a 2 x 2 macro mesh with 6 x 6 cross
+    RVEs, classical scheme in 2 load steps, with the inner Newton starting
+    from the Eq. (reduction) prediction or from the last converged load step
+    (the reading of Table 2): macro iteration counts, inner residual sequence
+    lengths and converged nodal positions equal the oracle's."""
+    from paper_2312_12771_gb300.driver import MonolithicFE2, NewtonLog
+    from paper_2312_12771_gb300.fe2 import Fe2Context
+    X, conn, left, right = W.cook_mesh(2, 2)
+    fixed = np.zeros(2 * len(X), np.uint8)
+    for n in left:
+        fixed[2 * n:2 * n + 2] = 1
+    b = W.cook_batch(4 * len(conn), 6)
+    ctx = Fe2Context(dim=2, precision="fp64")
+    fe = MonolithicFE2(ctx, X, conn, fixed, b)
+    log = NewtonLog()
+    kw = dict(tol_macro=1e-9, tol_micro=1e-11)
+    fe.run(np.eye(2), 2, scheme="staggered", traction=(right, W.MEMBRANE_TRACTION), log=log,
+           micro_start=micro_start, **kw)
+    q = fe.ctx.macro_get_positions()
+    rves = [dict(N=6, phase=b.phase[k], mat=b.mat[k]) for k in range(b.nrve)]
+    fo = O.traction_load(X, right, W.MEMBRANE_TRACTION)
+    mrec = []
+    out, iters, _, q_ref = O.staggered_fe2((X, conn, left), rves, np.eye(2), n_steps=2, fext=fo,
+                                           micro_start=micro_start, micro_record=mrec, **kw)
+    assert log.iters == iters
+    assert np.abs(q - q_ref).max() <= 1e-8 * np.abs(q_ref).max()
+    # the same number of inner residual evaluations per macro iteration
+    count = lambda rec: sorted({(k, it): sum(1 for x in rec if x[:2] == (k, it)) for (k, it, _) in rec}.items())
+    assert count(log.micro_history) == count(mrec)
+    ctx.close()

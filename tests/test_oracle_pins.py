@@ -599,6 +599,36 @@ def test_staggered_and_monolithic_reach_the_same_equilibrium():
             assert r1 < 10.0 * r0 * r0 + 1e-11
 
 
+def test_staggered_restart_from_last_converged_state():
+    """Section 5.2, Table 2 reading: when every inner Newton restarts from the
+    micro states of the last converged load step, the classical scheme still
+    reaches the monolithic equilibrium (the same discrete equations), its
+    inner iterations restart at the same residual whenever Fbar has
+    converged (equal first inner residuals in the last two macro iterations
+    of a load step, as in the paper's table).""" 
+    macro = O.macro_mesh(3, 2)          # interior nodes: a real macro Newton
+    rves = []
+    for b in range(24):
+        c, r = W.random_inclusions(W.GLOBAL_SEED, 100 + b)
+        rves.append(dict(N=4, phase=W.inclusion_phase(4, 2, c, r),
+                         mat=W.neohooke_mat(1.0, 10.0, 20.0, 200.0)))
+    F = np.diag([1.06, 1.0]) + np.array([[0.0, 0.02], [0.0, 0.0]])
+    mono, it_m, q_m = O.monolithic_fe2(macro, rves, F, n_steps=2, tol_macro=1e-11, tol_micro=1e-11)
+    mrec = []
+    stag, it_s, micro, q_s = O.staggered_fe2(macro, rves, F, n_steps=2, tol_macro=1e-11, tol_micro=1e-12,
+                                             micro_start="last_converged", micro_record=mrec)
+    assert np.abs(q_m - q_s).max() < 1e-10
+    for a, b in zip(mono, stag):
+        assert O.rel_err(b["Cbar"], a["Cbar"]) < 1e-9
+    assert micro > 0
+    first = {}
+    for k, it, r in mrec:
+        first.setdefault((k, it), r)
+    last = max(it for (k, it) in first if k == 2)
+    r_a, r_b = first[(2, last - 1)], first[(2, last)]
+    assert abs(r_a - r_b) <= 1e-6 * r_b
+
+
 def test_mooney_rivlin_membrane_form_and_limits():
     """Section 5.2: the printed two-dimensional membrane energy
     alpha (F:F - 2) + beta (F:F + J^2 - 3) + kappa/2 (J-1)^2 - 2 (alpha+2beta) ln J
