@@ -411,7 +411,11 @@ def run_serving(args, dev):
     simulate(srv, ids[:summary_n], Fb[:summary_n], z)
     _, _, _, cap_direct = simulate(srv, ids[:summary_n], Fb[:summary_n], z)
     srv.close()
-    srv = Server(ctx, max_batch=args.serve_batch, lanes=2)
+    # the tuner's choice of batch limit, lane count and mixed-size batches on this stream
+    from paper_2312_12771_gb300 import tune
+    tuned = tune.tune_server(ctx, ids[:summary_n], Fb[:summary_n], sizes[:summary_n])
+    cfg = tuned["best"]
+    srv = Server(ctx, max_batch=cfg["max_batch"], lanes=cfg["lanes"], mixed=cfg["mixed"])
     sweep, bad = [], 0
     kept = None
     for n in nreqs:
@@ -436,7 +440,12 @@ def run_serving(args, dev):
            "summary_n_req": summary_n, "capacity_solves_per_s": main["capacity_solves_per_s"],
            "capacity_without_graphs": round(cap_direct, 1), "offered_rate": at08["offered"],
            "throughput_solves_per_s": at08["throughput"], "p50_ms": at08["p50_ms"], "p99_ms": at08["p99_ms"],
-           "graphs_captured_replayed": list(srv.graph_stats()), "max_batch": args.serve_batch, "lanes": 2,
+           "graphs_captured_replayed": list(srv.graph_stats()), "max_batch": cfg["max_batch"],
+           "lanes": cfg["lanes"], "mixed_size_batches": cfg["mixed"],
+           "tuned": {"config": cfg, "burst_capacity": tuned["capacity"], "default_config": tune.DEFAULT_SERVER,
+                     "default_burst_capacity": tuned["default"],
+                     "gain": round(tuned["capacity"] / max(tuned["default"], 1e-9), 3), "table": tuned["table"]},
+           "memory_stats": list(srv.memory_stats()),
            "status_nonzero": bad, "hbm_budget_gb": args.serve_budget_gb, "sweep": sweep}
     srv.close()
     # the served results of the 0.8 x capacity run, sampled per mesh size, against the oracle
@@ -972,6 +981,10 @@ def main():
             "fp64_path": {"value": round(value64, 1), "ms_per_step": round(ms64 / R["fp64"]["steps"], 3),
                           "steps": R["fp64"]["steps"], "kernels": kern64},
             "tensor_core_path": tc_leg, "pipelined_factor_path": panel_leg,
+            "factor_kernel_timings_ms": {k: v for k, v in (
+                ("cuda_core", round(ms / mx["steps"], 4)),
+                ("tensor_core", tc_leg["ms_per_step"] if tc_leg else None),
+                ("cuda_core_pipelined", panel_leg["ms_per_step"] if panel_leg else None)) if v is not None},
             "speedup_mixed_vs_fp64": round(value / value64, 2),
             "max_rel_err_mixed_vs_fp64_gpu": err_mixed_vs_fp64,
             "status_nonzero": int((mx["status"] != 0).sum()),

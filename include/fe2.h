@@ -382,8 +382,8 @@ const char* fe2_noalloc_last_error(void);
  * own CUDA stream, factorisation workspace, pinned staging and completion
  * event: a batch formed while another runs is launched at once and overlaps it
  * on the device.  A batch takes up to max_batch queued requests of one mesh
- * size (that of the oldest request) whose RVE is not already in flight, in
- * submission order.  Results are bit-identical to solving the RVE alone.
+ * size (that of the oldest request; any sizes with fe2_server_mixed_sizes)
+ * whose RVE is not already in flight, in submission order.  Results are bit-identical to solving the RVE alone.
  *
  * fe2_server_submit: queue n requests (rve_ids [host], Fbar [host]
  *   double[n][d][d]); tickets [host] long long[n] receives their ids.
@@ -399,6 +399,9 @@ const char* fe2_noalloc_last_error(void);
  *   batches of that shape; on by default, enable = 0 launches every kernel
  *   from the host instead.  The results are the same either way.
  * fe2_server_graph_stats: captures and replays so far ([host], may be NULL).
+ * fe2_server_mixed_sizes: enable = 1 lets a batch take the oldest queued
+ *   requests whatever their mesh sizes (one launch of uneven RVEs, shared
+ *   memory and workspace sized for the largest); default 0 (one size per batch).
  * fe2_server_bucket: with graphs on, round each batch down to a power of two
  *   (the rest stay at the head of the queue) so that captured graphs are
  *   replayed (default on).
@@ -417,6 +420,7 @@ int fe2_server_pending(const fe2_server* srv);
 fe2_status fe2_server_use_graphs(fe2_server* srv, int enable);
 fe2_status fe2_server_graph_stats(const fe2_server* srv, long long* captures, long long* replays);
 fe2_status fe2_server_bucket(fe2_server* srv, int enable);
+fe2_status fe2_server_mixed_sizes(fe2_server* srv, int enable);
 fe2_status fe2_server_memory_stats(const fe2_server* srv, long long* admitted, long long* evicted,
                                    long long* deferred, size_t* device_bytes);
 

@@ -1641,6 +1641,7 @@ struct fe2_server {
     std::unordered_set<int> inflight;
     long long next_ticket = 1;
     bool bucket = true;                 // batch sizes rounded down to powers of two (graph reuse)
+    bool mixed = false;                 // batches may mix mesh sizes (one launch of uneven RVEs)
     long long n_deferred = 0;           // requests passed over for lack of device memory
 };
 
@@ -1918,7 +1919,7 @@ fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes) {
             }
             const int N = ctx->mirror[id].N;
             if (Nsel < 0) Nsel = N;
-            if (N != Nsel) {
+            if (N != Nsel && !srv->mixed) {
                 ++it;
                 continue;
             }
@@ -1986,6 +1987,12 @@ int fe2_server_take(fe2_server* srv, int max, long long* tickets, double* sigma,
 fe2_status fe2_server_use_graphs(fe2_server* srv, int enable) {
     if (!srv) return FE2_ERR_ARG;
     srv->use_graphs = enable != 0;
+    return FE2_OK;
+}
+
+fe2_status fe2_server_mixed_sizes(fe2_server* srv, int enable) {
+    if (!srv) return FE2_ERR_ARG;
+    srv->mixed = enable != 0;
     return FE2_OK;
 }
 

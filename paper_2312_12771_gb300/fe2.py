@@ -97,6 +97,7 @@ _SIGS = {
     "fe2_server_use_graphs": (_I, [_P, _I]),
     "fe2_server_graph_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "fe2_server_bucket": (_I, [_P, _I]),
+    "fe2_server_mixed_sizes": (_I, [_P, _I]),
     "fe2_server_memory_stats": (_I, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                      C.POINTER(C.c_longlong), C.POINTER(C.c_size_t)]),
     "fe2_selftest_wait_timeout": (_I, [_P, _P]),

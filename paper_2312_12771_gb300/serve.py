@@ -18,7 +18,7 @@ from .fe2 import Fe2Error, FE2_OK, _DP, _IP, fe2_last_error
 
 
 class Server:
-    def __init__(self, ctx, max_batch=1024, lanes=2, graphs=True, bucket=True):
+    def __init__(self, ctx, max_batch=1024, lanes=2, graphs=True, bucket=True, mixed=False):
         self.ctx = ctx
         self.lib = ctx.lib
         self.h = C.c_void_p()
@@ -27,6 +27,7 @@ class Server:
             raise Fe2Error(st, f"fe2_server_create: {fe2_last_error(ctx.h)}")
         self.lib.fe2_server_use_graphs(self.h, 1 if graphs else 0)
         self.lib.fe2_server_bucket(self.h, 1 if bucket else 0)
+        self.lib.fe2_server_mixed_sizes(self.h, 1 if mixed else 0)
         self.dd = ctx.dim * ctx.dim
 
     def memory_stats(self):
