@@ -47,7 +47,7 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*
 // dx^T R; X' is stored.  The estimate |tr(dx_M^T R_M)| / ||Cbar|| *
 // ||dx_M|| / ||X_M|| is that product.
 template <int SECOND>
-__global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
+__global__ void __launch_bounds__(256, 2) k_schur2(const RveDev* __restrict__ tab, const int* __restrict__ ids,
                                                 Workspace ws, int corrected, double* __restrict__ sigma,
                                                 double* __restrict__ Cbar, int* __restrict__ status,
                                                 double* __restrict__ err, const double* __restrict__ tol,
@@ -65,11 +65,15 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
 #pragma unroll
     for (int k = 0; k < NA; ++k) acc[k] = 0.0;
     for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-        double b[4], x[5], xn[5], rr[5];
-#pragma unroll
-        for (int a = 0; a < 4; ++a) b[a] = B[(size_t)a * nm + m];
+        double x[5], rr[5];
 #pragma unroll
         for (int c = 0; c < 5; ++c) x[c] = X[(size_t)c * nm + m];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const double b = B[(size_t)a * nm + m];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc[a * 5 + c] += b * x[c];
+        }
         if (corrected) {
 #pragma unroll
             for (int c = 0; c < 5; ++c) rr[c] = R[(size_t)c * nm + m];
@@ -78,28 +82,23 @@ __global__ void __launch_bounds__(256) k_schur2(const RveDev* __restrict__ tab, 
             for (int c = 0; c < 5; ++c) rr[c] = 0.0;
         }
         if constexpr (SECOND) {
+            // x becomes X' = X + dx (stored): the correction term uses X'
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
                 const double dx = (double)dX[(size_t)c * nmp + m];
-                xn[c] = x[c] + dx;
                 if (c < 4) {
                     acc[NA - 3] += dx * rr[c];
                     acc[NA - 2] += dx * dx;
                     acc[NA - 1] += x[c] * x[c];
                 }
-                X[(size_t)c * nm + m] = xn[c];
+                x[c] += dx;
+                X[(size_t)c * nm + m] = x[c];
             }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 5; ++c) xn[c] = x[c];
         }
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                acc[a * 5 + c] += b[a] * x[c];
-                acc[20 + a * 5 + c] += xn[a] * rr[c];
-            }
+            for (int c = 0; c < 5; ++c) acc[20 + a * 5 + c] += x[a] * rr[c];
     }
     cta_sum<NA>(acc, red);
     if (threadIdx.x == 0) {
