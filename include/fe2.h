@@ -403,8 +403,8 @@ const char* fe2_noalloc_last_error(void);
  *   requests whatever their mesh sizes (one launch of uneven RVEs, shared
  *   memory and workspace sized for the largest); default 0 (one size per batch).
  * fe2_server_bucket: with graphs on, round each batch down to a power of two
- *   (the rest stay at the head of the queue) so that captured graphs are
- *   replayed (default on).
+ *   or 1.5 times one (the rest stay at the head of the queue) so that
+ *   captured graphs are replayed (default on).
  * fe2_server_memory_stats: defined RVEs admitted and evicted so far, requests
  *   passed over for lack of memory, device bytes held against the budget
  *   ([host], may be NULL).

@@ -1941,11 +1941,16 @@ fe2_status fe2_server_pump(fe2_server* srv, int* busy_lanes) {
             it = srv->queue.erase(it);
         }
         if (srv->bucket && srv->use_graphs && L.batch.size() > 1) {
-            // a power-of-two batch size, so that lanes replay their captured graphs; the
+            // a batch size from a short list, so that lanes replay their captured graphs; the
             // rest go back to the head of the queue in their order (their admission copies,
             // queued on this lane's idle stream, complete first: another lane may take them)
+            // sizes 1, 2, 3, 4, 6, 8, 12, 16, 24, ...: powers of two and 1.5 times them, so at
+            // most a third of the batch waits for the next one
             size_t m = 1;
-            while (2 * m <= L.batch.size()) m *= 2;
+            for (size_t p = 1; p <= L.batch.size(); p *= 2) {
+                m = p;
+                if (p + p / 2 <= L.batch.size() && p >= 2) m = p + p / 2;
+            }
             if (m < L.batch.size()) CK(cudaStreamSynchronize(L.s));
             for (size_t k = L.batch.size(); k-- > m;) {
                 taken.erase(L.batch[k].rve);
