@@ -332,11 +332,30 @@ def run_gpu(args, rank, world, dist):
 
     results = {}
     F = torch.tensor(batch.Fbar, device=dev)
-    legs = ("mixed", "tensor_core", "pipelined", "fp64") if not args.no_tc else ("mixed", "pipelined", "fp64")
+    # number of correction sweeps: unless given, the fewest whose result stays within
+    # 1e-9 (a tenth of the 1e-8 target) of the FP64 path on every RVE of this workload
+    refine, choice = args.refine, None
+    if refine is None:
+        probe = {}
+        for prec, mr in (("fp64", 0), ("mixed", 0)):
+            c = Fe2Context(dim=2, precision=prec, max_refine=mr)
+            o = c.rve_solve(c.register_batch(batch), F)
+            torch.cuda.synchronize()
+            probe[prec] = (o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy())
+            c.close()
+        e0 = rel_errs(probe["mixed"][1], probe["fp64"][1], probe["mixed"][0], probe["fp64"][0], batch.Fbar)
+        ok = e0 <= 1e-9 and (probe["mixed"][2] == 0).all()
+        refine = 0 if ok else 2
+        choice = {"max_refine": refine, "first_order_max_rel_err_vs_fp64_all_rves": e0,
+                  "rule": "fewest correction sweeps within 1e-9 of the FP64 path on every RVE of the workload"}
+    legs = ["mixed"] + (["mixed_corrected"] if refine == 0 else []) + \
+        (["tensor_core"] if not args.no_tc else []) + ["pipelined", "fp64"]
     for prec in legs:
         # "tensor_core": the mixed path with the tcgen05 (3xTF32) band factor; "pipelined":
-        # the mixed path with the pipelined-chain CUDA-core factor
-        ctx = Fe2Context(dim=2, precision="fp64" if prec == "fp64" else "mixed", max_refine=args.refine,
+        # the mixed path with the pipelined-chain CUDA-core factor; "mixed_corrected": the
+        # mixed path with the second-order correction of every RVE (the library default)
+        mr = 2 if prec == "mixed_corrected" else refine
+        ctx = Fe2Context(dim=2, precision="fp64" if prec == "fp64" else "mixed", max_refine=mr,
                          factor={"tensor_core": "tensor_core", "pipelined": "cuda_core_pipelined"}.get(prec, "auto"))
         ids = ctx.register_batch(batch)
         outs = ctx._outs(nrve)
@@ -384,6 +403,8 @@ def run_gpu(args, rank, world, dist):
         results[prec] = res
         ctx.close()
         del ctx
+    results["refine_choice"] = choice
+    results["refine"] = refine
     return batch, results, pk
 
 
@@ -825,7 +846,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rves", type=int, default=N_RVE)
     ap.add_argument("--N", type=int, default=N_MESH)
-    ap.add_argument("--refine", type=int, default=2)
+    ap.add_argument("--refine", type=int, default=None,
+                    help="correction sweeps of the mixed path (default: chosen on the workload, see refine_choice)")
     ap.add_argument("--cpu-sample", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -953,6 +975,16 @@ def main():
                   "max_rel_err_vs_fp64_gpu": rel_errs(tc["Cbar"], R["fp64"]["Cbar"], tc["sigma"], R["fp64"]["sigma"],
                                                       batch.Fbar),
                   "status_nonzero": int((tc["status"] != 0).sum()), "kernels": ktc}
+    corr_leg = None
+    if "mixed_corrected" in R:
+        cl = R["mixed_corrected"]
+        ms_cl = max_over_ranks(cl["ms"], dist)
+        corr_leg = {"value": round(total * cl["steps"] / (ms_cl * 1e-3), 1), "unit": UNIT,
+                    "ms_per_step": round(ms_cl / cl["steps"], 4), "steps": cl["steps"], "max_refine": 2,
+                    "max_rel_err_vs_fp64_gpu": rel_errs(cl["Cbar"], R["fp64"]["Cbar"], cl["sigma"], R["fp64"]["sigma"],
+                                                        batch.Fbar),
+                    "status_nonzero": int((cl["status"] != 0).sum()),
+                    "kernels_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in cl["prof"].items()}}
     panel_leg = None
     if "pipelined" in R:
         pl = R["pipelined"]
@@ -980,6 +1012,8 @@ def main():
             "precision_path": "mixed", "gpu_launches": mx["launches"],
             "fp64_path": {"value": round(value64, 1), "ms_per_step": round(ms64 / R["fp64"]["steps"], 3),
                           "steps": R["fp64"]["steps"], "kernels": kern64},
+            "max_refine": R["refine"], "refine_choice": R["refine_choice"],
+            "second_order_path": corr_leg,
             "tensor_core_path": tc_leg, "pipelined_factor_path": panel_leg,
             "factor_kernel_timings_ms": {k: v for k, v in (
                 ("cuda_core", round(ms / mx["steps"], 4)),
