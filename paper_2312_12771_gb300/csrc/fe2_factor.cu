@@ -1033,6 +1033,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                 const int c = t % NB, rr = t / NB;
                 const T* Lc = Lb + c * LDL;
                 const T* xp = xr + rr * 2 * S + s0 + c - NB;  // x(j0 + c + off) = xp[off]
+                const T yv = ysrc[(size_t)rr * nmp + j0 + c];  // issued before the dot product
                 T s0a = T(0), s1a = T(0), s2a = T(0), s3a = T(0);
                 int off = NB - c;
                 for (; off + 3 <= kd; off += 4) {
@@ -1042,7 +1043,7 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                     s3a += Lc[off + 3] * xp[off + 3];
                 }
                 for (; off <= kd; ++off) s0a += Lc[off] * xp[off];
-                tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - ((s0a + s1a) + (s2a + s3a));
+                tv[rr][c] = yv - ((s0a + s1a) + (s2a + s3a));
             }
         }
         __syncthreads();
@@ -1160,6 +1161,18 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
         }
         const T* Lb = ls.buf(b);
         const T* db = ls.dinv(b);
+        // residual rows that refill the ring slots this block frees, loaded now so that
+        // their latency overlaps the triangle and the rows below
+        double pre[(MAX_NR * NB + FACT_THREADS - 1) / FACT_THREADS];
+#pragma unroll
+        for (int q = 0; q < (MAX_NR * NB + FACT_THREADS - 1) / FACT_THREADS; ++q) {
+            const int k = tid + q * FACT_THREADS;
+            pre[q] = 0.0;
+            if (k < nr * NB) {
+                const int rr = k / NB, row = j0 + S + (k - rr * NB);
+                if (row < nm) pre[q] = Rg[(size_t)rr * nm + row];
+            }
+        }
         // triangle: warp rr, lane c owns b_c; column sweep
         for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
             T bv = bw[rr * S + wrapS(jb + lane, S)], yc = T(0);
@@ -1181,10 +1194,13 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
             fwd_rows_below<T, 10>(Lb, yt, bw, kd, LDL, S, jb, nr);
         else
             fwd_rows_below<T, MAX_NR>(Lb, yt, bw, kd, LDL, S, jb, nr);
-        for (int k = tid; k < nr * NB; k += blockDim.x) {
-            const int rr = k / NB, c = k - rr * NB;
-            const int row = j0 + S + c;
-            bw[rr * S + wrapS(jb + c, S)] = (row < nm) ? (T)Rg[(size_t)rr * nm + row] : T(0);
+#pragma unroll
+        for (int q = 0; q < (MAX_NR * NB + FACT_THREADS - 1) / FACT_THREADS; ++q) {
+            const int k = tid + q * FACT_THREADS;
+            if (k < nr * NB) {
+                const int rr = k / NB, c = k - rr * NB;
+                bw[rr * S + wrapS(jb + c, S)] = (T)pre[q];
+            }
         }
         __syncthreads();
         if (b + 1 < nblk && ls.nbuf == 1) ls.issue(b + 1, j0 + NB);  // the buffer is free again
