@@ -31,24 +31,44 @@ constexpr int STG_COMPS = 36;           // 9 neighbour blocks x 2 x 2 per node r
 
 __device__ __forceinline__ int wrapS(int x, int S) { return x >= S ? x - S : x; }
 
+// Packed copy of the factored diagonal block L11 for the panel-row solve:
+// column c holds rows 4 floor(c/4) .. NB-1 (a multiple of 4 entries, so every
+// column starts on a 16-byte boundary and is read as 16-byte broadcasts), and
+// its diagonal entry holds the reciprocal pivot 1 / L11(c, c) instead of L11(c, c).
+__host__ __device__ constexpr int l11_off(int c) {
+    int o = 0;
+    for (int k = 0; k < c; ++k) o += NB - 4 * (k / 4);
+    return o;
+}
+constexpr int L11P_LEN = l11_off(NB);
+
 template <typename T>
 struct FactLayout {
-    int kd, S, LDW, KR, KP, nr, nblk;
-    size_t offPn, offBw, offDinv, offBlk, offStg, offBstg, total;
+    int kd, S, LDW, KR, KP, RB, nr, nblk;
+    size_t offPn, offL11, offBw, offDinv, offBlk, offStg, offBstg, total;
     __host__ __device__ void init(int kd_, int nr_) {
         kd = kd_;
         nr = nr_;
         S = kd + NB;
         LDW = (kd + 2) & ~1;  // even: aligned pairs in a column, conflict-free update write-back
         KR = kd + nr;
-        KP = (KR + 31) & ~31;
-        const int RB = KP / 32, CB = (kd + 31) / 32;
+        // Pn column stride: KR rounded up to 4 (16-byte columns).  The update blocks
+        // cover RB = ceil(KR / 32) row blocks; their lanes beyond KP read the start
+        // of the next column, or for the last column a zero pad of 32 RB - KP entries
+        // behind Pn, and drop the results, as they drop every row >= KR.  Pn is only
+        // written while no update block runs, so these reads race with nothing.
+        KP = (KR + 3) & ~3;
+        RB = (KR + 31) / 32;
+        const int CB = (kd + 31) / 32;
         nblk = 0;
         for (int K = 0; K < CB; ++K) nblk += RB - K;
         size_t o = (size_t)S * LDW * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offPn = o;
-        o += (size_t)NB * KP * sizeof(T);
+        o += (size_t)pn_len() * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offL11 = o;
+        o += (size_t)L11P_LEN * sizeof(T);
         offBw = o;
         o += (size_t)nr * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
@@ -65,6 +85,7 @@ struct FactLayout {
         o += (size_t)nr * NB * sizeof(T);
         total = (o + 15) & ~(size_t)15;
     }
+    __host__ __device__ int pn_len() const { return NB * KP + 32 * RB - KP; }
 };
 
 template <typename T>
@@ -124,18 +145,29 @@ __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __rest
     }
 }
 
-// Step C of the right-looking solve of one panel row v against L11 (rows of
-// L11 read as broadcasts from the ring window).  The half bandwidth is at least
-// NB (the registration clamps it), so every entry of L11 lies in the band.
+// Step C of the right-looking solve of one panel row v against L11: column C
+// of the packed L11 (rows 4 floor(C/4) .. NB-1, the reciprocal pivot on the
+// diagonal) arrives as 16-byte broadcasts.  The half bandwidth is at least NB
+// (the registration clamps it), so every entry of L11 lies in the band.
 template <typename T, int C>
-__device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict__ W, int base, int S, int LDW,
-                                                const T* __restrict__ dinv) {
+__device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict__ L11p) {
     if constexpr (C < NB) {
-        const T* Lc = W + (size_t)(base + C >= S ? base + C - S : base + C) * LDW;
-        v[C] *= dinv[C];
+        constexpr int g0 = C / 4;
+        const T* col = L11p + l11_off(C) - 4 * g0;  // col[i] = L11(i, C), i >= 4 g0
 #pragma unroll
-        for (int c2 = C + 1; c2 < NB; ++c2) v[c2] -= v[C] * Lc[c2 - C];
-        panel_row_steps<T, C + 1>(v, W, base, S, LDW, dinv);
+        for (int g = g0; g < NB / 4; ++g) {
+            T lc[4];
+            Vec4<T>::load(col + 4 * g, lc);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int c2 = 4 * g + u;
+                if (c2 == C)
+                    v[C] *= lc[u];
+                else if (c2 > C)
+                    v[c2] -= v[C] * lc[u];
+            }
+        }
+        panel_row_steps<T, C + 1>(v, L11p);
     }
 }
 
@@ -280,6 +312,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     const int nmp = r.nm_pad, nm = r.nm, nn = r.nn;
     T* W = (T*)smem;
     T* Pn = (T*)(smem + lay.offPn);
+    T* L11p = (T*)(smem + lay.offL11);
     T* Bw = (T*)(smem + lay.offBw);
     T* dinv = (T*)(smem + lay.offDinv);
     unsigned* blk = (unsigned*)(smem + lay.offBlk);
@@ -297,12 +330,13 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     // ---- init: block list, zero buffers, first kd columns straight from HBM
     if (tid == 0) {
         s_bad = 0;
-        const int RB = KP / 32, CB = (kd + 31) / 32;
+        const int RB = lay.RB, CB = (kd + 31) / 32;
         int x = 0;
         for (int K = 0; K < CB; ++K)
             for (int I = K; I < RB; ++I) blk[x++] = (unsigned)I | ((unsigned)K << 16);
     }
-    for (int k = tid; k < NB * KP; k += blockDim.x) Pn[k] = T(0);
+    for (int k = tid; k < lay.pn_len(); k += blockDim.x) Pn[k] = T(0);
+    for (int k = tid; k < L11P_LEN; k += blockDim.x) L11p[k] = T(0);
     for (int k = tid; k < S * LDW; k += blockDim.x) W[k] = T(0);
     for (int k = tid; k < nr * S; k += blockDim.x) {
         const int rr = k / S, c = k - rr * S;
@@ -355,7 +389,12 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
             for (int c = 0; c < NB; ++c)
                 if (c <= lane && lane - c <= kd) W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] = a[c];
-            Dg[j0 + lane] = dinv[lane];
+            const T dl = dinv[lane];
+            Dg[j0 + lane] = dl;
+            // packed L11 for the panel rows (a[c] is zero above the diagonal)
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (lane >= 4 * (c / 4)) L11p[l11_off(c) + lane - 4 * (c / 4)] = (lane == c) ? dl : a[c];
         } else {
             const int t0 = tid - 32, nt = blockDim.x - 32;
             if (j0 > 0) {  // L and y of the previous panel out, before its slots are reused
@@ -412,7 +451,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) v[c] = Bp[wrapS(base + c, S)];
             }
-            panel_row_steps<T, 0>(v, W, base, S, LDW, dinv);
+            panel_row_steps<T, 0>(v, L11p);
 #pragma unroll
             for (int c = 0; c < NB; ++c) Pn[c * KP + tid] = v[c];
             if (tid < kd) {
