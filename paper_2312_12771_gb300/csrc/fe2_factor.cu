@@ -16,7 +16,8 @@
 //      solve (forward elimination y = L^-1 b).  Idle threads prefetch the
 //      stencil rows of the next NB columns into shared memory (coalesced);
 //   C  rank-NB update of the trailing kd x kd window and of the RHS rows,
-//      8x8 register tiles; the finished panel is streamed to HBM;
+//      8 x 4 register tiles per lane (paired FP32 FMAs); the finished panel is
+//      streamed to HBM;
 //   D  the freed ring slots are cleared and receive the next NB columns.
 // Ring slots are addressed with a running base and a compare-subtract wrap.
 #include "fe2_internal.cuh"
@@ -148,7 +149,9 @@ __device__ __forceinline__ void chol_block_steps(T (&a)[NB], int lane, T* __rest
 // Step C of the right-looking solve of one panel row v against L11: column C
 // of the packed L11 (rows 4 floor(C/4) .. NB-1, the reciprocal pivot on the
 // diagonal) arrives as 16-byte broadcasts.  The half bandwidth is at least NB
-// (the registration clamps it), so every entry of L11 lies in the band.
+// (the registration clamps it), so every entry of L11 lies in the band.  In FP32
+// the groups after C's own go through the paired FMA (the same roundings as two
+// scalar FMAs).
 template <typename T, int C>
 __device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict__ L11p) {
     if constexpr (C < NB) {
@@ -158,6 +161,15 @@ __device__ __forceinline__ void panel_row_steps(T (&v)[NB], const T* __restrict_
         for (int g = g0; g < NB / 4; ++g) {
             T lc[4];
             Vec4<T>::load(col + 4 * g, lc);
+            if constexpr (sizeof(T) == 4) {
+                if (g > g0) {
+                    const float2 m = make_float2(-v[C], -v[C]);
+                    const float2 p0 = __ffma2_rn(m, make_float2(lc[0], lc[1]), make_float2(v[4 * g], v[4 * g + 1]));
+                    const float2 p1 = __ffma2_rn(m, make_float2(lc[2], lc[3]), make_float2(v[4 * g + 2], v[4 * g + 3]));
+                    v[4 * g] = p0.x, v[4 * g + 1] = p0.y, v[4 * g + 2] = p1.x, v[4 * g + 3] = p1.y;
+                    continue;
+                }
+            }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int c2 = 4 * g + u;
@@ -211,6 +223,61 @@ __device__ __forceinline__ void prefetch_columns(T* __restrict__ Stg, T* __restr
     }
 }
 
+// acc[u][w] = sum_c Pn[c][r0 + u] Pn[c][q0 + 8w] (u < 8, w < 4), accumulated over c
+// in order.  In FP32 the row pairs (u, u+1) go through the paired FMA of sm_100+
+// (two independent round-to-nearest FMAs in one instruction): the same sums bit for
+// bit in half the FMA instructions.
+template <typename T>
+__device__ __forceinline__ void block_products(T (&acc)[8][4], const T* __restrict__ Pn, int KP, int r0, int q0) {
+    if constexpr (sizeof(T) == 4) {
+        float2 acc2[4][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc2[h][w] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int c = 0; c < NB; ++c) {
+            const float* pc = Pn + c * KP;
+            const float4 a0 = *reinterpret_cast<const float4*>(pc + r0);
+            const float4 a1 = *reinterpret_cast<const float4*>(pc + r0 + 4);
+            const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                                  make_float2(a1.z, a1.w)};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float b = pc[q0 + 8 * w];
+                const float2 bb = make_float2(b, b);
+#pragma unroll
+                for (int h = 0; h < 4; ++h) acc2[h][w] = __ffma2_rn(ap[h], bb, acc2[h][w]);
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                acc[2 * h][w] = acc2[h][w].x;
+                acc[2 * h + 1][w] = acc2[h][w].y;
+            }
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+#pragma unroll 4
+        for (int c = 0; c < NB; ++c) {
+            const T* pc = Pn + c * KP;
+            T a[8], bb[4];
+            Vec4<T>::load(pc + r0, a);
+            Vec4<T>::load(pc + r0 + 4, a + 4);
+#pragma unroll
+            for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + 8 * w];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
+        }
+    }
+}
+
 // Block b (32 x 32 rows x columns of the window, from the block list) of the
 // rank-NB update of the panel whose first column sits in ring slot pb:
 // W(t1, t2) -= sum_c Pn[c][t1] Pn[c][t2] for kd > t2, KR > t1 >= t2 (rows t1 >= kd
@@ -229,23 +296,7 @@ __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, i
     const int I = bv & 0xffff, K = bv >> 16;
     const int r0 = 32 * I + 8 * rg, q0 = 32 * K + cg;
     T acc[8][4];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
-#pragma unroll 4
-    for (int c = 0; c < NB; ++c) {
-        const T* pc = Pn + c * KP;
-        T a[8], bb[4];
-        Vec4<T>::load(pc + r0, a);
-        Vec4<T>::load(pc + r0 + 4, a + 4);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + 8 * w];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
-    }
+    block_products(acc, Pn, KP, r0, q0);
     if (I > K && r0 + 8 <= kd && q0 + 24 < kd) {
         T old[4][8];
         int cb[4];
@@ -282,16 +333,21 @@ __device__ __forceinline__ void update_block(const unsigned* __restrict__ blk, i
 }
 
 // Columns [j0, j0+NB) of L (ring slots pb ..) and their y rows to global memory,
-// by warps w0, w0+nw, ... (columns) and threads t0, t0+nt, ... (y).
+// by warps w0, w0+nw, ... (columns) and threads t0, t0+nt, ... (y).  The ring
+// slots are cleared behind the copy: they receive the entering columns next.
 template <typename T>
-__device__ __forceinline__ void write_panel(const T* __restrict__ W, const T* __restrict__ Bw, T* __restrict__ Lg,
+__device__ __forceinline__ void write_panel(T* __restrict__ W, const T* __restrict__ Bw, T* __restrict__ Lg,
                                             T* __restrict__ Yg, int pb, int j0, int S, int LDW, int kd, int nr,
                                             int nmp, int w0, int nw, int t0, int nt, int lane) {
     const int LDL = kd + 1;
     for (int c = w0; c < NB; c += nw) {
-        const T* Wc = W + (size_t)wrapS(pb + c, S) * LDW;
+        T* Wc = W + (size_t)wrapS(pb + c, S) * LDW;
         T* dst = Lg + (size_t)(j0 + c) * LDL;
-        for (int off = lane; off < LDL; off += 32) dst[off] = Wc[off];
+        for (int off = lane; off < LDW; off += 32) {
+            const T v = Wc[off];
+            if (off < LDL) dst[off] = v;
+            Wc[off] = T(0);
+        }
     }
     for (int k = t0; k < nr * NB; k += nt) {
         const int rr = k / NB, c = k - rr * NB;
@@ -397,17 +453,12 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                 if (lane >= 4 * (c / 4)) L11p[l11_off(c) + lane - 4 * (c / 4)] = (lane == c) ? dl : a[c];
         } else {
             const int t0 = tid - 32, nt = blockDim.x - 32;
-            if (j0 > 0) {  // L and y of the previous panel out, before its slots are reused
+            if (j0 > 0) {  // L and y of the previous panel out; its slots are cleared for reuse
                 write_panel<T>(W, Bw, Lg, Yg, pbase, j0 - NB, S, LDW, kd, nr, nmp, warp - 1, nwarps - 1, t0, nt,
                                lane);
                 bar_sync_named(1, nt);
             }
             const int c0 = j0 + kd;  // first entering column; its slot is base + kd (mod S)
-            for (int c = warp - 1; c < NB; c += nwarps - 1) {
-                T* Wc = W + (size_t)wrapS(base + kd + c, S) * LDW;
-                for (int off = lane; off < LDW; off += 32) Wc[off] = T(0);
-            }
-            bar_sync_named(1, nt);
             const int qa = c0 / 2 + 1;
             for (int p = t0; p < NB * 9; p += nt) {
                 const int x = p / 9, off = p - 9 * x, cn = c0 + x;
@@ -640,23 +691,7 @@ __device__ __forceinline__ void update_block_la(unsigned bv, const T* __restrict
     const int I = bv & 0xffff, K = bv >> 16;
     const int r0 = 32 * I + 8 * rg, q0 = 32 * K + cg;
     T acc[8][4];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
-#pragma unroll 4
-    for (int c = 0; c < NB; ++c) {
-        const T* pc = Pn + c * KP;
-        T a[8], bb[4];
-        Vec4<T>::load(pc + r0, a);
-        Vec4<T>::load(pc + r0 + 4, a + 4);
-#pragma unroll
-        for (int w = 0; w < 4; ++w) bb[w] = pc[q0 + 8 * w];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) acc[u][w] += a[u] * bb[w];
-    }
+    block_products(acc, Pn, KP, r0, q0);
     if (I > K && r0 + 8 <= kd && q0 + 24 < kd) {
         T old[4][8];
         int cb[4];
