@@ -355,6 +355,62 @@ __device__ __forceinline__ void write_panel(T* __restrict__ W, const T* __restri
     }
 }
 
+// Warp 0: factor the diagonal block of the panel whose first column sits in ring
+// slot bs (columns [j0, j0+NB)), write it back, its reciprocal pivots to Dg and
+// the packed copy of L11 for the panel rows.
+template <typename T>
+__device__ __forceinline__ void diag_block(T* __restrict__ W, T* __restrict__ dinv, T* __restrict__ L11p,
+                                           T* __restrict__ Dg, int bs, int j0, int S, int LDW, int kd, int lane,
+                                           int* s_bad) {
+    T a[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS(bs + c, S) * LDW + (lane - c)] : T(0);
+    int badb = 0;
+    chol_block_steps<T, 0>(a, lane, dinv, badb);
+    if (lane == 0 && badb) *s_bad = 1;
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (c <= lane && lane - c <= kd) W[(size_t)wrapS(bs + c, S) * LDW + (lane - c)] = a[c];
+    const T dl = dinv[lane];
+    Dg[j0 + lane] = dl;
+    // packed L11 for the panel rows (a[c] is zero above the diagonal)
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (lane >= 4 * (c / 4)) L11p[l11_off(c) + lane - 4 * (c / 4)] = (lane == c) ? dl : a[c];
+}
+
+// Entering columns [c0, c0+NB) (ring slots slot0 ..) from the staged stencil rows,
+// and their right-hand-side rows, by threads t0, t0+nt, ...  The slots are zero.
+template <typename T>
+__device__ __forceinline__ void enter_columns(T* __restrict__ W, T* __restrict__ Bw, const T* __restrict__ Stg,
+                                              const T* __restrict__ Bstg, const int* __restrict__ nbr, int c0,
+                                              int slot0, int S, int LDW, int nm, int nmp, int nr, int t0, int nt) {
+    const int qa = c0 / 2 + 1;
+    for (int p = t0; p < NB * 9; p += nt) {
+        const int x = p / 9, off = p - 9 * x, cn = c0 + x;
+        T* Wc = W + (size_t)wrapS(slot0 + x, S) * LDW;
+        if (cn < nm) {
+            const int q = cn / 2 + 1, cc = cn & 1;
+            const int qn = nbr[q * 9 + off];
+            if (qn != 0) {
+#pragma unroll
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int row = 2 * (qn - 1) + c2;
+                    if (row >= cn) Wc[row - cn] = Stg[((off * 2 + cc) * 2 + c2) * STG_NODES + (q - qa)];
+                }
+            }
+        } else if (cn < nmp && off == 0) {
+            Wc[0] = T(1);  // padding columns: identity
+        }
+    }
+    for (int p = t0; p < nr * NB; p += nt) {
+        const int rr = p / NB, x = p - rr * NB;
+        Bw[rr * S + wrapS(slot0 + x, S)] = (c0 + x < nm) ? Bstg[p] : T(0);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_factor(const RveDev* __restrict__ tab,
                                                                                       const int* __restrict__ ids,
@@ -418,77 +474,30 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     }
     __syncthreads();
 
-    // Look-ahead schedule per panel j (columns [j0, j0+NB), ring slot base):
-    //   1: warp 0 factors the diagonal block; warps 1.. bring in the entering columns,
-    //      prefetch the next ones and run the update blocks of panel j-1 that were left
-    //      over (column blocks K >= 1, which do not touch panel j's columns);
-    //   2: panel rows (L21 and y) by warps 0 .. ceil(KR/32)-1;
-    //   3: the first nwarps update blocks of panel j (all K = 0 blocks, which the next
-    //      diagonal block and panel rows need).
-    // L and y of panel j go out at the start of phase 1 of panel j+1 (warps 1..), before
-    // the entering columns reuse its ring slots; those of the last panel after the loop.
-    // Pn holds panel j from phase 2 of panel j until phase 2 of panel j+1.
-    const int nfirst = min(lay.nblk, nwarps);
-    int base = 0;   // ring slot of column j0
-    int pbase = 0;  // ring slot of the previous panel's first column
+    // Schedule per panel j (columns [j0, j0+NB), ring slot base; its trailing window
+    // is columns [j0+NB, j0+NB+kd)):
+    //   P  the panel rows (L21 and y) against the packed L11, one thread per row;
+    //   U  the rank-NB update of the trailing window in 32 x 32 blocks.  Warp 0 takes
+    //      block (0, 0), which completes the next panel's diagonal block (no later
+    //      update touches it), and factors that block at once.  Warps 1.. write
+    //      panel j out (clearing its ring slots), bring the next panel's entering
+    //      columns [j0+NB+kd, j0+2NB+kd) into those slots, stage the columns after
+    //      them and take the other update blocks.  The entering columns lie beyond
+    //      panel j's trailing window, so its update does not touch them.
+    // Before the loop: panel 0's diagonal block (warp 0) and its entering columns
+    // [kd, kd+NB) (warps 1..).
+    if (warp == 0) {
+        diag_block<T>(W, dinv, L11p, Dg, 0, 0, S, LDW, kd, lane, &s_bad);
+    } else {
+        const int t0 = tid - 32, nt = blockDim.x - 32;
+        enter_columns<T>(W, Bw, Stg, Bstg, nbr, kd, kd, S, LDW, nm, nmp, nr, t0, nt);
+        bar_sync_named(1, nt);  // the staged columns are consumed: stage the next ones
+        prefetch_columns<T>(Stg, Bstg, sten, r.rhs, S, nm, nn, nr, t0, nt);
+    }
+    __syncthreads();
+    int base = 0;  // ring slot of column j0
     for (int j0 = 0; j0 < nmp; j0 += NB) {
-        // ---- 1
-        if (warp == 0) {
-            T a[NB];
-#pragma unroll
-            for (int c = 0; c < NB; ++c)
-                a[c] = (c <= lane && lane - c <= kd) ? W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] : T(0);
-            int badb = 0;
-            chol_block_steps<T, 0>(a, lane, dinv, badb);
-            if (lane == 0 && badb) s_bad = 1;
-            __syncwarp();
-#pragma unroll
-            for (int c = 0; c < NB; ++c)
-                if (c <= lane && lane - c <= kd) W[(size_t)wrapS(base + c, S) * LDW + (lane - c)] = a[c];
-            const T dl = dinv[lane];
-            Dg[j0 + lane] = dl;
-            // packed L11 for the panel rows (a[c] is zero above the diagonal)
-#pragma unroll
-            for (int c = 0; c < NB; ++c)
-                if (lane >= 4 * (c / 4)) L11p[l11_off(c) + lane - 4 * (c / 4)] = (lane == c) ? dl : a[c];
-        } else {
-            const int t0 = tid - 32, nt = blockDim.x - 32;
-            if (j0 > 0) {  // L and y of the previous panel out; its slots are cleared for reuse
-                write_panel<T>(W, Bw, Lg, Yg, pbase, j0 - NB, S, LDW, kd, nr, nmp, warp - 1, nwarps - 1, t0, nt,
-                               lane);
-                bar_sync_named(1, nt);
-            }
-            const int c0 = j0 + kd;  // first entering column; its slot is base + kd (mod S)
-            const int qa = c0 / 2 + 1;
-            for (int p = t0; p < NB * 9; p += nt) {
-                const int x = p / 9, off = p - 9 * x, cn = c0 + x;
-                T* Wc = W + (size_t)wrapS(base + kd + x, S) * LDW;
-                if (cn < nm) {
-                    const int q = cn / 2 + 1, cc = cn & 1;
-                    const int qn = nbr[q * 9 + off];
-                    if (qn != 0) {
-#pragma unroll
-                        for (int c2 = 0; c2 < 2; ++c2) {
-                            const int row = 2 * (qn - 1) + c2;
-                            if (row >= cn) Wc[row - cn] = Stg[((off * 2 + cc) * 2 + c2) * STG_NODES + (q - qa)];
-                        }
-                    }
-                } else if (cn < nmp && off == 0) {
-                    Wc[0] = T(1);
-                }
-            }
-            for (int p = t0; p < nr * NB; p += nt) {
-                const int rr = p / NB, x = p - rr * NB;
-                Bw[rr * S + wrapS(base + kd + x, S)] = (c0 + x < nm) ? Bstg[p] : T(0);
-            }
-            bar_sync_named(1, nt);  // the staged columns are consumed: stage the next ones
-            prefetch_columns<T>(Stg, Bstg, sten, r.rhs, j0 + S, nm, nn, nr, t0, nt);
-            if (j0 > 0)
-                for (int b = nfirst + warp - 1; b < lay.nblk; b += nwarps - 1)
-                    update_block<T>(blk, b, Pn, W, Bw, pbase, S, LDW, KP, kd, KR, lane);
-        }
-        __syncthreads();
-        // ---- 2: panel rows (L21 and y)
+        // ---- P: panel rows (L21 and y)
         if (tid < KR) {
             T v[NB];
             if (tid < kd) {
@@ -518,15 +527,30 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             }
         }
         __syncthreads();
-        // ---- 3: the first update blocks of this panel (its L and y go out in the
-        //         next panel's phase 1)
-        for (int b = warp; b < nfirst; b += nwarps)
-            update_block<T>(blk, b, Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
+        // ---- U: update of the trailing window (none after the last panel)
+        const bool more = j0 + NB < nmp;
+        const int nbase = wrapS(base + NB, S);
+        if (warp == 0) {
+            if (more) {
+                update_block<T>(blk, 0, Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
+                __syncwarp();
+                diag_block<T>(W, dinv, L11p, Dg, nbase, j0 + NB, S, LDW, kd, lane, &s_bad);
+            }
+        } else {
+            const int t0 = tid - 32, nt = blockDim.x - 32;
+            write_panel<T>(W, Bw, Lg, Yg, base, j0, S, LDW, kd, nr, nmp, warp - 1, nwarps - 1, t0, nt, lane);
+            if (more) {
+                bar_sync_named(1, nt);  // panel j's slots are cleared
+                enter_columns<T>(W, Bw, Stg, Bstg, nbr, j0 + NB + kd, base, S, LDW, nm, nmp, nr, t0, nt);
+                bar_sync_named(1, nt);  // the staged columns are consumed: stage the next ones
+                prefetch_columns<T>(Stg, Bstg, sten, r.rhs, j0 + NB + S, nm, nn, nr, t0, nt);
+                for (int b = warp; b < lay.nblk; b += nwarps - 1)
+                    update_block<T>(blk, b, Pn, W, Bw, base, S, LDW, KP, kd, KR, lane);
+            }
+        }
         __syncthreads();
-        pbase = base;
-        base = wrapS(base + NB, S);
+        base = nbase;
     }
-    write_panel<T>(W, Bw, Lg, Yg, pbase, nmp - NB, S, LDW, kd, nr, nmp, warp, nwarps, tid, blockDim.x, lane);
     if (tid == 0 && s_bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NOT_PD;
 }
 
