@@ -985,21 +985,26 @@ constexpr size_t SOLVE_SMEM_CAP = 220 * 1024;  // dynamic + static shared memory
 template <typename T>
 struct SolveLayout {
     int kd, S, LDL, nr, nmp, nbuf;
-    size_t blk, offL1, offX, offBar, total;
-    __host__ __device__ void init(int kd_, int nr_, int nmp_) {
+    size_t blk, offL1, offX, offY, offBar, total;
+    // ysm: the refinement solve keeps its full y [nr][nmp] in shared memory (wide
+    // bands, one CTA per SM either way); otherwise y stays in the slot's workspace
+    __host__ __device__ void init(int kd_, int nr_, int nmp_, bool ysm) {
         kd = kd_;
         nr = nr_;
         nmp = nmp_;
         S = kd + NB;
         LDL = kd + 1;
         blk = ((size_t)NB * LDL * sizeof(T) + NB * sizeof(T) + 127) & ~(size_t)127;
-        const size_t rest = (((size_t)nr * 2 * S * sizeof(T) + 15) & ~(size_t)15) + 32 +
-                            (size_t)(MAX_NR + YT_LD) * NB * sizeof(T);
+        const size_t rest = (((size_t)nr * 2 * S * sizeof(T) + 15) & ~(size_t)15) +
+                            (ysm ? (size_t)nr * nmp * sizeof(T) : 0) + 32 + (size_t)(MAX_NR + YT_LD) * NB * sizeof(T);
         nbuf = 2 * blk + rest <= SOLVE_SMEM_CAP ? 2 : 1;
         offL1 = blk;
         size_t o = nbuf * blk;
         offX = o;                                   // x ring [nr][2S] (mirrored) or rhs ring [nr][S]
         o += (size_t)nr * 2 * S * sizeof(T);
+        o = (o + 15) & ~(size_t)15;
+        offY = o;                                   // full y [nr][nmp] (refinement solve, ysm)
+        if (ysm) o += (size_t)nr * nmp * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offBar = o;
         o += 16;
@@ -1178,7 +1183,7 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_backward(const RveDev* __
     __shared__ int s_to;
     const RveDev r = tab[ids[blockIdx.x]];
     SolveLayout<T> lay;
-    lay.init(r.kd, r.nr, r.nm_pad);
+    lay.init(r.kd, r.nr, r.nm_pad, false);
     if (threadIdx.x == 0) s_to = 0;
     LStream<T> ls;
     ls.init(smem, lay, (const T*)(ws.base + blockIdx.x * ws.stride),
@@ -1214,10 +1219,11 @@ __device__ __forceinline__ void fwd_rows_below(const T* __restrict__ Lb, const T
 }
 
 // Refinement correction: dx = L^-T L^-1 R (R = FP64 residual), X += dx (or dx
-// written to the slot's y region, to_y).  The forward pass writes y to the
-// slot's y region (the factor's y there is consumed by then), and the backward
-// pass overwrites each block of it with dx only after reading it, so the kernel
-// keeps no full y in shared memory.
+// written to the slot's y region, to_y).  Narrow bands: the forward pass writes y
+// to the slot's y region (the factor's y there is consumed by then) and the
+// backward pass overwrites each block of it with dx only after reading it, so no
+// full y sits in shared memory and four CTAs share an SM.  Wide bands (one CTA per
+// SM either way) keep y in shared memory.
 template <typename T, bool WIDE>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDev* __restrict__ tab,
                                                                      const int* __restrict__ ids, Workspace ws,
@@ -1228,14 +1234,15 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
     if (active && !active[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
     SolveLayout<T> lay;
-    lay.init(r.kd, r.nr, r.nm_pad);
+    lay.init(r.kd, r.nr, r.nm_pad, WIDE);
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
     if (threadIdx.x == 0) s_to = 0;
     LStream<T> ls;
     ls.init(smem, lay, (const T*)(ws.base + blockIdx.x * ws.stride),
             (const T*)(ws.base + blockIdx.x * ws.stride + ws.offD));
     T* bw = (T*)(smem + lay.offX);   // ring [nr][S] of pending right-hand-side rows
-    T* ys = (T*)(ws.base + blockIdx.x * ws.stride + ws.offY);  // y [nr][nmp], then dx (to_y)
+    T* yw = (T*)(ws.base + blockIdx.x * ws.stride + ws.offY);  // the slot's y region
+    T* ys = WIDE ? (T*)(smem + lay.offY) : yw;                   // y [nr][nmp]
     __shared__ __align__(16) T yt[NB * YT_LD];  // y of the current block, [column][right-hand side]
     const double* Rg = (const double*)(ws.base + blockIdx.x * ws.stride + ws.offR);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1305,9 +1312,9 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
         jb = wrapS(jb + NB, S);
     }
     int k0 = nblk;
-    // to_y: dx goes to the slot's y region in place of y, for the second-order
-    // corrected Schur complement; else X += dx
-    T* dxg = to_y ? ys : nullptr;
+    // to_y: dx goes to the slot's y region (over y where y lives there), for the
+    // second-order corrected Schur complement; else X += dx
+    T* dxg = to_y ? yw : nullptr;
     if (!backward_pass<T, WIDE>(r, lay, ls, k0, bw, ys, 1, &s_to, dxg) && tid == 0) status[blockIdx.x] = FE2_ERR_TIMEOUT;
 }
 
@@ -1396,7 +1403,7 @@ template <typename T>
 cudaError_t launch_backward(const RveDev* tab, const int* ids, int n, Workspace ws, int accumulate, int maxkd,
                             int maxnr, int maxnm_pad, int* status, cudaStream_t s) {
     SolveLayout<T> lay;
-    lay.init(maxkd, maxnr, maxnm_pad);
+    lay.init(maxkd, maxnr, maxnm_pad, false);
     auto kern = maxkd > BW_WIDE ? k_band_backward<T, true> : k_band_backward<T, false>;
     cudaError_t e = set_smem(kern, lay.total);
     if (e != cudaSuccess) return e;
@@ -1408,7 +1415,7 @@ template <typename T>
 cudaError_t launch_solve_correct(const RveDev* tab, const int* ids, int n, Workspace ws, int maxkd, int maxnr,
                                  int maxnm_pad, int* status, const int* active, cudaStream_t s, int to_y) {
     SolveLayout<T> lay;
-    lay.init(maxkd, maxnr, maxnm_pad);
+    lay.init(maxkd, maxnr, maxnm_pad, maxkd > BW_WIDE);
     auto kern = maxkd > BW_WIDE ? k_band_solve_correct<T, true> : k_band_solve_correct<T, false>;
     cudaError_t e = set_smem(kern, lay.total);
     if (e != cudaSuccess) return e;
@@ -1426,11 +1433,11 @@ cudaError_t launch_residual(const RveDev* tab, const int* ids, int n, Workspace 
 size_t solve_smem_bytes(int kd, int nr, int nmp, bool fp64) {
     if (fp64) {
         SolveLayout<double> l;
-        l.init(kd, nr, nmp);
+        l.init(kd, nr, nmp, kd > BW_WIDE);
         return l.total + (MAX_NR + YT_LD) * NB * sizeof(double);
     }
     SolveLayout<float> l;
-    l.init(kd, nr, nmp);
+    l.init(kd, nr, nmp, kd > BW_WIDE);
     return l.total + (MAX_NR + YT_LD) * NB * sizeof(float);
 }
 

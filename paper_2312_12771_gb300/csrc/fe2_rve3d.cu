@@ -621,18 +621,40 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
                     }
                 }
                 T acc[32];
+                if constexpr (sizeof(T) == 4) {
+                    // column pairs through the paired FP32 FMA: the same roundings as
+                    // two scalar FMAs in half the instructions
+                    float2 acc2[16];
 #pragma unroll
-                for (int w = 0; w < 32; ++w) acc[w] = T(0);
+                    for (int w = 0; w < 16; ++w) acc2[w] = make_float2(0.f, 0.f);
 #pragma unroll 2
-                for (int c = 0; c < NB; ++c) {
-                    const T* pc = Pn + c * KP;
-                    const T av = pc[t1];
+                    for (int c = 0; c < NB; ++c) {
+                        const float* pc = Pn + c * KP;
+                        const float av = pc[t1];
+                        const float2 a2 = make_float2(av, av);
 #pragma unroll
-                    for (int w4 = 0; w4 < 8; ++w4) {
-                        T bb[4];
-                        Ld4<T>::load(pc + q0 + 4 * w4, bb);
+                        for (int w4 = 0; w4 < 8; ++w4) {
+                            const float4 b4 = *reinterpret_cast<const float4*>(pc + q0 + 4 * w4);
+                            acc2[2 * w4] = __ffma2_rn(a2, make_float2(b4.x, b4.y), acc2[2 * w4]);
+                            acc2[2 * w4 + 1] = __ffma2_rn(a2, make_float2(b4.z, b4.w), acc2[2 * w4 + 1]);
+                        }
+                    }
 #pragma unroll
-                        for (int x = 0; x < 4; ++x) acc[4 * w4 + x] += av * bb[x];
+                    for (int w = 0; w < 16; ++w) acc[2 * w] = acc2[w].x, acc[2 * w + 1] = acc2[w].y;
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 32; ++w) acc[w] = T(0);
+#pragma unroll 2
+                    for (int c = 0; c < NB; ++c) {
+                        const T* pc = Pn + c * KP;
+                        const T av = pc[t1];
+#pragma unroll
+                        for (int w4 = 0; w4 < 8; ++w4) {
+                            T bb[4];
+                            Ld4<T>::load(pc + q0 + 4 * w4, bb);
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) acc[4 * w4 + x] += av * bb[x];
+                        }
                     }
                 }
                 if constexpr (sizeof(T) == 4) {
