@@ -44,7 +44,7 @@ FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 128, 2, 2070.0
 # valid only for the kernel source it was taken on: the sha1 prefix of the
 # factor's part of fe2_factor.cu (from STG_NODES to the solves), else the bench
 # reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "880a891b1ed2", "bytes": (113839360 + 288499200) / 304}
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "dc35e4690602", "bytes": (114273280 + 288874496) / 304}
 # launches whose work depends on how many RVEs the error estimate flags for an
 # FP64-residual refinement sweep; their algorithmic work per launch is not known
 # to the bench, so no roofline is reported for them
