@@ -516,58 +516,64 @@ def run_serving(args, dev):
 
 def run_hex8(args):
     """Config-5 style: 8^3 Hex8 RVEs, centred sphere vf 0.2, mu_i/mu_m = 10,
-    kappa = 10 mu, simple shear gamma = 0.02 (first load step of 5); mixed path."""
+    kappa = 10 mu, simple shear gamma = 0.02 (first load step of 5).  The FP64
+    path runs first; the mixed path then takes the fewest correction sweeps
+    whose result stays within 1e-9 of it on every RVE (the headline's rule)."""
     import torch
     from paper_2312_12771_gb300.fe2 import Fe2Context
     b = W.sphere_batch(args.hex8_rves, 8, gamma=0.02)
     b.Fbar = W.perturbed_F(b, 9, 1e-3)
-    ctx = Fe2Context(dim=3, precision="mixed", max_refine=2)
-    ids = ctx.register_batch(b)
     F = torch.tensor(b.Fbar, device="cuda")
-    outs = ctx._outs(b.nrve)
-    for _ in range(2):
-        ctx.rve_solve(ids, F, out=outs)
-    torch.cuda.synchronize()
-    ctx.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(ctx.stream)
-    steps = 3
-    for _ in range(steps):
-        ctx.rve_solve(ids, F, out=outs)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    prof = ctx.profile_read()
-    out = {"workload": f"{b.nrve} Hex8 8^3 RVEs (n_m = 1533, kd = 440), sphere vf 0.2, NH, shear 0.02",
-           "solves_per_s": round(b.nrve / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
-           "status_nonzero": int((outs[2] != 0).sum().item()),
-           "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof.items()}}
-    idx = [0, 1, b.nrve // 3, b.nrve // 2, b.nrve - 1]
-    out["vs_oracle"] = oracle_errors(getattr(args, "pool", None),
-                                     [(8, b.phase[k], b.mat[k], b.Fbar[k], 3, None) for k in idx],
-                                     outs[0][idx].cpu().numpy(), outs[1][idx].cpu().numpy())
-    mixed = [t.cpu().numpy().copy() for t in outs]
-    ctx.close()
-    # the FP64 path on the same RVEs (wide-band FP64 factor, L streamed one block at a time)
+
+    def timed(ctx, ids, outs, warm, steps):
+        for _ in range(warm):
+            ctx.rve_solve(ids, F, out=outs)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        e0.record(ctx.stream)
+        for _ in range(steps):
+            ctx.rve_solve(ids, F, out=outs)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps, ctx.profile_read()
+
+    # the FP64 path (wide-band FP64 factor, L streamed one block at a time)
     ctx = Fe2Context(dim=3, precision="fp64")
+    ids = ctx.register_batch(b)
+    outs = ctx._outs(b.nrve)
+    ms64, prof64 = timed(ctx, ids, outs, 1, 2)
+    ref = [t.cpu().numpy().copy() for t in outs]
+    ctx.close()
+    # correction sweeps chosen on the workload
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=0)
     ids = ctx.register_batch(b)
     outs = ctx._outs(b.nrve)
     ctx.rve_solve(ids, F, out=outs)
     torch.cuda.synchronize()
-    ctx.profile(True)
-    e0.record(ctx.stream)
-    for _ in range(2):
-        ctx.rve_solve(ids, F, out=outs)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1) / 2
-    prof = ctx.profile_read()
+    first = rel_errs(outs[1].cpu().numpy(), ref[1], outs[0].cpu().numpy(), ref[0], b.Fbar, 3)
+    refine = 0 if first <= 1e-9 and (outs[2] == 0).all().item() else 2
+    ctx.close()
+    ctx = Fe2Context(dim=3, precision="mixed", max_refine=refine)
+    ids = ctx.register_batch(b)
+    outs = ctx._outs(b.nrve)
+    ms, prof = timed(ctx, ids, outs, 2, 3)
+    out = {"workload": f"{b.nrve} Hex8 8^3 RVEs (n_m = 1533, kd = 440), sphere vf 0.2, NH, shear 0.02",
+           "solves_per_s": round(b.nrve / (ms * 1e-3), 1), "ms_per_step": round(ms, 3),
+           "status_nonzero": int((outs[2] != 0).sum().item()),
+           "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof.items()},
+           "refine_choice": {"max_refine": refine, "first_order_max_rel_err_vs_fp64_all_rves": first,
+                             "rule": "fewest correction sweeps within 1e-9 of the FP64 path on every RVE"}}
+    idx = [0, 1, b.nrve // 3, b.nrve // 2, b.nrve - 1]
+    out["vs_oracle"] = oracle_errors(getattr(args, "pool", None),
+                                     [(8, b.phase[k], b.mat[k], b.Fbar[k], 3, None) for k in idx],
+                                     outs[0][idx].cpu().numpy(), outs[1][idx].cpu().numpy())
     out["fp64_path"] = {"solves_per_s": round(b.nrve / (ms64 * 1e-3), 1), "ms_per_step": round(ms64, 3),
-                        "status_nonzero": int((outs[2] != 0).sum().item()),
-                        "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof.items()}}
+                        "status_nonzero": int((ref[2] != 0).sum()),
+                        "kernels_ms": {k: round(v[0] / v[1], 3) for k, v in prof64.items()}}
     out["speedup_mixed_vs_fp64"] = round(ms64 / ms, 2)
-    out["max_rel_err_mixed_vs_fp64_gpu"] = rel_errs(mixed[1], outs[1].cpu().numpy(), mixed[0],
-                                                    outs[0].cpu().numpy(), b.Fbar, 3)
+    out["max_rel_err_mixed_vs_fp64_gpu"] = rel_errs(outs[1].cpu().numpy(), ref[1], outs[0].cpu().numpy(),
+                                                    ref[0], b.Fbar, 3)
     ctx.close()
     return out
 
