@@ -434,7 +434,9 @@ def run_serving(args, dev):
     srv.close()
     # the tuner's choice of batch limit, lane count and mixed-size batches on this stream
     from paper_2312_12771_gb300 import tune
-    tuned = tune.tune_server(ctx, ids[:summary_n], Fb[:summary_n], sizes[:summary_n])
+    # the smallest batches within 5 % of the best capacity (shorter waits); the
+    # capacity-first choice is measured beside it at the summary point below
+    tuned = tune.tune_server(ctx, ids[:summary_n], Fb[:summary_n], sizes[:summary_n], slack=0.05)
     cfg = tuned["best"]
     srv = Server(ctx, max_batch=cfg["max_batch"], lanes=cfg["lanes"], mixed=cfg["mixed"])
     sweep, bad = [], 0
@@ -456,6 +458,20 @@ def run_serving(args, dev):
         sweep.append(row)
     main = next(r for r in sweep if r["n_req"] == summary_n)
     at08 = min(main["rates"], key=lambda r: abs(r["x_capacity"] - 0.8))
+    # the capacity-first configuration at the same point (0.8 x its own capacity)
+    top = max(tuned["table"], key=lambda r: r["capacity"])
+    topcfg = {k: top[k] for k in ("max_batch", "lanes", "mixed")}
+    capacity_first = None
+    if topcfg != cfg:
+        s2 = Server(ctx, max_batch=topcfg["max_batch"], lanes=topcfg["lanes"], mixed=topcfg["mixed"])
+        n = summary_n
+        simulate(s2, ids[:n], Fb[:n], np.zeros(n))
+        _, _, _, cap2 = simulate(s2, ids[:n], Fb[:n], np.zeros(n))
+        res2, p50b, p99b, thr2 = simulate(s2, ids[:n], Fb[:n], W.poisson_arrivals(W.GLOBAL_SEED, n, 0.8 * cap2))
+        bad += int((res2["status"] != 0).sum())
+        s2.close()
+        capacity_first = {"config": topcfg, "capacity_solves_per_s": round(cap2, 1), "offered_rate": round(0.8 * cap2, 1),
+                          "throughput_solves_per_s": round(thr2, 1), "p50_ms": round(p50b, 3), "p99_ms": round(p99b, 3)}
     out = {"workload": "NH RVEs, N in {16,24,32,48} (uniform), random inclusions; one request per RVE per "
                        "macro iteration, Poisson arrivals at multiples of the measured burst capacity",
            "summary_n_req": summary_n, "capacity_solves_per_s": main["capacity_solves_per_s"],
@@ -463,9 +479,12 @@ def run_serving(args, dev):
            "throughput_solves_per_s": at08["throughput"], "p50_ms": at08["p50_ms"], "p99_ms": at08["p99_ms"],
            "graphs_captured_replayed": list(srv.graph_stats()), "max_batch": cfg["max_batch"],
            "lanes": cfg["lanes"], "mixed_size_batches": cfg["mixed"],
-           "tuned": {"config": cfg, "burst_capacity": tuned["capacity"], "default_config": tune.DEFAULT_SERVER,
+           "tuned": {"config": cfg, "rule": "smallest batch limit, then fewest lanes, within 5 % of the best "
+                                             "burst capacity", "burst_capacity": tuned["capacity"],
+                     "best_burst_capacity": tuned["max_capacity"], "default_config": tune.DEFAULT_SERVER,
                      "default_burst_capacity": tuned["default"],
                      "gain": round(tuned["capacity"] / max(tuned["default"], 1e-9), 3), "table": tuned["table"]},
+           "capacity_first": capacity_first,
            "memory_stats": list(srv.memory_stats()),
            "status_nonzero": bad, "hbm_budget_gb": args.serve_budget_gb, "sweep": sweep}
     srv.close()

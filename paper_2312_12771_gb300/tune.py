@@ -9,7 +9,9 @@ keyed by device name, dimension, precision and the multiset of mesh sizes:
   timed as whole RVE solves (CUDA events) and checked to give the same
   statuses;
 * ``tune_server``: the serving configuration (batch limit, lane count,
-  mixed-size batches), timed as the burst capacity of a request stream.
+  mixed-size batches), timed as the burst capacity of a request stream;
+  optionally the smallest batches within a given fraction of the best
+  capacity, for shorter waits.
 
 The panel width (32) and the one RVE per CTA are fixed by the kernels'
 design and are not tuned.
@@ -111,11 +113,14 @@ def burst_capacity(ctx, ids, Fbar, max_batch, lanes, mixed, reps=2):
 
 
 def tune_server(ctx, ids, Fbar, sizes, max_batches=(128, 256, 512, 1024), lanes=(2, 3, 4),
-                mixed=(False, True), cache=None):
+                mixed=(False, True), cache=None, slack=0.0):
     """Burst capacity of every (max_batch, lanes, mixed) candidate on the
-    caller's RVEs; returns {"best": config, "capacity": solves/s,
-    "default": solves/s of DEFAULT_SERVER, "table": [...]}."""
-    key = cache_key("server", ctx.dim, ctx.precision, sizes)
+    caller's RVEs; returns {"best": config, "capacity": its solves/s,
+    "max_capacity": the best solves/s, "default": solves/s of DEFAULT_SERVER,
+    "table": [...]}.  Candidates within `slack` (a fraction) of the best
+    capacity are ranked by batch limit, then lane count: smaller batches and
+    fewer concurrent ones keep a request's wait shorter."""
+    key = cache_key("server", ctx.dim, ctx.precision, sizes) + f"|slack{slack:g}"
     hit = _load(cache).get(key)
     if hit:
         return dict(hit, cached=True)
@@ -125,12 +130,14 @@ def tune_server(ctx, ids, Fbar, sizes, max_batches=(128, 256, 512, 1024), lanes=
             for mx in mixed:
                 cap = burst_capacity(ctx, ids, Fbar, mb, ln, mx)
                 table.append({"max_batch": mb, "lanes": ln, "mixed": mx, "capacity": round(cap, 1)})
-    best = max(table, key=lambda r: r["capacity"])
+    top = max(r["capacity"] for r in table)
+    near = [r for r in table if r["capacity"] >= (1.0 - slack) * top]
+    best = min(near, key=lambda r: (r["max_batch"], r["lanes"], -r["capacity"]))
     dflt = next((r["capacity"] for r in table if r["max_batch"] == DEFAULT_SERVER["max_batch"] and
                  r["lanes"] == DEFAULT_SERVER["lanes"] and r["mixed"] == DEFAULT_SERVER["mixed"]), None)
     if dflt is None:
         dflt = round(burst_capacity(ctx, ids, Fbar, **DEFAULT_SERVER), 1)
     res = {"best": {k: best[k] for k in ("max_batch", "lanes", "mixed")}, "capacity": best["capacity"],
-           "default": dflt, "table": table}
+           "max_capacity": top, "slack": slack, "default": dflt, "table": table}
     _store(cache, key, res)
     return dict(res, cached=False)
