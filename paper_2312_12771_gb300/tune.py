@@ -112,6 +112,15 @@ def burst_capacity(ctx, ids, Fbar, max_batch, lanes, mixed, reps=2):
     return best
 
 
+def choose_server(table, slack=0.0):
+    """The configuration picked from a measured table: among the rows whose
+    capacity is within `slack` of the best, the smallest batch limit, then the
+    fewest lanes, then the highest capacity.  Returns (row, best capacity)."""
+    top = max(r["capacity"] for r in table)
+    near = [r for r in table if r["capacity"] >= (1.0 - slack) * top]
+    return min(near, key=lambda r: (r["max_batch"], r["lanes"], -r["capacity"])), top
+
+
 def tune_server(ctx, ids, Fbar, sizes, max_batches=(128, 256, 512, 1024), lanes=(2, 3, 4),
                 mixed=(False, True), cache=None, slack=0.0):
     """Burst capacity of every (max_batch, lanes, mixed) candidate on the
@@ -130,9 +139,7 @@ def tune_server(ctx, ids, Fbar, sizes, max_batches=(128, 256, 512, 1024), lanes=
             for mx in mixed:
                 cap = burst_capacity(ctx, ids, Fbar, mb, ln, mx)
                 table.append({"max_batch": mb, "lanes": ln, "mixed": mx, "capacity": round(cap, 1)})
-    top = max(r["capacity"] for r in table)
-    near = [r for r in table if r["capacity"] >= (1.0 - slack) * top]
-    best = min(near, key=lambda r: (r["max_batch"], r["lanes"], -r["capacity"]))
+    best, top = choose_server(table, slack)
     dflt = next((r["capacity"] for r in table if r["max_batch"] == DEFAULT_SERVER["max_batch"] and
                  r["lanes"] == DEFAULT_SERVER["lanes"] and r["mixed"] == DEFAULT_SERVER["mixed"]), None)
     if dflt is None:

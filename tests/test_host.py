@@ -112,3 +112,20 @@ def test_symbolic_column_counts_match_the_oracle_factor(d, N):
     kd = max(int(c[-1]) - j for j, c in enumerate(sym) if len(c))
     if d == 2:
         assert kd == 4 * N + 5
+
+
+def test_serving_tuner_choice_rule():
+    """The serving tuner's pick from a measured table: the best capacity with no
+    slack; within a slack, the smallest batch limit, then the fewest lanes."""
+    from paper_2312_12771_gb300.tune import choose_server
+    table = [{"max_batch": mb, "lanes": ln, "mixed": False, "capacity": c}
+             for mb, ln, c in ((128, 2, 62.0), (128, 4, 78.8), (256, 3, 81.1), (256, 4, 82.5),
+                               (512, 2, 74.1), (512, 4, 80.8))]
+    best, top = choose_server(table)
+    assert top == 82.5 and (best["max_batch"], best["lanes"]) == (256, 4)
+    best, _ = choose_server(table, slack=0.05)
+    assert (best["max_batch"], best["lanes"]) == (128, 4)
+    best, _ = choose_server(table, slack=0.02)
+    assert (best["max_batch"], best["lanes"]) == (256, 3)
+    best, _ = choose_server(table, slack=1.0)
+    assert (best["max_batch"], best["lanes"]) == (128, 2)
