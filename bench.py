@@ -42,9 +42,9 @@ N_RVE, N_MESH = 4096, 32
 FP32_LANES, FP64_FMA_PER_SM, SM_MAX_MHZ = 128, 2, 2070.0
 # DRAM bytes per RVE of the FP32 band factor from one ncu capture of 304 RVEs;
 # valid only for the kernel source it was taken on: the sha1 prefix of the
-# factor's part of fe2_factor.cu (from STG_NODES to the solves), else the bench
-# reports traffic = null.
-FACTOR_TRAFFIC_PER_RVE = {"sha1": "dc35e4690602", "bytes": (114273280 + 288874496) / 304}
+# factor's part of fe2_factor.cu (from STG_NODES to the solves) and of the panel
+# helpers in fe2_panel.cuh, else the bench reports traffic = null.
+FACTOR_TRAFFIC_PER_RVE = {"sha1": "0908b3c9eea9", "bytes": (113930752 + 289247488) / 304}
 # launches whose work depends on how many RVEs the error estimate flags for an
 # FP64-residual refinement sweep; their algorithmic work per launch is not known
 # to the bench, so no roofline is reported for them
@@ -64,14 +64,15 @@ def sm_count():
 
 def factor_source_sha1():
     import hashlib
-    src = os.path.join(ROOT, "paper_2312_12771_gb300", "csrc", "fe2_factor.cu")
+    csrc = os.path.join(ROOT, "paper_2312_12771_gb300", "csrc")
     try:
-        t = open(src).read()
+        t = open(os.path.join(csrc, "fe2_factor.cu")).read()
         a = t.index("constexpr int STG_NODES")
         b = t.index("// ------------------------------------------------------------------ solves")
+        h = open(os.path.join(csrc, "fe2_panel.cuh")).read()
     except (OSError, ValueError):
         return None
-    return hashlib.sha1(t[a:b].encode()).hexdigest()[:12]
+    return hashlib.sha1((t[a:b] + h).encode()).hexdigest()[:12]
 
 
 def factor_traffic(nrve):

@@ -19,6 +19,7 @@
 // global read-modify-write latency is the limit, and a second RVE per SM hides
 // part of it.
 #include "fe2_internal.cuh"
+#include "fe2_panel.cuh"
 #include "fe2_ptx.cuh"
 
 namespace fe2 {
@@ -416,54 +417,19 @@ struct GwLayout {
         o += (size_t)nr * S * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offDinv = o;
-        o += NB * sizeof(T);
+        o += 2 * NB * sizeof(T);  // dinv, then one column of the diagonal block
         o = (o + 15) & ~(size_t)15;
         offBlk = o;
         o += (size_t)nblk * 4;
         o = (o + 15) & ~(size_t)15;
-        offL11 = o;
-        o += (size_t)NB * (NB + 1) * sizeof(T);
+        offL11 = o;  // packed L11 (fe2_panel.cuh)
+        o += (size_t)L11P_LEN * sizeof(T);
         o = (o + 15) & ~(size_t)15;
         offOld = o;  // FP32: per warp, old window values of GW_PRE columns of its update block
         if (sizeof(T) == 4) o += (size_t)(FACT_THREADS / 32) * GW_PRE * NB * sizeof(T);
         total = (o + 15) & ~(size_t)15;
     }
 };
-
-// Step C of the solve of one panel row v against L11, staged in shared memory
-// as L11s[c][r] = L(r, c) with stride NB + 1 (the half bandwidth is at least NB)
-template <typename T, int C>
-__device__ __forceinline__ void gw_row_steps_s(T (&v)[NB], const T* __restrict__ L11s, const T* __restrict__ dinv) {
-    if constexpr (C < NB) {
-        const T* Lc = L11s + C * (NB + 1);
-        v[C] *= dinv[C];
-#pragma unroll
-        for (int c2 = C + 1; c2 < NB; ++c2) v[c2] -= v[C] * Lc[c2];
-        gw_row_steps_s<T, C + 1>(v, L11s, dinv);
-    }
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void gw_chol_steps(T (&a)[NB], int lane, T* __restrict__ dinv, int& bad) {
-    if constexpr (K < NB) {
-        T piv = __shfl_sync(0xffffffffu, a[K], K);
-        const bool badk = !(piv > T(0));
-        if (badk) piv = T(1);
-        const T dk = rsqrt(piv);
-        if (lane == K)
-            a[K] = piv * dk;
-        else if (lane > K)
-            a[K] *= dk;
-        if (lane == 0) dinv[K] = dk;
-        bad |= badk;
-#pragma unroll
-        for (int c = K + 1; c < NB; ++c) {
-            const T lck = __shfl_sync(0xffffffffu, a[K], c);
-            if (lane >= c) a[c] -= a[K] * lck;
-        }
-        gw_chol_steps<T, K + 1>(a, lane, dinv, bad);
-    }
-}
 
 // Columns [c0, c0 + ncol) of K_mm into their columns of L (stride LDW), one
 // (column, neighbour) pair per item, items t0, t0 + nt, ...; the columns must be
@@ -505,7 +471,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
     T* Bw = (T*)(smem + lay.offBw);
     T* dinv = (T*)(smem + lay.offDinv);
     unsigned* blk = (unsigned*)(smem + lay.offBlk);
-    T* L11s = (T*)(smem + lay.offL11);
+    T* L11p = (T*)(smem + lay.offL11);
     __shared__ int s_bad;
     char* slot = ws.base + blockIdx.x * ws.stride;
     T* Lg = (T*)slot;
@@ -538,15 +504,15 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
             for (int c = 0; c < NB; ++c)
                 a[c] = (c <= lane && lane - c <= kd) ? Lg[(size_t)(j0 + c) * LDW + (lane - c)] : T(0);
             int badb = 0;
-            gw_chol_steps<T, 0>(a, lane, dinv, badb);
+            chol_block_steps<T, 0>(a, lane, dinv, badb);
             if (lane == 0 && badb) s_bad = 1;
             __syncwarp();
 #pragma unroll
-            for (int c = 0; c < NB; ++c) {
+            for (int c = 0; c < NB; ++c)
                 if (c <= lane && lane - c <= kd) Lg[(size_t)(j0 + c) * LDW + (lane - c)] = a[c];
-                L11s[c * (NB + 1) + lane] = (c <= lane && lane - c <= kd) ? a[c] : T(0);
-            }
-            Dg[j0 + lane] = dinv[lane];
+            const T dl = dinv[lane];
+            Dg[j0 + lane] = dl;
+            diag_pack<T>(a, dl, L11p, lane);
         } else {
             const int nt = blockDim.x - 32, t0 = tid - 32;
             for (int x = warp - 1; x < NB; x += nwarps - 1) {
@@ -575,7 +541,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 #pragma unroll
                 for (int c = 0; c < NB; ++c) v[c] = Bw[(t - kd) * S + wrapS3(base + c, S)];
             }
-            gw_row_steps_s<T, 0>(v, L11s, dinv);
+            panel_row_steps<T, 0>(v, L11p);
 #pragma unroll
             for (int c = 0; c < NB; ++c) Pn[c * KP + t] = v[c];
             if (t < kd) {
