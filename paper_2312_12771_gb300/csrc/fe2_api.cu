@@ -243,7 +243,16 @@ static bool use_smem_factor(int kd, int nr, bool fp64, int max_smem, int d) {
 // the band fits it; the CUDA-core kernel otherwise (and by default).
 static bool use_tc_factor(const fe2_ctx* ctx, int maxkd, int maxnr) {
     return ctx->cfg.factor_kernel == FE2_FACTOR_TENSOR_CORE &&
-           factor_tc_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem);
+           (factor_tc2_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem) ||
+            factor_tc_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem));
+}
+
+// The tensor-core factor: two RVEs per SM where the band allows it, else one.
+static cudaError_t launch_tc_factor(const fe2_ctx* ctx, const RveDev* tab, const int* ids, int n, Workspace ws,
+                                    int* st, int maxkd, int maxnr, cudaStream_t s) {
+    if (factor_tc2_eligible(maxkd, maxnr, ctx->cfg.dim, ctx->max_smem))
+        return launch_factor_tc2(tab, ids, n, ws, st, maxkd, maxnr, s);
+    return launch_factor_tc(tab, ids, n, ws, st, maxkd, maxnr, s);
 }
 
 // The pipelined band factor when the context asks for it and the band fits it.
@@ -521,7 +530,7 @@ static fe2_status condense_impl(fe2_ctx* ctx, int n, const int* ids, const int* 
             if (l.gw)
                 TIMED("band_factor_fp32_gw", launch_factor_gw<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else if (use_tc_factor(ctx, b.maxkd, b.maxnr))
-                TIMED("band_factor_tc", launch_factor_tc(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
+                TIMED("band_factor_tc", launch_tc_factor(ctx, ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else if (use_la_factor(ctx, b.maxkd, b.maxnr, false))
                 TIMED("band_factor_fp32_pipelined", launch_factor_la<float>(ctx->d_tab, di, m, ws, stp, b.maxkd, b.maxnr, ctx->stream));
             else
@@ -1760,7 +1769,7 @@ static fe2_status lane_enqueue(fe2_server* srv, Lane& L, int n, const BatchInfo&
         if (l.gw)
             CK(launch_factor_gw<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else if (tc)
-            CK(launch_factor_tc(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
+            CK(launch_tc_factor(ctx, ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else if (use_la_factor(ctx, b.maxkd, b.maxnr, false))
             CK(launch_factor_la<float>(ctx->d_tab, L.d_ids, n, ws, L.d_st, b.maxkd, b.maxnr, s));
         else

@@ -34,6 +34,7 @@
 // additions at the big term's magnitude.  The dropped Ps Ps^T term and the
 // tf32 rounding of Ps are O(2^-22) relative.
 #include "fe2_internal.cuh"
+#include "fe2_panel.cuh"
 #include "fe2_ptx.cuh"
 #include "fe2_tc.cuh"
 
@@ -538,6 +539,325 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_band_factor_tc(const RveDev* 
     }
 }
 
+// ------------------------------------------------------------ two RVEs per SM
+// k_band_factor_tc2: the band factor with the trailing update on the tensor
+// cores in a layout small enough for two CTAs (two RVEs) per SM, so that one
+// RVE's diagonal-block chain overlaps the other's work and the update blocks
+// no longer compete with the chain for the CUDA cores:
+//   * the window is a ring of kd columns (column c in slot c mod kd), not kd +
+//     NB: a panel's own columns leave it when its rows are solved, and the
+//     columns that enter take their slots;
+//   * finished values go to HBM from registers (no staging buffer);
+//   * the operand P = [L21; y] (rows 0..KR-1, zero up to PR, K = NB) is held
+//     once, split in tf32 parts Pb + Ps, K-major with the 128-byte swizzle.
+// Per panel j (columns [j0, j0+NB), ring slot base; trailing window columns
+// [j0+NB, j0+NB+kd), trailing column t2 in slot base + NB + t2):
+//   P  one thread per row t < KR solves its row against the packed L11 and
+//      writes it to HBM (L21 row or y) and to Pb / Ps;
+//   U  one thread issues D = P P^T (3xTF32, small cross terms first) in two
+//      groups -- tile A columns 0..31 and tile B (rows >= 128 against columns
+//      < 128, transposed), then tile A columns 32..n0-1 and tile C (rows >= 128
+//      against columns >= 128) -- each committed to an mbarrier.  Warp 0
+//      applies the first 32 x 32 of tile A (the next panel's diagonal block)
+//      and factors that block at once (L11 to HBM and to the packed copy);
+//      warps 1-3 apply the rest of the first group's tile A, warp 4 the first
+//      quarter of tile B; warps 4-7 bring the next columns [j0+kd, j0+kd+NB)
+//      into panel j's slots (they are the last NB columns of panel j's trailing
+//      window); then warps 1-7 apply the second group.
+// Tile A: tensor-memory lane = window row t1 < 128, column t2.  Tile B: lane
+// = column t2 < 128, column 128 + (t1 - 128).  Tile C: lane = t1 - (PR - 128),
+// column 128 + nB + (t2 - 128).
+constexpr int TC2_THREADS = 256;
+
+struct Tc2Layout {
+    int kd, LDW, KR, PR, nr, n0, nB, n11, tcols;
+    size_t offPs, offW, offBw, offL11, offDinv, offMisc, total;
+    __host__ __device__ void init(int kd_, int nr_) {
+        kd = kd_;
+        nr = nr_;
+        LDW = kd + 1;
+        KR = kd + nr;
+        PR = max(128, (KR + 15) & ~15);
+        n0 = min(128, (kd + 15) & ~15);
+        nB = PR - 128;
+        n11 = kd > 128 ? ((kd - 128 + 15) & ~15) : 0;
+        tcols = 32;
+        while (tcols < 128 + nB + n11) tcols <<= 1;
+        size_t o = (size_t)PR * 128;  // Pb at 0 (1024-aligned base)
+        offPs = o;
+        o += (size_t)PR * 128;
+        offW = o;
+        o += (size_t)kd * LDW * 4;
+        o = (o + 15) & ~(size_t)15;
+        offBw = o;
+        o += (size_t)nr * kd * 4;
+        o = (o + 15) & ~(size_t)15;
+        offL11 = o;
+        o += (size_t)L11P_LEN * 4;
+        offDinv = o;
+        o += 2 * NB * 4;  // reciprocal pivots, then one column of the diagonal block
+        offMisc = o;
+        o += 64;
+        total = o + 1024;  // slack for aligning the base to 1024 B
+    }
+};
+
+__device__ __forceinline__ int wrap1(int x, int n) { return x >= n ? x - n : x; }
+
+// Warp 0: factor the diagonal block of the panel starting at column jd (ring
+// slot bs), write L11 and the reciprocal pivots to HBM and the packed L11.
+__device__ __forceinline__ void tc2_diag(const float* __restrict__ W, float* __restrict__ dinv,
+                                         float* __restrict__ L11p, float* __restrict__ Lg, float* __restrict__ Dg,
+                                         int bs, int jd, int kd, int LDW, int lane, int& bad) {
+    float a[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[c] = (c <= lane) ? W[(size_t)wrap1(bs + c, kd) * LDW + (lane - c)] : 0.f;
+    chol_block_steps<float, 0>(a, lane, dinv, bad);
+    __syncwarp();
+    const int LDL = kd + 1;
+#pragma unroll
+    for (int c = 0; c < NB; ++c)
+        if (c <= lane) Lg[(size_t)(jd + c) * LDL + (lane - c)] = a[c];
+    const float dl = dinv[lane];
+    Dg[jd + lane] = dl;
+    diag_pack<float>(a, dl, L11p, lane);
+}
+
+// Columns [c0, c0+NB) of K_mm (ring slots s0 ..) and their right-hand-side
+// entries, by threads t0, t0+nt, ... (the slots are cleared first; `nb` is the
+// named barrier of these threads).
+__device__ __forceinline__ void tc2_enter(float* __restrict__ W, float* __restrict__ Bw, const RveDev& r, int c0, int s0,
+                                          int kd, int LDW, int nmp, int t0, int nt, int nb) {
+    const int nm = r.nm, nn = r.nn, nr = r.nr;
+    // the items' stencil values first, so that their latency overlaps the clearing
+    constexpr int IT = (NB * 9 + 127) / 128;
+    float val[IT][2];
+    int qn_[IT];
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int p = t0 + i * nt, x = p / 9, off = p - 9 * x, cn = c0 + x;
+        qn_[i] = 0;
+        val[i][0] = val[i][1] = 0.f;
+        if (p < NB * 9 && cn < nm) {
+            const int q = cn / 2 + 1, cc = cn & 1;
+            qn_[i] = r.nbr[q * 9 + off];
+            val[i][0] = (float)r.stencil[(size_t)((off * 2 + cc) * 2 + 0) * nn + q];
+            val[i][1] = (float)r.stencil[(size_t)((off * 2 + cc) * 2 + 1) * nn + q];
+        }
+    }
+    for (int k = t0; k < NB * LDW; k += nt) {
+        const int x = k / LDW;
+        W[(size_t)wrap1(s0 + x, kd) * LDW + (k - x * LDW)] = 0.f;
+    }
+    bar_sync(nb, nt);
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int p = t0 + i * nt, x = p / 9, off = p - 9 * x, cn = c0 + x;
+        if (p >= NB * 9 || cn >= nmp) continue;
+        float* Wc = W + (size_t)wrap1(s0 + x, kd) * LDW;
+        if (cn < nm) {
+            const int qn = qn_[i];
+            if (qn != 0)
+#pragma unroll
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const int row = 2 * (qn - 1) + c2;
+                    if (row >= cn && row - cn <= kd) Wc[row - cn] = val[i][c2];
+                }
+        } else if (off == 0) {
+            Wc[0] = 1.f;  // padding columns: identity
+        }
+    }
+    for (int p = t0; p < nr * NB; p += nt) {
+        const int rr = p / NB, x = p - rr * NB, cn = c0 + x;
+        Bw[rr * kd + wrap1(s0 + x, kd)] = (cn < nm) ? (float)r.rhs[(size_t)rr * nm + cn] : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(TC2_THREADS, 2) k_band_factor_tc2(const RveDev* __restrict__ tab,
+                                                                    const int* __restrict__ ids, Workspace ws,
+                                                                    int* __restrict__ status) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const RveDev r = tab[ids[blockIdx.x]];
+    Tc2Layout lay;
+    lay.init(r.kd, r.nr);
+    const int kd = lay.kd, LDW = lay.LDW, KR = lay.KR, PR = lay.PR, nr = lay.nr;
+    const int nm = r.nm, nmp = r.nm_pad, nn = r.nn;
+    unsigned char* Pb = sm;
+    unsigned char* Ps = sm + lay.offPs;
+    float* W = (float*)(sm + lay.offW);
+    float* Bw = (float*)(sm + lay.offBw);
+    float* L11p = (float*)(sm + lay.offL11);
+    float* dinv = (float*)(sm + lay.offDinv);
+    uint64_t* bar1 = (uint64_t*)(sm + lay.offMisc);
+    uint64_t* bar2 = (uint64_t*)(sm + lay.offMisc + 8);
+    uint32_t* tslot = (uint32_t*)(sm + lay.offMisc + 16);
+    int* s_bad = (int*)(sm + lay.offMisc + 20);
+    int* s_ok = (int*)(sm + lay.offMisc + 24);
+    float* Lg = (float*)(ws.base + blockIdx.x * ws.stride);
+    float* Yg = (float*)(ws.base + blockIdx.x * ws.stride + ws.offY);
+    float* Dg = (float*)(ws.base + blockIdx.x * ws.stride + ws.offD);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int LDL = kd + 1;
+
+    // ---- set-up: tensor memory, barriers, zero operands and window, first kd columns
+    if (warp == 0) {
+        tmem_alloc(tslot, (uint32_t)lay.tcols);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        *s_bad = 0;
+        *s_ok = 1;
+        mbar_init(bar1, 1);
+        mbar_init(bar2, 1);
+        mbar_fence_init();
+    }
+    for (int k = tid; k < PR * 64; k += TC2_THREADS) ((float*)sm)[k] = 0.f;  // Pb and Ps
+    for (int k = tid; k < kd * LDW; k += TC2_THREADS) W[k] = 0.f;
+    for (int k = tid; k < nr * kd; k += TC2_THREADS) {
+        const int rr = k / kd, c = k - rr * kd;
+        Bw[k] = (c < nm) ? (float)r.rhs[(size_t)rr * nm + c] : 0.f;
+    }
+    __syncthreads();
+    for (int c = tid; c < min(kd, nmp); c += TC2_THREADS) {
+        if (c < nm)
+            add_column(W + (size_t)c * LDW, c, r.stencil, r.nbr, nn, kd);
+        else
+            W[(size_t)c * LDW] = 1.f;  // padding columns: identity
+    }
+    __syncthreads();
+    int bad = 0;
+    if (warp == 0) tc2_diag(W, dinv, L11p, Lg, Dg, 0, 0, kd, LDW, lane, bad);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t pb = smem_u32(Pb), ps = smem_u32(Ps);
+    uint32_t phase = 0;
+    int base = 0;  // ring slot of column j0
+    for (int j0 = 0; j0 < nmp; j0 += NB, phase ^= 1u) {
+        const bool more = j0 + NB < nmp;
+        // ---- P: panel rows (L21, y) to HBM and to the operand tiles
+        if (tid < KR) {
+            const int t = tid;
+            float v[NB];
+            if (t < kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = NB + t - c;
+                    v[c] = (off <= kd) ? W[(size_t)wrap1(base + c, kd) * LDW + off] : 0.f;
+                }
+            } else {
+                const float* Bp = Bw + (t - kd) * kd;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) v[c] = Bp[wrap1(base + c, kd)];
+            }
+            panel_row_steps<float, 0>(v, L11p);
+            if (t < kd) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int off = NB + t - c;
+                    if (off <= kd) Lg[(size_t)(j0 + c) * LDL + off] = v[c];
+                }
+            } else {
+                float* yp = Yg + (size_t)(t - kd) * nmp + j0;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) yp[c] = v[c];
+            }
+            if (more) {
+#pragma unroll
+                for (int c4 = 0; c4 < NB / 4; ++c4) {
+                    float b[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) b[u] = tf32_rna(v[4 * c4 + u]);
+                    const uint32_t o = sw128_offset(t, 4 * c4);
+                    *reinterpret_cast<float4*>(Pb + o) = make_float4(b[0], b[1], b[2], b[3]);
+                    *reinterpret_cast<float4*>(Ps + o) =
+                        make_float4(v[4 * c4] - b[0], v[4 * c4 + 1] - b[1], v[4 * c4 + 2] - b[2], v[4 * c4 + 3] - b[3]);
+                }
+                fence_async_smem();
+            }
+        }
+        __syncthreads();
+        if (!more) break;
+        // ---- U: the trailing update on the tensor cores
+        const int nbase = wrap1(base + NB, kd);
+        const Win w{W, Bw, kd, kd, LDW, KR, nbase};
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t r128 = 128 * 128;  // operand row 128
+            mma3(tmem, pb, ps, pb, ps, idesc_tf32(128, 32));
+            if (lay.nB > 0) mma3(tmem + 128, pb, ps, pb + r128, ps + r128, idesc_tf32(128, lay.nB));
+            mma_commit(bar1);
+            if (lay.n0 > 32) mma3(tmem + 32, pb, ps, pb + 32 * 128, ps + 32 * 128, idesc_tf32(128, lay.n0 - 32));
+            if (lay.n11 > 0) {
+                const uint32_t a0 = (uint32_t)(PR - 128) * 128;
+                mma3(tmem + 128 + lay.nB, pb + a0, ps + a0, pb + r128, ps + r128, idesc_tf32(128, lay.n11));
+            }
+            mma_commit(bar2);
+        }
+        const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        if (warp < 4) {
+            // first group: tile A, columns 0..31
+            if (lane == 0 && !mbar_wait_sleep(bar1, phase)) *s_ok = 0;
+            __syncwarp();
+            tc_fence_after();
+            epi_chunk(w, tq, 0, 32 * warp + lane, 0);
+            if (warp == 0) {
+                __syncwarp();
+                tc2_diag(W, dinv, L11p, Lg, Dg, nbase, j0 + NB, kd, LDW, lane, bad);
+            }
+        } else {
+            if (warp == 4 && lay.nB > 0) {
+                // first group: tile B, columns t2 < 32
+                if (lane == 0 && !mbar_wait_sleep(bar1, phase)) *s_ok = 0;
+                __syncwarp();
+                tc_fence_after();
+                for (int ch = 0; ch < (lay.nB + 31) / 32; ++ch) epi_chunk(w, tq + 128 + 32 * ch, 1, lane, 128 + 32 * ch);
+            }
+            // the next columns [j0+kd, j0+kd+NB) into panel j's slots
+            if (j0 + kd < nmp) tc2_enter(W, Bw, r, j0 + kd, base, kd, LDW, nmp, tid - 128, 128, 1);
+        }
+        if (warp > 0) {
+            bar_sync(2, TC2_THREADS - 32);  // the entering columns are in place
+            // second group: tile A columns 32.., tile B quarters 1-3, tile C
+            if (lane == 0 && !mbar_wait_sleep(bar2, phase)) *s_ok = 0;
+            __syncwarp();
+            tc_fence_after();
+            const int q = warp & 3, sh = warp >> 2;  // warps q and q + 4 share quarter q (q >= 1)
+            int job = 0;
+            for (int ch = 1; ch <= q && 32 * ch < lay.n0; ++ch, ++job)
+                if (q > 0 && (job & 1) == sh) epi_chunk(w, tq + 32 * ch, 0, 32 * q + lane, 32 * ch);
+            if (q > 0)
+                for (int ch = 0; ch < (lay.nB + 31) / 32; ++ch, ++job)
+                    if ((job & 1) == sh) epi_chunk(w, tq + 128 + 32 * ch, 1, 32 * q + lane, 128 + 32 * ch);
+            if (lay.n11 > 0 && 32 * q + 31 >= 256 - PR)
+                for (int ch = 0; ch < (lay.n11 + 31) / 32; ++ch, ++job)
+                    if (q == 0 ? sh == 1 : (job & 1) == sh) {
+                        const int t1 = PR - 128 + 32 * q + lane;
+                        epi_chunk(w, tq + 128 + lay.nB + 32 * ch, 0, t1 >= 128 ? t1 : KR, 128 + 32 * ch);
+                    }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (!*s_ok) break;  // the tensor core did not answer: give up on this RVE
+        base = nbase;
+    }
+    if (warp == 0 && bad) *s_bad = 1;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)lay.tcols);
+    if (tid == 0) {
+        const int st = status[blockIdx.x];
+        if (!*s_ok && st == FE2_OK)
+            status[blockIdx.x] = FE2_ERR_TIMEOUT;
+        else if (*s_bad && st == FE2_OK)
+            status[blockIdx.x] = FE2_ERR_NOT_PD;
+    }
+}
+
 }  // namespace
 
 bool factor_tc_eligible(int kd, int nr, int d, int max_smem) {
@@ -546,6 +866,25 @@ bool factor_tc_eligible(int kd, int nr, int d, int max_smem) {
     l.init(kd, nr);
     return 32 + kd + nr <= TC_ROW_THREADS && nr * NB <= 64 * MAX_RHS_PER_LOADER && l.KP <= 256 && l.tcols <= 512 &&
            (int)l.total <= max_smem;
+}
+
+// Two CTAs per SM need both the shared memory and the tensor memory of two.
+bool factor_tc2_eligible(int kd, int nr, int d, int max_smem) {
+    if (d != 2 || kd < 64) return false;
+    Tc2Layout l;
+    l.init(kd, nr);
+    return l.KR <= TC2_THREADS && l.PR <= 256 && l.tcols <= 256 && (int)l.total <= max_smem &&
+           2 * (l.total + 1024) <= 233472;
+}
+
+cudaError_t launch_factor_tc2(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                              int maxnr, cudaStream_t s) {
+    Tc2Layout lay;
+    lay.init(maxkd, maxnr);
+    cudaError_t e = cudaFuncSetAttribute(k_band_factor_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
+    if (e != cudaSuccess) return e;
+    k_band_factor_tc2<<<n, TC2_THREADS, lay.total, s>>>(tab, ids, ws, status);
+    return cudaGetLastError();
 }
 
 size_t factor_tc_smem_bytes(int kd, int nr) {

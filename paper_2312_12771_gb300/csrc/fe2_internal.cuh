@@ -78,6 +78,9 @@ cudaError_t launch_factor_la(const RveDev* tab, const int* ids, int n, Workspace
                              int maxnr, cudaStream_t s);
 // tensor-core FP32 band factor (2D): eligibility, shared memory, launch
 bool factor_tc_eligible(int kd, int nr, int d, int max_smem);
+bool factor_tc2_eligible(int kd, int nr, int d, int max_smem);
+cudaError_t launch_factor_tc2(const RveDev* tab, const int* ids, int n, Workspace ws, int* status, int maxkd,
+                              int maxnr, cudaStream_t s);
 size_t factor_tc_smem_bytes(int kd, int nr);
 cudaError_t launch_factor_tc(const RveDev* tab, const int* ids, int n, Workspace ws, int* status,
                              int maxkd, int maxnr, cudaStream_t s);
