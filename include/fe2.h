@@ -74,9 +74,11 @@ enum { FE2_MODEL_LINEAR = 0, FE2_MODEL_NEOHOOKE = 1, FE2_MODEL_MOONEY_RIVLIN = 2
  * take the previous panel's trailing update blocks from a shared counter
  * (2D bands with 32 + kd + d*d+1 <= 224; measured slower on GB300, kept as an
  * option).  FE2_FACTOR_TENSOR_CORE (mixed path): the dense trailing updates as
- * tcgen05 MMAs (3xTF32, fp32 accumulation in tensor memory), one RVE per SM,
- * for 2D bands with 32 + kd + d*d+1 <= 192 whose shared memory fits; other
- * bands take the CUDA-core kernel.  FE2_FACTOR_AUTO is the library's choice,
+ * tcgen05 MMAs (3xTF32, fp32 accumulation in tensor memory); two RVEs per SM
+ * (a window ring of kd columns, 256 tensor-memory columns each) for 2D bands
+ * with kd >= 64 and kd + d*d+1 <= 256 whose layout fits two CTAs per SM, else
+ * one RVE per SM for 2D bands with 32 + kd + d*d+1 <= 192 whose shared memory
+ * fits; other bands take the CUDA-core kernel.  FE2_FACTOR_AUTO is the library's choice,
  * currently FE2_FACTOR_CUDA_CORE (measured fastest on GB300 for these bands).
  * 3D (Hex8) bands always take the wide-band kernel. */
 enum { FE2_FACTOR_AUTO = 0, FE2_FACTOR_CUDA_CORE = 1, FE2_FACTOR_TENSOR_CORE = 2, FE2_FACTOR_CUDA_CORE_PIPELINED = 3 };
