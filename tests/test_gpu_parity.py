@@ -621,12 +621,13 @@ def C_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-@pytest.mark.parametrize("N", [3, 8, 24, 30, 32])
+@pytest.mark.parametrize("N", [3, 8, 16, 20, 24, 30, 32])
 def test_tensor_core_factor_parity(torch, N):
     """Mixed path with the tcgen05 (3xTF32) band factor against the oracle and
-    against the CUDA-core FP32 factor.  N spans the operand shapes: one
-    128-row tile (N <= 24), two row tiles without (N = 30) and with (N = 32)
-    the corner tile beyond column 128."""
+    against the CUDA-core FP32 factor.  N spans the kernels and operand shapes:
+    one RVE per SM (N = 3, 8), two per SM with one 128-row tile (N = 16, 20,
+    24), two row tiles without (N = 30) and with (N = 32) the corner tile
+    beyond column 128."""
     b = W.fiber_batch(4, N, dF_scale=2e-3)
     out = {}
     for kern in ("tensor_core", "cuda_core"):
@@ -644,6 +645,26 @@ def test_tensor_core_factor_parity(torch, N):
         check(b, sig, Cb, st, refs, idx, TOL["mixed"])
     dC = (out["tensor_core"][1] - out["cuda_core"][1]).abs().max().item()
     assert dC <= 1e-8 * out["cuda_core"][1].abs().max().item()
+
+
+def test_tensor_core_factor_mixed_sizes(torch):
+    """The two-RVE-per-SM tensor-core factor with RVEs of 16^2, 24^2 and 32^2 in
+    one launch (each CTA lays out its own band inside the launch's largest):
+    every result against the oracle, and bitwise equal to the same RVE solved
+    alone."""
+    sizes = np.array([16, 24, 32, 24, 16, 32], np.int32)
+    b = W.inclusion_batch(len(sizes), sizes, stretch=1.04)
+    ctx = ctx_for(torch, "mixed", factor="tensor_core")
+    ids = ctx.register_batch(b)
+    F = torch.tensor(b.Fbar, device="cuda")
+    sig, Cb, st, err = ctx.rve_solve(ids, F)
+    torch.cuda.synchronize()
+    idx = list(range(b.nrve))
+    check(b, sig, Cb, st, oracle_batch(b, idx), idx, TOL["mixed"])
+    for k in (0, 1, 2):
+        s1, C1, _, _ = ctx.rve_solve(ids[k:k + 1], F[k:k + 1])
+        torch.cuda.synchronize()
+        assert torch.equal(C1[0], Cb[k]) and torch.equal(s1[0], sig[k])
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
