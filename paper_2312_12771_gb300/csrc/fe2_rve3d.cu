@@ -384,13 +384,6 @@ __device__ __forceinline__ int wrapS3(int x, int S) { return x >= S ? x - S : x;
 template <typename T>
 struct Ld4;
 template <>
-struct Ld4<float> {
-    __device__ __forceinline__ static void load(const float* p, float* o) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
-    }
-};
-template <>
 struct Ld4<double> {
     __device__ __forceinline__ static void load(const double* p, double* o) {
         const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
