@@ -357,31 +357,34 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
             for (int kL = 0; kL < 4; ++kL) mme[4 * iJ + kL] += wq * A[iJ >> 1][iJ & 1][kL >> 1][kL & 1];
             mme[16 + iJ] += wq * P[iJ >> 1][iJ & 1];
         }
+        // the quadrature weight rides on the row node's gradient: t = wq G_a A, so the
+        // element integrals accumulate with FMAs and no separate product by wq
+        double Gw[8];
+#pragma unroll
+        for (int x = 0; x < 8; ++x) Gw[x] = wq * G[x];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            double t[2][2][2];  // t[i][k][L] = sum_J G_aJ A_iJkL
+            double t[2][2][2];  // t[i][k][L] = wq sum_J G_aJ A_iJkL
             for (int i = 0; i < 2; ++i)
                 for (int k = 0; k < 2; ++k)
                     for (int L = 0; L < 2; ++L)
-                        t[i][k][L] = G[2 * a] * A[i][0][k][L] + G[2 * a + 1] * A[i][1][k][L];
+                        t[i][k][L] = Gw[2 * a] * A[i][0][k][L] + Gw[2 * a + 1] * A[i][1][k][L];
 #pragma unroll
             for (int b = a; b < 4; ++b) {
                 const int p = ec_pair(a, b);
                 for (int i = 0; i < 2; ++i)
                     for (int k = 0; k < 2; ++k) {
-                        const double v = t[i][k][0] * G[2 * b] + t[i][k][1] * G[2 * b + 1];
                         double* o = out + (4 * p + 2 * i + k) * stride;
-                        *o = g == 0 ? wq * v : __fma_rn(wq, v, *o);
+                        *o = __fma_rn(t[i][k][1], G[2 * b + 1], __fma_rn(t[i][k][0], G[2 * b], g == 0 ? 0.0 : *o));
                     }
             }
             for (int i = 0; i < 2; ++i) {
-                const double v = P[i][0] * G[2 * a] + P[i][1] * G[2 * a + 1];
                 double* o = out + (40 + 2 * a + i) * stride;
-                *o = g == 0 ? wq * v : __fma_rn(wq, v, *o);
+                *o = __fma_rn(P[i][1], Gw[2 * a + 1], __fma_rn(P[i][0], Gw[2 * a], g == 0 ? 0.0 : *o));
                 for (int k = 0; k < 2; ++k)
                     for (int L = 0; L < 2; ++L) {
                         double* o2 = out + (48 + 8 * a + 4 * i + 2 * k + L) * stride;
-                        *o2 = g == 0 ? wq * t[i][k][L] : __fma_rn(wq, t[i][k][L], *o2);
+                        *o2 = g == 0 ? t[i][k][L] : *o2 + t[i][k][L];
                     }
             }
         }
