@@ -117,18 +117,20 @@ __device__ __forceinline__ void elem3_row(const double* __restrict__ cache, cons
         for (int q = 0; q < 8; ++q) {
             const double* c = cache + (size_t)q * 90 * E3_ELEMS + el;  // c[k * E3_ELEMS]: entry k of (q, el)
             const double(*G)[3] = Gt[q];
-            f += wq * (c[(81 + 3 * i) * E3_ELEMS] * G[A][0] + c[(81 + 3 * i + 1) * E3_ELEMS] * G[A][1] +
-                       c[(81 + 3 * i + 2) * E3_ELEMS] * G[A][2]);
+            // the quadrature weight rides on row node A's gradient: every integral below
+            // accumulates with FMAs and no separate product by wq
+            const double g0 = wq * G[A][0], g1 = wq * G[A][1], g2 = wq * G[A][2];
+            f += c[(81 + 3 * i) * E3_ELEMS] * g0 + c[(81 + 3 * i + 1) * E3_ELEMS] * g1 +
+                 c[(81 + 3 * i + 2) * E3_ELEMS] * g2;
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
                 for (int L = 0; L < 3; ++L) {
-                    const double tv = G[A][0] * c[(27 * i + 3 * k + L) * E3_ELEMS] +
-                                      G[A][1] * c[(27 * i + 9 + 3 * k + L) * E3_ELEMS] +
-                                      G[A][2] * c[(27 * i + 18 + 3 * k + L) * E3_ELEMS];
-                    kM[3 * k + L] += wq * tv;
+                    const double tv = g0 * c[(27 * i + 3 * k + L) * E3_ELEMS] + g1 * c[(27 * i + 9 + 3 * k + L) * E3_ELEMS] +
+                                      g2 * c[(27 * i + 18 + 3 * k + L) * E3_ELEMS];
+                    kM[3 * k + L] += tv;
 #pragma unroll
-                    for (int b = A; b < 8; ++b) kr[b - A][k] += wq * tv * G[b][L];
+                    for (int b = A; b < 8; ++b) kr[b - A][k] += tv * G[b][L];
                 }
         }
 #pragma unroll
