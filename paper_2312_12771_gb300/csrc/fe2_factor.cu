@@ -885,7 +885,7 @@ struct SolveLayout {
         kd = kd_;
         nr = nr_;
         nmp = nmp_;
-        S = kd + NB;
+        S = (kd + NB + 3) & ~3;  // a multiple of 4: ring rows j0 + NB + 4m start on 16 bytes
         LDL = kd + 1;
         blk = ((size_t)NB * LDL * sizeof(T) + NB * sizeof(T) + 127) & ~(size_t)127;
         const size_t rest = (((size_t)nr * 2 * S * sizeof(T) + 15) & ~(size_t)15) +
@@ -956,15 +956,14 @@ struct LStream {
 // Result written to X (accumulate = 0) or added to X (accumulate = 1) in FP64.
 constexpr int BW_WIDE = 256;  // half bandwidths above this take the lane-split panel dot products
 
-// The panel's dot products of the backward solve: tv[rr][c] = y(j0 + c) -
-// sum_{off = NB - c .. kd} L(j0 + c + off, j0 + c) x(j0 + c + off) for every
-// right-hand side rr < nr (NRT >= nr, compile-time when it equals nr).  Warp w
+// The panel's dot products of the backward solve, wide bands:
+// tv[rr NB + c] = sum_{off = NB - c .. kd} L(j0 + c + off, j0 + c) x(j0 + c + off) for
+// every right-hand side rr < nr (NRT >= nr, compile-time when it equals nr).  Warp w
 // takes columns c = w, w + nwarps, ..; lane l the offsets NB - c + l + 32k; the
 // lanes' partial sums meet in a butterfly (a fixed order: deterministic).
 template <typename T, int NRT>
-__device__ __forceinline__ void panel_dots(const T* __restrict__ Lb, const T* __restrict__ xr,
-                                           const T* __restrict__ ysrc, T (*tv)[NB], int s0, int j0, int kd, int S,
-                                           int LDL, int nr, int nmp, int warp, int lane) {
+__device__ __forceinline__ void panel_dots(const T* __restrict__ Lb, const T* __restrict__ xr, T* __restrict__ tv,
+                                           int s0, int kd, int S, int LDL, int nr, int warp, int lane) {
     const int nw = blockDim.x >> 5;
     for (int c = warp; c < NB; c += nw) {
         const T* Lc = Lb + c * LDL;
@@ -984,7 +983,70 @@ __device__ __forceinline__ void panel_dots(const T* __restrict__ Lb, const T* __
             T v = acc[rr];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) tv[rr][c] = ysrc[(size_t)rr * nmp + j0 + c] - v;
+            if (lane == 0) tv[rr * NB + c] = v;
+        }
+    }
+}
+
+// Right-hand sides per warp in the narrow-band dot products.
+constexpr int BW_CHUNK = 5;
+
+// The panel's dot products of the backward solve, narrow FP32 bands: partial sums
+// tv[(p nr + rr) NB + c] = sum over the rows j0 + NB + q of part p of
+// L(j0 + NB + q, j0 + c) x(j0 + NB + q).  Lane c owns column c; a warp takes one
+// part of the kd rows and up to BW_CHUNK right-hand sides, so every L entry it loads
+// serves all of them, and x comes as 16-byte broadcasts of four rows (s0 and the
+// parts start on multiples of 4).  The nparts partial sums (nparts nr <= MAX_NR)
+// are added in part order by the triangle.
+template <typename T>
+__device__ __forceinline__ void panel_dots_rows(const T* __restrict__ Lb, const T* __restrict__ xr,
+                                                T* __restrict__ tv, int s0, int kd, int S, int LDL, int nr,
+                                                int nparts, int warp, int lane) {
+    const int nw = blockDim.x >> 5;
+    const int nch = (nr + BW_CHUNK - 1) / BW_CHUNK;
+    const int qp = ((kd + nparts - 1) / nparts + 3) & ~3;  // rows per part
+    const T* Lc = Lb + lane * LDL + NB - lane;             // L(j0 + NB + q, j0 + lane) = Lc[q]
+    const int qlim = kd - NB + lane;                         // in the band while q <= qlim
+    for (int it = warp; it < nch * nparts; it += nw) {
+        const int ch = it % nch, p = it / nch;
+        const int r0 = ch * BW_CHUNK;
+        const int qa = p * qp, qb = min(kd, qa + qp);
+        const T* xq = xr + r0 * 2 * S + s0;  // x(j0 + NB + q) of right-hand side r0 + k: xq[k 2S + q]
+        T acc[BW_CHUNK];
+#pragma unroll
+        for (int k = 0; k < BW_CHUNK; ++k) acc[k] = T(0);
+        for (int q = qa; q < qb; q += 4) {
+            T l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) l[u] = (q + u <= qlim) ? Lc[q + u] : T(0);
+#pragma unroll
+            for (int k = 0; k < BW_CHUNK; ++k) {
+                if (r0 + k < nr) {
+                    T xv[4];
+                    Vec4<T>::load(xq + k * 2 * S + q, xv);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[k] += l[u] * xv[u];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < BW_CHUNK; ++k)
+            if (r0 + k < nr) tv[(p * nr + r0 + k) * NB + lane] = acc[k];
+    }
+}
+
+// The backward triangle's sweep for K right-hand sides of one warp: lane c2 sends
+// x_c2 = t_c2 / L(c2, c2), every lane c subtracts L(c2, c) x_c2 (zero unless c < c2
+// within the band).  Fully unrolled: the L loads do not wait on the chain.
+template <typename T, int K>
+__device__ __forceinline__ void tri_sweep(T* acc, const T* __restrict__ Lb, int LDL, int kd, int lane, T dme) {
+#pragma unroll
+    for (int c2 = NB - 1; c2 > 0; --c2) {
+        const T l = (lane < c2 && c2 - lane <= kd) ? Lb[lane * LDL + (c2 - lane)] : T(0);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const T xv = __shfl_sync(0xffffffffu, acc[q] * dme, c2);
+            acc[q] -= l * xv;
         }
     }
 }
@@ -995,7 +1057,11 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                               T* __restrict__ dxout = nullptr) {
     const int kd = lay.kd, S = lay.S, LDL = lay.LDL, nr = lay.nr, nmp = lay.nmp, nm = r.nm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    __shared__ T tv[MAX_NR][NB];
+    const int nw = blockDim.x >> 5;
+    constexpr int RPW = (MAX_NR + FACT_THREADS / 32 - 1) / (FACT_THREADS / 32);  // right-hand sides per warp
+    constexpr bool ROWS = !WIDE && sizeof(T) == 4;  // lane-per-column dot products
+    __shared__ __align__(16) T tv[MAX_NR * NB];      // partial dot products [part][rr][c]
+    const int nparts = ROWS ? MAX_NR / nr : 1;
     for (int k = tid; k < nr * 2 * S; k += blockDim.x) xr[k] = T(0);
     const int nblk = nmp / NB;
     ls.issue(k0, nmp - NB);
@@ -1005,28 +1071,36 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
         const int k = k0 + (nblk - 1 - b);
         const int j0 = b * NB;
         if (b > 0 && ls.nbuf == 2) ls.issue(k + 1, j0 - NB);
+        // y of this warp's right-hand sides rr = warp + q nw, loaded ahead of the wait
+        T acc[RPW];
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int rr = warp + q * nw;
+            acc[q] = rr < nr ? ysrc[(size_t)rr * nmp + j0 + lane] : T(0);
+        }
         if (!ls.wait(k)) *s_to = 1;
         __syncthreads();
         if (*s_to) return false;
         const T* Lb = ls.buf(k);
         const T* db = ls.dinv(k);
         const int s0 = wrapS(jb + NB, S);
-        // t = y_b - sum_{i >= j0+NB} L(i, c) x(i).  WIDE (launches whose widest band
-        // exceeds BW_WIDE): warp w takes columns w, w + nw, .., its lanes split the rows,
-        // and every L entry loaded serves all nr right-hand sides.  Otherwise one thread
-        // per (c, rr), whose dot product is short (the lane split would be dominated by
-        // its reductions).  Both compute the same sums.
+        // sums over the rows i >= j0 + NB of L(i, c) x(i) for the panel's columns c.
+        // WIDE (launches whose widest band exceeds BW_WIDE): warp w takes columns w,
+        // w + nw, .., its lanes split the rows.  Narrow FP32: lane c takes column c, the
+        // warps split the rows and the right-hand sides.  Narrow FP64: one thread per
+        // (c, rr), whose dot product is short.
         if constexpr (WIDE) {
             if (nr == 10)
-                panel_dots<T, 10>(Lb, xr, ysrc, tv, s0, j0, kd, S, LDL, nr, nmp, warp, lane);
+                panel_dots<T, 10>(Lb, xr, tv, s0, kd, S, LDL, nr, warp, lane);
             else
-                panel_dots<T, MAX_NR>(Lb, xr, ysrc, tv, s0, j0, kd, S, LDL, nr, nmp, warp, lane);
+                panel_dots<T, MAX_NR>(Lb, xr, tv, s0, kd, S, LDL, nr, warp, lane);
+        } else if constexpr (ROWS) {
+            panel_dots_rows<T>(Lb, xr, tv, s0, kd, S, LDL, nr, nparts, warp, lane);
         } else {
             for (int t = tid; t < NB * nr; t += blockDim.x) {
                 const int c = t % NB, rr = t / NB;
                 const T* Lc = Lb + c * LDL;
                 const T* xp = xr + rr * 2 * S + s0 + c - NB;  // x(j0 + c + off) = xp[off]
-                const T yv = ysrc[(size_t)rr * nmp + j0 + c];  // issued before the dot product
                 T s0a = T(0), s1a = T(0), s2a = T(0), s3a = T(0);
                 int off = NB - c;
                 for (; off + 3 <= kd; off += 4) {
@@ -1036,28 +1110,71 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                     s3a += Lc[off + 3] * xp[off + 3];
                 }
                 for (; off <= kd; ++off) s0a += Lc[off] * xp[off];
-                tv[rr][c] = yv - ((s0a + s1a) + (s2a + s3a));
+                tv[rr * NB + c] = (s0a + s1a) + (s2a + s3a);
             }
         }
         __syncthreads();
-        // NB x NB triangle L11^T x = t: warp rr handles RHS rr, lane c owns x_c
-        for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
-            T acc = tv[rr][lane], xc = T(0);
-            for (int c2 = NB - 1; c2 >= 0; --c2) {
-                T xv = (lane == c2) ? acc * db[c2] : T(0);
-                xv = __shfl_sync(0xffffffffu, xv, c2);
-                if (lane == c2) xc = xv;
-                if (lane < c2 && c2 - lane <= kd) acc -= Lb[lane * LDL + (c2 - lane)] * xv;
+        // NB x NB triangle L11^T x = y_b - sums.  Warp w takes the right-hand sides w,
+        // w + nw, ..; lane c owns t_c of each and ends with x_c.
+        T xo[RPW];
+        if constexpr (WIDE) {
+            // one sweep for all of the warp's right-hand sides (fully unrolled): a lane's t
+            // stops changing once the sweep has passed it, so x_c = t_c / L(c, c) at the
+            // end is the value it sent
+            const T dme = db[lane];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const int rr = warp + q * nw;
+                if (rr < nr) {
+                    T sum = tv[rr * NB + lane];
+                    for (int p = 1; p < nparts; ++p) sum += tv[(p * nr + rr) * NB + lane];
+                    acc[q] -= sum;
+                }
             }
-            const int idx = wrapS(jb + lane, S);
-            xr[rr * 2 * S + idx] = xc;
-            xr[rr * 2 * S + idx + S] = xc;
-            const int row = j0 + lane;
-            if (dxout) {
-                dxout[(size_t)rr * nmp + row] = xc;  // the correction itself, X untouched
-            } else if (row < nm) {
-                double* Xp = r.X + (size_t)rr * nm + row;
-                *Xp = accumulate ? (*Xp + (double)xc) : (double)xc;
+            const int nq = nr > warp ? (nr - warp + nw - 1) / nw : 0;
+            if (nq == 1)
+                tri_sweep<T, 1>(acc, Lb, LDL, kd, lane, dme);
+            else if (nq == 2)
+                tri_sweep<T, 2>(acc, Lb, LDL, kd, lane, dme);
+            else if (nq >= 3)
+                tri_sweep<T, RPW>(acc, Lb, LDL, kd, lane, dme);
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) xo[q] = acc[q] * dme;
+        } else {
+            // one sweep per right-hand side: lane c2's x_c2 goes to every lane by a shuffle
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const int rr = warp + q * nw;
+                xo[q] = T(0);
+                if (rr < nr) {
+                    T t = tv[rr * NB + lane];
+                    for (int p = 1; p < nparts; ++p) t += tv[(p * nr + rr) * NB + lane];
+                    T a = acc[q] - t, xc = T(0);
+                    for (int c2 = NB - 1; c2 >= 0; --c2) {
+                        T xv = (lane == c2) ? a * db[c2] : T(0);
+                        xv = __shfl_sync(0xffffffffu, xv, c2);
+                        if (lane == c2) xc = xv;
+                        if (lane < c2 && c2 - lane <= kd) a -= Lb[lane * LDL + (c2 - lane)] * xv;
+                    }
+                    xo[q] = xc;
+                }
+            }
+        }
+        const int idx = wrapS(jb + lane, S);
+        const int row = j0 + lane;
+#pragma unroll
+        for (int q = 0; q < RPW; ++q) {
+            const int rr = warp + q * nw;
+            if (rr < nr) {
+                const T xc = xo[q];
+                xr[rr * 2 * S + idx] = xc;
+                xr[rr * 2 * S + idx + S] = xc;
+                if (dxout) {
+                    dxout[(size_t)rr * nmp + row] = xc;  // the correction itself, X untouched
+                } else if (row < nm) {
+                    double* Xp = r.X + (size_t)rr * nm + row;
+                    *Xp = accumulate ? (*Xp + (double)xc) : (double)xc;
+                }
             }
         }
         __syncthreads();
