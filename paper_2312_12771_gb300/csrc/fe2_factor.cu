@@ -1051,6 +1051,23 @@ __device__ __forceinline__ void tri_sweep(T* acc, const T* __restrict__ Lb, int 
     }
 }
 
+// The forward triangle's sweep (L11 y = b) for K right-hand sides of one warp:
+// lane c sends y_c = b_c / L(c, c), every lane below subtracts L(lane, c) y_c.  A
+// lane's b stops changing once the sweep has reached it, so y_c = b_c / L(c, c) at
+// the end is the value it sent.
+template <typename T, int K>
+__device__ __forceinline__ void fwd_sweep(T* acc, const T* __restrict__ Lb, int LDL, int kd, int lane, T dme) {
+#pragma unroll
+    for (int c = 0; c < NB - 1; ++c) {
+        const T l = (lane > c && lane - c <= kd) ? Lb[c * LDL + (lane - c)] : T(0);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const T yv = __shfl_sync(0xffffffffu, acc[q] * dme, c);
+            acc[q] -= l * yv;
+        }
+    }
+}
+
 template <typename T, bool WIDE>
 __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout<T>& lay, LStream<T>& ls, int& k0,
                               T* __restrict__ xr, const T* __restrict__ ysrc, int accumulate, int* s_to,
@@ -1288,17 +1305,46 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_solve_correct(const RveDe
                 if (row < nm) pre[q] = Rg[(size_t)rr * nm + row];
             }
         }
-        // triangle: warp rr, lane c owns b_c; column sweep
-        for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
-            T bv = bw[rr * S + wrapS(jb + lane, S)], yc = T(0);
-            for (int c = 0; c < NB; ++c) {
-                T yv = (lane == c) ? bv * db[c] : T(0);
-                yv = __shfl_sync(0xffffffffu, yv, c);
-                if (lane == c) yc = yv;
-                if (lane > c && lane - c <= kd) bv -= Lb[c * LDL + (lane - c)] * yv;
+        // triangle L11 y = b: lane c owns b_c.  Wide bands: warp w takes the right-hand
+        // sides w, w + nw, .. in one unrolled sweep; otherwise one sweep per right-hand side.
+        if constexpr (WIDE) {
+            constexpr int RPW = (MAX_NR + FACT_THREADS / 32 - 1) / (FACT_THREADS / 32);
+            const int nw = blockDim.x >> 5;
+            const T dme = db[lane];
+            T acc[RPW];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const int rr = warp + q * nw;
+                acc[q] = rr < nr ? bw[rr * S + wrapS(jb + lane, S)] : T(0);
             }
-            ys[(size_t)rr * nmp + j0 + lane] = yc;
-            yt[lane * YT_LD + rr] = yc;
+            const int nq = nr > warp ? (nr - warp + nw - 1) / nw : 0;
+            if (nq == 1)
+                fwd_sweep<T, 1>(acc, Lb, LDL, kd, lane, dme);
+            else if (nq == 2)
+                fwd_sweep<T, 2>(acc, Lb, LDL, kd, lane, dme);
+            else if (nq >= 3)
+                fwd_sweep<T, RPW>(acc, Lb, LDL, kd, lane, dme);
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) {
+                const int rr = warp + q * nw;
+                if (rr < nr) {
+                    const T yc = acc[q] * dme;
+                    ys[(size_t)rr * nmp + j0 + lane] = yc;
+                    yt[lane * YT_LD + rr] = yc;
+                }
+            }
+        } else {
+            for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
+                T bv = bw[rr * S + wrapS(jb + lane, S)], yc = T(0);
+                for (int c = 0; c < NB; ++c) {
+                    T yv = (lane == c) ? bv * db[c] : T(0);
+                    yv = __shfl_sync(0xffffffffu, yv, c);
+                    if (lane == c) yc = yv;
+                    if (lane > c && lane - c <= kd) bv -= Lb[c * LDL + (lane - c)] * yv;
+                }
+                ys[(size_t)rr * nmp + j0 + lane] = yc;
+                yt[lane * YT_LD + rr] = yc;
+            }
         }
         __syncthreads();
         // rows below the block: b_i -= sum_c L(i, c) y_c, one thread per row i for every
