@@ -40,7 +40,14 @@ __device__ __forceinline__ double grad3(int q, int a, int J, double h) {
     return v;
 }
 
-__device__ void consti3(const double* m, const double F[3][3], double P[3][3], double A[3][3][3][3]) {
+// The law at one Gauss point in the form A_iJkL = al d_ik d_JL + be H_iJ H_kL +
+// ga H_iL H_kJ, with P.  Linear (small strain, H = I): A = lambda d_iJ d_kL +
+// mu (d_ik d_JL + d_iL d_Jk).  Compressible Neo-Hooke, W = mu/2 (tr C - 3) -
+// mu ln J + kappa/2 (J - 1)^2: P = mu F + s H with H = cof F = J F^-T and
+// s = kappa (J - 1) - mu / J; dH_iJ/dF_kL = (H_iJ H_kL - H_iL H_kJ) / J gives
+// A = mu d_ik d_JL + (c + s/J) H_iJ H_kL - (s/J) H_iL H_kJ, c = mu / J^2 + kappa.
+__device__ void law3(const double* m, const double F[3][3], double& al, double& be, double& ga, double H[3][3],
+                     double P[3][3]) {
     const int model = (int)m[0];
     if (model == FE2_MODEL_LINEAR) {
         const double E = m[1], nu = m[2];
@@ -50,17 +57,14 @@ __device__ void consti3(const double* m, const double F[3][3], double P[3][3], d
             for (int J = 0; J < 3; ++J) eps[i][J] = 0.5 * (F[i][J] + F[J][i]) - (i == J ? 1.0 : 0.0);
         const double tr = eps[0][0] + eps[1][1] + eps[2][2];
         for (int i = 0; i < 3; ++i)
-            for (int J = 0; J < 3; ++J) P[i][J] = (i == J ? lam * tr : 0.0) + 2.0 * mu * eps[i][J];
-        for (int i = 0; i < 3; ++i)
-            for (int J = 0; J < 3; ++J)
-                for (int k = 0; k < 3; ++k)
-                    for (int L = 0; L < 3; ++L)
-                        A[i][J][k][L] = (i == J && k == L ? lam : 0.0) +
-                                        mu * ((i == k && J == L ? 1.0 : 0.0) + (i == L && J == k ? 1.0 : 0.0));
+            for (int J = 0; J < 3; ++J) {
+                P[i][J] = (i == J ? lam * tr : 0.0) + 2.0 * mu * eps[i][J];
+                H[i][J] = i == J ? 1.0 : 0.0;
+            }
+        al = mu, be = lam, ga = mu;
         return;
     }
     const double mu = m[1], kappa = m[2];
-    double H[3][3];
     for (int i = 0; i < 3; ++i)
         for (int J = 0; J < 3; ++J) {
             const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, J1 = (J + 1) % 3, J2 = (J + 2) % 3;
@@ -70,20 +74,7 @@ __device__ void consti3(const double* m, const double F[3][3], double P[3][3], d
     const double s = kappa * (Jd - 1.0) - mu / Jd, c = mu / (Jd * Jd) + kappa;
     for (int i = 0; i < 3; ++i)
         for (int J = 0; J < 3; ++J) P[i][J] = mu * F[i][J] + s * H[i][J];
-    for (int i = 0; i < 3; ++i)
-        for (int J = 0; J < 3; ++J) {
-            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, J1 = (J + 1) % 3, J2 = (J + 2) % 3;
-            for (int k = 0; k < 3; ++k)
-                for (int L = 0; L < 3; ++L) {
-                    // dH_iJ / dF_kL with H_iJ = F_i1J1 F_i2J2 - F_i1J2 F_i2J1
-                    double dH = 0.0;
-                    if (k == i1 && L == J1) dH += F[i2][J2];
-                    if (k == i2 && L == J2) dH += F[i1][J1];
-                    if (k == i1 && L == J2) dH -= F[i2][J1];
-                    if (k == i2 && L == J1) dH -= F[i1][J2];
-                    A[i][J][k][L] = (i == k && J == L ? mu : 0.0) + c * H[i][J] * H[k][L] + s * dH;
-                }
-        }
+    al = mu, be = c + s / Jd, ga = -s / Jd;
 }
 
 // S1 + S2: the rows of every (element, local node a) written to the element
@@ -93,66 +84,45 @@ __device__ void consti3(const double* m, const double F[3][3], double P[3][3], d
 // caches A (81) and P (9) in shared memory.  Phase 2: one thread per (element, a,
 // component i) integrates row i of node a (24 + 9 + 1 accumulators, in registers).
 constexpr int E3_ELEMS = 32;  // elements per CTA of the Hex8 assembly (one per lane)
-constexpr int E3_THREADS = 8 * 32;  // phase 1: warp = Gauss point; phase 2: warp = element row node
-// Row a of the element matrices of one element per lane (warp-uniform a): the
-// rows (a, i), i = 0..2, in turn, each integrated over the 8 Gauss points from
-// the cached law, and only the blocks k_e(a, b), b >= a (major symmetry of A:
-// the gather reads k_e(a, b), b < a, as the transpose of k_e(b, a)).  Loop
-// order (q, k, L, b) as in the full form.
-template <int A>
-__device__ __forceinline__ void elem3_row(const double* __restrict__ cache, const double (*Gt)[8][3], int el, int e,
-                                          int nn, double wq, double* __restrict__ E) {
-    constexpr int RC = elem_row_comps(3);
-    const int c0 = A * RC;
-#pragma unroll 1
-    for (int i = 0; i < 3; ++i) {
-        double kr[8 - A][3], kM[9], f = 0.0;
-#pragma unroll
-        for (int b = 0; b < 8 - A; ++b)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) kr[b][k] = 0.0;
-#pragma unroll
-        for (int kL = 0; kL < 9; ++kL) kM[kL] = 0.0;
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-            const double* c = cache + (size_t)q * 90 * E3_ELEMS + el;  // c[k * E3_ELEMS]: entry k of (q, el)
-            const double(*G)[3] = Gt[q];
-            // the quadrature weight rides on row node A's gradient: every integral below
-            // accumulates with FMAs and no separate product by wq
-            const double g0 = wq * G[A][0], g1 = wq * G[A][1], g2 = wq * G[A][2];
-            f += c[(81 + 3 * i) * E3_ELEMS] * g0 + c[(81 + 3 * i + 1) * E3_ELEMS] * g1 +
-                 c[(81 + 3 * i + 2) * E3_ELEMS] * g2;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-#pragma unroll
-                for (int L = 0; L < 3; ++L) {
-                    const double tv = g0 * c[(27 * i + 3 * k + L) * E3_ELEMS] + g1 * c[(27 * i + 9 + 3 * k + L) * E3_ELEMS] +
-                                      g2 * c[(27 * i + 18 + 3 * k + L) * E3_ELEMS];
-                    kM[3 * k + L] += tv;
-#pragma unroll
-                    for (int b = A; b < 8; ++b) kr[b - A][k] += tv * G[b][L];
-                }
-        }
-#pragma unroll
-        for (int b = A; b < 8; ++b)
-#pragma unroll
-            for (int k = 0; k < 3; ++k) E[(size_t)(c0 + 9 * b + 3 * i + k) * nn + e] = kr[b - A][k];
-        E[(size_t)(c0 + 72 + i) * nn + e] = f;
-#pragma unroll
-        for (int kL = 0; kL < 9; ++kL) E[(size_t)(c0 + 75 + 9 * i + kL) * nn + e] = kM[kL];
+constexpr int E3_THREADS = 8 * 32;  // phase 1: warp = Gauss point; phase 2: warps share the element's blocks
+constexpr int E3_C = 45;            // cached values per (Gauss point, element)
+
+// Node pair p of the element matrix: p < 28 the pairs a < b in row order, then
+// the diagonal pairs (p - 28, p - 28).
+__device__ __forceinline__ void pair3(int p, int& a, int& b) {
+    if (p >= 28) {
+        a = b = p - 28;
+        return;
     }
+    a = 0;
+    while (p >= 7 - a) p -= 7 - a, ++a;
+    b = a + 1 + p;
 }
 
-// S1-S2 for Hex8 RVEs: a CTA takes E3_ELEMS (32) elements.  Phase 1: warp q,
-// lane = element, evaluates the law at Gauss point q into shared memory
-// (element fastest).  Phase 2: warp a, lane = element, integrates the element
-// matrix rows of node a (elem3_row).  K_MM and Pint of the element: the 90
-// components split over the warps, Gauss points summed in order.
-__global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __restrict__ tab,
-                                                                const int* __restrict__ ids,
-                                                                const double* __restrict__ Fbar) {
-    extern __shared__ __align__(16) double cache3[];  // [8 GP][90][E3_ELEMS]
+// S1-S2 for Hex8 RVEs: a CTA takes E3_ELEMS (32) elements.
+//
+// Both laws give a tangent of the form A_iJkL = al d_ik d_JL + be H_iJ H_kL +
+// ga H_iL H_kJ (Neo-Hooke: H = cof F, al = mu, be = c + s/J, ga = -s/J with
+// P = mu F + s H; linear: H = I, al = mu, be = lambda, ga = mu).  With
+// h_b = H G_b the node-pair block of the element stiffness is
+//   k_e(a, b)_ik = sum_q w [al (G_a . G_b) d_ik + be h_a,i h_b,k + ga h_b,i h_a,k],
+// which needs no 81-entry tangent.  The macro coupling is K_mM = k_e X (X the
+// element's node coordinates relative to its first node: trilinear gradients
+// reproduce linear fields, sum_b G_b (x) X_b = I at every Gauss point).
+//
+// Phase 1: warp q, lane = element, evaluates the law at Gauss point q and caches
+// w al, w be, w ga, H, w P and h_b (element fastest).  Phase 2: the 36 node-pair
+// blocks (b >= a; the gather reads k_e(b, a) as the transpose of k_e(a, b)) go to
+// the warps in turn; warp w also integrates f of node w, and warps 4-7, which
+// hold one pair fewer, the 45 distinct entries of K_MM and Pint.  Gauss points
+// are summed in order.  Phase 3: warp a forms the K_mM rows of node a from the
+// finished blocks.
+__global__ void __launch_bounds__(E3_THREADS, 2) k_assemble_elems3(const RveDev* __restrict__ tab,
+                                                                   const int* __restrict__ ids,
+                                                                   const double* __restrict__ Fbar) {
+    extern __shared__ __align__(16) double cache3[];  // [8 GP][E3_C][E3_ELEMS]
     __shared__ double Gt[8][8][3];                     // [GP][node][J]
+    __shared__ double Dg[8][8][8];                     // [GP][a][b]: G_a . G_b
     const RveDev r = tab[ids[blockIdx.y]];
     const int N = r.N, nn = r.nn;
     const double h = 1.0 / N, wq = 0.125 * h * h * h;
@@ -160,6 +130,12 @@ __global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __
     for (int k = tid; k < 8 * 8 * 3; k += blockDim.x) {
         const int q = k / 24, b = (k / 3) % 8, J = k % 3;
         Gt[q][b][J] = grad3(q, b, J, h);
+    }
+    for (int k = tid; k < 8 * 8 * 8; k += blockDim.x) {
+        const int q = k / 64, a = (k / 8) % 8, b = k % 8;
+        double d = 0.0;
+        for (int J = 0; J < 3; ++J) d += grad3(q, a, J, h) * grad3(q, b, J, h);
+        Dg[q][a][b] = d;
     }
     double Fb[9];
     for (int k = 0; k < 9; ++k) Fb[k] = Fbar[9 * blockIdx.y + k];
@@ -180,31 +156,117 @@ __global__ void __launch_bounds__(E3_THREADS) k_assemble_elems3(const RveDev* __
                 for (int J = 0; J < 3; ++J) F[c][J] += w * Gt[q][b][J];
             }
         }
-        double P[3][3], A[3][3][3][3];
-        consti3(r.mat + 4 * r.phase[e], F, P, A);
-        double* c = cache3 + (size_t)q * 90 * E3_ELEMS + el;
-        for (int k = 0; k < 81; ++k) c[k * E3_ELEMS] = A[k / 27][(k / 9) % 3][(k / 3) % 3][k % 3];
-        for (int k = 0; k < 9; ++k) c[(81 + k) * E3_ELEMS] = P[k / 3][k % 3];
+        double al, be, ga, H[3][3], P[3][3];
+        law3(r.mat + 4 * r.phase[e], F, al, be, ga, H, P);
+        double* c = cache3 + (size_t)q * E3_C * E3_ELEMS + el;
+        c[0] = wq * al;
+        c[E3_ELEMS] = wq * be;
+        c[2 * E3_ELEMS] = wq * ga;
+        for (int k = 0; k < 9; ++k) c[(3 + k) * E3_ELEMS] = H[k / 3][k % 3];
+        for (int k = 0; k < 9; ++k) c[(12 + k) * E3_ELEMS] = wq * P[k / 3][k % 3];
+        for (int b = 0; b < 8; ++b)
+            for (int i = 0; i < 3; ++i)
+                c[(21 + 3 * b + i) * E3_ELEMS] = H[i][0] * Gt[q][b][0] + H[i][1] * Gt[q][b][1] + H[i][2] * Gt[q][b][2];
     }
     __syncthreads();
-    if (e >= nn) return;
-    double* E = r.elem;
-    switch (warp) {  // warp-uniform
-        case 0: elem3_row<0>(cache3, Gt, el, e, nn, wq, E); break;
-        case 1: elem3_row<1>(cache3, Gt, el, e, nn, wq, E); break;
-        case 2: elem3_row<2>(cache3, Gt, el, e, nn, wq, E); break;
-        case 3: elem3_row<3>(cache3, Gt, el, e, nn, wq, E); break;
-        case 4: elem3_row<4>(cache3, Gt, el, e, nn, wq, E); break;
-        case 5: elem3_row<5>(cache3, Gt, el, e, nn, wq, E); break;
-        case 6: elem3_row<6>(cache3, Gt, el, e, nn, wq, E); break;
-        default: elem3_row<7>(cache3, Gt, el, e, nn, wq, E); break;
-    }
-    // K_MM (81) and Pint (9) of the element: components ck = warp, warp + 8, ..
+    // lanes past the last element take no part below but reach every barrier
+    const bool live = e < nn;
     constexpr int RC = elem_row_comps(3);
-    for (int ck = warp; ck < 90; ck += 8) {
-        double m = 0.0;
-        for (int q = 0; q < 8; ++q) m += wq * cache3[((size_t)q * 90 + ck) * E3_ELEMS + el];
-        E[(size_t)(8 * RC + ck) * nn + e] = m;
+    double* E = r.elem;
+    const double* ce = cache3 + el;
+    // node-pair blocks k_e(a, b), b >= a
+    for (int p = warp; live && p < 36; p += 8) {
+        int a, b;
+        pair3(p, a, b);
+        double acc[9], dacc = 0.0;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[t] = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            const double* c = ce + (size_t)q * E3_C * E3_ELEMS;
+            const double al = c[0], be = c[E3_ELEMS], ga = c[2 * E3_ELEMS];
+            double ha[3], hb[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                ha[i] = c[(21 + 3 * a + i) * E3_ELEMS];
+                hb[i] = c[(21 + 3 * b + i) * E3_ELEMS];
+            }
+            dacc += al * Dg[q][a][b];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double bha = be * ha[i], ghb = ga * hb[i];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) acc[3 * i + k] += bha * hb[k] + ghb * ha[k];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                E[(size_t)(a * RC + 9 * b + 3 * i + k) * nn + e] = i == k ? acc[3 * i + k] + dacc : acc[3 * i + k];
+    }
+    // f of node a = warp: sum_q w P G_a
+    if (live) {
+        const int a = warp;
+        double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+            const double* c = ce + (size_t)q * E3_C * E3_ELEMS;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int J = 0; J < 3; ++J) f[i] += c[(12 + 3 * i + J) * E3_ELEMS] * Gt[q][a][J];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) E[(size_t)(a * RC + 72 + i) * nn + e] = f[i];
+    }
+    // K_MM (45 distinct entries m = 3i + J <= n = 3k + L) and Pint on warps 4-7
+    if (live && warp >= 4) {
+        for (int t = warp - 4; t < 54; t += 4) {
+            double s = 0.0;
+            if (t < 45) {
+                int m = 0, u = t;
+                while (u >= 9 - m) u -= 9 - m, ++m;
+                const int n = m + u;
+                const int i = m / 3, J = m % 3, k = n / 3, L = n % 3;
+#pragma unroll 1
+                for (int q = 0; q < 8; ++q) {
+                    const double* c = ce + (size_t)q * E3_C * E3_ELEMS;
+                    double v = c[E3_ELEMS] * (c[(3 + m) * E3_ELEMS] * c[(3 + n) * E3_ELEMS]) +
+                               c[2 * E3_ELEMS] * (c[(3 + 3 * i + L) * E3_ELEMS] * c[(3 + 3 * k + J) * E3_ELEMS]);
+                    if (i == k && J == L) v += c[0];
+                    s += v;
+                }
+                E[(size_t)(8 * RC + 9 * m + n) * nn + e] = s;
+                if (n != m) E[(size_t)(8 * RC + 9 * n + m) * nn + e] = s;
+            } else {
+                const int m = t - 45;
+                for (int q = 0; q < 8; ++q) s += ce[((size_t)q * E3_C + 12 + m) * E3_ELEMS];
+                E[(size_t)(8 * RC + 81 + m) * nn + e] = s;
+            }
+        }
+    }
+    // phase 3: K_mM rows of node a = warp, k_e(a, .) X = h sum_{b: bit L of b} k_e(a, b), from the
+    // blocks written above (this CTA's global writes are visible after the barrier)
+    __syncthreads();
+    if (live) {
+        const int a = warp;
+#pragma unroll 1
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                double v[8];
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    v[b] = b >= a ? E[(size_t)(a * RC + 9 * b + 3 * i + k) * nn + e]
+                                  : E[(size_t)(b * RC + 9 * a + 3 * k + i) * nn + e];
+                const double sx = (v[1] + v[3]) + (v[5] + v[7]), sy = (v[2] + v[3]) + (v[6] + v[7]),
+                             sz = (v[4] + v[5]) + (v[6] + v[7]);
+                const size_t o = (size_t)(a * RC + 75 + 9 * i + 3 * k) * nn + e;
+                E[o] = h * sx;
+                E[o + nn] = h * sy;
+                E[o + 2 * (size_t)nn] = h * sz;
+            }
     }
 }
 
@@ -665,7 +727,7 @@ __global__ void __launch_bounds__(FACT_THREADS, sizeof(T) == 4 ? 2 : 1) k_band_f
 
 cudaError_t launch_assemble_elems3(const RveDev* tab, const int* ids, int n, const double* Fbar, int maxN,
                                    cudaStream_t s) {
-    const size_t smem = (size_t)E3_ELEMS * 8 * 90 * sizeof(double);
+    const size_t smem = (size_t)E3_ELEMS * 8 * E3_C * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_assemble_elems3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((maxN * maxN * maxN + E3_ELEMS - 1) / E3_ELEMS, n);
