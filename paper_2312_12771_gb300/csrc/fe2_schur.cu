@@ -16,26 +16,57 @@ namespace fe2 {
 
 namespace {
 
-// Deterministic CTA sum of NV partials per thread; thread 0 receives the totals.
+// One level of a warp reduce-scatter: a lane holds M partial sums (index base + k);
+// it keeps the lower or the upper half by its lane bit O and adds the partner's copy
+// of that half, so the warp spends about NV additions in all instead of one
+// five-level butterfly (5 NV additions) per value.  m is the lane's count of real
+// values (the upper half is padded with zeros when M is odd).
+template <int M, int O>
+__device__ __forceinline__ void rs_level(double* v, int lane, int& base, int& m) {
+    constexpr int H = (M + 1) / 2;
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        const double lo = v[k], hi = (H + k < M) ? v[H + k] : 0.0;
+        v[k] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, O);
+    }
+    if (up) {
+        base += H;
+        m = m > H ? m - H : 0;
+    } else {
+        m = m < H ? m : H;
+    }
+    if constexpr (O > 1) rs_level<H, O / 2>(v, lane, base, m);
+}
+
+template <int M, int O>
+struct RsCount {
+    static constexpr int value = RsCount<(M + 1) / 2, O / 2>::value;
+};
+template <int M>
+struct RsCount<M, 0> {
+    static constexpr int value = M;
+};
+
+// Deterministic CTA sum of NV partials per thread: tot[k] = sum over the CTA of v[k],
+// visible to every thread on return.  Warps reduce-scatter (rs_level), then thread k
+// adds the warps' sums of index k in warp order.
 template <int NV>
-__device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*/) {
+__device__ __forceinline__ void cta_sum(double (&v)[NV], double* red /*[NV][33]*/, double* tot /*[NV]*/) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int base = 0, m = NV;
+    rs_level<NV, 16>(v, lane, base, m);
+    constexpr int MF = RsCount<NV, 16>::value;
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        double x = v[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[k * 33 + warp] = x;
+    for (int k = 0; k < MF; ++k)
+        if (k < m) red[(base + k) * 33 + warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double x = 0.0;
+        for (int w = 0; w < nw; ++w) x += red[threadIdx.x * 33 + w];
+        tot[threadIdx.x] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double x = 0.0;
-            for (int w = 0; w < nw; ++w) x += red[k * 33 + w];
-            v[k] = x;
-        }
-    }
 }
 
 // One CTA per RVE (2D: d^2 = 4, nr = 5).  G1 = rhs^T X (4 x 5), G2 = X_M^T R (4 x 5).
@@ -100,37 +131,50 @@ __global__ void __launch_bounds__(256, 2) k_schur2(const RveDev* __restrict__ ta
 #pragma unroll
             for (int c = 0; c < 5; ++c) acc[20 + a * 5 + c] += x[a] * rr[c];
     }
-    cta_sum<NA>(acc, red);
-    if (threadIdx.x == 0) {
-        double cn = 0.0, corr = 0.0;
+    __shared__ double tot[NA];
+    cta_sum<NA>(acc, red, tot);
+    // warp 0: lane t < 16 forms Cbar entry t, lanes 16-19 sigma_eff; the norms meet in a
+    // fixed-order butterfly
+    if (threadIdx.x < 32) {
+        const int t = threadIdx.x;
+        double v = 0.0, g = 0.0;
         int bad = 0;
-        for (int a = 0; a < 4; ++a) {
-            for (int b2 = 0; b2 < 4; ++b2) {
-                double v = r.KMM[a * 4 + b2] - acc[a * 5 + b2];
-                if (corrected) {
-                    v -= acc[20 + a * 5 + b2];
-                    corr += acc[20 + a * 5 + b2] * acc[20 + a * 5 + b2];
-                }
-                cn += v * v;
-                bad |= !isfinite(v);
-                Cbar[(size_t)blockIdx.x * 16 + a * 4 + b2] = v;  // |Omega| = 1
+        if (t < 16) {
+            const int a = t >> 2, b2 = t & 3;
+            v = r.KMM[t] - tot[a * 5 + b2];
+            if (corrected) {
+                g = tot[20 + a * 5 + b2];
+                v -= g;
             }
-            double sg = r.Pint[a] - acc[a * 5 + 4];
-            if (corrected) sg -= acc[20 + a * 5 + 4];
-            bad |= !isfinite(sg);
+            bad = !isfinite(v);
+            Cbar[(size_t)blockIdx.x * 16 + t] = v;  // |Omega| = 1
+        } else if (t < 20) {
+            const int a = t - 16;
+            double sg = r.Pint[a] - tot[a * 5 + 4];
+            if (corrected) sg -= tot[20 + a * 5 + 4];
+            bad = !isfinite(sg);
             sigma[(size_t)blockIdx.x * 4 + a] = sg;
         }
-        // first order: (first-order term)^2 / |Cbar|^2; second order: the size of the
-        // second-order term times the relative size of the FP32 correction
-        double e = 0.0;
-        if (corrected == 1) e = corr / fmax(cn, 1e-300);
-        if constexpr (SECOND)
-            e = fabs(acc[NA - 3]) / sqrt(fmax(cn, 1e-300)) * sqrt(acc[NA - 2] / fmax(acc[NA - 1], 1e-300));
-        if (err) err[blockIdx.x] = e;
-        if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
-        const bool over = corrected && !(e <= *tol);
-        if (redo) redo[blockIdx.x] = (over && status[blockIdx.x] == FE2_OK) ? 1 : 0;
-        if (final_sweep && over && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NO_CONV;
+        double cn = v * v, corr = g * g;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cn += __shfl_xor_sync(0xffffffffu, cn, o);
+            corr += __shfl_xor_sync(0xffffffffu, corr, o);
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (t == 0) {
+            // first order: (first-order term)^2 / |Cbar|^2; second order: the size of the
+            // second-order term times the relative size of the FP32 correction
+            double e = 0.0;
+            if (corrected == 1) e = corr / fmax(cn, 1e-300);
+            if constexpr (SECOND)
+                e = fabs(tot[NA - 3]) / sqrt(fmax(cn, 1e-300)) * sqrt(tot[NA - 2] / fmax(tot[NA - 1], 1e-300));
+            if (err) err[blockIdx.x] = e;
+            if (bad && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NAN;
+            const bool over = corrected && !(e <= *tol);
+            if (redo) redo[blockIdx.x] = (over && status[blockIdx.x] == FE2_OK) ? 1 : 0;
+            if (final_sweep && over && status[blockIdx.x] == FE2_OK) status[blockIdx.x] = FE2_ERR_NO_CONV;
+        }
     }
 }
 
