@@ -324,9 +324,60 @@ __device__ __forceinline__ int ec_pair(int a, int b) {  // a <= b
     return a == 0 ? b : (a == 1 ? 3 + b : (a == 2 ? 5 + b : 9));
 }
 
+// block (a, b) entry (c, c2) of an element from its compact components at E (stride)
+__device__ __forceinline__ double ec_kr(const double* E, int stride, int a, int b, int c, int c2) {
+    return a <= b ? E[(4 * ec_pair(a, b) + 2 * c + c2) * stride] : E[(4 * ec_pair(b, a) + 2 * c2 + c) * stride];
+}
+
+// The law at one Gauss point in the form A_iJkL = al d_ik d_JL + be H_iJ H_kL +
+// ga H_iL H_kJ, with P (plane strain).  Linear: H = I, al = mu, be = lambda,
+// ga = mu.  The hyperelastic laws Psi = a/2 F:F + g(J) of consti2: P = a F + g' H
+// with H = cof F, and as dH_iJ/dF_kL = (H_iJ H_kL - H_iL H_kJ) / J in 2D,
+// al = a, be = g'' + g'/J, ga = -g'/J.
+__device__ __forceinline__ void law2(const double* m, const double F[2][2], double& al, double& be, double& ga,
+                                     double H[2][2], double P[2][2]) {
+    const int model = (int)m[0];
+    if (model == FE2_MODEL_LINEAR) {
+        double lam, mu;
+        lame(m[1], m[2], lam, mu);
+        const double e01 = 0.5 * (F[0][1] + F[1][0]), tr = (F[0][0] - 1.0) + (F[1][1] - 1.0);
+        P[0][0] = lam * tr + 2.0 * mu * (F[0][0] - 1.0);
+        P[1][1] = lam * tr + 2.0 * mu * (F[1][1] - 1.0);
+        P[0][1] = P[1][0] = 2.0 * mu * e01;
+        H[0][0] = H[1][1] = 1.0;
+        H[0][1] = H[1][0] = 0.0;
+        al = mu, be = lam, ga = mu;
+        return;
+    }
+    H[0][0] = F[1][1], H[0][1] = -F[1][0], H[1][0] = -F[0][1], H[1][1] = F[0][0];
+    const double J = F[0][0] * F[1][1] - F[0][1] * F[1][0];
+    const double iJ = 1.0 / J;  // one FP64 division per Gauss point
+    double a, s, c;
+    if (model == FE2_MODEL_MOONEY_RIVLIN) {
+        const double alp = m[1], bet = m[2], kappa = m[3], q = 2.0 * (alp + 2.0 * bet);
+        a = 2.0 * (alp + bet);
+        s = 2.0 * bet * J + kappa * (J - 1.0) - q * iJ;
+        c = 2.0 * bet + kappa + q * iJ * iJ;
+    } else {
+        const double kappa = m[2];
+        a = m[1];
+        s = kappa * (J - 1.0) - a * iJ;  // dPsi/dJ
+        c = a * iJ * iJ + kappa;         // d^2Psi/dJ^2
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int K = 0; K < 2; ++K) P[i][K] = a * F[i][K] + s * H[i][K];
+    al = a, be = c + s * iJ, ga = -s * iJ;
+}
+
 // All rows of element (ex, ey) at (Fbar, w~) into out[c * stride], c < EC_COMP,
 // summed over the Gauss points in order; mme = K_MM (16) and Pint (4) of the element.
-// Gt[(g * 4 + b) * 2 + J] = dN_b/dX_J at Gauss point g.
+// Gt[(g * 4 + b) * 2 + J] = dN_b/dX_J at Gauss point g; Gt[32 + 10 g + p] = G_a . G_b
+// of pair p = (a, b).  With the tangent in the form of law2 and h_b = H G_b,
+//   k_e(a, b)_ik = sum_g w [al (G_a . G_b) d_ik + be h_a,i h_b,k + ga h_b,i h_a,k].
+// Bilinear gradients reproduce linear fields (sum_b G_b (x) X_b = I, X_b the node
+// coordinates h (b & 1, b >> 1) in the element), so k_eM = sum_g w G_a A = k_e X,
+// K_MM = X^T k_e X and Pint = sum_a f_a (x) X_a: formed once per element from the
+// blocks and f, instead of at every Gauss point.
 __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const double Fb[4],
                                           const double* __restrict__ Gt, double* __restrict__ out, int stride,
                                           double (&mme)[20]) {
@@ -340,8 +391,6 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
         for (int c = 0; c < 2; ++c) we[b][c] = (q == 0 || r.zero_w) ? 0.0 : r.w[2 * (q - 1) + c];
     }
 #pragma unroll
-    for (int k = 0; k < 20; ++k) mme[k] = 0.0;
-#pragma unroll
     for (int g = 0; g < 4; ++g) {
         const double* G = Gt + g * 8;
         double F[2][2];
@@ -351,55 +400,92 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
                 for (int b = 0; b < 4; ++b) v += we[b][i] * G[2 * b + J];
                 F[i][J] = v;
             }
-        double P[2][2], A[2][2][2][2];
-        consti2(m, F, P, A);
-        for (int iJ = 0; iJ < 4; ++iJ) {
-            for (int kL = 0; kL < 4; ++kL) mme[4 * iJ + kL] += wq * A[iJ >> 1][iJ & 1][kL >> 1][kL & 1];
-            mme[16 + iJ] += wq * P[iJ >> 1][iJ & 1];
-        }
-        // the quadrature weight rides on the row node's gradient: t = wq G_a A, so the
-        // element integrals accumulate with FMAs and no separate product by wq
-        double Gw[8];
+        double al, be, ga, H[2][2], P[2][2];
+        law2(m, F, al, be, ga, H, P);
+        al *= wq, be *= wq, ga *= wq;
+        const double Pw[2][2] = {{wq * P[0][0], wq * P[0][1]}, {wq * P[1][0], wq * P[1][1]}};
+        double hb[4][2];
 #pragma unroll
-        for (int x = 0; x < 8; ++x) Gw[x] = wq * G[x];
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) hb[b][i] = H[i][0] * G[2 * b] + H[i][1] * G[2 * b + 1];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-            double t[2][2][2];  // t[i][k][L] = wq sum_J G_aJ A_iJkL
-            for (int i = 0; i < 2; ++i)
-                for (int k = 0; k < 2; ++k)
-                    for (int L = 0; L < 2; ++L)
-                        t[i][k][L] = Gw[2 * a] * A[i][0][k][L] + Gw[2 * a + 1] * A[i][1][k][L];
 #pragma unroll
             for (int b = a; b < 4; ++b) {
                 const int p = ec_pair(a, b);
-                for (int i = 0; i < 2; ++i)
-                    for (int k = 0; k < 2; ++k) {
-                        double* o = out + (4 * p + 2 * i + k) * stride;
-                        *o = __fma_rn(t[i][k][1], G[2 * b + 1], __fma_rn(t[i][k][0], G[2 * b], g == 0 ? 0.0 : *o));
+                const double ad = al * Gt[32 + 10 * g + p];
+                if (a == b) {
+                    // symmetric block: (be + ga) h_a h_a^T + al |G_a|^2 I
+                    const double bg = be + ga;
+                    const double v00 = bg * hb[a][0] * hb[a][0] + ad, v01 = bg * hb[a][0] * hb[a][1],
+                                 v11 = bg * hb[a][1] * hb[a][1] + ad;
+                    double* o = out + 4 * p * stride;
+                    o[0] = g == 0 ? v00 : o[0] + v00;
+                    o[stride] = g == 0 ? v01 : o[stride] + v01;
+                    o[2 * stride] = g == 0 ? v01 : o[2 * stride] + v01;
+                    o[3 * stride] = g == 0 ? v11 : o[3 * stride] + v11;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const double bha = be * hb[a][i], ghb = ga * hb[b][i];
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            double* o = out + (4 * p + 2 * i + k) * stride;
+                            const double v = __fma_rn(bha, hb[b][k], ghb * hb[a][k]);
+                            *o = (g == 0 ? 0.0 : *o) + (i == k ? v + ad : v);
+                        }
                     }
+                }
             }
+#pragma unroll
             for (int i = 0; i < 2; ++i) {
                 double* o = out + (40 + 2 * a + i) * stride;
-                *o = __fma_rn(P[i][1], Gw[2 * a + 1], __fma_rn(P[i][0], Gw[2 * a], g == 0 ? 0.0 : *o));
-                for (int k = 0; k < 2; ++k)
-                    for (int L = 0; L < 2; ++L) {
-                        double* o2 = out + (48 + 8 * a + 4 * i + 2 * k + L) * stride;
-                        *o2 = g == 0 ? t[i][k][L] : *o2 + t[i][k][L];
-                    }
+                *o = __fma_rn(Pw[i][1], G[2 * a + 1], __fma_rn(Pw[i][0], G[2 * a], g == 0 ? 0.0 : *o));
             }
         }
     }
+    // k_eM rows (k_e X), K_MM = X^T k_e X, Pint = sum_a f_a (x) X_a
+#pragma unroll
+    for (int k = 0; k < 20; ++k) mme[k] = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const double v1 = ec_kr(out, stride, a, 1, i, k), v2 = ec_kr(out, stride, a, 2, i, k),
+                             v3 = ec_kr(out, stride, a, 3, i, k);
+                const double kx = h * (v1 + v3), ky = h * (v2 + v3);  // columns (k, L = x), (k, L = y)
+                out[(48 + 8 * a + 4 * i + 2 * k) * stride] = kx;
+                out[(48 + 8 * a + 4 * i + 2 * k + 1) * stride] = ky;
+                // K_MM[(i, J)][(k, L)] = h sum_{a: bit J of a} k_eM[a][i][(k, L)]
+                if (a & 1) {
+                    mme[4 * (2 * i) + 2 * k] += h * kx;
+                    mme[4 * (2 * i) + 2 * k + 1] += h * ky;
+                }
+                if (a & 2) {
+                    mme[4 * (2 * i + 1) + 2 * k] += h * kx;
+                    mme[4 * (2 * i + 1) + 2 * k + 1] += h * ky;
+                }
+            }
+            const double f = out[(40 + 2 * a + i) * stride];
+            if (a & 1) mme[16 + 2 * i] += h * f;
+            if (a & 2) mme[16 + 2 * i + 1] += h * f;
+        }
 }
 
-// block (a, b) entry (c, c2) of an element from its compact components at E (stride)
-__device__ __forceinline__ double ec_kr(const double* E, int stride, int a, int b, int c, int c2) {
-    return a <= b ? E[(4 * ec_pair(a, b) + 2 * c + c2) * stride] : E[(4 * ec_pair(b, a) + 2 * c2 + c) * stride];
-}
-
+// Gt[0, 32): dN_b/dX_J at Gauss point g ((g * 4 + b) * 2 + J); Gt[32, 72): G_a . G_b of
+// pair p = ec_pair(a, b) at Gauss point g (32 + 10 g + p).  Needs 72 threads.
 __device__ __forceinline__ void ec_gradients(double* Gt, int N) {
-    if (threadIdx.x < 32) {
-        const int t = threadIdx.x, g = t >> 3, b = (t >> 1) & 3, J = t & 1;
+    const int t = threadIdx.x;
+    if (t < 32) {
+        const int g = t >> 3, b = (t >> 1) & 3, J = t & 1;
         Gt[t] = grad2(g, b, J, 1.0 / N);
+    } else if (t < 72) {
+        const int g = (t - 32) / 10, p = (t - 32) % 10;
+        const int a = p < 4 ? 0 : (p < 7 ? 1 : (p < 9 ? 2 : 3)), b = p < 4 ? p : (p < 7 ? p - 3 : (p < 9 ? p - 5 : 3));
+        Gt[t] = grad2(g, a, 0, 1.0 / N) * grad2(g, b, 0, 1.0 / N) + grad2(g, a, 1, 1.0 / N) * grad2(g, b, 1, 1.0 / N);
     }
 }
 
@@ -411,7 +497,7 @@ __global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __rest
                                                             const int* __restrict__ ids,
                                                             const double* __restrict__ Fbar) {
     extern __shared__ __align__(16) double ebuf[];  // [(R + 1) slots][EC_COMP][N]
-    __shared__ double Gt[32];
+    __shared__ double Gt[72];
     __shared__ double red[256];
     const RveDev r = tab[ids[blockIdx.x]];
     const int N = r.N, tid = threadIdx.x;
@@ -468,7 +554,7 @@ __global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __rest
 __global__ void __launch_bounds__(128) k_assemble_elems_ec2(const RveDev* __restrict__ tab,
                                                             const int* __restrict__ ids,
                                                             const double* __restrict__ Fbar) {
-    __shared__ double Gt[32];
+    __shared__ double Gt[72];
     const RveDev r = tab[ids[blockIdx.y]];
     ec_gradients(Gt, r.N);
     __syncthreads();
@@ -500,7 +586,7 @@ __global__ void __launch_bounds__(256) k_assemble_fused_elem_ec2(const RveDev* _
                                                                  const int* __restrict__ ids,
                                                                  const double* __restrict__ Fbar) {
     extern __shared__ __align__(16) double ebuf[];  // [(R + 1) slots][EC_COMP][N]
-    __shared__ double Gt[32];
+    __shared__ double Gt[72];
     __shared__ double red[256];
     const RveDev r = tab[ids[blockIdx.x]];
     const int N = r.N, nq = r.nq, nn = r.nn, nm = r.nm, tid = threadIdx.x;
