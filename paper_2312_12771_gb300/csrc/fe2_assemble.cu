@@ -298,26 +298,47 @@ __global__ void __launch_bounds__(256) k_assemble_fused_elem2(const RveDev* __re
 // The fused kernel stages strips of element rows in shared memory and gathers the
 // node rows from them; the split path stores the same values in the per-element
 // layout of k_assemble_elems2 and gathers with k_reduce2.  Both sum in the same
-// order, so they agree bit for bit.
+// order, so they agree bit for bit.  The RVE paths stage the first 48 components
+// only: their gathers form K_mM from the stencil rows (km_from_stencil).  The
+// element-RVE path keeps all 80.
 constexpr int EC_COMP = 80;
 constexpr int EC_SMEM_MAX = 200 * 1024;
+constexpr int EC2_COMP = 48;
+constexpr int EC2_SMEM_MAX = 100 * 1024;  // two CTAs per SM
 constexpr int EC_NMAX = 160;  // larger meshes take the per-(element, a) path
 
-// element rows per strip: at most 256 elements, (R + 1) rows staged
-__host__ __device__ inline int ec_rows(int N) {
+// element rows per strip: at most 256 elements, (R + 1) rows of comps values staged
+__host__ __device__ inline int ec_rows(int N, int comps = EC_COMP, int smax = EC_SMEM_MAX) {
     int R = 256 / N;
     if (R > N) R = N;
-    while (R > 1 && (size_t)(R + 1) * EC_COMP * N * sizeof(double) > (size_t)EC_SMEM_MAX) --R;
+    while (R > 1 && (size_t)(R + 1) * comps * N * sizeof(double) > (size_t)smax) --R;
     return R;
 }
 
-__host__ __device__ inline size_t ec_smem_bytes(int maxN) {
+__host__ __device__ inline size_t ec_smem_bytes(int maxN, int comps = EC_COMP, int smax = EC_SMEM_MAX) {
     size_t b = 0;
     for (int N = 3; N <= maxN; ++N) {
-        const size_t x = (size_t)(ec_rows(N) + 1) * EC_COMP * N * sizeof(double);
+        const size_t x = (size_t)(ec_rows(N, comps, smax) + 1) * comps * N * sizeof(double);
         b = x > b ? x : b;
     }
     return b;
+}
+
+// K_mM of a node row from its 9 stencil blocks st[off] = K(q, q + off): the node's
+// elements give sum_b k_e(a, b) X_b = sum_b k_e(a, b) (X_b - X_a) (rows of k_e sum to
+// zero) with X_b - X_a = h (ox, oy), so K_mM[c][(c2, L)] = h sum_off off_L st[off][c][c2].
+__device__ __forceinline__ void km_from_stencil(const double st[9][2][2], double h, double kM[2][4]) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2) {
+            const double x = ((st[2][c][c2] - st[0][c][c2]) + (st[5][c][c2] - st[3][c][c2])) +
+                             (st[8][c][c2] - st[6][c][c2]);
+            const double y = ((st[6][c][c2] - st[0][c][c2]) + (st[7][c][c2] - st[1][c][c2])) +
+                             (st[8][c][c2] - st[2][c][c2]);
+            kM[c][2 * c2] = h * x;
+            kM[c][2 * c2 + 1] = h * y;
+        }
 }
 
 __device__ __forceinline__ int ec_pair(int a, int b) {  // a <= b
@@ -369,7 +390,8 @@ __device__ __forceinline__ void law2(const double* m, const double F[2][2], doub
     al = a, be = c + s * iJ, ga = -s * iJ;
 }
 
-// All rows of element (ex, ey) at (Fbar, w~) into out[c * stride], c < EC_COMP,
+// All rows of element (ex, ey) at (Fbar, w~) into out[c * stride], c < EC_COMP
+// (c < EC2_COMP without the k_eM rows, KM = false),
 // summed over the Gauss points in order; mme = K_MM (16) and Pint (4) of the element.
 // Gt[(g * 4 + b) * 2 + J] = dN_b/dX_J at Gauss point g; Gt[32 + 10 g + p] = G_a . G_b
 // of pair p = (a, b).  With the tangent in the form of law2 and h_b = H G_b,
@@ -378,6 +400,7 @@ __device__ __forceinline__ void law2(const double* m, const double F[2][2], doub
 // coordinates h (b & 1, b >> 1) in the element), so k_eM = sum_g w G_a A = k_e X,
 // K_MM = X^T k_e X and Pint = sum_a f_a (x) X_a: formed once per element from the
 // blocks and f, instead of at every Gauss point.
+template <bool KM>
 __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const double Fb[4],
                                           const double* __restrict__ Gt, double* __restrict__ out, int stride,
                                           double (&mme)[20]) {
@@ -457,8 +480,10 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
                 const double v1 = ec_kr(out, stride, a, 1, i, k), v2 = ec_kr(out, stride, a, 2, i, k),
                              v3 = ec_kr(out, stride, a, 3, i, k);
                 const double kx = h * (v1 + v3), ky = h * (v2 + v3);  // columns (k, L = x), (k, L = y)
-                out[(48 + 8 * a + 4 * i + 2 * k) * stride] = kx;
-                out[(48 + 8 * a + 4 * i + 2 * k + 1) * stride] = ky;
+                if (KM) {
+                    out[(48 + 8 * a + 4 * i + 2 * k) * stride] = kx;
+                    out[(48 + 8 * a + 4 * i + 2 * k + 1) * stride] = ky;
+                }
                 // K_MM[(i, J)][(k, L)] = h sum_{a: bit J of a} k_eM[a][i][(k, L)]
                 if (a & 1) {
                     mme[4 * (2 * i) + 2 * k] += h * kx;
@@ -493,7 +518,7 @@ __device__ __forceinline__ void ec_gradients(double* Gt, int N) {
 // shared memory (one thread per element), then the node rows they complete are
 // gathered (one thread per node).  Element row N-1 is integrated first as well,
 // for node row 0 (its K_MM / Pint count once, in the last strip).
-__global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __restrict__ tab,
+__global__ void __launch_bounds__(256, 2) k_assemble_fused_ec2(const RveDev* __restrict__ tab,
                                                             const int* __restrict__ ids,
                                                             const double* __restrict__ Fbar) {
     extern __shared__ __align__(16) double ebuf[];  // [(R + 1) slots][EC_COMP][N]
@@ -501,7 +526,7 @@ __global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __rest
     __shared__ double red[256];
     const RveDev r = tab[ids[blockIdx.x]];
     const int N = r.N, tid = threadIdx.x;
-    const int R = ec_rows(N), slots = R + 1, sl = EC_COMP * N;
+    const int R = ec_rows(N, EC2_COMP, EC2_SMEM_MAX), slots = R + 1, sl = EC2_COMP * N;
     ec_gradients(Gt, N);
     double Fb[4];
     for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.x + k];
@@ -510,14 +535,14 @@ __global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __rest
     __syncthreads();
     if (tid < N) {  // element row N - 1 as row u = -1 (slot 0)
         double mme[20];
-        elem_all2(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
+        elem_all2<false>(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
     }
     for (int s0 = 0; s0 < N; s0 += R) {
         const int nrow = min(R, N - s0);
         if (tid < nrow * N) {
             const int du = tid / N, ex = tid - du * N, u = s0 + du;
             double mme[20];
-            elem_all2(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
+            elem_all2<false>(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
             for (int k = 0; k < 20; ++k) mm[k] += mme[k];
         }
         __syncthreads();
@@ -536,9 +561,8 @@ __global__ void __launch_bounds__(256) k_assemble_fused_ec2(const RveDev* __rest
                         for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += ec_kr(E, N, a, b, c, c2);
                 }
                 for (int c = 0; c < 2; ++c) f[c] += E[(40 + 2 * a + c) * N];
-                for (int c = 0; c < 2; ++c)
-                    for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(48 + 8 * a + 4 * c + kL) * N];
             }
+            km_from_stencil(st, 1.0 / N, kM);
             store_row(r, q, st, f, kM);
         }
         __syncthreads();
@@ -563,9 +587,9 @@ __global__ void __launch_bounds__(128) k_assemble_elems_ec2(const RveDev* __rest
     const int N = r.N, ex = e % N, ey = e / N, nn = r.nn, RC = elem_row_comps(2);
     double Fb[4];
     for (int k = 0; k < 4; ++k) Fb[k] = Fbar[4 * blockIdx.y + k];
-    double loc[EC_COMP];
+    double loc[EC2_COMP];
     double mme[20];
-    elem_all2(r, ex, ey, Fb, Gt, loc, 1, mme);
+    elem_all2<false>(r, ex, ey, Fb, Gt, loc, 1, mme);
     double* E = r.elem;
     for (int a = 0; a < 4; ++a) {
         int c0 = a * RC;
@@ -573,8 +597,7 @@ __global__ void __launch_bounds__(128) k_assemble_elems_ec2(const RveDev* __rest
             for (int c = 0; c < 2; ++c)
                 for (int c2 = 0; c2 < 2; ++c2) E[(size_t)(c0++) * nn + e] = ec_kr(loc, 1, a, b, c, c2);
         for (int c = 0; c < 2; ++c) E[(size_t)(c0++) * nn + e] = loc[40 + 2 * a + c];
-        for (int c = 0; c < 2; ++c)
-            for (int kL = 0; kL < 4; ++kL) E[(size_t)(c0++) * nn + e] = loc[48 + 8 * a + 4 * c + kL];
+        // the k_eM slots stay unwritten: k_reduce2<true> forms K_mM from the stencil rows
     }
     for (int k = 0; k < 20; ++k) E[(size_t)(4 * RC + k) * nn + e] = mme[k];
 }
@@ -601,14 +624,14 @@ __global__ void __launch_bounds__(256) k_assemble_fused_elem_ec2(const RveDev* _
         for (int k = 0; k < 20; ++k) mm[k] = 0.0;
         if (tid < N) {
             double mme[20];
-            elem_all2(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
+            elem_all2<true>(r, tid, N - 1, Fb, Gt, ebuf + tid, N, mme);
         }
         for (int s0 = 0; s0 < N; s0 += R) {
             const int nrow = min(R, N - s0);
             if (tid < nrow * N) {
                 const int du = tid / N, ex = tid - du * N, u = s0 + du;
                 double mme[20];
-                elem_all2(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
+                elem_all2<true>(r, ex, u, Fb, Gt, ebuf + (size_t)((u + 1) % slots) * sl + ex, N, mme);
                 for (int k = 0; k < 20; ++k) mm[k] += mme[k];
             }
             __syncthreads();
@@ -708,15 +731,17 @@ __global__ void __launch_bounds__(256) k_reduce2(const RveDev* __restrict__ tab,
                     for (int c2 = 0; c2 < 2; ++c2) st[off][c][c2] += E[(size_t)(c0++) * nn + e];
             }
             for (int c = 0; c < 2; ++c) f[c] += E[(size_t)(c0++) * nn + e];
-            for (int c = 0; c < 2; ++c)
-                for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
+            if (!EC)
+                for (int c = 0; c < 2; ++c)
+                    for (int kL = 0; kL < 4; ++kL) kM[c][kL] += E[(size_t)(c0++) * nn + e];
             if (!EC && a == 0)
                 for (int k = 0; k < 20; ++k) mm[k] += E[(size_t)(4 * RC + k) * nn + e];
         }
+        if (EC) km_from_stencil(st, 1.0 / N, kM);  // as the fused kernel's gather
         store_row(r, q, st, f, kM);
     }
     if (EC) {
-        const int R = ec_rows(N);
+        const int R = ec_rows(N, EC2_COMP, EC2_SMEM_MAX);
         for (int s0 = 0; s0 < N; s0 += R) {
             const int nrow = min(R, N - s0);
             if ((int)threadIdx.x < nrow * N) {
@@ -933,7 +958,7 @@ cudaError_t launch_assemble_fused(const RveDev* tab, const int* ids, int n, cons
                                   int maxN, int all_linear, cudaStream_t s) {
     if (d != 2) return cudaErrorNotSupported;
     if (!all_linear && maxN <= EC_NMAX) {
-        const size_t smem = ec_smem_bytes(maxN);
+        const size_t smem = ec_smem_bytes(maxN, EC2_COMP, EC2_SMEM_MAX);
         cudaError_t e = cudaFuncSetAttribute(k_assemble_fused_ec2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
