@@ -21,6 +21,7 @@
 #include "fe2_internal.cuh"
 #include "fe2_panel.cuh"
 #include "fe2_ptx.cuh"
+#include "fe2_reduce.cuh"
 
 namespace fe2 {
 
@@ -364,13 +365,19 @@ __global__ void __launch_bounds__(128) k_residual3(const RveDev* __restrict__ ta
     }
 }
 
-// S6 in 3D: G1 = rhs^T X (9 x 10), G2 = X_M^T R (9 x 10); corrected Schur.
+// One CTA per RVE (3D: d^2 = 9, nr = 10): G1 = rhs_M^T X (9 x 10) and G2 = X'_M^T R
+// (9 x 10, X' = X + dx on the second-order pass, corrected = 2), in three passes over
+// the macro components, three at a time: every thread keeps 60 partial sums over its
+// DOFs in registers and the CTA adds them (cta_sum).  The epilogue runs on 90 threads,
+// the norms of the error estimate meet in one more CTA sum.
 __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, const int* __restrict__ ids,
                                                 Workspace ws, int corrected, double* __restrict__ sigma,
                                                 double* __restrict__ Cbar, int* __restrict__ status,
                                                 double* __restrict__ err, const double* __restrict__ tol,
                                                 int* __restrict__ redo, int only_flagged, int final_sweep) {
-    __shared__ double red[256];
+    constexpr int AC = 3, NV = 2 * AC * 10;
+    __shared__ double red[NV * 33];
+    __shared__ double tp[NV];
     __shared__ double tot[183];
     if (only_flagged && !redo[blockIdx.x]) return;
     const RveDev r = tab[ids[blockIdx.x]];
@@ -379,58 +386,80 @@ __global__ void __launch_bounds__(256) k_schur3(const RveDev* __restrict__ tab, 
     // corrected = 2: the FP32 correction dx of every column in the slot's y region;
     // the correction term uses X' = X + dx (as in the 2D kernel), X' is stored
     const float* dX = (const float*)(ws.base + blockIdx.x * ws.stride + ws.offY);
-    const int nv = corrected == 2 ? 183 : (corrected ? 180 : 90);
-    for (int v = 0; v < nv; ++v) {
-        const int which = v / 90, a = (v % 90) / 10, b = v % 10;
-        double acc = 0.0;
-        for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-            if (v >= 180) {
-                for (int c = 0; c < 9; ++c) {
-                    const double dx = (double)dX[(size_t)c * nmp + m];
-                    const double x = r.X[(size_t)c * nm + m];
-                    acc += v == 180 ? dx * R[(size_t)c * nm + m] : (v == 181 ? dx * dx : x * x);
+    const int tid = threadIdx.x;
+    for (int a0 = 0; a0 < 9; a0 += AC) {
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        for (int m = tid; m < nm; m += blockDim.x) {
+            double ra[AC], xa[AC];
+#pragma unroll
+            for (int q = 0; q < AC; ++q) {
+                ra[q] = r.rhs[(size_t)(a0 + q) * nm + m];
+                double x = r.X[(size_t)(a0 + q) * nm + m];
+                if (corrected == 2) x += (double)dX[(size_t)(a0 + q) * nmp + m];
+                xa[q] = x;
+            }
+#pragma unroll
+            for (int b = 0; b < 10; ++b) {
+                const double xb = r.X[(size_t)b * nm + m];
+#pragma unroll
+                for (int q = 0; q < AC; ++q) acc[q * 10 + b] += ra[q] * xb;
+                if (corrected) {
+                    const double rb = R[(size_t)b * nm + m];
+#pragma unroll
+                    for (int q = 0; q < AC; ++q) acc[AC * 10 + q * 10 + b] += xa[q] * rb;
                 }
-            } else if (which == 0) {
-                acc += r.rhs[(size_t)a * nm + m] * r.X[(size_t)b * nm + m];
-            } else {
-                double xa = r.X[(size_t)a * nm + m];
-                if (corrected == 2) xa += (double)dX[(size_t)a * nmp + m];
-                acc += xa * R[(size_t)b * nm + m];
             }
         }
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
+        cta_sum<NV>(acc, red, tp);
+        if (tid < NV) {
+            const int w = tid / (AC * 10), q = (tid / 10) % AC, b = tid % 10;
+            tot[w * 90 + (a0 + q) * 10 + b] = tp[tid];
         }
-        if (threadIdx.x == 0) tot[v] = red[0];
-        __syncthreads();
     }
-    if (corrected == 2)
-        for (int k = threadIdx.x; k < 10 * nm; k += blockDim.x) {
+    if (corrected == 2) {
+        double ex[3] = {0.0, 0.0, 0.0};
+        for (int m = tid; m < nm; m += blockDim.x)
+            for (int c = 0; c < 9; ++c) {
+                const double dx = (double)dX[(size_t)c * nmp + m];
+                const double x = r.X[(size_t)c * nm + m];
+                ex[0] += dx * R[(size_t)c * nm + m];
+                ex[1] += dx * dx;
+                ex[2] += x * x;
+            }
+        cta_sum<3>(ex, red, tot + 180);
+        for (int k = tid; k < 10 * nm; k += blockDim.x) {
             const int c = k / nm, m = k - c * nm;
             r.X[k] += (double)dX[(size_t)c * nmp + m];
         }
-    if (threadIdx.x == 0) {
-        double cn = 0.0, corr = 0.0;
-        int bad = 0;
-        for (int a = 0; a < 9; ++a) {
-            for (int b = 0; b < 9; ++b) {
-                double v = r.KMM[a * 9 + b] - tot[a * 10 + b];
-                if (corrected) {
-                    v -= tot[90 + a * 10 + b];
-                    corr += tot[90 + a * 10 + b] * tot[90 + a * 10 + b];
-                }
-                cn += v * v;
-                bad |= !isfinite(v);
-                Cbar[(size_t)blockIdx.x * 81 + a * 9 + b] = v;
-            }
-            double sg = r.Pint[a] - tot[a * 10 + 9];
-            if (corrected) sg -= tot[90 + a * 10 + 9];
-            bad |= !isfinite(sg);
-            sigma[(size_t)blockIdx.x * 9 + a] = sg;
+    }
+    __syncthreads();
+    // thread t < 81: Cbar entry (a, b) = (t / 9, t % 9); 81 <= t < 90: sigma_eff component
+    double nv[2] = {0.0, 0.0};
+    int bad = 0;
+    if (tid < 81) {
+        const int a = tid / 9, b = tid % 9;
+        double v = r.KMM[tid] - tot[a * 10 + b];
+        if (corrected) {
+            const double g = tot[90 + a * 10 + b];
+            v -= g;
+            nv[1] = g * g;
         }
+        nv[0] = v * v;
+        bad = !isfinite(v);
+        Cbar[(size_t)blockIdx.x * 81 + tid] = v;
+    } else if (tid < 90) {
+        const int a = tid - 81;
+        double sg = r.Pint[a] - tot[a * 10 + 9];
+        if (corrected) sg -= tot[90 + a * 10 + 9];
+        bad = !isfinite(sg);
+        sigma[(size_t)blockIdx.x * 9 + a] = sg;
+    }
+    bad = __syncthreads_or(bad);
+    cta_sum<2>(nv, red, tp);
+    if (tid == 0) {
+        const double cn = tp[0], corr = tp[1];
         double e = 0.0;
         if (corrected == 1) e = corr / fmax(cn, 1e-300);
         if (corrected == 2) e = fabs(tot[180]) / sqrt(fmax(cn, 1e-300)) * sqrt(tot[181] / fmax(tot[182], 1e-300));
