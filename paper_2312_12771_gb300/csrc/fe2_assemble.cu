@@ -438,16 +438,19 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
             for (int b = a; b < 4; ++b) {
                 const int p = ec_pair(a, b);
                 const double ad = al * Gt[32 + 10 * g + p];
+                // every entry accumulates with chained FMAs (a b + c d added to a sum would cost
+                // a multiply, an FMA and an add)
                 if (a == b) {
                     // symmetric block: (be + ga) h_a h_a^T + al |G_a|^2 I
-                    const double bg = be + ga;
-                    const double v00 = bg * hb[a][0] * hb[a][0] + ad, v01 = bg * hb[a][0] * hb[a][1],
-                                 v11 = bg * hb[a][1] * hb[a][1] + ad;
+                    const double b0 = (be + ga) * hb[a][0], b1 = (be + ga) * hb[a][1];
                     double* o = out + 4 * p * stride;
-                    o[0] = g == 0 ? v00 : o[0] + v00;
-                    o[stride] = g == 0 ? v01 : o[stride] + v01;
-                    o[2 * stride] = g == 0 ? v01 : o[2 * stride] + v01;
-                    o[3 * stride] = g == 0 ? v11 : o[3 * stride] + v11;
+                    const double v00 = __fma_rn(b0, hb[a][0], g == 0 ? ad : o[0] + ad);
+                    const double v01 = __fma_rn(b0, hb[a][1], g == 0 ? 0.0 : o[stride]);
+                    const double v11 = __fma_rn(b1, hb[a][1], g == 0 ? ad : o[3 * stride] + ad);
+                    o[0] = v00;
+                    o[stride] = v01;
+                    o[2 * stride] = v01;
+                    o[3 * stride] = v11;
                 } else {
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
@@ -455,8 +458,8 @@ __device__ __forceinline__ void elem_all2(const RveDev& r, int ex, int ey, const
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
                             double* o = out + (4 * p + 2 * i + k) * stride;
-                            const double v = __fma_rn(bha, hb[b][k], ghb * hb[a][k]);
-                            *o = (g == 0 ? 0.0 : *o) + (i == k ? v + ad : v);
+                            const double prev = g == 0 ? (i == k ? ad : 0.0) : (i == k ? *o + ad : *o);
+                            *o = __fma_rn(bha, hb[b][k], __fma_rn(ghb, hb[a][k], prev));
                         }
                     }
                 }

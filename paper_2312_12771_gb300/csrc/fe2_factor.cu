@@ -1398,8 +1398,10 @@ __global__ void __launch_bounds__(256) k_residual2(const RveDev* __restrict__ ta
         for (int rr = 0; rr < 5; ++rr) {
             // the two DOFs of a node are adjacent and 16-byte aligned (nm is even)
             const double2 xv = *reinterpret_cast<const double2*>(r.X + (size_t)rr * nm + 2 * (qn - 1));
-            acc[0][rr] += k00 * xv.x + k01 * xv.y;
-            acc[1][rr] += k10 * xv.x + k11 * xv.y;
+            // two chained FMAs: written as acc += a b + c d it costs a multiply, an FMA and
+            // an add, and FP64 instructions set this kernel's pace
+            acc[0][rr] = __fma_rn(k01, xv.y, __fma_rn(k00, xv.x, acc[0][rr]));
+            acc[1][rr] = __fma_rn(k11, xv.y, __fma_rn(k10, xv.x, acc[1][rr]));
         }
     }
 #pragma unroll

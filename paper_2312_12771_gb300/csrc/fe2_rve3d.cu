@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(E3_THREADS, 2) k_assemble_elems3(const RveDev*
             for (int i = 0; i < 3; ++i) {
                 const double bha = be * ha[i], ghb = ga * hb[i];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) acc[3 * i + k] += bha * hb[k] + ghb * ha[k];
+                for (int k = 0; k < 3; ++k) acc[3 * i + k] = __fma_rn(ghb, ha[k], __fma_rn(bha, hb[k], acc[3 * i + k]));
             }
         }
 #pragma unroll
