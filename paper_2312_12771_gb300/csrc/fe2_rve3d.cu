@@ -114,10 +114,9 @@ __device__ __forceinline__ void pair3(int p, int& a, int& b) {
 // Phase 1: warp q, lane = element, evaluates the law at Gauss point q and caches
 // w al, w be, w ga, H, w P and h_b (element fastest).  Phase 2: the 36 node-pair
 // blocks (b >= a; the gather reads k_e(b, a) as the transpose of k_e(a, b)) go to
-// the warps in turn; warp w also integrates f of node w, and warps 4-7, which
-// hold one pair fewer, the 45 distinct entries of K_MM and Pint.  Gauss points
-// are summed in order.  Phase 3: warp a forms the K_mM rows of node a from the
-// finished blocks.
+// the warps in turn; warp w also integrates f of node w.  Gauss points are summed
+// in order.  Phase 3: warp a forms the K_mM rows of node a from the finished
+// blocks.  Phase 4: K_MM and Pint from those rows and f (the same identity).
 __global__ void __launch_bounds__(E3_THREADS, 2) k_assemble_elems3(const RveDev* __restrict__ tab,
                                                                    const int* __restrict__ ids,
                                                                    const double* __restrict__ Fbar) {
@@ -221,32 +220,6 @@ __global__ void __launch_bounds__(E3_THREADS, 2) k_assemble_elems3(const RveDev*
 #pragma unroll
         for (int i = 0; i < 3; ++i) E[(size_t)(a * RC + 72 + i) * nn + e] = f[i];
     }
-    // K_MM (45 distinct entries m = 3i + J <= n = 3k + L) and Pint on warps 4-7
-    if (live && warp >= 4) {
-        for (int t = warp - 4; t < 54; t += 4) {
-            double s = 0.0;
-            if (t < 45) {
-                int m = 0, u = t;
-                while (u >= 9 - m) u -= 9 - m, ++m;
-                const int n = m + u;
-                const int i = m / 3, J = m % 3, k = n / 3, L = n % 3;
-#pragma unroll 1
-                for (int q = 0; q < 8; ++q) {
-                    const double* c = ce + (size_t)q * E3_C * E3_ELEMS;
-                    double v = c[E3_ELEMS] * (c[(3 + m) * E3_ELEMS] * c[(3 + n) * E3_ELEMS]) +
-                               c[2 * E3_ELEMS] * (c[(3 + 3 * i + L) * E3_ELEMS] * c[(3 + 3 * k + J) * E3_ELEMS]);
-                    if (i == k && J == L) v += c[0];
-                    s += v;
-                }
-                E[(size_t)(8 * RC + 9 * m + n) * nn + e] = s;
-                if (n != m) E[(size_t)(8 * RC + 9 * n + m) * nn + e] = s;
-            } else {
-                const int m = t - 45;
-                for (int q = 0; q < 8; ++q) s += ce[((size_t)q * E3_C + 12 + m) * E3_ELEMS];
-                E[(size_t)(8 * RC + 81 + m) * nn + e] = s;
-            }
-        }
-    }
     // phase 3: K_mM rows of node a = warp, k_e(a, .) X = h sum_{b: bit L of b} k_e(a, b), from the
     // blocks written above (this CTA's global writes are visible after the barrier)
     __syncthreads();
@@ -268,6 +241,21 @@ __global__ void __launch_bounds__(E3_THREADS, 2) k_assemble_elems3(const RveDev*
                 E[o + nn] = h * sy;
                 E[o + 2 * (size_t)nn] = h * sz;
             }
+    }
+    // phase 4: K_MM = X^T k_e X and Pint = sum_a f_a (x) X_a, from the finished rows:
+    // K_MM[(i, J)][(k, L)] = h sum_{a: bit J of a} K_mM[a][i][(k, L)], Pint[(i, J)] likewise
+    // from f_a; entry t = 9 m + n (t < 81) or Pint m = t - 81 on warp t % 8
+    __syncthreads();
+    if (live) {
+        for (int t = warp; t < 90; t += 8) {
+            const int m = t < 81 ? t / 9 : t - 81, i = m / 3, J = m % 3;
+            const int col = t < 81 ? 75 + 9 * i + t % 9 : 72 + i;
+            double sum = 0.0;
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+                if ((a >> J) & 1) sum += E[(size_t)(a * RC + col) * nn + e];
+            E[(size_t)(8 * RC + t) * nn + e] = h * sum;
+        }
     }
 }
 
