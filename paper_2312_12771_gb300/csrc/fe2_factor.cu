@@ -1166,10 +1166,11 @@ __device__ __forceinline__ bool backward_pass(const RveDev& r, const SolveLayout
                 if (rr < nr) {
                     T t = tv[rr * NB + lane];
                     for (int p = 1; p < nparts; ++p) t += tv[(p * nr + rr) * NB + lane];
+                    // the pivot reciprocal stays in a register, off the sweep's chain
+                    const T dme = db[lane];
                     T a = acc[q] - t, xc = T(0);
                     for (int c2 = NB - 1; c2 >= 0; --c2) {
-                        T xv = (lane == c2) ? a * db[c2] : T(0);
-                        xv = __shfl_sync(0xffffffffu, xv, c2);
+                        const T xv = __shfl_sync(0xffffffffu, a * dme, c2);
                         if (lane == c2) xc = xv;
                         if (lane < c2 && c2 - lane <= kd) a -= Lb[lane * LDL + (c2 - lane)] * xv;
                     }
